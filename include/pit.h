@@ -1,0 +1,214 @@
+/*
+ * pit.h -- C ABI of libpit.so, a single-GPU (GB300, sm_103a) implementation of
+ * the hot path of the parallel-in-time sparse-grid combination method of
+ * Griebel, Schweitzer and Troska (arXiv 2509.22156, "A parallel-in-time
+ * combination method for parabolic problems"):
+ *
+ *   - the fine propagator Phi, one backward-Euler step (I + dt L) u = u_prev + dt f
+ *     (Sec. 2, Eqs. "parabolic_problem_time_propagation" and "..._LES"),
+ *     solved matrix-free by CG (symmetric operators) or BiCGStab (drift
+ *     operators) as in Sec. 4.1;
+ *   - on every component grid of the combination technique
+ *     (Sec. 2.1.1, Eq. "combination_technique_solution");
+ *   - inside two- or three-level FAS multigrid reduction in time with FCF
+ *     relaxation, independently per grid (Sec. 3.3, Alg. 2; Sec. 3.4, Alg. 3);
+ *   - followed by the weighted combination sum (Eq. "combination_technique_solution").
+ *
+ * Conventions shared by every entry point:
+ *   - Vectors are FP64 in the canonical packed layout: grid g occupies
+ *     [offsets[g], offsets[g+1]) of a vector of n_total values; grids are
+ *     ordered by layer w ascending, then by level multi-index l
+ *     lexicographically; inside a grid the interior nodes are in C order with
+ *     the last axis fastest; node c_i (0-based) on axis i sits at
+ *     lo_i + (c_i + 1) h_i with h_i = (hi_i - lo_i) / 2^{l_i}.  A batch of
+ *     n_batch vectors is n_batch consecutive packed vectors.
+ *   - Pointers are caller-owned.  Where a parameter says "host or device", the
+ *     library detects the memory kind (cudaPointerGetAttributes) and stages
+ *     host data through its own device buffers.  Where it says "device", it
+ *     must be device memory of the problem's GPU.
+ *   - All work is ordered on the CUDA stream given at creation.  Functions
+ *     that return statistics or decide on convergence synchronise that stream
+ *     before returning; the others are asynchronous.
+ *   - No C++ exception crosses the ABI.  Every function returns a pit_status;
+ *     pit_last_error() gives a thread-local message for the last failure.
+ *     Invalid sizes, levels and options are rejected before any launch.
+ *   - The library never falls back to a CPU path: without a usable CUDA device
+ *     pit_problem_create returns PIT_ERR_CUDA.
+ */
+#ifndef PIT_H
+#define PIT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIT_MAX_DIM 6
+#define PIT_MAX_HIST 64
+
+typedef struct pit_problem *pit_problem_t; /* opaque, owned by the library */
+
+typedef enum {
+    PIT_OK = 0,
+    PIT_ERR_INVALID_ARG = 1,
+    PIT_ERR_CUDA = 2,
+    PIT_ERR_OOM = 3,
+    PIT_ERR_NOCONV = 4,     /* a Krylov solve or MGRIT hit its iteration cap   */
+    PIT_ERR_BREAKDOWN = 5,  /* Krylov breakdown (zero denominator)              */
+    PIT_ERR_NONFINITE = 6,  /* NaN or Inf met in a residual or input            */
+    PIT_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up               */
+    PIT_ERR_UNSUPPORTED = 8 /* valid request outside what this build supports   */
+} pit_status;
+
+typedef enum {
+    PIT_OP_HEAT = 0,    /* L = -Laplace (Sec. 4.2, Eq. "heat_equation"), (2d+1)-point stencil */
+    PIT_OP_VARHEAT = 1, /* L = -div(a grad), a = 1 + A sin(2 pi x1) cos(2 pi x2) sin(2 pi x3)...
+                           evaluated at face midpoints; symmetric, CG                        */
+    PIT_OP_OU = 2       /* Fokker-Planck operator of dX = -theta X dt + sigma dW
+                           (Sec. 4.4, Eq. "sde_fokker_planck" with diagonal drift):
+                           donor-cell upwind drift + central diffusion; BiCGStab            */
+} pit_op;
+
+typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1 } pit_prec;
+
+typedef enum {
+    PIT_COARSE_IMPLICIT = 0, /* Phi_coarse = backward Euler with dT = m dt (Sec. 3.3.1)  */
+    PIT_COARSE_EXACT = 1,    /* Phi_coarse = m fine steps (exact coarse correction)        */
+    PIT_COARSE_LEARNED = 2   /* learned network (not in the paper; see pit_train_coarse)   */
+} pit_coarse;
+
+/* Problem: d-dimensional box [lo, hi], zero Dirichlet values, combination
+ * level level_n (the paper's L) with minimum level level0 (the paper's L0,
+ * Sec. 2.1.1), operator op with parameters theta, sigma (OU) and vamp
+ * (variable-coefficient amplitude A). */
+typedef struct {
+    int d;
+    int level_n;
+    int level0;
+    int op;
+    double lo[PIT_MAX_DIM];
+    double hi[PIT_MAX_DIM];
+    double theta;
+    double sigma;
+    double vamp;
+} pit_problem_desc;
+
+/* Options of one batched backward-Euler solve.
+ *   prec = PIT_PREC_FP64:  Krylov in FP64 until ||b - A x||_2 <= rtol ||b||_2
+ *                          or maxit iterations.
+ *   prec = PIT_PREC_MIXED: FP64 iterative refinement: r = b - A x in FP64,
+ *                          FP32 Krylov on A e = r to relative inner_rtol
+ *                          (at most maxit iterations), x += e in FP64; at most
+ *                          ir_maxit passes; the same FP64 stopping rule. */
+typedef struct {
+    int prec;
+    double rtol;
+    int maxit;
+    double inner_rtol;
+    int ir_maxit;
+} pit_solve_opts;
+
+typedef struct {
+    int n_items;          /* (batch entry, grid) pairs solved                  */
+    int n_failed;         /* items that did not meet rtol                      */
+    int max_iters;        /* largest Krylov iteration count of one item        */
+    long long sum_iters;  /* Krylov iterations summed over items               */
+    int max_refine;       /* largest number of refinement passes (mixed)       */
+    int status;           /* worst item status as a pit_status                  */
+} pit_phi_stats;
+
+/* MGRIT options (Sec. 3.3, Alg. 2 with FCF relaxation; Sec. 4.1 stopping rule:
+ * a grid stops when all its C-point residual l2 norms are <= tol).
+ * nsteps must be a multiple of m^(levels-1). */
+typedef struct {
+    double t0, t1;
+    int nsteps;
+    int m;
+    int levels;           /* 2 or 3 */
+    double tol;
+    int maxit;            /* MGRIT cycle cap */
+    int coarse;           /* pit_coarse */
+    pit_solve_opts fine;  /* options of every fine-level Phi solve   */
+    pit_solve_opts crs;   /* options of every coarse-level Phi solve */
+} pit_mgrit_opts;
+
+typedef struct {
+    int max_cycles;                 /* cycles of the slowest grid                   */
+    int n_converged;                /* grids that met tol                           */
+    double res_hist[PIT_MAX_HIST];  /* max over grids of the residual, per cycle    */
+    long long phi_items;            /* (state, grid) backward-Euler solves executed  */
+    long long krylov_iters;         /* Krylov iterations summed over all solves      */
+    int learned_used;               /* 1 if the learned coarse propagator was used   */
+    int fallback;                   /* 1 if it was replaced by the implicit one      */
+    double ms;                      /* wall time of the call                        */
+} pit_mgrit_stats;
+
+/* Creates a problem on the current CUDA device: enumerates the component
+ * grids (Eq. "combination_technique_solution"; l >= level0 componentwise,
+ * |l|_1 = level_n + d - 1 - w, w = 0..d-1), uploads the grid table and
+ * allocates workspaces lazily.  stream is a cudaStream_t (NULL = legacy
+ * default stream).  Errors: PIT_ERR_INVALID_ARG (d outside 1..6, level0 < 1,
+ * level_n < level0, hi <= lo, unknown op), PIT_ERR_CUDA (no device). */
+pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_problem_t *out);
+
+/* Releases every device buffer, graph and stream object of the problem. */
+pit_status pit_problem_destroy(pit_problem_t p);
+
+/* Grid table (host pointers, each optional): number of grids G, n_total,
+ * levels (G*d ints), combination coefficients (-1)^w C(d-1, w) (G doubles),
+ * offsets (G+1 long longs). */
+pit_status pit_problem_info(pit_problem_t p, int *n_grids, long long *n_total, int *levels,
+                            double *coef, long long *offsets);
+
+/* Samples an initial value at every interior node of every grid.
+ * kind 0: sum of K product-sine modes, params = [K, (A_k, m_k1..m_kd) for k < K]:
+ *         u0(x) = sum_k A_k prod_i sin(pi m_ki (x_i - lo_i) / (hi_i - lo_i))
+ * kind 1: product Gaussian, params = [mean_1..mean_d, std_1..std_d].
+ * params: host, n_params doubles.  u0: host or device, n_total doubles. */
+pit_status pit_sample_initial(pit_problem_t p, int kind, const double *params, int n_params, double *u0);
+
+/* Stencil application q = (I + dt L) p for a batch (the matrix of
+ * Eq. "parabolic_problem_time_propagation_LES" times dt).  p, q: device,
+ * n_batch * n_total doubles, must not overlap. */
+pit_status pit_apply(pit_problem_t p, double dt, int n_batch, const double *pv, double *qv);
+
+/* Batched backward-Euler step Phi (Sec. 2, Eq. "parabolic_problem_time_propagation"):
+ * for every batch entry b and grid g solve (I + dt L) x = u_prev + dt f with
+ * initial guess u_prev, write x to u_next.  f may be NULL (f = 0).
+ * u_prev, f, u_next: device, n_batch * n_total doubles; u_next may alias
+ * u_prev exactly (in-place step), no other overlap.  stats may be NULL; when
+ * given, the call synchronises and fills it, and returns PIT_ERR_NOCONV,
+ * PIT_ERR_BREAKDOWN or PIT_ERR_NONFINITE if any item failed. */
+pit_status pit_phi_batch(pit_problem_t p, double dt, int n_batch, const double *u_prev,
+                         const double *f, double *u_next, const pit_solve_opts *opts,
+                         pit_phi_stats *stats);
+
+/* Time-sequential stepping (Alg. 1 with s = 1): nsteps backward-Euler steps
+ * of size dt from u0 on every grid.  u0, uT: host or device, n_total doubles,
+ * may alias.  Synchronises; stats may be NULL. */
+pit_status pit_sequential_solve(pit_problem_t p, const double *u0, double dt, int nsteps,
+                                const pit_solve_opts *opts, double *uT, pit_phi_stats *stats);
+
+/* CTMGRIT^loc with s = 1 (Alg. 3): independent MGRIT (Alg. 2, FCF, FAS) on
+ * every grid from u0 over [t0, t1] with nsteps fine steps, returning the
+ * final state of every grid.  The initial guess at every time point is u0.
+ * u0, uT: host or device, n_total doubles.  Synchronises once per cycle to
+ * read the residual norms.  Returns PIT_ERR_NOCONV if a grid did not meet
+ * tol within maxit cycles (uT then holds the last iterate). */
+pit_status pit_mgrit_solve(pit_problem_t p, const double *u0, const pit_mgrit_opts *opts,
+                           double *uT, pit_mgrit_stats *stats);
+
+/* Combination sum (Eq. "combination_technique_solution"):
+ * out[k] = sum_g coef_g * I_g[u_g](pts[k]), I_g the piecewise d-linear
+ * interpolant on grid g with zero boundary values (Sec. 2.2.2).
+ * u: host or device, n_total doubles; pts: host or device, n_pts * d doubles
+ * (row-major); out: host or device, n_pts doubles.  Points outside the box
+ * are clamped to its boundary cell. */
+pit_status pit_combine(pit_problem_t p, const double *u, int n_pts, const double *pts, double *out);
+
+/* Thread-local text of the last error. */
+const char *pit_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIT_H */

@@ -65,10 +65,10 @@ def lib():
             L.or_dense_solve.restype = c_int
             L.or_dense_solve.argtypes = [vp, c_int, c_double, vp, vp]
             L.or_sequential.restype = c_int
-            L.or_sequential.argtypes = [vp, vp, c_double, c_int, c_double, c_int, vp]
+            L.or_sequential.argtypes = [vp, vp, c_double, c_int, c_double, c_int, vp, vp]
             L.or_mgrit.restype = c_int
             L.or_mgrit.argtypes = [vp, vp, c_double, c_int, c_int, c_int, c_double, c_int, c_int,
-                                   vp, c_double, c_int, vp, vp, vp]
+                                   vp, c_double, c_int, vp, vp, vp, vp]
             L.or_combine.argtypes = [vp, vp, c_int, vp, vp]
             L.or_interp.argtypes = [vp, c_int, vp, c_int, vp, vp]
             L.or_initial.restype = c_int
@@ -175,24 +175,36 @@ class Problem:
             raise RuntimeError("grid too large for the dense solve")
         return x
 
-    def sequential(self, u0, dt, nsteps, rtol=1e-14, maxit=100000) -> np.ndarray:
+    def _gmask(self, grids):
+        if grids is None:
+            return None
+        m = np.zeros(self.G, dtype=np.uint8)
+        m[np.asarray(grids, dtype=np.int64)] = 1
+        return m
+
+    def sequential(self, u0, dt, nsteps, rtol=1e-14, maxit=100000, grids=None) -> np.ndarray:
+        """Sequential stepping; with `grids`, only those grids are computed
+        (the other entries of the result are zero)."""
         u0 = _f64(u0)
-        out = np.empty_like(u0)
-        st = lib().or_sequential(self._h, _p(u0), dt, nsteps, rtol, maxit, _p(out))
+        out = np.zeros_like(u0)
+        gm = self._gmask(grids)
+        st = lib().or_sequential(self._h, _p(u0), dt, nsteps, rtol, maxit, _p(out), _p(gm))
         if st != 0:
             raise RuntimeError(f"oracle sequential: {STATUS.get(st, st)}")
         return out
 
     def mgrit(self, u0, dt, nsteps, m, levels=2, tol=1e-10, maxit=100, coarse_kind=0,
-              theta=None, rtol=1e-14, krylov_maxit=100000, check=True):
-        """Returns (uT, cycles per grid, residual history G x maxit, status)."""
+              theta=None, rtol=1e-14, krylov_maxit=100000, check=True, grids=None):
+        """Returns (uT, cycles per grid, residual history G x maxit, status);
+        with `grids`, only those grids are computed."""
         u0 = _f64(u0)
-        out = np.empty_like(u0)
+        out = np.zeros_like(u0)
+        gm = self._gmask(grids)
         its = np.zeros(self.G, dtype=np.int32)
         hist = np.full((self.G, maxit), np.nan)
         th = _f64(theta) if theta is not None else None
         st = lib().or_mgrit(self._h, _p(u0), dt, nsteps, m, levels, tol, maxit, coarse_kind,
-                            _p(th), rtol, krylov_maxit, _p(out), _p(its), _p(hist))
+                            _p(th), rtol, krylov_maxit, _p(out), _p(its), _p(hist), _p(gm))
         if check and st != 0:
             raise RuntimeError(f"oracle mgrit: {STATUS.get(st, st)}")
         return out, its, hist, st

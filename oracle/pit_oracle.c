@@ -441,12 +441,13 @@ int or_dense_solve(void *vp, int g, double dt, const double *b, double *x)
 /* Time-sequential solution (Alg. 1 with s = 1): nsteps backward-Euler steps
  * on every grid, f = 0. */
 int or_sequential(void *vp, const double *u0, double dt, int nsteps, double rtol, int maxit,
-                  double *uT)
+                  double *uT, const unsigned char *gmask /* G or NULL: grids to compute */)
 {
     or_problem *P = (or_problem *)vp;
     int worst = OR_OK;
 #pragma omp parallel for schedule(dynamic)
     for (int g = 0; g < P->G; ++g) {
+        if (gmask && !gmask[g]) continue;
         long long n = P->off[g + 1] - P->off[g];
         double *u = uT + P->off[g];
         memcpy(u, u0 + P->off[g], sizeof(double) * n);
@@ -774,7 +775,7 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
  * = residual measured in cycle k (when non-NULL). */
 int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev, double tol,
              int maxit, int coarse_kind, const double *theta, double rtol, int krylov_maxit,
-             double *uT, int *iters, double *res_hist)
+             double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */)
 {
     or_problem *P = (or_problem *)vp;
     if (m < 2 || nlev < 2) return OR_EINVAL;
@@ -784,6 +785,7 @@ int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev,
     int worst = OR_OK;
 #pragma omp parallel for schedule(dynamic)
     for (int g = 0; g < P->G; ++g) {
+        if (gmask && !gmask[g]) continue;
         long long n = P->off[g + 1] - P->off[g];
         double *v = malloc(sizeof(double) * (size_t)(nsteps + 1) * n);
         for (int k = 0; k <= nsteps; ++k) memcpy(v + (long long)k * n, u0 + P->off[g], sizeof(double) * n);

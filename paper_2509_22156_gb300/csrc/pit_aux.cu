@@ -1,0 +1,238 @@
+// Auxiliary kernels of libpit: stencil application, initial values, face
+// coefficients of the variable-coefficient operator, the combination sum and
+// the MGRIT residual norms.
+#include "pit_internal.cuh"
+
+namespace pit {
+
+__device__ __forceinline__ int axis_coord(const GridInfo &G, int j, int i) { return (j / G.S[i]) % G.N[i]; }
+
+// Variable diffusion coefficient a(x) = 1 + A prod_i f_i(x_i), f alternating
+// sin(2 pi x), cos(2 pi x), ... (d = 3: 1 + A sin(2 pi x1) cos(2 pi x2) sin(2 pi x3)).
+__device__ double varcoef(const OpParams &op, const double *x)
+{
+    double prod = 1.0;
+    for (int i = 0; i < op.d; ++i) prod *= (i % 2 == 0) ? sin(2.0 * M_PI * x[i]) : cos(2.0 * M_PI * x[i]);
+    return 1.0 + op.vamp * prod;
+}
+
+// q = (I + dt L) p, one CTA per (batch entry, grid), FP64 with coefficients
+// evaluated per node (the reference application of the operator).
+__global__ void apply_kernel(const GridInfo *grids, int G, long long ntot, double dt, const double *p, double *q,
+                             const double *faces, OpParams op)
+{
+    const int g = blockIdx.x % G, b = blockIdx.x / G;
+    const GridInfo GI = grids[g];
+    const double *pg = p + (long long)b * ntot + GI.off;
+    double *qg = q + (long long)b * ntot + GI.off;
+    const int d = op.d;
+    for (int j = threadIdx.x; j < GI.n; j += blockDim.x) {
+        double s = 0.0, diag = 1.0;
+        for (int i = 0; i < d; ++i) {
+            const int c = axis_coord(GI, j, i);
+            const double h = GI.h[i], ih2 = 1.0 / (h * h);
+            double dd, dm, dp;
+            if (op.op == PIT_OP_HEAT) {
+                dd = 2.0 * ih2; dm = -ih2; dp = -ih2;
+            } else if (op.op == PIT_OP_VARHEAT) {
+                const double am = faces[(GI.off + j) * (2 * d) + 2 * i];
+                const double ap = faces[(GI.off + j) * (2 * d) + 2 * i + 1];
+                dd = (am + ap) * ih2; dm = -am * ih2; dp = -ap * ih2;
+            } else {
+                const double x = op.lo[i] + (double)(c + 1) * h;
+                const double vp = -op.theta * (x + 0.5 * h), vm = -op.theta * (x - 0.5 * h);
+                const double s2 = 0.5 * op.sigma * op.sigma * ih2;
+                dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
+                dm = -fmax(vm, 0.0) / h - s2;
+                dp = fmin(vp, 0.0) / h - s2;
+            }
+            diag += dt * dd;
+            if (c > 0) s += dt * dm * pg[j - GI.S[i]];
+            if (c < GI.N[i] - 1) s += dt * dp * pg[j + GI.S[i]];
+        }
+        qg[j] = diag * pg[j] + s;
+    }
+}
+
+cudaError_t launch_apply(const GridInfo *grids, int G, long long ntot, int n_batch, double dt, const double *p,
+                         double *q, const double *faces, OpParams op, cudaStream_t s)
+{
+    const long long blocks = (long long)G * n_batch;
+    if (blocks == 0) return cudaSuccess;
+    apply_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, G, ntot, dt, p, q, faces, op);
+    return cudaGetLastError();
+}
+
+// Initial values at the interior nodes (kind 0: sum of product-sine modes,
+// kind 1: product Gaussian); one CTA per grid.
+__global__ void initial_kernel(const GridInfo *grids, OpParams op, const double *hi, int kind, const double *prm,
+                               double *u)
+{
+    const GridInfo GI = grids[blockIdx.x];
+    const int d = op.d;
+    for (int j = threadIdx.x; j < GI.n; j += blockDim.x) {
+        double x[PIT_D];
+        for (int i = 0; i < d; ++i) x[i] = op.lo[i] + (double)(axis_coord(GI, j, i) + 1) * GI.h[i];
+        double v = 0.0;
+        if (kind == 0) {
+            const int K = (int)prm[0];
+            for (int k = 0; k < K; ++k) {
+                const double *pk = prm + 1 + k * (d + 1);
+                double prod = pk[0];
+                for (int i = 0; i < d; ++i) prod *= sin(M_PI * pk[1 + i] * (x[i] - op.lo[i]) / (hi[i] - op.lo[i]));
+                v += prod;
+            }
+        } else {
+            v = 1.0;
+            for (int i = 0; i < d; ++i) {
+                const double z = (x[i] - prm[i]) / prm[d + i];
+                v *= exp(-0.5 * z * z) / (prm[d + i] * sqrt(2.0 * M_PI));
+            }
+        }
+        u[GI.off + j] = v;
+    }
+}
+
+cudaError_t launch_initial(const GridInfo *grids, int G, OpParams op, const double *hi, int kind,
+                           const double *params_dev, int n_params, double *u, cudaStream_t s)
+{
+    (void)n_params;
+    initial_kernel<<<G, 256, 0, s>>>(grids, op, hi, kind, params_dev, u);
+    return cudaGetLastError();
+}
+
+// Face values a(x -+ h_i/2 e_i) of every node (2d per node, packed like the
+// state vectors), computed once per problem.
+__global__ void faces_kernel(const GridInfo *grids, OpParams op, double *faces)
+{
+    const GridInfo GI = grids[blockIdx.x];
+    const int d = op.d;
+    for (int j = threadIdx.x; j < GI.n; j += blockDim.x) {
+        double x[PIT_D];
+        for (int i = 0; i < d; ++i) x[i] = op.lo[i] + (double)(axis_coord(GI, j, i) + 1) * GI.h[i];
+        for (int i = 0; i < d; ++i) {
+            const double xi = x[i];
+            x[i] = xi - 0.5 * GI.h[i];
+            faces[(GI.off + j) * (2 * d) + 2 * i] = varcoef(op, x);
+            x[i] = xi + 0.5 * GI.h[i];
+            faces[(GI.off + j) * (2 * d) + 2 * i + 1] = varcoef(op, x);
+            x[i] = xi;
+        }
+    }
+}
+
+cudaError_t launch_faces(const GridInfo *grids, int G, OpParams op, double *faces, cudaStream_t s)
+{
+    faces_kernel<<<G, 256, 0, s>>>(grids, op, faces);
+    return cudaGetLastError();
+}
+
+// Combination sum (Eq. "combination_technique_solution") at arbitrary points:
+// out[k] = sum_g coef_g I_g[u_g](x_k), I_g piecewise d-linear with zero
+// boundary values.  One thread per point, grids summed in canonical order.
+__global__ void combine_kernel(const GridInfo *grids, const double *coef, const int *levels, int G, OpParams op,
+                               const double *u, int n_pts, const double *pts, double *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_pts) return;
+    const int d = op.d;
+    double x[PIT_D];
+    for (int i = 0; i < d; ++i) x[i] = pts[(long long)k * d + i];
+    double acc = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const GridInfo &GI = grids[g];
+        int cell[PIT_D];
+        double t[PIT_D];
+        for (int i = 0; i < d; ++i) {
+            const int M = 1 << levels[g * d + i];
+            const double s = (x[i] - op.lo[i]) / GI.h[i];
+            int c = (int)floor(s);
+            c = c < 0 ? 0 : (c > M - 1 ? M - 1 : c);
+            cell[i] = c;
+            t[i] = s - (double)c;
+        }
+        double val = 0.0;
+        for (int corner = 0; corner < (1 << d); ++corner) {
+            double w = 1.0;
+            long long idx = 0;
+            bool inside = true;
+            for (int i = 0; i < d; ++i) {
+                const int bit = (corner >> i) & 1;
+                const int node = cell[i] + bit;  // 0 and 2^l are boundary nodes
+                w *= bit ? t[i] : (1.0 - t[i]);
+                if (node <= 0 || node > GI.N[i]) inside = false;
+                else idx += (long long)(node - 1) * GI.S[i];
+            }
+            if (inside) val += w * u[GI.off + idx];
+        }
+        acc += coef[g] * val;
+    }
+    out[k] = acc;
+}
+
+cudaError_t launch_combine(const GridInfo *grids, const double *coef, const int *levels, int G, OpParams op,
+                           const double *u, int n_pts, const double *pts, double *out, cudaStream_t s)
+{
+    if (n_pts == 0) return cudaSuccess;
+    combine_kernel<<<(n_pts + 127) / 128, 128, 0, s>>>(grids, coef, levels, G, op, u, n_pts, pts, out);
+    return cudaGetLastError();
+}
+
+// resid[j*G + g] = ||a_j - b_j||_2 over grid g (one CTA per (j, g), fixed-order
+// reduction).
+__global__ void resid_norm_kernel(const GridInfo *grids, int G, const double *a, long long a_stride,
+                                  const double *b, long long b_stride, const int *active, double *resid)
+{
+    const int g = blockIdx.x % G, j = blockIdx.x / G;
+    if (active && !active[g]) return;
+    const GridInfo GI = grids[g];
+    const double *aj = a + (long long)j * a_stride + GI.off;
+    const double *bj = b + (long long)j * b_stride + GI.off;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < GI.n; t += blockDim.x) {
+        const double r = aj[t] - bj[t];
+        s += r * r;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        resid[(long long)j * G + g] = sqrt(tot);
+    }
+}
+
+cudaError_t launch_resid_norms(const GridInfo *grids, int G, long long ntot, int nb, const double *a,
+                               long long a_stride, const double *b, long long b_stride, const int *active,
+                               double *resid, cudaStream_t s)
+{
+    (void)ntot;
+    const long long blocks = (long long)nb * G;
+    if (blocks == 0) return cudaSuccess;
+    resid_norm_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, G, a, a_stride, b, b_stride, active, resid);
+    return cudaGetLastError();
+}
+
+__global__ void resid_max_kernel(int G, int nb, const double *resid, const int *active, double *rmax)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    if (active && !active[g]) return;
+    double m = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double r = resid[(long long)j * G + g];
+        if (r > m || r != r) m = r;
+        if (m != m) break;
+    }
+    rmax[g] = m;
+}
+
+cudaError_t launch_resid_max(int G, int nb, const double *resid, const int *active, double *rmax, cudaStream_t s)
+{
+    resid_max_kernel<<<(G + 127) / 128, 128, 0, s>>>(G, nb, resid, active, rmax);
+    return cudaGetLastError();
+}
+
+}  // namespace pit

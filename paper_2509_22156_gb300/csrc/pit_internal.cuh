@@ -1,0 +1,92 @@
+// Internal declarations of libpit: device-side grid table, operator
+// coefficients, launch arguments and the launchers shared by the API and the
+// kernels.  Method: Griebel, Schweitzer, Troska, arXiv 2509.22156.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pit.h"
+
+#define PIT_D PIT_MAX_DIM
+
+namespace pit {
+
+// One component grid Omega_l (Sec. 2.1.1): N_i = 2^{l_i} - 1 interior nodes per
+// axis, C-order strides S_i with the last axis fastest, mesh width h_i.
+struct GridInfo {
+    long long off;      // packed offset of the grid in a state vector
+    int n;              // interior nodes
+    int pad;
+    int N[PIT_D];
+    int S[PIT_D];
+    double h[PIT_D];
+};
+
+struct OpParams {
+    int op;             // pit_op
+    int d;
+    double lo[PIT_D];
+    double theta, sigma, vamp;
+};
+
+// Global counters filled by the backward-Euler kernels (one atomic per item).
+struct DevStats {
+    unsigned long long sum_iters;
+    unsigned long long items;
+    int max_iters;
+    int n_failed;
+    int max_refine;
+    int worst;          // largest pit_status code seen
+};
+
+// Arguments of one batched backward-Euler launch over the grids of a bucket.
+// Entry b of the batch reads in + b*in_stride (+ grid offset) and writes
+// out + b*out_stride; out must not overlap in.  After the solve
+// out = post_scale * x + gpost (gpost may be NULL).
+struct PhiArgs {
+    const GridInfo *grids;
+    const int *bucket_grids;
+    int n_bucket;
+    int n_batch;
+    double dt;
+    const double *in;    long long in_stride;
+    const double *f;     long long f_stride;
+    const double *gpost; long long g_stride;
+    double post_scale;
+    double *out;         long long out_stride;
+    const int *active;   // per grid, NULL = all active
+    const double *faces; // variable coefficient at the 2d faces of every node (FP64), or NULL
+    OpParams op;
+    double rtol;
+    int maxit;
+    float inner_rtol;
+    int ir_maxit;
+    DevStats *stats;
+};
+
+enum Prec { PLAIN = 0, MIXED = 1 };
+
+// Shared-memory bytes a backward-Euler item of n nodes needs.
+size_t phi_smem_bytes(int prec, int op, int d, int n);
+// Launch one bucket (grid-per-CTA, whole Krylov solve on chip).
+cudaError_t launch_phi_bucket(int prec, const PhiArgs &a, int threads, size_t smem, cudaStream_t s);
+// Raise the dynamic shared-memory limit of every backward-Euler kernel.
+cudaError_t phi_kernels_init(size_t max_smem);
+
+cudaError_t launch_apply(const GridInfo *grids, int G, long long ntot, int n_batch, double dt,
+                         const double *p, double *q, const double *faces, OpParams op, cudaStream_t s);
+cudaError_t launch_initial(const GridInfo *grids, int G, OpParams op, const double *hi, int kind,
+                           const double *params_dev, int n_params, double *u, cudaStream_t s);
+cudaError_t launch_faces(const GridInfo *grids, int G, OpParams op, double *faces, cudaStream_t s);
+cudaError_t launch_combine(const GridInfo *grids, const double *coef, const int *levels, int G, OpParams op,
+                           const double *u, int n_pts, const double *pts, double *out, cudaStream_t s);
+// resid[j*G + g] = || a_j - b_j ||_2 on grid g, for active grids; j < nb.
+cudaError_t launch_resid_norms(const GridInfo *grids, int G, long long ntot, int nb, const double *a,
+                               long long a_stride, const double *b, long long b_stride, const int *active,
+                               double *resid, cudaStream_t s);
+// rmax[g] = max_j resid[j*G + g] (NaN propagates), active grids only.
+cudaError_t launch_resid_max(int G, int nb, const double *resid, const int *active, double *rmax,
+                             cudaStream_t s);
+
+}  // namespace pit

@@ -1,0 +1,217 @@
+"""GPU parity: libpit (through its C ABI) against the CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances (relative L2 per vector unless stated):
+  FP64 path vs FP64 oracle       1e-10 (both Krylov solves run to 1e-13 or
+                                 tighter, so their difference is ~kappa*1e-13)
+  mixed path vs FP64 oracle      1e-6 required; the FP64 refinement reaches
+                                 the same 1e-12 target, checked at 1e-9
+  stencil, initial values,       1e-13 (same formulas, different rounding order)
+  combination sum
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_22156_gb300 import binding as B
+from paper_2509_22156_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_22156_gb300 import build
+    build.build()
+    B.load()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CASES = {
+    # name: (d, n, L0, op, lo, hi, dt)
+    "heat2d": (2, 5, 1, W.OP_HEAT, [0.0] * 2, [1.0] * 2, 0.1 / 64),
+    "heat3d": (3, 6, 1, W.OP_HEAT, [0.0] * 3, [1.0] * 3, 0.05 / 1024),
+    "heat6d": (6, 4, 1, W.OP_HEAT, [0.0] * 6, [1.0] * 6, 0.02 / 512),
+    "varheat3d": (3, 5, 1, W.OP_VARHEAT, [0.0] * 3, [1.0] * 3, 0.1 / 2048),
+    "ou4d": (4, 4, 1, W.OP_OU, [-6.0] * 4, [6.0] * 4, 1.0 / 512),
+    "ou2d_l0": (2, 7, 2, W.OP_OU, [-6.0] * 2, [6.0] * 2, 1.0 / 64),
+}
+
+
+def pair(name):
+    d, n, L0, op, lo, hi, dt = CASES[name]
+    P = B.Problem(d, n, L0, op, lo, hi)
+    O = oracle.Problem(d, n, L0, op, lo, hi)
+    return P, O, dt
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_grid_table_matches_oracle(name):
+    P, O, _ = pair(name)
+    assert (P.G, P.n_total) == (O.G, O.n_total)
+    np.testing.assert_array_equal(P.levels, O.levels)
+    np.testing.assert_array_equal(P.coef, O.coef)
+    np.testing.assert_array_equal(P.offsets, O.offsets)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_initial_values_match_oracle(k):
+    wl = W.workload(k)
+    n = min(wl.n, 6)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    P.sample_initial(wl.ic_kind, wl.ic_params, u)
+    ref = O.initial(wl.ic_kind, wl.ic_params)
+    assert rel(host(u), ref) < 1e-14
+    # host output buffer path
+    uh = np.empty(P.n_total)
+    P.sample_initial(wl.ic_kind, wl.ic_params, uh)
+    np.testing.assert_array_equal(uh, host(u))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_matches_oracle(name):
+    P, O, dt = pair(name)
+    nb = 3
+    p = W.random_vector(101, nb * P.n_total)
+    q = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    P.apply(dt, cuda(p), q)
+    ref = O.apply(dt, p)
+    assert rel(host(q), ref) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [B.PIT_PREC_FP64, B.PIT_PREC_MIXED])
+@pytest.mark.parametrize("name", list(CASES))
+def test_phi_batch_matches_oracle(name, prec):
+    P, O, dt = pair(name)
+    nb = 4
+    u = W.random_vector(202, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    opts = B.solve_opts(prec, rtol=1e-12, maxit=20000, inner_rtol=1e-4, ir_maxit=30)
+    st = P.phi_batch(dt, cuda(u), out, opts)
+    assert st.n_items == nb * P.G and st.n_failed == 0
+    ref = O.phi(dt, u, rtol=1e-15)
+    got = host(out)
+    for b in range(nb):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < (1e-10 if prec == B.PIT_PREC_FP64 else 1e-9), (b, g)
+    if prec == B.PIT_PREC_MIXED:
+        assert st.max_refine >= 1
+
+
+def test_phi_in_place_forcing_and_empty_batch():
+    P, O, dt = pair("heat3d")
+    u = W.random_vector(5, 2 * P.n_total)
+    f = W.random_vector(6, 2 * P.n_total)
+    x = cuda(u)
+    opts = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13)
+    P.phi_batch(dt, x, x, opts, f=cuda(f))   # in place, with forcing
+    assert rel(host(x), O.phi(dt, u, f, rtol=1e-15)) < 1e-10
+    st = P.phi_batch(dt, x, x, opts, n_batch=0)
+    assert st is not None
+
+
+def test_phi_reports_nonconvergence_and_nonfinite():
+    P, O, dt = pair("heat3d")
+    u = cuda(W.random_vector(7, P.n_total))
+    out = torch.empty_like(u)
+    with pytest.raises(B.PitError) as e:
+        P.phi_batch(dt, u, out, B.solve_opts(B.PIT_PREC_FP64, rtol=1e-14, maxit=1))
+    assert e.value.status == B.PIT_ERR_NOCONV
+    bad = u.clone()
+    bad[3] = float("nan")
+    with pytest.raises(B.PitError) as e:
+        P.phi_batch(dt, bad, out, B.solve_opts(B.PIT_PREC_FP64))
+    assert e.value.status == B.PIT_ERR_NONFINITE
+    with pytest.raises(B.PitError) as e:
+        P.phi_batch(dt, bad, out, B.solve_opts(B.PIT_PREC_MIXED))
+    assert e.value.status == B.PIT_ERR_NONFINITE
+    # the context is still usable
+    P.phi_batch(dt, u, out, B.solve_opts(B.PIT_PREC_FP64))
+
+
+@pytest.mark.parametrize("prec", [B.PIT_PREC_FP64, B.PIT_PREC_MIXED])
+def test_sequential_matches_oracle_workload1(prec):
+    wl = W.workload(1)
+    P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    uT = np.empty(P.n_total)
+    P.sequential_solve(u0, wl.dt, wl.nsteps, uT, B.solve_opts(prec, rtol=1e-13, ir_maxit=30))
+    ref = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-15)
+    assert rel(uT, ref) < (1e-10 if prec == B.PIT_PREC_FP64 else 1e-9)
+
+
+MG_CASES = {
+    # name: (workload, n, nsteps, m, levels, coarse)
+    "w1": (1, 5, 64, 4, 2, B.PIT_COARSE_IMPLICIT),
+    "w1_exact": (1, 5, 64, 4, 2, B.PIT_COARSE_EXACT),
+    "w2_small": (2, 5, 128, 8, 2, B.PIT_COARSE_IMPLICIT),
+    "w2_3lev": (2, 4, 64, 4, 3, B.PIT_COARSE_IMPLICIT),
+    "w3_small": (3, 3, 64, 8, 2, B.PIT_COARSE_IMPLICIT),
+    "w4_small": (4, 4, 128, 8, 2, B.PIT_COARSE_IMPLICIT),
+    "w5_small": (5, 3, 64, 4, 3, B.PIT_COARSE_IMPLICIT),
+}
+
+
+@pytest.mark.parametrize("prec", [B.PIT_PREC_FP64, B.PIT_PREC_MIXED])
+@pytest.mark.parametrize("name", list(MG_CASES))
+def test_mgrit_matches_oracle(name, prec):
+    k, n, N, m, lev, coarse = MG_CASES[name]
+    wl = W.workload(k)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    tol = 1e-10 * np.abs(u0).max()
+    fine = B.solve_opts(prec, rtol=1e-13, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=40, coarse=coarse, fine=fine)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    dt = (wl.t1 - wl.t0) / N
+    ref, its, hist, _ = O.mgrit(u0, dt, N, m, lev, tol=tol, maxit=40, coarse_kind=coarse, rtol=1e-15)
+    got = host(uT)
+    assert rel(got, ref) < (1e-10 if prec == B.PIT_PREC_FP64 else 1e-9)
+    assert st.n_converged == P.G
+    # same number of cycles as the oracle on the slowest grid (converged-grid
+    # masking follows the per-grid stopping rule)
+    assert abs(st.max_cycles - int(its.max())) <= (0 if prec == B.PIT_PREC_FP64 else 1)
+    # and the fixed point is the sequential solution
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert rel(got, seq) < 1e-7
+
+
+@pytest.mark.parametrize("name", ["heat2d", "heat3d", "ou2d_l0", "heat6d"])
+def test_combine_matches_oracle(name):
+    P, O, _ = pair(name)
+    d = P.d
+    lo, hi = CASES[name][4], CASES[name][5]
+    u = W.random_vector(303, P.n_total)
+    pts = W.eval_points(d, lo, hi, n_uniform=4096, n_diag=65, seed=9)
+    out = torch.empty(pts.shape[0], dtype=torch.float64, device="cuda")
+    P.combine(cuda(u), cuda(pts), out)
+    ref = O.combine(u, pts)
+    assert rel(host(out), ref) < 1e-13
+    # host pointers: the library stages them
+    outh = np.empty(pts.shape[0])
+    P.combine(u, pts, outh)
+    assert rel(outh, ref) < 1e-13
+    # empty point set
+    P.combine(u, pts[:0].copy(), outh[:0].copy())
