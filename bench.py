@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the CTMGRIT^loc hot path on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole path over the heat workload of level 9 in
+d = 3 (109 component grids, 73,915 nodes, 1024 backward-Euler steps on
+[0, 0.05], two-level MGRIT with m = 16 and FCF relaxation, FP32 Krylov inside
+FP64 refinement): pit_mgrit_solve from the resident initial value, then
+pit_combine at 65,794 evaluation points.  The metric is DoF-steps/s =
+n_total * nsteps / time per step, with the time to solve to the MGRIT
+tolerance reported beside it together with the error against the CPU
+oracle's sequential solution on a sample of grids.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pit|reference]
+
+Timing: CUDA events on the problem's stream around each step, L2 flushed
+(a 256 MiB write) before every timed step, barrier + synchronize on both
+sides, max over ranks.  Under torchrun every rank solves its own replica of
+the workload (independent problems, weak scaling); no collective is on the
+data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time to 1e-6 error & DoF-steps/s, plain FP64 vs mixed/batched/learned, 1 GB300"
+UNIT = "DoF-steps/s"
+SM_COUNT = 152
+SMEM_BYTES_PER_CLK = 128  # 32 banks x 4 B per SM and clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pit", choices=["pit", "reference"])
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--no-forms", action="store_true", help="skip the plain-FP64 and sequential forms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * (max(sm) if sm else 0)]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def phi_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pit_phi.cu", "pit_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2509_22156_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "phi_heat_mixed_heat3d_n9.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256_16") != phi_source_hash():
+            return None
+        return float(kv["dram_bytes_per_item"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def solver_setup(wl, B):
+    """Options of the chosen form and of the plain FP64 form."""
+    mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-10, maxit=4000, inner_rtol=1e-4, ir_maxit=12)
+    plain = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-10, maxit=8000)
+    tol = 1e-8  # MGRIT stopping rule: every C-point residual l2 norm <= 1e-8 (absolute)
+    chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=mixed, crs=mixed)
+    fp64 = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=plain, crs=plain)
+    return chosen, fp64, mixed, plain
+
+
+def run_pit(args, rank, world, local):
+    import torch
+    from paper_2509_22156_gb300 import binding as B
+    from paper_2509_22156_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    wl = W.workload(args.workload)
+    P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi, wl.theta, wl.sigma, wl.vamp, stream=stream.cuda_stream)
+    chosen, fp64, mixed, plain = solver_setup(wl, B)
+    u0 = torch.empty(P.n_total, dtype=torch.float64, device=dev)
+    P.sample_initial(wl.ic_kind, wl.ic_params, u0)
+    pts_h = W.eval_points(wl.d, wl.lo, wl.hi)
+    pts = torch.from_numpy(pts_h).to(dev)
+    uT = torch.empty_like(u0)
+    out = torch.empty(pts_h.shape[0], dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    dofsteps = P.n_total * wl.nsteps
+
+    def step(opts, u_in, o):
+        st = P.mgrit_solve(u_in, opts, uT)
+        P.combine(uT, pts, o)
+        return st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(chosen, u0, out)
+    barrier()
+    clocks = Clocks(local)
+    P.profile_enable(True)
+    total_ms, launches, stats = 0.0, 0, None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0.record(stream)
+        stats = step(chosen, u0, out)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    prof = P.profile_read()
+    P.profile_enable(False)
+    barrier()
+    clk = clocks.stop()
+    ms_step = total_ms / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * dofsteps / (ms_step / 1e3)
+    gpu_launches = int(sum(prof.launches))
+
+    # end to end through the C ABI with host buffers (pinned): H2D of u0 and
+    # D2H of the combined values inside the timed region
+    u0_h = torch.empty(P.n_total, dtype=torch.float64).pin_memory()
+    u0_h.copy_(u0.cpu())
+    out_h = torch.empty(pts_h.shape[0], dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.fill_(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(chosen, u0_h, out_h)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+
+    # roofline of the dominant kernel (grid-resident backward-Euler solver,
+    # heat operator, FP32 inner CG): shared-memory bytes moved per node and
+    # Krylov iteration by this schedule, over its event time
+    d = wl.d
+    smem_bytes_per_point_iter = 2 + 4 * (2 * d + 1) + 4 + 16 + 8 + 8 + 4
+    phi_ms = prof.ms[0]
+    phi_launches = int(prof.launches[0])
+    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_smem = SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9  # GB/s
+    achieved = prof.point_iters * smem_bytes_per_point_iter / (phi_ms / 1e3) / 1e9 if phi_ms > 0 else None
+    trf = ncu_traffic()
+    items_per_launch = prof.phi_items / max(1, phi_launches)
+    roofline = {"bound": "smem", "kernel": "phi_kernel<HEAT,MIXED> (grid-resident CG, FP32 inner)",
+                "achieved": achieved, "peak": peak_smem, "unit": "GB/s",
+                "frac": (achieved / peak_smem) if achieved else None,
+                "traffic": (trf * items_per_launch) if trf is not None else None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {SMEM_BYTES_PER_CLK} B/clk x {sm_mhz:.0f} MHz "
+                               "(sm_max_mhz of MEASURED_PEAKS.json)",
+                "phi_ms_per_step": phi_ms / args.steps, "phi_launches_per_step": phi_launches / args.steps,
+                "phi_share_of_step": (phi_ms / args.steps) / ms_step,
+                "point_iters_per_step": prof.point_iters / args.steps,
+                "smem_bytes_per_point_iter": smem_bytes_per_point_iter}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (FP32 inner Krylov inside FP64 refinement)",
+        "data": "synthetic (analytic initial value, seeded evaluation points)",
+        "config": {"workload": wl.name, "d": wl.d, "level": wl.n, "grids": P.G, "n_total": P.n_total,
+                   "nsteps": wl.nsteps, "t": [wl.t0, wl.t1], "mgrit": f"two-level FCF m={wl.m}",
+                   "coarse": "implicit backward Euler dT = m dt", "mgrit_tol_abs": chosen.tol,
+                   "krylov_rtol": chosen.fine.rtol, "inner_rtol": chosen.fine.inner_rtol,
+                   "eval_points": int(pts_h.shape[0]), "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_tol_ms": ms_step, "mgrit_cycles": stats.max_cycles,
+        "mgrit_res_hist": [stats.res_hist[i] for i in range(min(stats.max_cycles, 64))],
+        "krylov_iters_per_step": stats.krylov_iters, "phi_solves_per_step": stats.phi_items,
+        "gpu_launches": gpu_launches,
+        "e2e": {"value": world * dofsteps / (e2e_step / 1e3), "unit": UNIT, "ms_per_step": e2e_step,
+                "h2d_bytes_per_step": P.n_total * 8, "d2h_bytes_per_step": int(pts_h.shape[0]) * 8},
+        "roofline": roofline, "clocks": clk,
+    }
+
+    uT_h = uT.cpu().numpy().copy()
+    if not args.no_forms and rank == 0:
+        forms = {}
+        # plain FP64 MGRIT (same workload, FP64 Krylov)
+        step(fp64, u0, out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = step(fp64, u0, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        forms["plain_fp64_mgrit"] = {"ms": ms, "value": dofsteps / (ms / 1e3), "cycles": st.max_cycles}
+        uT_fp64 = uT.cpu().numpy().copy()
+        # time-sequential stepping on the GPU, FP64 and mixed
+        for name, so in (("sequential_fp64", plain), ("sequential_mixed", mixed)):
+            e0.record(stream)
+            P.sequential_solve(u0, wl.dt, wl.nsteps, uT, so)
+            P.combine(uT, pts, out)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3)}
+        forms["chosen_vs_plain_fp64_speedup"] = forms["plain_fp64_mgrit"]["ms"] / ms_step
+        forms["chosen_vs_mixed_minus_fp64_rel_l2"] = float(np.linalg.norm(uT_h - uT_fp64) / np.linalg.norm(uT_fp64))
+        result["forms"] = forms
+
+    if not args.no_cpu and rank == 0 and world == 1:
+        result["cpu_baseline"], result["accuracy"] = cpu_baseline(wl, uT_h, P.offsets, chosen)
+        err = result["accuracy"].get("max_rel_l2_vs_oracle_sequential")
+        if err is not None and err > 1e-6:
+            result["time_to_tol_ms"] = None
+    P.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result if rank == 0 else None
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, n_grids_target):
+    import oracle
+    O = oracle.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi, wl.theta, wl.sigma, wl.vamp)
+    stride = max(1, O.G // n_grids_target)
+    grids = list(range(0, O.G, stride))[:n_grids_target]
+    return O, grids
+
+
+def cpu_baseline(wl, uT_gpu, offsets, chosen, n_grids=12):
+    """The oracle (plain C, FP64, OpenMP over independent grids) on a bounded
+    sample of the same workload: every `stride`-th grid, all time steps, the
+    same MGRIT and Krylov tolerances."""
+    import oracle
+    O, grids = oracle_sample(wl, n_grids)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(min(cores, len(grids)))
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    t0 = time.perf_counter()
+    uT, its, _, st = O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64, rtol=1e-10,
+                             check=False, grids=grids)
+    t_mg = time.perf_counter() - t0
+    dof = sum(int(O.offsets[g + 1] - O.offsets[g]) for g in grids)
+    seq = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14, grids=grids)
+    errs, errs_mg = [], []
+    for g in grids:
+        sl = slice(int(offsets[g]), int(offsets[g + 1]))
+        errs.append(float(np.linalg.norm(uT_gpu[sl] - seq[sl]) / np.linalg.norm(seq[sl])))
+        errs_mg.append(float(np.linalg.norm(uT_gpu[sl] - uT[sl]) / np.linalg.norm(uT[sl])))
+    base = {"value": dof * wl.nsteps / t_mg, "unit": UNIT, "cores": min(cores, len(grids)), "kind": "oracle",
+            "sample": f"{len(grids)} of {O.G} grids ({dof} of {O.n_total} nodes), all {wl.nsteps} steps, "
+                      f"two-level MGRIT m={wl.m}, FP64 CG rtol 1e-10, {t_mg:.1f} s",
+            "seconds": t_mg}
+    acc = {"grids_sampled": grids, "max_rel_l2_vs_oracle_sequential": max(errs),
+           "max_rel_l2_vs_oracle_mgrit": max(errs_mg)}
+    return base, acc
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step solves a bounded sample of
+    the workload on the host cores; rank 0 alone."""
+    from paper_2509_22156_gb300 import workloads as W
+    import oracle
+    if rank != 0:
+        return None
+    wl = W.workload(args.workload)
+    O, grids = oracle_sample(wl, 6)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(min(cores, len(grids)))
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    dof = sum(int(O.offsets[g + 1] - O.offsets[g]) for g in grids)
+
+    def step():
+        O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=1e-8, maxit=64, rtol=1e-10, check=False, grids=grids)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    value = dof * wl.nsteps / (ms / 1e3)
+    sample = f"{len(grids)} of {O.G} grids ({dof} nodes), all {wl.nsteps} steps per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(cores, len(grids)), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_pit(args, rank, world, local)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

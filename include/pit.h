@@ -137,6 +137,7 @@ typedef struct {
     double res_hist[PIT_MAX_HIST];  /* max over grids of the residual, per cycle    */
     long long phi_items;            /* (state, grid) backward-Euler solves executed  */
     long long krylov_iters;         /* Krylov iterations summed over all solves      */
+    long long point_iters;          /* Krylov iterations weighted by grid nodes      */
     int learned_used;               /* 1 if the learned coarse propagator was used   */
     int fallback;                   /* 1 if it was replaced by the implicit one      */
     double ms;                      /* wall time of the call                        */
@@ -204,6 +205,24 @@ pit_status pit_mgrit_solve(pit_problem_t p, const double *u0, const pit_mgrit_op
  * (row-major); out: host or device, n_pts doubles.  Points outside the box
  * are clamped to its boundary cell. */
 pit_status pit_combine(pit_problem_t p, const double *u, int n_pts, const double *pts, double *out);
+
+/* Kernel timing of a problem: while enabled, every kernel the library
+ * launches is bracketed by CUDA events recorded on the problem's stream.
+ * pit_profile_read synchronises the stream and returns, since the last
+ * enable, per kernel family: launches, summed device milliseconds, and for
+ * the backward-Euler kernels the work done (Krylov iterations and refinement
+ * passes weighted by grid nodes).  Family 0 = backward-Euler solver,
+ * 1 = MGRIT residual norms, 2 = combination sum, 3 = other. */
+typedef struct {
+    long long launches[4];
+    double ms[4];
+    long long phi_items;
+    long long point_iters;   /* sum over items of nodes x Krylov iterations       */
+    long long point_passes;  /* sum over items of nodes x FP64 residual passes    */
+} pit_profile;
+
+pit_status pit_profile_enable(pit_problem_t p, int on);
+pit_status pit_profile_read(pit_problem_t p, pit_profile *out);
 
 /* Thread-local text of the last error. */
 const char *pit_last_error(void);

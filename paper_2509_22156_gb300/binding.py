@@ -32,7 +32,8 @@ PIT_PREC_FP64, PIT_PREC_MIXED = 0, 1
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
 
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
-            "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_last_error"]
+            "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",
+            "pit_profile_read", "pit_last_error"]
 
 
 class pit_problem_desc(ctypes.Structure):
@@ -60,8 +61,13 @@ class pit_mgrit_opts(ctypes.Structure):
 class pit_mgrit_stats(ctypes.Structure):
     _fields_ = [("max_cycles", ctypes.c_int), ("n_converged", ctypes.c_int),
                 ("res_hist", ctypes.c_double * MAX_HIST), ("phi_items", ctypes.c_longlong),
-                ("krylov_iters", ctypes.c_longlong), ("learned_used", ctypes.c_int), ("fallback", ctypes.c_int),
-                ("ms", ctypes.c_double)]
+                ("krylov_iters", ctypes.c_longlong), ("point_iters", ctypes.c_longlong),
+                ("learned_used", ctypes.c_int), ("fallback", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+class pit_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("phi_items", ctypes.c_longlong),
+                ("point_iters", ctypes.c_longlong), ("point_passes", ctypes.c_longlong)]
 
 
 _lib = None
@@ -89,6 +95,8 @@ def load(path: str = LIB_PATH):
         L.pit_sequential_solve.argtypes = [vp, vp, cd, ci, P(pit_solve_opts), vp, P(pit_phi_stats)]
         L.pit_mgrit_solve.argtypes = [vp, vp, P(pit_mgrit_opts), vp, P(pit_mgrit_stats)]
         L.pit_combine.argtypes = [vp, vp, ci, vp, vp]
+        L.pit_profile_enable.argtypes = [vp, ci]
+        L.pit_profile_read.argtypes = [vp, P(pit_profile)]
         L.pit_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name != "pit_last_error":
@@ -200,6 +208,14 @@ class Problem:
         if check:
             _check(rc, "pit_mgrit_solve")
         return st if check else (st, rc)
+
+    def profile_enable(self, on=True):
+        _check(load().pit_profile_enable(self._h, 1 if on else 0), "pit_profile_enable")
+
+    def profile_read(self) -> pit_profile:
+        pr = pit_profile()
+        _check(load().pit_profile_read(self._h, ctypes.byref(pr)), "pit_profile_read")
+        return pr
 
     def combine(self, u, pts, out):
         n_pts = (pts.size if isinstance(pts, np.ndarray) else pts.numel()) // self.d

@@ -1,6 +1,7 @@
 // C ABI of libpit (declared in include/pit.h): problem set-up, the batched
 // backward-Euler propagator, time-sequential stepping, the MGRIT driver and
 // the combination sum.  Method: Griebel, Schweitzer, Troska, arXiv 2509.22156.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -65,12 +66,6 @@ struct DBuf {
     double *d() const { return (double *)p; }
 };
 
-struct Bucket {
-    int threads;
-    size_t smem;
-    int n;           // grids
-    int *d_grids;    // device list
-};
 
 }  // namespace
 
@@ -93,13 +88,24 @@ struct pit_problem {
     double *d_faces = nullptr;
     DevStats *d_stats = nullptr;
     DevStats *h_stats = nullptr;  // pinned
-    std::vector<Bucket> buckets[2];
+    int *d_order = nullptr;          // grids by decreasing size
+    uint16_t *d_masks = nullptr;     // neighbour masks, packed like a state
+    size_t smem_need[2] = {0, 0};    // per precision form
     bool planned[2] = {false, false};
+    int threads[2][2] = {{0, 0}, {0, 0}};  // [prec][wide batch]; 0 = not tuned yet
+    int forced_threads[2] = {0, 0};        // pit_tune override [wide batch]
     // workspaces
     DBuf w_in, w_out, w_pts, w_u, w_prm;
-    DBuf m_U, m_W0, m_W1, m_UT, m_GC, m_res, m_rmax, m_UT1, m_GC1, m_T0, m_T1, m_act;
+    DBuf m_U, m_R, m_UT, m_GC, m_res, m_UT1, m_GC1, m_T0, m_act, w_tune;
+    std::vector<double> h_res;
     double *h_rmax = nullptr;  // pinned, G
     int *h_act = nullptr;      // pinned, G
+    // kernel timing (pit_profile_enable / pit_profile_read)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> prof_recs;  // (family, first event index)
+    long long prof_items = 0, prof_point_iters = 0, prof_point_passes = 0;
 };
 
 namespace {
@@ -114,6 +120,29 @@ int ptr_is_device(const void *p)
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+// Records a CUDA event pair around the next launch when profiling is on.
+struct ProfScope {
+    pit_problem *P;
+    long long idx = -1;
+    ProfScope(pit_problem *P_, int family) : P(P_)
+    {
+        if (!P->prof_on) return;
+        while (P->ev_pool.size() < P->ev_used + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+            P->ev_pool.push_back(e);
+        }
+        idx = (long long)P->ev_used;
+        P->ev_used += 2;
+        P->prof_recs.push_back({family, (size_t)idx});
+        cudaEventRecord(P->ev_pool[idx], P->stream);
+    }
+    ~ProfScope()
+    {
+        if (idx >= 0) cudaEventRecord(P->ev_pool[idx + 1], P->stream);
+    }
+};
 
 // Component grids of Eq. "combination_technique_solution": for w = 0..d-1 all
 // l with l_i >= L0 and |l|_1 = L + d - 1 - w, lexicographically ascending.
@@ -169,86 +198,77 @@ pit_status check_solve_opts(const pit_solve_opts *o)
     return PIT_OK;
 }
 
-// Threads of the CTA that owns a grid of n nodes: about four nodes per
-// thread, a whole number of warps, at most 512 (the kernels' launch bound).
-int threads_for(int n)
-{
-    int t = (n + 3) / 4;
-    t = (t + 31) & ~31;
-    if (t < 32) t = 32;
-    if (t > 512) t = 512;
-    return t;
-}
-
+// Shared memory the multi-step kernel needs for the largest grid.
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
-    std::vector<std::vector<int>> groups;
-    std::vector<int> thr;
-    std::vector<size_t> sm;
+    size_t need = 0;
+    int gmax = 0;
     for (int g = 0; g < P->G; ++g) {
-        const int n = P->info[g].n;
-        const int t = threads_for(n);
-        const size_t bytes = phi_smem_bytes(prec, P->desc.op, P->desc.d, n);
-        if (bytes > P->max_smem)
-            return fail(PIT_ERR_UNSUPPORTED,
-                        "grid %d (%d nodes) needs %zu bytes of shared memory for the on-chip solve; this device "
-                        "offers %zu",
-                        g, n, bytes, P->max_smem);
-        size_t k = 0;
-        while (k < thr.size() && thr[k] != t) ++k;
-        if (k == thr.size()) {
-            thr.push_back(t);
-            sm.push_back(0);
-            groups.emplace_back();
-        }
-        groups[k].push_back(g);
-        if (bytes > sm[k]) sm[k] = bytes;
+        const size_t bytes = phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[g].n);
+        if (bytes > need) { need = bytes; gmax = g; }
     }
-    for (size_t k = 0; k < groups.size(); ++k) {
-        Bucket B;
-        B.threads = thr[k];
-        B.smem = sm[k];
-        B.n = (int)groups[k].size();
-        CU(cudaMalloc(&B.d_grids, sizeof(int) * B.n));
-        CU(cudaMemcpy(B.d_grids, groups[k].data(), sizeof(int) * B.n, cudaMemcpyHostToDevice));
-        P->buckets[prec].push_back(B);
-    }
+    if (need > P->max_smem)
+        return fail(PIT_ERR_UNSUPPORTED,
+                    "grid %d (%d nodes) needs %zu bytes of shared memory for the on-chip solve in this precision "
+                    "form; the device offers %zu",
+                    gmax, P->info[gmax].n, need, P->max_smem);
+    P->smem_need[prec] = need;
     P->planned[prec] = true;
     return PIT_OK;
 }
 
-struct PhiCall {
+// One multi-step launch (see StepArgs).
+struct StepCall {
     double dt;
     int nb;
+    int nsteps;
     const double *in;
     long long is;
-    const double *f;
-    long long fs;
-    const double *gp;
-    long long gs;
-    double scale;
-    double *out;
-    long long os;
+    const double *f = nullptr;
+    long long fs = 0;
+    const double *g = nullptr;
+    long long gs = 0, gst = 0;
+    double *out_steps = nullptr;
+    long long oss = 0, osst = 0;
+    double *out_last = nullptr;
+    long long ols = 0;
+    double scale = 1.0;
+    const double *h = nullptr;
+    long long hs = 0;
+    const double *cmp = nullptr;
+    long long cs = 0;
+    double *norms = nullptr;
 };
 
-pit_status run_phi(pit_problem *P, const pit_solve_opts &o, const PhiCall &c, const int *active)
+StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
 {
-    const int prec = o.prec == PIT_PREC_MIXED ? MIXED : PLAIN;
-    TRY(plan(P, prec));
-    PhiArgs a;
+    StepArgs a;
     a.grids = P->d_grids;
+    a.masks = P->d_masks;
+    a.order = P->d_order;
+    a.n_grids = P->G;
     a.n_batch = c.nb;
+    a.nsteps = c.nsteps;
     a.dt = c.dt;
     a.in = c.in;
     a.in_stride = c.is;
     a.f = c.f;
     a.f_stride = c.fs;
-    a.gpost = c.gp;
+    a.g = c.g;
     a.g_stride = c.gs;
-    a.post_scale = c.scale;
-    a.out = c.out;
-    a.out_stride = c.os;
+    a.g_step = c.gst;
+    a.out_steps = c.out_steps;
+    a.os_stride = c.oss;
+    a.os_step = c.osst;
+    a.out_last = c.out_last;
+    a.ol_stride = c.ols;
+    a.out_scale = c.scale;
+    a.h = c.h;
+    a.h_stride = c.hs;
+    a.cmp = c.cmp;
+    a.cmp_stride = c.cs;
+    a.norms = c.norms;
     a.active = active;
     a.faces = P->d_faces;
     a.op = P->op;
@@ -257,11 +277,64 @@ pit_status run_phi(pit_problem *P, const pit_solve_opts &o, const PhiCall &c, co
     a.inner_rtol = (float)o.inner_rtol;
     a.ir_maxit = o.ir_maxit;
     a.stats = P->d_stats;
-    for (const Bucket &B : P->buckets[prec]) {
-        a.bucket_grids = B.d_grids;
-        a.n_bucket = B.n;
-        CU(launch_phi_bucket(prec, a, B.threads, B.smem, P->stream));
+    return a;
+}
+
+// Autotuner: the CTA size of a launch class (precision form x wide/narrow
+// batch) is chosen once per problem by timing one backward-Euler step of the
+// first real call of that class with every candidate, output to scratch.
+pit_status tune(pit_problem *P, int prec, bool wide, const pit_solve_opts &o, const StepCall &c, const int *active)
+{
+    int &slot = P->threads[prec][wide ? 1 : 0];
+    if (slot) return PIT_OK;
+    if (P->forced_threads[wide ? 1 : 0]) {
+        slot = P->forced_threads[wide ? 1 : 0];
+        return PIT_OK;
     }
+    const int cand[4] = {64, 128, 256, 512};
+    CU(P->w_tune.ensure(sizeof(double) * P->ntot * c.nb));
+    StepCall t;
+    t.dt = c.dt;
+    t.nb = c.nb;
+    t.nsteps = 1;
+    t.in = c.in;
+    t.is = c.is;
+    t.out_last = P->w_tune.d();
+    t.ols = P->ntot;
+    StepArgs a = make_args(P, o, t, active);
+    a.stats = nullptr;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_t = 128;
+    for (int k = 0; k < 4; ++k) {
+        for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
+            CU(cudaEventRecord(e0, P->stream));
+            CU(launch_steps(prec, a, cand[k], P->smem_need[prec], P->stream));
+            CU(cudaEventRecord(e1, P->stream));
+        }
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_t = cand[k]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    slot = best_t;
+    return PIT_OK;
+}
+
+pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
+{
+    const int prec = o.prec == PIT_PREC_MIXED ? MIXED : PLAIN;
+    TRY(plan(P, prec));
+    if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
+    const bool wide = c.nb >= 8;
+    TRY(tune(P, prec, wide, o, c, active));
+    StepArgs a = make_args(P, o, c, active);
+    ProfScope ps(P, 0);
+    CU(launch_steps(prec, a, P->threads[prec][wide ? 1 : 0], P->smem_need[prec], P->stream));
     return PIT_OK;
 }
 
@@ -276,6 +349,11 @@ pit_status read_stats(pit_problem *P, DevStats &s)
     CU(cudaMemcpyAsync(P->h_stats, P->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, P->stream));
     CU(cudaStreamSynchronize(P->stream));
     s = *P->h_stats;
+    if (P->prof_on) {
+        P->prof_items += (long long)s.items;
+        P->prof_point_iters += (long long)s.point_iters;
+        P->prof_point_passes += (long long)s.point_passes;
+    }
     return PIT_OK;
 }
 
@@ -407,6 +485,16 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     CUB(cudaMallocHost(&P->h_stats, sizeof(DevStats)));
     CUB(cudaMallocHost(&P->h_rmax, sizeof(double) * P->G));
     CUB(cudaMallocHost(&P->h_act, sizeof(int) * P->G));
+    {
+        std::vector<int> order(P->G);
+        for (int g = 0; g < P->G; ++g) order[g] = g;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return P->info[a].n > P->info[b].n; });
+        CUB(cudaMalloc(&P->d_order, sizeof(int) * P->G));
+        CUB(cudaMemcpy(P->d_order, order.data(), sizeof(int) * P->G, cudaMemcpyHostToDevice));
+    }
+    CUB(cudaMalloc(&P->d_masks, sizeof(uint16_t) * P->ntot));
+    CUB(launch_masks(P->d_grids, P->G, d, P->d_masks, P->stream));
     if (desc->op == PIT_OP_VARHEAT) {
         CUB(cudaMalloc(&P->d_faces, sizeof(double) * P->ntot * 2 * d));
         CUB(launch_faces(P->d_grids, P->G, P->op, P->d_faces, P->stream));
@@ -421,8 +509,8 @@ pit_status pit_problem_destroy(pit_problem_t P)
 {
     if (!P) return PIT_OK;
     cudaStreamSynchronize(P->stream);
-    for (int k = 0; k < 2; ++k)
-        for (Bucket &B : P->buckets[k]) cudaFree(B.d_grids);
+    cudaFree(P->d_order);
+    cudaFree(P->d_masks);
     cudaFree(P->d_grids);
     cudaFree(P->d_coef);
     cudaFree(P->d_levels);
@@ -432,9 +520,10 @@ pit_status pit_problem_destroy(pit_problem_t P)
     if (P->h_stats) cudaFreeHost(P->h_stats);
     if (P->h_rmax) cudaFreeHost(P->h_rmax);
     if (P->h_act) cudaFreeHost(P->h_act);
-    DBuf *bufs[] = {&P->w_in, &P->w_out, &P->w_pts, &P->w_u, &P->w_prm, &P->m_U, &P->m_W0, &P->m_W1, &P->m_UT,
-                    &P->m_GC, &P->m_res, &P->m_rmax, &P->m_UT1, &P->m_GC1, &P->m_T0, &P->m_T1, &P->m_act};
+    DBuf *bufs[] = {&P->w_in, &P->w_out, &P->w_pts, &P->w_u,   &P->w_prm, &P->m_U,  &P->m_R, &P->m_UT,
+                    &P->m_GC, &P->m_res, &P->m_UT1, &P->m_GC1, &P->m_T0,  &P->m_act, &P->w_tune};
     for (DBuf *b : bufs) b->release();
+    for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     delete P;
     return PIT_OK;
 }
@@ -474,7 +563,10 @@ pit_status pit_sample_initial(pit_problem_t P, int kind, const double *params, i
         CU(P->w_u.ensure(sizeof(double) * P->ntot));
         target = P->w_u.d();
     }
-    CU(launch_initial(P->d_grids, P->G, P->op, P->d_hi, kind, P->w_prm.d(), n_params, target, P->stream));
+    {
+        ProfScope ps(P, 3);
+        CU(launch_initial(P->d_grids, P->G, P->op, P->d_hi, kind, P->w_prm.d(), n_params, target, P->stream));
+    }
     if (!dev) CU(cudaMemcpyAsync(u0, target, sizeof(double) * P->ntot, cudaMemcpyDeviceToHost, P->stream));
     CU(cudaStreamSynchronize(P->stream));
     return PIT_OK;
@@ -484,6 +576,7 @@ pit_status pit_apply(pit_problem_t P, double dt, int n_batch, const double *pv, 
 {
     if (!P || !pv || !qv || n_batch < 0) return fail(PIT_ERR_INVALID_ARG, "bad argument");
     if (!ptr_is_device(pv) || !ptr_is_device(qv)) return fail(PIT_ERR_INVALID_ARG, "p and q must be device memory");
+    ProfScope ps(P, 3);
     CU(launch_apply(P->d_grids, P->G, P->ntot, n_batch, dt, pv, qv, P->d_faces, P->op, P->stream));
     return PIT_OK;
 }
@@ -507,15 +600,27 @@ pit_status pit_phi_batch(pit_problem_t P, double dt, int n_batch, const double *
         CU(P->w_out.ensure(bytes));
         target = P->w_out.d();
     }
-    if (stats) TRY(reset_stats(P));
-    PhiCall c{dt, n_batch, u_prev, P->ntot, f, P->ntot, nullptr, 0, 1.0, target, P->ntot};
-    TRY(run_phi(P, *opts, c, nullptr));
+    const bool want = stats || P->prof_on;
+    if (want) TRY(reset_stats(P));
+    StepCall c;
+    c.dt = dt;
+    c.nb = n_batch;
+    c.nsteps = 1;
+    c.in = u_prev;
+    c.is = P->ntot;
+    c.f = f;
+    c.fs = P->ntot;
+    c.out_last = target;
+    c.ols = P->ntot;
+    TRY(run_steps(P, *opts, c, nullptr));
     if (alias) CU(cudaMemcpyAsync(u_next, target, bytes, cudaMemcpyDeviceToDevice, P->stream));
-    if (stats) {
+    if (want) {
         DevStats s;
         TRY(read_stats(P, s));
-        fill_phi_stats(s, stats);
-        TRY(status_of(s));
+        if (stats) {
+            fill_phi_stats(s, stats);
+            TRY(status_of(s));
+        }
     }
     return PIT_OK;
 }
@@ -524,22 +629,34 @@ pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, in
                                 const pit_solve_opts *opts, double *uT, pit_phi_stats *stats)
 {
     if (!P || !u0 || !uT || nsteps < 0) return fail(PIT_ERR_INVALID_ARG, "bad argument");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(PIT_ERR_INVALID_ARG, "dt must be finite and >= 0");
     TRY(check_solve_opts(opts));
     const size_t bytes = sizeof(double) * P->ntot;
-    CU(P->m_T0.ensure(bytes));
-    CU(P->m_T1.ensure(bytes));
     const double *src;
     TRY(stage_in(P, P->w_in, u0, P->ntot, &src));
-    CU(cudaMemcpyAsync(P->m_T0.p, src, bytes, cudaMemcpyDeviceToDevice, P->stream));
-    TRY(reset_stats(P));
-    double *a = P->m_T0.d(), *b = P->m_T1.d();
-    for (int s = 0; s < nsteps; ++s) {
-        PhiCall c{dt, 1, a, P->ntot, nullptr, 0, nullptr, 0, 1.0, b, P->ntot};
-        TRY(run_phi(P, *opts, c, nullptr));
-        std::swap(a, b);
+    const bool dev_out = ptr_is_device(uT);
+    double *target = uT;
+    if (!dev_out || src == uT) {
+        CU(P->m_T0.ensure(bytes));
+        target = P->m_T0.d();
     }
-    CU(cudaMemcpyAsync(uT, a, bytes, ptr_is_device(uT) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       P->stream));
+    TRY(reset_stats(P));
+    if (nsteps == 0) {
+        CU(cudaMemcpyAsync(target, src, bytes, cudaMemcpyDeviceToDevice, P->stream));
+    } else {
+        // every grid is one CTA that takes all nsteps steps on chip
+        StepCall c;
+        c.dt = dt;
+        c.nb = 1;
+        c.nsteps = nsteps;
+        c.in = src;
+        c.is = P->ntot;
+        c.out_last = target;
+        c.ols = P->ntot;
+        TRY(run_steps(P, *opts, c, nullptr));
+    }
+    if (target != uT)
+        CU(cudaMemcpyAsync(uT, target, bytes, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream));
     DevStats s;
     TRY(read_stats(P, s));
     if (stats) fill_phi_stats(s, stats);
@@ -551,6 +668,18 @@ pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, in
 
 // ---------------------------------------------------------------------------
 // MGRIT driver (Sec. 3.3, Alg. 2 with FCF relaxation; Alg. 3 per grid).
+//
+// Level 0 stores C-points only (Sec. 3.3.2): U[j] = u_{jm}, j = 0..Nc.  One
+// cycle is four launches of the multi-step kernel:
+//   FC    R[j+1]  = Phi^m(U[j])            (F-relaxation + C-relaxation)
+//   F     UT[j]   = Phi^m(R[j]),  res[j] = ||UT[j] - R[j+1]||   (F-relaxation,
+//                  C-point residual r_{j+1} = Phi(u_{(j+1)m-1}) - u_{(j+1)m})
+//   FAS   GC[j]   = UT[j] - Phi_c(R[j])    (restricted residual + Phi_c of the
+//                  restricted solution: the coarse right-hand side of Alg. 2)
+//   sweep U[j+1]  = Phi_c(U[j]) + GC[j]    (coarse solve; its result is the
+//                  corrected C-point, the F-points follow from the next FC)
+// R[0] = U[0] = u0.  With three levels the sweep is replaced by one two-level
+// cycle of the level-1 problem (points R[0..Nc], forcing GC), written into U.
 namespace {
 
 struct Mg {
@@ -561,59 +690,81 @@ struct Mg {
     const int *active;
 };
 
-// One step of level `lev` for nb states: out_k = scale * Phi_lev(in_k) + gp_k.
-pit_status mg_step(Mg &M, int lev, int nb, const double *in, long long is, const double *gp, long long gs,
-                   double scale, double *out, long long os)
+// Coarse propagator of level 1: backward Euler with m dt, or m fine steps.
+void coarse_call(Mg &M, StepCall &c, int level)
 {
-    pit_problem *P = M.P;
-    if (nb <= 0) return PIT_OK;
-    if (lev == 1 && M.o->coarse == PIT_COARSE_EXACT) {
-        // m fine steps; intermediate states in T0/T1
-        const size_t bytes = sizeof(double) * M.nt * nb;
-        CU(P->m_T0.ensure(bytes));
-        CU(P->m_T1.ensure(bytes));
-        const double *src = in;
-        long long sst = is;
-        double *bufs[2] = {P->m_T0.d(), P->m_T1.d()};
-        for (int s = 0; s < M.o->m; ++s) {
-            const bool last = (s == M.o->m - 1);
-            double *dst = last ? out : bufs[s & 1];
-            PhiCall c{M.dt, nb, src, sst, nullptr, 0, last ? gp : nullptr, gs, last ? scale : 1.0, dst,
-                      last ? os : M.nt};
-            TRY(run_phi(P, M.o->fine, c, M.active));
-            src = dst;
-            sst = M.nt;
-        }
-        return PIT_OK;
+    if (level == 1 && M.o->coarse == PIT_COARSE_EXACT) {
+        c.dt = M.dt;
+        c.nsteps *= M.o->m;
+    } else {
+        double dtl = M.dt;
+        for (int q = 0; q < level; ++q) dtl *= M.o->m;
+        c.dt = dtl;
     }
-    double dtl = M.dt;
-    for (int q = 0; q < lev; ++q) dtl *= M.o->m;
-    const pit_solve_opts &so = lev == 0 ? M.o->fine : M.o->crs;
-    PhiCall c{dtl, nb, in, is, nullptr, 0, gp, gs, scale, out, os};
-    return run_phi(P, so, c, M.active);
 }
 
-// Level-1 two-level cycle of a three-level hierarchy: the level-1 points are
-// the level-0 C-points V[0..N1] (all stored), forcing of point k is F[k-1];
-// coarsest level solved by a sequential sweep.
-pit_status mg_level1_cycle(Mg &M, double *V, int N1, const double *F)
+// Two-level cycle of level 1 in a three-level hierarchy: level-1 points are V
+// (read) -> W (written), Nc1 = N1/m intervals, forcing of level-1 point k is
+// F[k-1]; the level-2 problem is solved by a sequential sweep.
+pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const double *F)
 {
     pit_problem *P = M.P;
     const int m = M.o->m, Nc = N1 / m;
     const long long nt = M.nt, sm = (long long)m * nt;
-    auto Vp = [&](int k) { return V + (long long)k * nt; };
-    auto Fp = [&](int k) { return F + (long long)(k - 1) * nt; };  // forcing of level-1 point k >= 1
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int i = 1; i < m; ++i) TRY(mg_step(M, 1, Nc, Vp(i - 1), sm, Fp(i), sm, 1.0, Vp(i), sm));
-        if (pass == 0) TRY(mg_step(M, 1, Nc, Vp(m - 1), sm, Fp(m), sm, 1.0, Vp(m), sm));
-    }
+    const pit_solve_opts &so = M.o->crs;
     CU(P->m_UT1.ensure(sizeof(double) * nt * Nc));
     CU(P->m_GC1.ensure(sizeof(double) * nt * Nc));
     double *UT1 = P->m_UT1.d(), *GC1 = P->m_GC1.d();
-    TRY(mg_step(M, 1, Nc, Vp(m - 1), sm, Fp(m), sm, 1.0, UT1, nt));          // utilde_j, j = 1..Nc
-    TRY(mg_step(M, 2, Nc, Vp(0), sm, UT1, nt, -1.0, GC1, nt));               // gc_j = utilde_j - Phi_2(v_{(j-1)m})
-    for (int j = 1; j <= Nc; ++j)
-        TRY(mg_step(M, 2, 1, Vp((j - 1) * m), nt, GC1 + (long long)(j - 1) * nt, nt, 1.0, Vp(j * m), nt));
+    if (W != V) CU(cudaMemcpyAsync(W, V, sizeof(double) * nt, cudaMemcpyDeviceToDevice, P->stream));
+    const double dt1 = M.dt * m;
+    // FC: F-points and C-point of every interval from the old C-points
+    StepCall fc;
+    fc.dt = dt1;
+    fc.nb = Nc;
+    fc.nsteps = m;
+    fc.in = V;
+    fc.is = sm;
+    fc.g = F;
+    fc.gs = sm;
+    fc.gst = nt;
+    fc.out_steps = W + nt;
+    fc.oss = sm;
+    fc.osst = nt;
+    fc.out_last = W + sm;
+    fc.ols = sm;
+    TRY(run_steps(P, so, fc, M.active));
+    // F-relaxation from the new C-points (F-points in place) and utilde
+    StepCall fr = fc;
+    fr.in = W;
+    fr.out_last = UT1;
+    fr.ols = nt;
+    TRY(run_steps(P, so, fr, M.active));
+    // coarse right-hand side and the level-2 sweep into the C-points of W
+    StepCall gc;
+    gc.dt = M.dt * m * m;
+    gc.nb = Nc;
+    gc.nsteps = 1;
+    gc.in = W;
+    gc.is = sm;
+    gc.out_last = GC1;
+    gc.ols = nt;
+    gc.scale = -1.0;
+    gc.h = UT1;
+    gc.hs = nt;
+    TRY(run_steps(P, so, gc, M.active));
+    StepCall sw;
+    sw.dt = M.dt * m * m;
+    sw.nb = 1;
+    sw.nsteps = Nc;
+    sw.in = W;
+    sw.is = nt;
+    sw.g = GC1;
+    sw.gst = nt;
+    sw.out_steps = W + sm;
+    sw.osst = sm;
+    sw.out_last = W + (long long)Nc * sm;
+    sw.ols = nt;
+    TRY(run_steps(P, so, sw, M.active));
     return PIT_OK;
 }
 
@@ -634,24 +785,25 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     long long div = o->m;
     if (o->levels == 3) div *= o->m;
     if (o->nsteps % div != 0) return fail(PIT_ERR_INVALID_ARG, "nsteps must be a multiple of m^(levels-1)");
+    if (o->levels == 3 && o->coarse == PIT_COARSE_EXACT)
+        return fail(PIT_ERR_UNSUPPORTED, "the exact coarse propagator is a two-level option");
     const int G = P->G, m = o->m, Nc = o->nsteps / m;
     const long long nt = P->ntot;
     const size_t vb = sizeof(double) * nt;
     CU(P->m_U.ensure(vb * (Nc + 1)));
-    CU(P->m_W0.ensure(vb * Nc));
-    CU(P->m_W1.ensure(vb * Nc));
+    CU(P->m_R.ensure(vb * (Nc + 1)));
     CU(P->m_UT.ensure(vb * Nc));
     CU(P->m_GC.ensure(vb * Nc));
     CU(P->m_res.ensure(sizeof(double) * G * Nc));
-    CU(P->m_rmax.ensure(sizeof(double) * G));
     CU(P->m_act.ensure(sizeof(int) * G));
-    double *U = P->m_U.d(), *UT = P->m_UT.d(), *GC = P->m_GC.d();
-    double *W[2] = {P->m_W0.d(), P->m_W1.d()};
+    P->h_res.resize((size_t)G * Nc);
+    double *U = P->m_U.d(), *R = P->m_R.d(), *UT = P->m_UT.d(), *GC = P->m_GC.d(), *res = P->m_res.d();
     int *act = (int *)P->m_act.p;
     const double *src;
     TRY(stage_in(P, P->w_in, u0, nt, &src));
     for (int j = 0; j <= Nc; ++j)
         CU(cudaMemcpyAsync(U + (long long)j * nt, src, vb, cudaMemcpyDeviceToDevice, P->stream));
+    CU(cudaMemcpyAsync(R, src, vb, cudaMemcpyDeviceToDevice, P->stream));
     for (int g = 0; g < G; ++g) P->h_act[g] = 1;
     CU(cudaMemcpyAsync(act, P->h_act, sizeof(int) * G, cudaMemcpyHostToDevice, P->stream));
     TRY(reset_stats(P));
@@ -659,42 +811,79 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     Mg M{P, o, (o->t1 - o->t0) / o->nsteps, nt, act};
     pit_mgrit_stats st;
     memset(&st, 0, sizeof(st));
-    std::vector<int> cycles(G, 0);
     int n_active = G, it = 0;
     while (n_active > 0 && it < o->maxit) {
-        // FCF relaxation; only the C-points are stored, W holds the F-values
-        int cur = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            TRY(mg_step(M, 0, Nc, U, nt, nullptr, 0, 1.0, W[0], nt));
-            cur = 0;
-            for (int i = 2; i < m; ++i) {
-                TRY(mg_step(M, 0, Nc, W[cur], nt, nullptr, 0, 1.0, W[cur ^ 1], nt));
-                cur ^= 1;
+        StepCall fc;  // FC relaxation
+        fc.dt = M.dt;
+        fc.nb = Nc;
+        fc.nsteps = m;
+        fc.in = U;
+        fc.is = nt;
+        fc.out_last = R + nt;
+        fc.ols = nt;
+        TRY(run_steps(P, o->fine, fc, act));
+        StepCall fr = fc;  // F relaxation, utilde and the C-point residuals
+        fr.in = R;
+        fr.out_last = UT;
+        fr.cmp = R + nt;
+        fr.cs = nt;
+        fr.norms = res;
+        TRY(run_steps(P, o->fine, fr, act));
+        CU(cudaMemcpyAsync(P->h_res.data(), res, sizeof(double) * G * Nc, cudaMemcpyDeviceToHost, P->stream));
+        StepCall gc;  // coarse right-hand side
+        gc.nb = Nc;
+        gc.nsteps = 1;
+        gc.in = R;
+        gc.is = nt;
+        gc.out_last = GC;
+        gc.ols = nt;
+        gc.scale = -1.0;
+        gc.h = UT;
+        gc.hs = nt;
+        coarse_call(M, gc, 1);
+        TRY(run_steps(P, o->crs, gc, act));
+        if (o->levels == 3) {
+            TRY(mg_level1_cycle(M, R, U, Nc, GC));
+        } else if (o->coarse == PIT_COARSE_EXACT) {
+            for (int j = 0; j < Nc; ++j) {
+                StepCall sw;
+                sw.nb = 1;
+                sw.nsteps = 1;
+                sw.in = U + (long long)j * nt;
+                sw.is = nt;
+                sw.out_last = U + (long long)(j + 1) * nt;
+                sw.ols = nt;
+                sw.h = GC + (long long)j * nt;
+                sw.hs = nt;
+                coarse_call(M, sw, 1);
+                TRY(run_steps(P, o->crs, sw, act));
             }
-            if (pass == 0) TRY(mg_step(M, 0, Nc, W[cur], nt, nullptr, 0, 1.0, U + nt, nt));  // C-relaxation
-        }
-        // utilde_j = Phi(u_{jm-1}) and the C-point residuals r_j = utilde_j - u_{jm}
-        TRY(mg_step(M, 0, Nc, W[cur], nt, nullptr, 0, 1.0, UT, nt));
-        CU(launch_resid_norms(P->d_grids, G, nt, Nc, UT, nt, U + nt, nt, act, P->m_res.d(), P->stream));
-        CU(launch_resid_max(G, Nc, P->m_res.d(), act, P->m_rmax.d(), P->stream));
-        CU(cudaMemcpyAsync(P->h_rmax, P->m_rmax.d(), sizeof(double) * G, cudaMemcpyDeviceToHost, P->stream));
-        // coarse FAS problem: gc_j = utilde_j - Phi_c(u_{(j-1)m}); v_j = Phi_c(v_{j-1}) + gc_j
-        TRY(mg_step(M, 1, Nc, U, nt, UT, nt, -1.0, GC, nt));
-        if (o->levels == 2) {
-            for (int j = 0; j < Nc; ++j)
-                TRY(mg_step(M, 1, 1, U + (long long)j * nt, nt, GC + (long long)j * nt, nt, 1.0,
-                            U + (long long)(j + 1) * nt, nt));
         } else {
-            TRY(mg_level1_cycle(M, U, Nc, GC));
+            StepCall sw;  // sequential coarse sweep, one CTA per grid
+            sw.nb = 1;
+            sw.nsteps = Nc;
+            sw.in = U;
+            sw.is = nt;
+            sw.g = GC;
+            sw.gst = nt;
+            sw.out_steps = U + nt;
+            sw.osst = nt;
+            sw.out_last = U + (long long)Nc * nt;
+            sw.ols = nt;
+            coarse_call(M, sw, 1);
+            TRY(run_steps(P, o->crs, sw, act));
         }
         CU(cudaStreamSynchronize(P->stream));
         double rmax = 0.0;
         n_active = 0;
         for (int g = 0; g < G; ++g) {
             if (!P->h_act[g]) continue;
-            const double r = P->h_rmax[g];
-            ++cycles[g];
-            if (!(r <= rmax) ) rmax = r;
+            double r = 0.0;
+            for (int j = 0; j < Nc; ++j) {
+                const double v = P->h_res[(size_t)j * G + g];
+                if (!(v <= r)) r = v;  // NaN propagates
+            }
+            if (!(r <= rmax)) rmax = r;
             if (r <= o->tol) P->h_act[g] = 0;
             else ++n_active;
         }
@@ -711,6 +900,7 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     st.n_converged = G - n_active;
     st.phi_items = (long long)ds.items;
     st.krylov_iters = (long long)ds.sum_iters;
+    st.point_iters = (long long)ds.point_iters;
     st.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = st;
     TRY(status_of(ds));
@@ -731,10 +921,41 @@ extern "C" pit_status pit_combine(pit_problem_t P, const double *u, int n_pts, c
         CU(P->w_out.ensure(sizeof(double) * n_pts));
         target = P->w_out.d();
     }
-    CU(launch_combine(P->d_grids, P->d_coef, P->d_levels, P->G, P->op, du, n_pts, dp, target, P->stream));
+    {
+        ProfScope ps(P, 2);
+        CU(launch_combine(P->d_grids, P->d_coef, P->d_levels, P->G, P->op, du, n_pts, dp, target, P->stream));
+    }
     if (!dev_out) {
         CU(cudaMemcpyAsync(out, target, sizeof(double) * n_pts, cudaMemcpyDeviceToHost, P->stream));
         CU(cudaStreamSynchronize(P->stream));
     }
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_profile_enable(pit_problem_t P, int on)
+{
+    if (!P) return fail(PIT_ERR_INVALID_ARG, "NULL problem");
+    CU(cudaStreamSynchronize(P->stream));
+    P->prof_on = on != 0;
+    P->ev_used = 0;
+    P->prof_recs.clear();
+    P->prof_items = P->prof_point_iters = P->prof_point_passes = 0;
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_profile_read(pit_problem_t P, pit_profile *out)
+{
+    if (!P || !out) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
+    CU(cudaStreamSynchronize(P->stream));
+    memset(out, 0, sizeof(*out));
+    for (const auto &r : P->prof_recs) {
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, P->ev_pool[r.second], P->ev_pool[r.second + 1]));
+        out->launches[r.first] += 1;
+        out->ms[r.first] += ms;
+    }
+    out->phi_items = P->prof_items;
+    out->point_iters = P->prof_point_iters;
+    out->point_passes = P->prof_point_passes;
     return PIT_OK;
 }

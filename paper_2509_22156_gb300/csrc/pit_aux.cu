@@ -121,6 +121,26 @@ __global__ void faces_kernel(const GridInfo *grids, OpParams op, double *faces)
     }
 }
 
+__global__ void masks_kernel(const GridInfo *grids, int d, uint16_t *masks)
+{
+    const GridInfo GI = grids[blockIdx.x];
+    for (int j = threadIdx.x; j < GI.n; j += blockDim.x) {
+        unsigned mk = 0;
+        for (int i = 0; i < d; ++i) {
+            const int c = axis_coord(GI, j, i);
+            if (c > 0) mk |= 1u << (2 * i);
+            if (c < GI.N[i] - 1) mk |= 1u << (2 * i + 1);
+        }
+        masks[GI.off + j] = (uint16_t)mk;
+    }
+}
+
+cudaError_t launch_masks(const GridInfo *grids, int G, int d, uint16_t *masks, cudaStream_t s)
+{
+    masks_kernel<<<G, 256, 0, s>>>(grids, d, masks);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_faces(const GridInfo *grids, int G, OpParams op, double *faces, cudaStream_t s)
 {
     faces_kernel<<<G, 256, 0, s>>>(grids, op, faces);

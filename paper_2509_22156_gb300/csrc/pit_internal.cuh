@@ -34,29 +34,42 @@ struct OpParams {
 struct DevStats {
     unsigned long long sum_iters;
     unsigned long long items;
+    unsigned long long point_iters;   // sum of nodes x Krylov iterations
+    unsigned long long point_passes;  // sum of nodes x FP64 residual passes
     int max_iters;
     int n_failed;
     int max_refine;
     int worst;          // largest pit_status code seen
 };
 
-// Arguments of one batched backward-Euler launch over the grids of a bucket.
-// Entry b of the batch reads in + b*in_stride (+ grid offset) and writes
-// out + b*out_stride; out must not overlap in.  After the solve
-// out = post_scale * x + gpost (gpost may be NULL).
-struct PhiArgs {
+// Arguments of one multi-step backward-Euler launch.  Item k of the launch
+// is grid order[k / n_batch] of batch entry b = k % n_batch.  Entry b starts
+// from in + b*in_stride (+ grid offset) and takes nsteps steps of size dt;
+// after step s (1-based) x <- x + g_s with g_s = g + b*g_stride + (s-1)*g_step
+// (g may be NULL); states after steps 1..nsteps-1 are written to out_steps +
+// b*os_stride + (s-1)*os_step when out_steps is non-NULL; the final state x is
+// written as out_scale * x + h_b to out_last + b*ol_stride, and, when cmp is
+// non-NULL, norms[b*n_grids + g] = ||x - cmp_b||_2.  No output may overlap the
+// input of the same item.
+struct StepArgs {
     const GridInfo *grids;
-    const int *bucket_grids;
-    int n_bucket;
+    const uint16_t *masks;  // neighbour mask of every node, packed like a state
+    const int *order;       // grids by decreasing size
+    int n_grids;
     int n_batch;
+    int nsteps;
     double dt;
-    const double *in;    long long in_stride;
-    const double *f;     long long f_stride;
-    const double *gpost; long long g_stride;
-    double post_scale;
-    double *out;         long long out_stride;
-    const int *active;   // per grid, NULL = all active
-    const double *faces; // variable coefficient at the 2d faces of every node (FP64), or NULL
+    const double *in;        long long in_stride;
+    const double *f;         long long f_stride;
+    const double *g;         long long g_stride, g_step;
+    double *out_steps;       long long os_stride, os_step;
+    double *out_last;        long long ol_stride;
+    double out_scale;
+    const double *h;         long long h_stride;
+    const double *cmp;       long long cmp_stride;
+    double *norms;
+    const int *active;       // per grid, NULL = all active
+    const double *faces;     // variable coefficient at the 2d faces of every node, or NULL
     OpParams op;
     double rtol;
     int maxit;
@@ -69,10 +82,12 @@ enum Prec { PLAIN = 0, MIXED = 1 };
 
 // Shared-memory bytes a backward-Euler item of n nodes needs.
 size_t phi_smem_bytes(int prec, int op, int d, int n);
-// Launch one bucket (grid-per-CTA, whole Krylov solve on chip).
-cudaError_t launch_phi_bucket(int prec, const PhiArgs &a, int threads, size_t smem, cudaStream_t s);
+// Launch one multi-step batch (grid-per-CTA, every Krylov solve on chip).
+cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s);
 // Raise the dynamic shared-memory limit of every backward-Euler kernel.
 cudaError_t phi_kernels_init(size_t max_smem);
+// Neighbour masks of every node (bit 2i: interior neighbour at -e_i, 2i+1: at +e_i).
+cudaError_t launch_masks(const GridInfo *grids, int G, int d, uint16_t *masks, cudaStream_t s);
 
 cudaError_t launch_apply(const GridInfo *grids, int G, long long ntot, int n_batch, double dt,
                          const double *p, double *q, const double *faces, OpParams op, cudaStream_t s);

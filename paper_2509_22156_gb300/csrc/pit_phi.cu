@@ -1,22 +1,26 @@
-// Batched backward-Euler propagator Phi (Sec. 2, Eq. "parabolic_problem_time_
-// propagation"): for every (batch entry, component grid) item solve
-//     (I + dt L_l) x = u_prev + dt f,   initial guess u_prev,
-// matrix-free, with CG for the symmetric operators and BiCGStab for the
-// drift operator (Sec. 4.1).
+// Batched multi-step backward-Euler propagator (Sec. 2, Eq. "parabolic_problem_
+// time_propagation"): every (batch entry, component grid) item is advanced by
+// nsteps backward-Euler steps
+//     (I + dt L_l) x_s = x_{s-1} + dt f,   x_s <- x_s + g_s (optional forcing),
+// each solved matrix-free with CG (symmetric operators) or BiCGStab (drift
+// operator, Sec. 4.1), initial guess x_{s-1}.
 //
-// Design (grid-resident): one CTA owns one item for the whole solve.  The
-// Krylov vectors live in shared memory, the dot products are reduced by warp
-// shuffles and one block barrier, and the iterate x is accumulated in the
-// output buffer.  HBM is touched once to read u_prev (and f) and once to
-// write x, instead of once per Krylov iteration; every grid of the
-// workloads (at most 9261 nodes) fits on one SM.
+// Design (grid-resident, multi-step): one CTA owns one item for all its
+// steps.  The FP64 state, the Krylov vectors and the neighbour masks live in
+// shared memory; dot products are reduced with warp shuffles and one block
+// barrier.  A whole F-relaxation interval (m - 1 steps) or a sequential
+// coarse sweep is one launch, HBM is touched once to read the start state
+// and once per stored output state, and the intermediate F-values never
+// leave the SM (the C-point-only storage of Sec. 3.3.2).
 //
-// Two precision forms:
+// Precision forms:
 //   PLAIN  Krylov in FP64 until ||b - A x|| <= rtol ||b||.
-//   MIXED  FP64 iterative refinement around an FP32 Krylov solve: the
-//          residual b - A x is formed in FP64 from the FP64 iterate, the
-//          correction equation is solved in FP32 to inner_rtol, and the
-//          correction is added in FP64; same FP64 stopping rule.
+//   MIXED  FP64 iterative refinement around an FP32 Krylov solve: residual
+//          b - A x formed in FP64 from the FP64 state, the correction
+//          equation solved in FP32 to inner_rtol, correction added in FP64;
+//          same FP64 stopping rule.
+// CG is the single-reduction (Chronopoulos-Gear) form: one fused block
+// reduction of (r,r) and (Ar,r) per iteration and two barriers.
 #include <type_traits>
 
 #include "pit_internal.cuh"
@@ -26,9 +30,8 @@ namespace pit {
 #define FULL_MASK 0xffffffffu
 
 // ----------------------------------------------------------------------------
-// Operator coefficients of node j in FP64: q_j = diag p_j + sum_i cm_i p_{j-e_i}
-// + cp_i p_{j+e_i}, with zero coefficients towards boundary nodes (zero
-// Dirichlet values).  Matches the oracle's operator definitions:
+// Operator coefficients of node j in FP64: (A p)_j = diag p_j + sum_i cm_i
+// p_{j-e_i} + cp_i p_{j+e_i}, zero towards boundary nodes (zero Dirichlet):
 //   heat    L p = sum_i (2 p_j - p_- - p_+) / h_i^2
 //   varheat L p = sum_i [a_+ (p_j - p_+) + a_- (p_j - p_-)] / h_i^2
 //   OU      L p = sum_i (F_+ - F_-) / h_i + (sigma^2/2)(2 p_j - p_- - p_+) / h_i^2,
@@ -67,7 +70,7 @@ __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, c
 }
 
 // Constant-coefficient heat stencil with a per-node neighbour mask
-// (bit 2i: node has an interior neighbour at -e_i, bit 2i+1: at +e_i).
+// (bit 2i: interior neighbour at -e_i, bit 2i+1: at +e_i).
 template <typename T>
 struct HeatSt {
     const uint16_t *mask;
@@ -75,16 +78,15 @@ struct HeatSt {
     int S[PIT_D];
     T diag;
     T off[PIT_D];
-    template <typename P>
-    __device__ __forceinline__ T operator()(const P *p, int j) const
+    __device__ __forceinline__ T operator()(const T *p, int j) const
     {
         const unsigned mk = mask[j];
-        T s = diag * (T)p[j];
+        T s = diag * p[j];
 #pragma unroll
         for (int i = 0; i < PIT_D; ++i) {
             if (i >= d) break;
-            const T pm = ((mk >> (2 * i)) & 1u) ? (T)p[j - S[i]] : T(0);
-            const T pp = ((mk >> (2 * i + 1)) & 1u) ? (T)p[j + S[i]] : T(0);
+            const T pm = ((mk >> (2 * i)) & 1u) ? p[j - S[i]] : T(0);
+            const T pp = ((mk >> (2 * i + 1)) & 1u) ? p[j + S[i]] : T(0);
             s += off[i] * (pm + pp);
         }
         return s;
@@ -92,7 +94,8 @@ struct HeatSt {
 };
 
 // Variable-coefficient stencil from a per-node table in shared memory
-// (structure of arrays: tab[k*ld + j], k = 0 diagonal, 1+2i minus, 2+2i plus).
+// (structure of arrays: tab[k*ld + j], k = 0 diagonal, 1+2i minus, 2+2i plus;
+// zero coefficients towards the boundary).
 template <typename T>
 struct TabSt {
     const uint16_t *mask;
@@ -115,38 +118,13 @@ struct TabSt {
     }
 };
 
-// FP64 stencil with coefficients evaluated on the fly (refinement residual of
-// the variable-coefficient operators; a few evaluations per solve).
-struct Op64St {
-    const GridInfo *G;
-    const OpParams *op;
-    const double *faces;
-    const uint16_t *mask;
-    double dt;
-    __device__ __forceinline__ double operator()(const double *p, int j) const
-    {
-        double diag, cm[PIT_D], cp[PIT_D];
-        op_coef(*op, *G, faces, j, dt, diag, cm, cp);
-        const unsigned mk = mask[j];
-        double s = diag * p[j];
-#pragma unroll
-        for (int i = 0; i < PIT_D; ++i) {
-            if (i >= op->d) break;
-            const double pm = ((mk >> (2 * i)) & 1u) ? p[j - G->S[i]] : 0.0;
-            const double pp = ((mk >> (2 * i + 1)) & 1u) ? p[j + G->S[i]] : 0.0;
-            s += cm[i] * pm + cp[i] * pp;
-        }
-        return s;
-    }
-};
-
 // ----------------------------------------------------------------------------
-// Block reductions.  Each warp reduces with shuffles, lane 0 stores its
-// partial in a 32-slot buffer, one barrier, and every thread adds the
-// partials in the same order: all threads hold the bitwise same sum and the
-// result does not depend on scheduling.  Callers alternate two buffers, so
-// one barrier per reduction is enough: a warp can only overwrite a buffer
-// after every warp has passed the barrier of the reduction in between.
+// Block reductions: warp shuffles, one partial per warp in a 32-slot buffer,
+// one barrier, then every warp reduces the partials with the same shuffle
+// tree and broadcasts lane 0: all threads hold the bitwise same value,
+// independent of scheduling.  Consecutive reductions alternate two buffers,
+// so one barrier per reduction suffices (a warp can only reuse a buffer after
+// every warp passed the barrier of the reduction in between).
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -157,25 +135,25 @@ __device__ __forceinline__ T warp_sum(T v)
 
 template <typename T>
 struct Reducer {
-    T *buf;    // two halves of 2 x 32 slots
-    int slot;  // reductions done so far; selects the half
+    T *buf;    // two halves of 4 x 32 slots
+    int slot;
     template <int K>
     __device__ __forceinline__ void sum(T *v)
     {
-        T *red = buf + (slot & 1) * 64;
+        T *red = buf + (slot & 1) * 128;
         ++slot;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            T x = warp_sum(v[k]);
+            const T x = warp_sum(v[k]);
             if (lane == 0) red[k * 32 + w] = x;
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            T s = T(0);
-            for (int q = 0; q < nw; ++q) s += red[k * 32 + q];
-            v[k] = s;
+            T x = (lane < nw) ? red[k * 32 + lane] : T(0);
+            x = warp_sum(x);
+            v[k] = __shfl_sync(FULL_MASK, x, 0);
         }
     }
 };
@@ -184,60 +162,94 @@ __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
 // ----------------------------------------------------------------------------
-// Conjugate gradients on A e = r0 (r holds r0, p = r0, rr = r0.r0 on entry),
-// accumulating the iterate into X (X may be global FP64 or shared FP32).
+// Single-reduction CG (Chronopoulos & Gear 1989) on A e = r0: r holds r0 on
+// entry (own nodes written by the caller), the iterate is accumulated into X
+// (FP64 state or FP32 correction).  Stops when (r,r) <= stop2.
 template <typename T, typename TX, class ST>
-__device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *q, Reducer<T> &R, T rr, T stop2,
-                       int maxit, int &status)
+__device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reducer<T> &R, T stop2, int maxit,
+                       int &status)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    int k = 0;
     status = PIT_OK;
+    __syncthreads();  // r complete
+    T v[2] = {T(0), T(0)};
+    for (int j = tid; j < n; j += nt) {
+        const T wj = A(r, j);
+        w[j] = wj;
+        const T rj = r[j];
+        v[0] += rj * rj;
+        v[1] += wj * rj;
+    }
+    R.template sum<2>(v);
+    T gam = v[0];
+    if (!(gam > stop2)) {
+        if (gam != gam) status = PIT_ERR_NONFINITE;
+        return 0;
+    }
+    if (!finite_pos(v[1])) {
+        status = (v[1] != v[1]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+        return 0;
+    }
+    T alpha = gam / v[1], beta = T(0);
+    bool first = true;
+    int k = 0;
     for (;;) {
-        if (!(rr > stop2)) {
-            if (rr != rr) status = PIT_ERR_NONFINITE;
+        if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+        for (int j = tid; j < n; j += nt) {
+            const T pj = first ? r[j] : r[j] + beta * p[j];
+            const T sj = first ? w[j] : w[j] + beta * s[j];
+            p[j] = pj;
+            s[j] = sj;
+            X[j] += (TX)(alpha * pj);
+            r[j] -= alpha * sj;
+        }
+        first = false;
+        ++k;
+        __syncthreads();
+        T u[2] = {T(0), T(0)};
+        for (int j = tid; j < n; j += nt) {
+            const T wj = A(r, j);
+            w[j] = wj;
+            const T rj = r[j];
+            u[0] += rj * rj;
+            u[1] += wj * rj;
+        }
+        R.template sum<2>(u);
+        if (!(u[0] > stop2)) {
+            if (u[0] != u[0]) status = PIT_ERR_NONFINITE;
             break;
         }
-        if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
-        __syncthreads();  // p complete
-        T pq[1] = {T(0)};
-        for (int j = tid; j < n; j += nt) {
-            const T qj = A(p, j);
-            q[j] = qj;
-            pq[0] += p[j] * qj;
-        }
-        R.template sum<1>(pq);
-        if (!finite_pos(pq[0])) { status = (pq[0] != pq[0]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
-        const T alpha = rr / pq[0];
-        T rn[1] = {T(0)};
-        for (int j = tid; j < n; j += nt) {
-            X[j] += (TX)(alpha * p[j]);
-            const T rj = r[j] - alpha * q[j];
-            r[j] = rj;
-            rn[0] += rj * rj;
-        }
-        R.template sum<1>(rn);
-        const T beta = rn[0] / rr;
-        for (int j = tid; j < n; j += nt) p[j] = r[j] + beta * p[j];
-        rr = rn[0];
-        ++k;
+        beta = u[0] / gam;
+        const T den = u[1] - beta * u[0] / alpha;
+        if (!finite_pos(den)) { status = (den != den) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        alpha = u[0] / den;
+        gam = u[0];
     }
     return k;
 }
 
-// BiCGStab (van der Vorst 1992) on A e = r0 (r holds r0, rh = r0, p = v = 0
-// on entry).  The vector s shares r's storage.
+// BiCGStab (van der Vorst 1992) on A e = r0: r holds r0 on entry; rh, p, v
+// are initialised here; s shares r's storage.
 template <typename T, typename TX, class ST>
-__device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v, T *t, Reducer<T> &R,
-                             T rr, T stop2, int maxit, int &status)
+__device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v, T *t, Reducer<T> &R, T stop2,
+                             int maxit, int &status)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    T rho = T(1), alpha = T(1), omega = T(1);
+    T rr[1] = {T(0)};
+    for (int j = tid; j < n; j += nt) {
+        const T rj = r[j];
+        rh[j] = rj;
+        p[j] = T(0);
+        v[j] = T(0);
+        rr[0] += rj * rj;
+    }
+    R.template sum<1>(rr);
+    T rho = T(1), alpha = T(1), omega = T(1), rrv = rr[0];
     int k = 0;
     status = PIT_OK;
     for (;;) {
-        if (!(rr > stop2)) {
-            if (rr != rr) status = PIT_ERR_NONFINITE;
+        if (!(rrv > stop2)) {
+            if (rrv != rrv) status = PIT_ERR_NONFINITE;
             break;
         }
         if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
@@ -283,43 +295,50 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         }
         R.template sum<1>(rn);
         rho = rho_n[0];
-        rr = rn[0];
+        rrv = rn[0];
         ++k;
-        if (omega == T(0) && rr > stop2) { status = PIT_ERR_BREAKDOWN; break; }
+        if (omega == T(0) && rrv > stop2) { status = PIT_ERR_BREAKDOWN; break; }
     }
     return k;
 }
 
 // ----------------------------------------------------------------------------
-// Shared-memory layout of one item (n nodes, rounded up to ld = n rounded to 4):
-//   vectors (nvec * ld of T), coefficient table (ntab * ld of T), mask (ld u16).
-__host__ __device__ inline int phi_nvec(int prec, int op)
+// Shared-memory layout of one item (ld = n rounded up to 4):
+//   FP64 arrays: x, [b (MIXED)], [Krylov vectors (PLAIN)], [table (var. coef.)]
+//   FP32 arrays: [Krylov vectors + table (MIXED)]
+//   u16 mask
+__host__ __device__ inline int krylov_vecs(int op, int prec)
 {
-    if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;
-    return prec == PLAIN ? 3 : 4;
+    if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e)
+    return prec == PLAIN ? 4 : 5;                        // r p s w (+ e)
 }
-
-__host__ __device__ inline int phi_ntab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
+__host__ __device__ inline int n_tab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
+__host__ __device__ inline int n_f64(int op, int prec, int d)
+{
+    return (prec == PLAIN ? 1 + krylov_vecs(op, prec) : 2) + n_tab(op, d);
+}
+__host__ __device__ inline int n_f32(int op, int prec, int d)
+{
+    return prec == MIXED ? krylov_vecs(op, prec) + n_tab(op, d) : 0;
+}
 
 size_t phi_smem_bytes(int prec, int op, int d, int n)
 {
     const size_t ld = (size_t)((n + 3) & ~3);
-    const size_t esz = prec == PLAIN ? 8 : 4;
-    return (size_t)(phi_nvec(prec, op) + phi_ntab(op, d)) * ld * esz + ld * 2 + 16;
+    return (size_t)n_f64(op, prec, d) * ld * 8 + (size_t)n_f32(op, prec, d) * ld * 4 + ld * 2 + 16;
 }
 
 template <int OP, int PREC>
-__global__ void __launch_bounds__(512) phi_kernel(PhiArgs a)
+__global__ void __launch_bounds__(512) steps_kernel(StepArgs a)
 {
     typedef typename std::conditional<PREC == PLAIN, double, float>::type T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ GridInfo GI;
-    __shared__ double red64[2 * 2 * 32];
-    __shared__ float red32[2 * 2 * 32];
+    __shared__ double red64[2 * 128];
+    __shared__ float red32[2 * 128];
 
-    const int gi = blockIdx.x % a.n_bucket;
-    const int b = blockIdx.x / a.n_bucket;
-    const int g = a.bucket_grids[gi];
+    const int g = a.order[blockIdx.x / a.n_batch];
+    const int b = blockIdx.x % a.n_batch;
     if (a.active && !a.active[g]) return;  // uniform over the block
     if (threadIdx.x == 0) GI = a.grids[g];
     __syncthreads();
@@ -328,46 +347,56 @@ __global__ void __launch_bounds__(512) phi_kernel(PhiArgs a)
     const int n = GI.n, d = a.op.d;
     const int ld = (n + 3) & ~3;
     const double dt = a.dt;
+    const int K = n_tab(OP, d);
+
+    double *x = reinterpret_cast<double *>(smem);
+    double *bvec = x + ld;  // MIXED only
+    double *v64 = x + ld;   // PLAIN Krylov vectors
+    double *tab64 = x + (size_t)(n_f64(OP, PREC, d) - K) * ld;
+    float *f32 = reinterpret_cast<float *>(x + (size_t)n_f64(OP, PREC, d) * ld);
+    float *tab32 = f32 + (size_t)krylov_vecs(OP, PREC) * ld;
+    uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)n_f32(OP, PREC, d) * ld);
+
     const double *in = a.in + (long long)b * a.in_stride + GI.off;
     const double *f = a.f ? a.f + (long long)b * a.f_stride + GI.off : nullptr;
-    double *out = a.out + (long long)b * a.out_stride + GI.off;
+    const uint16_t *gmask = a.masks + GI.off;
 
-    T *vec = reinterpret_cast<T *>(smem);
-    const int nvec = phi_nvec(PREC, OP);
-    T *tab = vec + (size_t)nvec * ld;
-    uint16_t *mask = reinterpret_cast<uint16_t *>(tab + (size_t)phi_ntab(OP, d) * ld);
-
-    // neighbour masks and (variable-coefficient operators) the coefficient table
     for (int j = tid; j < n; j += nt) {
-        unsigned mk = 0;
-#pragma unroll
-        for (int i = 0; i < PIT_D; ++i) {
-            if (i >= d) break;
-            const int c = (j / GI.S[i]) % GI.N[i];
-            if (c > 0) mk |= 1u << (2 * i);
-            if (c < GI.N[i] - 1) mk |= 1u << (2 * i + 1);
-        }
-        mask[j] = (uint16_t)mk;
-        if constexpr (OP != PIT_OP_HEAT) {
+        mask[j] = gmask[j];
+        x[j] = in[j];
+    }
+    if constexpr (OP != PIT_OP_HEAT) {
+        for (int j = tid; j < n; j += nt) {
             double diag, cm[PIT_D], cp[PIT_D];
             op_coef(a.op, GI, a.faces, j, dt, diag, cm, cp);
-            tab[j] = (T)diag;
+            tab64[j] = diag;
+            if constexpr (PREC == MIXED) tab32[j] = (float)diag;
             for (int i = 0; i < d; ++i) {
-                tab[(1 + 2 * i) * ld + j] = (T)cm[i];
-                tab[(2 + 2 * i) * ld + j] = (T)cp[i];
+                tab64[(1 + 2 * i) * ld + j] = cm[i];
+                tab64[(2 + 2 * i) * ld + j] = cp[i];
+                if constexpr (PREC == MIXED) {
+                    tab32[(1 + 2 * i) * ld + j] = (float)cm[i];
+                    tab32[(2 + 2 * i) * ld + j] = (float)cp[i];
+                }
             }
         }
     }
-    // constant heat coefficients (FP64 and working precision)
+    // stencils in FP64 and in the working precision
     HeatSt<double> H64;
     HeatSt<T> HT;
-    H64.mask = HT.mask = mask;
-    H64.d = HT.d = d;
+    TabSt<double> T64;
+    TabSt<float> T32;
+    H64.mask = HT.mask = T64.mask = T32.mask = mask;
+    H64.d = HT.d = T64.d = T32.d = d;
+    T64.tab = tab64;
+    T32.tab = tab32;
+    T64.ld = T32.ld = ld;
     {
         double diag = 1.0;
         for (int i = 0; i < PIT_D; ++i) {
             const double ih2 = (i < d) ? 1.0 / (GI.h[i] * GI.h[i]) : 0.0;
-            H64.S[i] = HT.S[i] = (i < d) ? GI.S[i] : 0;
+            const int S = (i < d) ? GI.S[i] : 0;
+            H64.S[i] = HT.S[i] = T64.S[i] = T32.S[i] = S;
             H64.off[i] = -dt * ih2;
             HT.off[i] = (T)(-dt * ih2);
             diag += 2.0 * dt * ih2;
@@ -375,117 +404,117 @@ __global__ void __launch_bounds__(512) phi_kernel(PhiArgs a)
         H64.diag = diag;
         HT.diag = (T)diag;
     }
-    TabSt<T> TT;
-    TT.mask = mask;
-    TT.tab = tab;
-    TT.ld = ld;
-    TT.d = d;
-    for (int i = 0; i < PIT_D; ++i) TT.S[i] = (i < d) ? GI.S[i] : 0;
-    Op64St O64{&GI, &a.op, a.faces, mask, dt};
-    __syncthreads();
 
     Reducer<double> R64{red64, 0};
     Reducer<float> R32{red32, 0};
     int status = PIT_OK, iters = 0, passes = 0;
 
-    if constexpr (PREC == PLAIN) {
-        T *r = vec, *p = vec + ld, *q = vec + 2 * ld;
-        T *rh = vec + 2 * ld, *v = vec + 3 * ld, *t = vec + 4 * ld;  // BiCGStab uses r, rh, p, v, t
-        double acc[2] = {0.0, 0.0};
-        for (int j = tid; j < n; j += nt) {
-            const double bj = in[j] + (f ? dt * f[j] : 0.0);
-            double Ax;
-            if constexpr (OP == PIT_OP_HEAT) Ax = H64(in, j);
-            else Ax = O64(in, j);
-            const double rj = bj - Ax;
-            r[j] = rj;
-            out[j] = in[j];
-            if constexpr (OP == PIT_OP_OU) { rh[j] = rj; p[j] = 0.0; v[j] = 0.0; }
-            else p[j] = rj;
-            acc[0] += bj * bj;
-            acc[1] += rj * rj;
-        }
-        R64.template sum<2>(acc);
-        const double stop2 = a.rtol * a.rtol * acc[0];
-        Reducer<double> &R = R64;
-        if constexpr (OP == PIT_OP_OU) {
-            iters = bicgstab_core<double, double>(TT, n, out, (double *)r, (double *)rh, (double *)p,
-                                                  (double *)v, (double *)t, R, acc[1], stop2, a.maxit, status);
-        } else if constexpr (OP == PIT_OP_HEAT) {
-            iters = cg_core<double, double>(H64, n, out, (double *)r, (double *)p, (double *)q, R, acc[1], stop2,
-                                            a.maxit, status);
-        } else {
-            iters = cg_core<double, double>(TT, n, out, (double *)r, (double *)p, (double *)q, R, acc[1], stop2,
-                                            a.maxit, status);
-        }
-        passes = 1;
-    } else {
-        float *e = (float *)vec, *r = (float *)vec + ld, *p = (float *)vec + 2 * ld, *q = (float *)vec + 3 * ld;
-        float *rh = (float *)vec + 3 * ld, *v = (float *)vec + 4 * ld, *t = (float *)vec + 5 * ld;
-        double bb[1] = {0.0};
-        for (int j = tid; j < n; j += nt) {
-            const double bj = in[j] + (f ? dt * f[j] : 0.0);
-            out[j] = in[j];
-            bb[0] += bj * bj;
-        }
-        R64.template sum<1>(bb);
-        const double stop2 = a.rtol * a.rtol * bb[0];
-        for (;;) {
-            __syncthreads();  // iterate visible to the whole block
-            double rn2[1] = {0.0};
+    for (int step = 1; step <= a.nsteps; ++step) {
+        __syncthreads();  // state complete
+        if constexpr (PREC == PLAIN) {
+            double *r = v64, *q1 = v64 + ld, *q2 = v64 + 2 * ld, *q3 = v64 + 3 * ld, *q4 = v64 + 4 * ld;
+            double bb[1] = {0.0};
             for (int j = tid; j < n; j += nt) {
-                const double bj = in[j] + (f ? dt * f[j] : 0.0);
+                const double bj = x[j] + (f ? dt * f[j] : 0.0);
                 double Ax;
-                if constexpr (OP == PIT_OP_HEAT) Ax = H64(out, j);
-                else Ax = O64(out, j);
-                const double rj = bj - Ax;
-                r[j] = (float)rj;
-                rn2[0] += rj * rj;
+                if constexpr (OP == PIT_OP_HEAT) Ax = H64(x, j);
+                else Ax = T64(x, j);
+                r[j] = bj - Ax;
+                bb[0] += bj * bj;
             }
-            R64.template sum<1>(rn2);
-            if (!(rn2[0] > stop2)) {
-                if (rn2[0] != rn2[0]) status = PIT_ERR_NONFINITE;
-                break;
-            }
-            if (passes >= a.ir_maxit) { status = PIT_ERR_NOCONV; break; }
-            const double rnorm = sqrt(rn2[0]);
-            const float inv = (float)(1.0 / rnorm);
-            float rr[1] = {0.0f};
-            for (int j = tid; j < n; j += nt) {
-                const float rj = r[j] * inv;
-                r[j] = rj;
-                e[j] = 0.0f;
-                if constexpr (OP == PIT_OP_OU) { rh[j] = rj; p[j] = 0.0f; v[j] = 0.0f; }
-                else p[j] = rj;
-                rr[0] += rj * rj;
-            }
-            R32.template sum<1>(rr);
-            const float stop32 = a.inner_rtol * a.inner_rtol * rr[0];
-            int st = PIT_OK, k;
-            if constexpr (OP == PIT_OP_OU)
-                k = bicgstab_core<float, float>(TT, n, e, r, rh, p, v, t, R32, rr[0], stop32, a.maxit, st);
-            else if constexpr (OP == PIT_OP_HEAT)
-                k = cg_core<float, float>(HT, n, e, r, p, q, R32, rr[0], stop32, a.maxit, st);
-            else
-                k = cg_core<float, float>(TT, n, e, r, p, q, R32, rr[0], stop32, a.maxit, st);
+            R64.template sum<1>(bb);  // also orders the residual before x changes
+            const double stop2 = a.rtol * a.rtol * bb[0];
+            int st, k;
+            if constexpr (OP == PIT_OP_OU) k = bicgstab_core<double, double>(T64, n, x, r, q1, q2, q3, q4, R64, stop2, a.maxit, st);
+            else if constexpr (OP == PIT_OP_HEAT) k = cg_core<double, double>(H64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
+            else k = cg_core<double, double>(T64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
             iters += k;
             ++passes;
-            if (st == PIT_ERR_NONFINITE) { status = st; break; }
-            // an inner solve that stalls (FP32 floor) or breaks down still
-            // yields a usable correction; the FP64 residual decides.
-            for (int j = tid; j < n; j += nt) out[j] += (double)e[j] * rnorm;
+            if (st > status) status = st;
+        } else {
+            float *e = f32, *r = f32 + ld, *q1 = f32 + 2 * ld, *q2 = f32 + 3 * ld, *q3 = f32 + 4 * ld;
+            float *q4 = f32 + 5 * ld;
+            double bb[1] = {0.0};
+            for (int j = tid; j < n; j += nt) {
+                const double bj = x[j] + (f ? dt * f[j] : 0.0);
+                bvec[j] = bj;
+                bb[0] += bj * bj;
+            }
+            R64.template sum<1>(bb);
+            const double stop2 = a.rtol * a.rtol * bb[0];
+            int st_step = PIT_OK;
+            for (int pass = 0;; ++pass) {
+                __syncthreads();  // x complete
+                double rn2[1] = {0.0};
+                for (int j = tid; j < n; j += nt) {
+                    double Ax;
+                    if constexpr (OP == PIT_OP_HEAT) Ax = H64(x, j);
+                    else Ax = T64(x, j);
+                    const double rj = bvec[j] - Ax;
+                    r[j] = (float)rj;
+                    rn2[0] += rj * rj;
+                }
+                R64.template sum<1>(rn2);
+                ++passes;
+                if (!(rn2[0] > stop2)) {
+                    if (rn2[0] != rn2[0]) st_step = PIT_ERR_NONFINITE;
+                    break;
+                }
+                if (pass >= a.ir_maxit) { st_step = PIT_ERR_NOCONV; break; }
+                const double rnorm = sqrt(rn2[0]);
+                const float inv = (float)(1.0 / rnorm);
+                for (int j = tid; j < n; j += nt) {
+                    r[j] *= inv;
+                    e[j] = 0.0f;
+                }
+                const float stop32 = a.inner_rtol * a.inner_rtol;
+                int st, k;
+                if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, e, r, q1, q2, q3, q4, R32, stop32, a.maxit, st);
+                else if constexpr (OP == PIT_OP_HEAT) k = cg_core<float, float>(HT, n, e, r, q1, q2, q3, R32, stop32, a.maxit, st);
+                else k = cg_core<float, float>(T32, n, e, r, q1, q2, q3, R32, stop32, a.maxit, st);
+                iters += k;
+                if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
+                // a stalled or broken-down inner solve still gives a usable
+                // correction; the FP64 residual decides
+                for (int j = tid; j < n; j += nt) x[j] += (double)e[j] * rnorm;
+            }
+            if (st_step > status) status = st_step;
         }
-    }
-    // out = post_scale * x + gpost: each thread its own nodes, after a barrier
-    // that ended every neighbour read of x.
-    __syncthreads();
-    const double *gp = a.gpost ? a.gpost + (long long)b * a.g_stride + GI.off : nullptr;
-    if (a.post_scale != 1.0 || gp) {
-        for (int j = tid; j < n; j += nt) out[j] = a.post_scale * out[j] + (gp ? gp[j] : 0.0);
+        // forcing of this step and the stored outputs (own nodes only)
+        const long long sb = (long long)(step - 1);
+        if (a.g) {
+            const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
+            for (int j = tid; j < n; j += nt) x[j] += gs[j];
+        }
+        if (step < a.nsteps) {
+            if (a.out_steps) {
+                double *os = a.out_steps + (long long)b * a.os_stride + sb * a.os_step + GI.off;
+                for (int j = tid; j < n; j += nt) os[j] = x[j];
+            }
+        } else {
+            double *ol = a.out_last + (long long)b * a.ol_stride + GI.off;
+            const double *h = a.h ? a.h + (long long)b * a.h_stride + GI.off : nullptr;
+            const double *cmp = a.cmp ? a.cmp + (long long)b * a.cmp_stride + GI.off : nullptr;
+            double acc[1] = {0.0};
+            for (int j = tid; j < n; j += nt) {
+                const double xj = x[j];
+                if (cmp) {
+                    const double dlt = xj - cmp[j];
+                    acc[0] += dlt * dlt;
+                }
+                ol[j] = a.out_scale * xj + (h ? h[j] : 0.0);
+            }
+            if (cmp) {
+                R64.template sum<1>(acc);
+                if (tid == 0) a.norms[(long long)b * a.n_grids + g] = sqrt(acc[0]);
+            }
+        }
     }
     if (tid == 0 && a.stats) {
         atomicAdd(&a.stats->sum_iters, (unsigned long long)iters);
-        atomicAdd(&a.stats->items, 1ull);
+        atomicAdd(&a.stats->items, (unsigned long long)a.nsteps);
+        atomicAdd(&a.stats->point_iters, (unsigned long long)iters * (unsigned long long)n);
+        atomicAdd(&a.stats->point_passes, (unsigned long long)passes * (unsigned long long)n);
         atomicMax(&a.stats->max_iters, iters);
         atomicMax(&a.stats->max_refine, passes);
         if (status != PIT_OK) {
@@ -501,9 +530,9 @@ cudaError_t phi_kernels_init(size_t max_smem)
 {
     cudaError_t e = cudaSuccess;
     const int bytes = (int)max_smem;
-#define PIT_SET(OPV, PV)                                                                                  \
-    if (e == cudaSuccess)                                                                                 \
-        e = cudaFuncSetAttribute(phi_kernel<OPV, PV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+#define PIT_SET(OPV, PV)                                                                                     \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(steps_kernel<OPV, PV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     PIT_SET(PIT_OP_HEAT, PLAIN) PIT_SET(PIT_OP_HEAT, MIXED)
     PIT_SET(PIT_OP_VARHEAT, PLAIN) PIT_SET(PIT_OP_VARHEAT, MIXED)
     PIT_SET(PIT_OP_OU, PLAIN) PIT_SET(PIT_OP_OU, MIXED)
@@ -512,19 +541,20 @@ cudaError_t phi_kernels_init(size_t max_smem)
     return e;
 }
 
-cudaError_t launch_phi_bucket(int prec, const PhiArgs &a, int threads, size_t smem, cudaStream_t s)
+cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s)
 {
-    const long long blocks = (long long)a.n_batch * a.n_bucket;
+    const long long blocks = (long long)a.n_batch * a.n_grids;
     if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL || smem > g_max_smem) return cudaErrorInvalidConfiguration;
+    if (blocks > 0x7fffffffLL || smem > g_max_smem || threads < 32 || threads > 512 || (threads & 31))
+        return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)blocks), block(threads);
     switch (a.op.op * 2 + prec) {
-    case PIT_OP_HEAT * 2 + PLAIN: phi_kernel<PIT_OP_HEAT, PLAIN><<<grid, block, smem, s>>>(a); break;
-    case PIT_OP_HEAT * 2 + MIXED: phi_kernel<PIT_OP_HEAT, MIXED><<<grid, block, smem, s>>>(a); break;
-    case PIT_OP_VARHEAT * 2 + PLAIN: phi_kernel<PIT_OP_VARHEAT, PLAIN><<<grid, block, smem, s>>>(a); break;
-    case PIT_OP_VARHEAT * 2 + MIXED: phi_kernel<PIT_OP_VARHEAT, MIXED><<<grid, block, smem, s>>>(a); break;
-    case PIT_OP_OU * 2 + PLAIN: phi_kernel<PIT_OP_OU, PLAIN><<<grid, block, smem, s>>>(a); break;
-    case PIT_OP_OU * 2 + MIXED: phi_kernel<PIT_OP_OU, MIXED><<<grid, block, smem, s>>>(a); break;
+    case PIT_OP_HEAT * 2 + PLAIN: steps_kernel<PIT_OP_HEAT, PLAIN><<<grid, block, smem, s>>>(a); break;
+    case PIT_OP_HEAT * 2 + MIXED: steps_kernel<PIT_OP_HEAT, MIXED><<<grid, block, smem, s>>>(a); break;
+    case PIT_OP_VARHEAT * 2 + PLAIN: steps_kernel<PIT_OP_VARHEAT, PLAIN><<<grid, block, smem, s>>>(a); break;
+    case PIT_OP_VARHEAT * 2 + MIXED: steps_kernel<PIT_OP_VARHEAT, MIXED><<<grid, block, smem, s>>>(a); break;
+    case PIT_OP_OU * 2 + PLAIN: steps_kernel<PIT_OP_OU, PLAIN><<<grid, block, smem, s>>>(a); break;
+    case PIT_OP_OU * 2 + MIXED: steps_kernel<PIT_OP_OU, MIXED><<<grid, block, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
