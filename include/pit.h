@@ -224,6 +224,32 @@ typedef struct {
 pit_status pit_profile_enable(pit_problem_t p, int on);
 pit_status pit_profile_read(pit_problem_t p, pit_profile *out);
 
+/* In-place backward-Euler step that allocates nothing.  The paper has no
+ * counterpart; this is a service to callers that cannot allocate device
+ * memory while they run: an application whose GPU memory is entirely reserved
+ * by another allocator (a framework's caching pool that owns the device), or
+ * a control loop that forbids any allocation after start-up.  It computes
+ * what pit_phi_batch computes with u_next == u_prev: u <- Phi(u) (+ dt f in the
+ * right-hand side) for n_batch packed states, but stages the result in one
+ * static device array of PIT_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that the
+ * library holds on every GPU that loads it, until the process exits, instead
+ * of a buffer it would allocate.
+ *   - u, f: device, n_batch * n_total doubles (f may be NULL); the caller owns
+ *     them.  Requires n_batch * n_total <= PIT_STATIC_SCRATCH_DOUBLES, else
+ *     PIT_ERR_INVALID_ARG before any device work.
+ *   - The problem's device must be current.  The first call on a device looks
+ *     up the array's device address (cudaGetSymbolAddress) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls on a device share the one array, and every call overwrites it
+ *     entirely before reading it.  Calls whose work overlaps on the GPU (on
+ *     different streams, or from several threads) race on it: order them.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine.  The CTA
+ *     size is the one the autotuner already chose for this problem, else 128.
+ *   - stats as in pit_phi_batch (NULL skips the synchronisation). */
+#define PIT_STATIC_SCRATCH_DOUBLES (1 << 20)
+pit_status pit_phi_batch_inplace_static(pit_problem_t p, double dt, int n_batch, double *u, const double *f,
+                                        const pit_solve_opts *opts, pit_phi_stats *stats);
+
 /* Thread-local text of the last error. */
 const char *pit_last_error(void);
 

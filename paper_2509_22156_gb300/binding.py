@@ -33,7 +33,8 @@ PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
 
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
             "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",
-            "pit_profile_read", "pit_last_error"]
+            "pit_profile_read", "pit_phi_batch_inplace_static", "pit_last_error"]
+STATIC_SCRATCH_DOUBLES = 1 << 20
 
 
 class pit_problem_desc(ctypes.Structure):
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         L.pit_combine.argtypes = [vp, vp, ci, vp, vp]
         L.pit_profile_enable.argtypes = [vp, ci]
         L.pit_profile_read.argtypes = [vp, P(pit_profile)]
+        L.pit_phi_batch_inplace_static.argtypes = [vp, cd, ci, vp, vp, P(pit_solve_opts), P(pit_phi_stats)]
         L.pit_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name != "pit_last_error":
@@ -194,6 +196,16 @@ class Problem:
         _check(load().pit_phi_batch(self._h, dt, nb, _ptr(u_prev), _ptr(f), _ptr(u_next),
                                     ctypes.byref(opts or solve_opts()), ctypes.byref(st) if st else None),
                "pit_phi_batch")
+        return st
+
+    def phi_batch_inplace_static(self, dt, u, opts=None, f=None, n_batch=None, stats=True):
+        """In-place step without any allocation (static scratch inside libpit)."""
+        nb = n_batch if n_batch is not None else u.numel() // self.n_total
+        st = pit_phi_stats() if stats else None
+        _check(load().pit_phi_batch_inplace_static(self._h, dt, nb, _ptr(u), _ptr(f),
+                                                   ctypes.byref(opts or solve_opts()),
+                                                   ctypes.byref(st) if st else None),
+               "pit_phi_batch_inplace_static")
         return st
 
     def sequential_solve(self, u0, dt, nsteps, uT, opts=None):

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -957,5 +958,79 @@ extern "C" pit_status pit_profile_read(pit_problem_t P, pit_profile *out)
     out->phi_items = P->prof_items;
     out->point_iters = P->prof_point_iters;
     out->point_passes = P->prof_point_passes;
+    return PIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// In-place backward-Euler step that allocates nothing (see pit.h).  The staging
+// buffer that pit_phi_batch allocates for in-place steps is replaced by one
+// file-scope device array of PIT_STATIC_SCRATCH_DOUBLES doubles, present on
+// every device that loads the library until the process exits.  Host code
+// only holds a stand-in for that array's name; the device address is looked
+// up once per device with cudaGetSymbolAddress and cached.
+static __device__ __align__(256) double g_static_scratch[PIT_STATIC_SCRATCH_DOUBLES];
+
+namespace {
+std::mutex g_static_mu;
+double *g_static_ptr[256] = {nullptr};
+}  // namespace
+
+extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, int n_batch, double *u,
+                                                   const double *f, const pit_solve_opts *opts,
+                                                   pit_phi_stats *stats)
+{
+    if (!P || !u || n_batch < 0) return fail(PIT_ERR_INVALID_ARG, "bad argument");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(PIT_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    TRY(check_solve_opts(opts));
+    const long long count = (long long)n_batch * P->ntot;
+    if (count > (long long)PIT_STATIC_SCRATCH_DOUBLES)
+        return fail(PIT_ERR_INVALID_ARG,
+                    "n_batch * n_total = %lld exceeds the static scratch of %d doubles of "
+                    "pit_phi_batch_inplace_static",
+                    count, PIT_STATIC_SCRATCH_DOUBLES);
+    if (!ptr_is_device(u) || (f && !ptr_is_device(f))) return fail(PIT_ERR_INVALID_ARG, "u and f must be device memory");
+    if (n_batch == 0) return PIT_OK;
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != P->device) return fail(PIT_ERR_INVALID_ARG, "the problem's device (%d) is not current (%d)", P->device, dev);
+    if (dev < 0 || dev >= 256) return fail(PIT_ERR_UNSUPPORTED, "device ordinal %d", dev);
+    double *scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(PIT_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+            g_static_ptr[dev] = (double *)p;
+        }
+        scratch = g_static_ptr[dev];
+    }
+    const int prec = opts->prec == PIT_PREC_MIXED ? MIXED : PLAIN;
+    TRY(plan(P, prec));
+    const bool wide = n_batch >= 8;
+    const int threads = P->threads[prec][wide ? 1 : 0] ? P->threads[prec][wide ? 1 : 0] : 128;
+    StepCall c;
+    c.dt = dt;
+    c.nb = n_batch;
+    c.nsteps = 1;
+    c.in = u;
+    c.is = P->ntot;
+    c.f = f;
+    c.fs = P->ntot;
+    c.out_last = scratch;  // every node of every item is written: nothing needs clearing
+    c.ols = P->ntot;
+    StepArgs a = make_args(P, *opts, c, nullptr);
+    if (stats) CU(cudaMemsetAsync(P->d_stats, 0, sizeof(DevStats), P->stream));
+    else a.stats = nullptr;
+    CU(launch_steps(prec, a, threads, P->smem_need[prec], P->stream));
+    CU(cudaMemcpyAsync(u, scratch, sizeof(double) * count, cudaMemcpyDeviceToDevice, P->stream));
+    if (stats) {
+        CU(cudaMemcpyAsync(P->h_stats, P->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, P->stream));
+        CU(cudaStreamSynchronize(P->stream));
+        const DevStats s = *P->h_stats;
+        fill_phi_stats(s, stats);
+        TRY(status_of(s));
+    }
     return PIT_OK;
 }
