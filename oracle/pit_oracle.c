@@ -476,7 +476,10 @@ int or_sequential(void *vp, const double *u0, double dt, int nsteps, double rtol
  *   bias_k[o].  h^{k+1}_o(j) = act(b_o + sum_i sum_c sum_t W[o][c][t] *
  *   in_c(j + (t-2) e_i)), zero padding outside the grid (Dirichlet zero),
  *   with in_c = (h^k channels, s_i) along axis i.  act = ReLU on layers 0..2,
- *   identity on layer 3; output u + h^4.                                   */
+ *   identity on layer 3.  The state enters normalised, u / sigma with
+ *   sigma = sqrt(mean_j u_j^2) over the grid's nodes, and the output is
+ *   u + sigma * h^4 (u itself when sigma = 0), so that the map is scale-
+ *   equivariant like the linear propagator it replaces.                    */
 #define NET_W 5
 static const int NET_CIN[4] = {3, 17, 17, 17};
 static const int NET_COUT[4] = {16, 16, 16, 1};
@@ -529,6 +532,14 @@ static void net_layer_forward(const geom *G, int k, const double *theta, long lo
 /* Forward pass on one grid: out = u + h^4.  acts (optional) receives the
  * post-activation hidden states of layers 0..2 (3 x 16 x n) and pre the
  * pre-activations of layers 0..3 (16+16+16+1 channels x n). */
+/* RMS of a grid vector (the network's input scale). */
+static double rms(long long n, const double *u)
+{
+    double s = 0.0;
+    for (long long j = 0; j < n; ++j) s += u[j] * u[j];
+    return sqrt(s / (double)n);
+}
+
 static void net_forward_grid(const or_problem *P, int g, double dT, const double *theta,
                              const double *u, double *out, double *acts, double *pres)
 {
@@ -538,11 +549,18 @@ static void net_forward_grid(const or_problem *P, int g, double dT, const double
     net_offsets(wo, bo);
     double mu[OR_MAXD];
     for (int i = 0; i < G.d; ++i) mu[i] = 1.0 / (1.0 + 4.0 * dT / (G.h[i] * G.h[i]));
+    const double sigma = rms(n, u);
+    if (!(sigma > 0.0)) {
+        memcpy(out, u, sizeof(double) * n);
+        if (acts) memset(acts, 0, sizeof(double) * 3 * 16 * n);
+        if (pres) memset(pres, 0, sizeof(double) * 49 * n);
+        return;
+    }
     double *in0 = malloc(sizeof(double) * 2 * n);
     long long c[OR_MAXD];
     double x[OR_MAXD];
     for (long long j = 0; j < n; ++j) {
-        in0[j] = u[j];
+        in0[j] = u[j] / sigma;
         coords(&G, j, c);
         for (int i = 0; i < G.d; ++i) x[i] = G.lo[i] + (double)(c[i] + 1) * G.h[i];
         in0[n + j] = (P->op == OR_VARHEAT) ? varcoef(P, x) : 1.0;
@@ -562,7 +580,7 @@ static void net_forward_grid(const or_problem *P, int g, double dT, const double
             in = h;
             /* next layer reads h while writing pre: distinct buffers */
         } else {
-            for (long long j = 0; j < n; ++j) out[j] = u[j] + pre[j];
+            for (long long j = 0; j < n; ++j) out[j] = u[j] + sigma * pre[j];
         }
     }
     free(in0); free(pre); free(h);
@@ -606,12 +624,17 @@ double or_net_loss_grad(void *vp, double dT, const double *theta, int n_batch, c
             net_forward_grid(P, g, dT, theta, ub, out, acts, pres);
             double yy = dot(n, yb, yb);
             if (yy <= 0.0) yy = 1.0;
+            const double sigma = rms(n, ub);
             double *dpre = malloc(sizeof(double) * 16 * n); /* grad wrt pre-activation of layer k */
             double *dh = malloc(sizeof(double) * 16 * n);   /* grad wrt input hidden of layer k */
             for (long long j = 0; j < n; ++j) {
                 double e = out[j] - yb[j];
                 loss += e * e / yy;
-                dpre[j] = 2.0 * e / yy;
+                dpre[j] = 2.0 * e / yy * sigma;
+            }
+            if (!(sigma > 0.0)) {
+                free(out); free(acts); free(pres); free(dpre); free(dh);
+                continue;
             }
             double mu[OR_MAXD];
             for (int i = 0; i < G.d; ++i) mu[i] = 1.0 / (1.0 + 4.0 * dT / (G.h[i] * G.h[i]));
@@ -620,7 +643,7 @@ double or_net_loss_grad(void *vp, double dT, const double *theta, int n_batch, c
             long long c[OR_MAXD];
             double x[OR_MAXD];
             for (long long j = 0; j < n; ++j) {
-                in0[j] = ub[j];
+                in0[j] = ub[j] / sigma;
                 coords(&G, j, c);
                 for (int i = 0; i < G.d; ++i) x[i] = G.lo[i] + (double)(c[i] + 1) * G.h[i];
                 in0[n + j] = (P->op == OR_VARHEAT) ? varcoef(P, x) : 1.0;

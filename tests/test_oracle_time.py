@@ -179,7 +179,15 @@ def test_net_gradient_finite_differences_and_identity():
     z = np.zeros(npar)
     np.testing.assert_array_equal(P.net_forward(dT, z, u), u)
     z[-1] = 0.25
-    np.testing.assert_allclose(P.net_forward(dT, z, u), u + 0.25, atol=1e-15)
+    # output bias b: u + sigma * b per grid, sigma = RMS of the grid's state
+    out = P.net_forward(dT, z, u)
+    for b in range(2):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            sigma = np.sqrt(np.mean(u[sl] ** 2))
+            np.testing.assert_allclose(out[sl], u[sl] + 0.25 * sigma, atol=1e-15)
+    # scale equivariance: N(alpha u) = alpha N(u) for alpha > 0
+    np.testing.assert_allclose(P.net_forward(dT, theta, 3.0 * u), 3.0 * P.net_forward(dT, theta, u), rtol=1e-12)
     # the loss of the identity map against y is sum ||u - y||^2 / ||y||^2
     l0, _ = P.net_loss_grad(dT, np.zeros(npar), u, y)
     ref = 0.0
