@@ -40,6 +40,7 @@ METRIC = "time to 1e-6 error & DoF-steps/s, plain FP64 vs mixed/batched/learned,
 UNIT = "DoF-steps/s"
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK = 128  # 32 banks x 4 B per SM and clock
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (non-tensor) rate
 
 
 def parse():
@@ -119,7 +120,7 @@ def measured_peaks():
 
 def phi_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("pit_phi.cu", "pit_internal.cuh"):
+    for f in ("pit_phi.cuh", "pit_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2509_22156_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -127,7 +128,7 @@ def phi_source_hash() -> str:
 def ncu_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "phi_heat_mixed_heat3d_n9.txt")
+    path = os.path.join(ROOT, "profiles", "steps_kernel_heat_mixed_heat3d_n9.txt")
     try:
         kv = {}
         for line in open(path):
@@ -142,11 +143,19 @@ def ncu_traffic():
 
 
 # ---------------------------------------------------------------------------
-def solver_setup(wl, B):
-    """Options of the chosen form and of the plain FP64 form."""
-    mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-10, maxit=4000, inner_rtol=1e-4, ir_maxit=12)
-    plain = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-10, maxit=8000)
-    tol = 1e-8  # MGRIT stopping rule: every C-point residual l2 norm <= 1e-8 (absolute)
+# Tolerances that reach the metric's accuracy: relative L2 error <= 1e-6 of the
+# combined solution against the oracle's sequential solution (MGRIT tolerance
+# 1e-7 on every C-point residual l2 norm, Krylov 1e-9 relative; checked by the
+# cpu_baseline leg).  The paper's own tolerances (1e-8 absolute, Sec. 4.1) are
+# timed as an extra form.
+MGRIT_TOL, KRYLOV_RTOL = 1e-7, 1e-9
+PAPER_TOL, PAPER_RTOL = 1e-8, 1e-10
+
+
+def solver_setup(wl, B, tol=MGRIT_TOL, rtol=KRYLOV_RTOL):
+    """Options of the chosen form (FP32 Krylov in FP64 refinement) and of the plain FP64 form."""
+    mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=rtol, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+    plain = B.solve_opts(B.PIT_PREC_FP64, rtol=rtol, maxit=8000)
     chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=mixed, crs=mixed)
     fp64 = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=plain, crs=plain)
     return chosen, fp64, mixed, plain
@@ -231,28 +240,41 @@ def run_pit(args, rank, world, local):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step = sum(e2e_ms) / len(e2e_ms)
 
-    # roofline of the dominant kernel (grid-resident backward-Euler solver,
-    # heat operator, FP32 inner CG): shared-memory bytes moved per node and
-    # Krylov iteration by this schedule, over its event time
+    # roofline of the dominant kernel (steps_kernel<HEAT, MIXED, 3>).  ncu
+    # shows it bound by the FP64 pipe (the refinement residual passes), so the
+    # roofline is FP64 arithmetic: algorithmic FP64 flops per node and FP64
+    # residual pass = (2d+1) multiply-adds of the stencil, 2 subtractions,
+    # 3 squared accumulations and the correction update = 4d + 12, over the
+    # kernel's event time, against GB300's nominal FP64 rate.  The shared-
+    # memory view of the FP32 inner iterations is reported beside it.
     d = wl.d
-    smem_bytes_per_point_iter = 2 + 4 * (2 * d + 1) + 4 + 16 + 8 + 8 + 4
     phi_ms = prof.ms[0]
     phi_launches = int(prof.launches[0])
-    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
-    peak_smem = SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9  # GB/s
-    achieved = prof.point_iters * smem_bytes_per_point_iter / (phi_ms / 1e3) / 1e9 if phi_ms > 0 else None
+    fp64_flops = prof.point_passes * (4 * d + 12)
+    fp64_peak = FP64_PEAK_TFLOPS
+    achieved = fp64_flops / (phi_ms / 1e3) / 1e12 if phi_ms > 0 else None
     trf = ncu_traffic()
     items_per_launch = prof.phi_items / max(1, phi_launches)
-    roofline = {"bound": "smem", "kernel": "phi_kernel<HEAT,MIXED> (grid-resident CG, FP32 inner)",
-                "achieved": achieved, "peak": peak_smem, "unit": "GB/s",
-                "frac": (achieved / peak_smem) if achieved else None,
+    smem_bytes_per_point_iter = 2 + 4 * (2 * d + 1) + 4 + 16 + 8 + 8 + 4
+    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_smem = SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9  # GB/s
+    smem_achieved = prof.point_iters * smem_bytes_per_point_iter / (phi_ms / 1e3) / 1e9 if phi_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "steps_kernel<HEAT,MIXED,3> (grid-resident multi-step BE, FP32 CG in FP64 refinement)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp64_peak) if achieved else None,
                 "traffic": (trf * items_per_launch) if trf is not None else None,
-                "peak_source": f"derived: {SM_COUNT} SMs x {SMEM_BYTES_PER_CLK} B/clk x {sm_mhz:.0f} MHz "
-                               "(sm_max_mhz of MEASURED_PEAKS.json)",
+                "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s, profiling recipe table); an FMA "
+                               "micro-benchmark on this pool measured 1.20",
+                "fp64_flops_per_node_pass": 4 * d + 12,
                 "phi_ms_per_step": phi_ms / args.steps, "phi_launches_per_step": phi_launches / args.steps,
                 "phi_share_of_step": (phi_ms / args.steps) / ms_step,
                 "point_iters_per_step": prof.point_iters / args.steps,
-                "smem_bytes_per_point_iter": smem_bytes_per_point_iter}
+                "fp64_passes_per_node_step": prof.point_passes / max(1, prof.point_steps),
+                "krylov_iters_per_node_step": prof.point_iters / max(1, prof.point_steps),
+                "smem_view": {"achieved": smem_achieved, "peak": peak_smem, "unit": "GB/s",
+                              "frac": (smem_achieved / peak_smem) if smem_achieved else None,
+                              "bytes_per_node_iter": smem_bytes_per_point_iter,
+                              "peak_source": f"derived: {SM_COUNT} SMs x {SMEM_BYTES_PER_CLK} B/clk x {sm_mhz:.0f} MHz"}}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -260,6 +282,7 @@ def run_pit(args, rank, world, local):
         "vs_baseline": None, "dtype": "f64 (FP32 inner Krylov inside FP64 refinement)",
         "data": "synthetic (analytic initial value, seeded evaluation points)",
         "config": {"workload": wl.name, "d": wl.d, "level": wl.n, "grids": P.G, "n_total": P.n_total,
+                   "accuracy_target": "relative L2 error <= 1e-6 of the combined solution vs the oracle's sequential solution",
                    "nsteps": wl.nsteps, "t": [wl.t0, wl.t1], "mgrit": f"two-level FCF m={wl.m}",
                    "coarse": "implicit backward Euler dT = m dt", "mgrit_tol_abs": chosen.tol,
                    "krylov_rtol": chosen.fine.rtol, "inner_rtol": chosen.fine.inner_rtol,
@@ -275,6 +298,7 @@ def run_pit(args, rank, world, local):
     }
 
     uT_h = uT.cpu().numpy().copy()
+    out_h_chosen = out.cpu().numpy().copy()
     if not args.no_forms and rank == 0:
         forms = {}
         # plain FP64 MGRIT (same workload, FP64 Krylov)
@@ -296,13 +320,22 @@ def run_pit(args, rank, world, local):
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3)}
+        # the paper's tolerances (MGRIT 1e-8 absolute, Krylov 1e-10), both precision forms
+        pch, pfp, _, _ = solver_setup(wl, B, PAPER_TOL, PAPER_RTOL)
+        for name, o in (("paper_tol_mixed_mgrit", pch), ("paper_tol_fp64_mgrit", pfp)):
+            e0.record(stream)
+            st = step(o, u0, out)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3), "cycles": st.max_cycles}
         forms["chosen_vs_plain_fp64_speedup"] = forms["plain_fp64_mgrit"]["ms"] / ms_step
         forms["chosen_vs_mixed_minus_fp64_rel_l2"] = float(np.linalg.norm(uT_h - uT_fp64) / np.linalg.norm(uT_fp64))
         result["forms"] = forms
 
     if not args.no_cpu and rank == 0 and world == 1:
-        result["cpu_baseline"], result["accuracy"] = cpu_baseline(wl, uT_h, P.offsets, chosen)
-        err = result["accuracy"].get("max_rel_l2_vs_oracle_sequential")
+        result["cpu_baseline"], result["accuracy"] = cpu_baseline(wl, uT_h, out_h_chosen, pts_h, chosen)
+        err = result["accuracy"].get("combined_rel_l2_vs_oracle_sequential")
         if err is not None and err > 1e-6:
             result["time_to_tol_ms"] = None
     P.close()
@@ -321,32 +354,41 @@ def oracle_sample(wl, n_grids_target):
     return O, grids
 
 
-def cpu_baseline(wl, uT_gpu, offsets, chosen, n_grids=12):
-    """The oracle (plain C, FP64, OpenMP over independent grids) on a bounded
-    sample of the same workload: every `stride`-th grid, all time steps, the
-    same MGRIT and Krylov tolerances."""
+def cpu_baseline(wl, uT_gpu, out_gpu, pts, chosen, n_grids=12):
+    """The oracle (plain C, FP64, OpenMP over independent grids) on the host
+    cores: (1) timed baseline: MGRIT on a bounded sample of the workload (every
+    stride-th grid, all time steps, the same MGRIT and Krylov tolerances);
+    (2) accuracy: the oracle's sequential solution of every grid and its
+    combination at the evaluation points, against the GPU result."""
     import oracle
     O, grids = oracle_sample(wl, n_grids)
     cores = os.cpu_count() or 1
     oracle.set_threads(min(cores, len(grids)))
     u0 = O.initial(wl.ic_kind, wl.ic_params)
     t0 = time.perf_counter()
-    uT, its, _, st = O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64, rtol=1e-10,
-                             check=False, grids=grids)
+    uT, its, _, st = O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64,
+                             rtol=chosen.fine.rtol, check=False, grids=grids)
     t_mg = time.perf_counter() - t0
     dof = sum(int(O.offsets[g + 1] - O.offsets[g]) for g in grids)
-    seq = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14, grids=grids)
-    errs, errs_mg = [], []
-    for g in grids:
-        sl = slice(int(offsets[g]), int(offsets[g + 1]))
-        errs.append(float(np.linalg.norm(uT_gpu[sl] - seq[sl]) / np.linalg.norm(seq[sl])))
-        errs_mg.append(float(np.linalg.norm(uT_gpu[sl] - uT[sl]) / np.linalg.norm(uT[sl])))
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    seq = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14)
+    t_seq = time.perf_counter() - t0
+    ref = O.combine(seq, pts)
+    err_comb = float(np.linalg.norm(out_gpu - ref) / np.linalg.norm(ref))
+    errs = [float(np.linalg.norm(uT_gpu[O.grid_slice(g)] - seq[O.grid_slice(g)]) /
+                  np.linalg.norm(seq[O.grid_slice(g)])) for g in range(O.G)]
+    errs_mg = [float(np.linalg.norm(uT_gpu[O.grid_slice(g)] - uT[O.grid_slice(g)]) /
+                     np.linalg.norm(uT[O.grid_slice(g)])) for g in grids]
     base = {"value": dof * wl.nsteps / t_mg, "unit": UNIT, "cores": min(cores, len(grids)), "kind": "oracle",
             "sample": f"{len(grids)} of {O.G} grids ({dof} of {O.n_total} nodes), all {wl.nsteps} steps, "
-                      f"two-level MGRIT m={wl.m}, FP64 CG rtol 1e-10, {t_mg:.1f} s",
-            "seconds": t_mg}
-    acc = {"grids_sampled": grids, "max_rel_l2_vs_oracle_sequential": max(errs),
-           "max_rel_l2_vs_oracle_mgrit": max(errs_mg)}
+                      f"two-level MGRIT m={wl.m} with the same tolerances, {t_mg:.1f} s",
+            "seconds": t_mg,
+            "oracle_sequential_all_grids": {"value": O.n_total * wl.nsteps / t_seq, "unit": UNIT, "cores": cores,
+                                            "seconds": t_seq, "krylov_rtol": 1e-14}}
+    acc = {"combined_rel_l2_vs_oracle_sequential": err_comb,
+           "max_grid_rel_l2_vs_oracle_sequential": max(errs),
+           "max_grid_rel_l2_vs_oracle_mgrit_sample": max(errs_mg), "oracle_mgrit_sample_grids": grids}
     return base, acc
 
 

@@ -73,7 +73,10 @@ typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1 } pit_prec;
 typedef enum {
     PIT_COARSE_IMPLICIT = 0, /* Phi_coarse = backward Euler with dT = m dt (Sec. 3.3.1)  */
     PIT_COARSE_EXACT = 1,    /* Phi_coarse = m fine steps (exact coarse correction)        */
-    PIT_COARSE_LEARNED = 2   /* learned network (not in the paper; see pit_train_coarse)   */
+    PIT_COARSE_LEARNED = 2   /* learned network (not in the paper; see pit_train_coarse); the
+                                implicit step replaces it when it was not accepted, and for
+                                the remaining cycles when a cycle's residual fails to drop
+                                below 0.9 times the previous one or is not finite          */
 } pit_coarse;
 
 /* Problem: d-dimensional box [lo, hi], zero Dirichlet values, combination
@@ -142,6 +145,73 @@ typedef struct {
     int fallback;                   /* 1 if it was replaced by the implicit one      */
     double ms;                      /* wall time of the call                        */
 } pit_mgrit_stats;
+
+/* ---------------------------------------------------------------------------
+ * Learned coarse propagator (not in the paper): an axis-separable network that
+ * replaces the coarse-level backward-Euler step Phi_c of MGRIT (Sec. 3.3.1).
+ * Phi_hat(u) = u + sigma h4(u / sigma), sigma the RMS of u on the grid; four
+ * layers of width-5 convolutions along every axis with weights shared by all
+ * axes, channels (u, a, s_i) -> 16 -> 16 -> 16 -> 1, ReLU on the hidden
+ * layers; a = diffusion coefficient at the nodes (1 for constant-coefficient
+ * operators), s_i = 1 / (1 + 4 dT / h_i^2) per axis; taps outside the grid read
+ * zero.  Parameter block (PIT_NET_PARAMS floats): for layer k = 0..3 the
+ * weights W_k[o][c][t] (Cout x Cin x 5, Cin = 3, 17, 17, 17; c = Cin-1 is the
+ * s channel; t = 0..4 is the tap at offset t-2), then the biases b_k[o].
+ * Weights are used rounded to BF16 (nearest even); activations and
+ * accumulation are FP32, the state FP64.  MGRIT never converges to anything
+ * but the fine solution whatever the coarse propagator (Alg. 2): the network
+ * only changes how many cycles are needed. */
+#define PIT_NET_PARAMS 3094
+
+typedef struct {
+    double dt_fine;        /* fine step of the pairs                            */
+    int m;                 /* pairs are (u, Phi^m u): coarse step dT = m dt_fine */
+    int n_pairs;           /* training pairs (one pair = one grid's state)     */
+    int n_holdout;         /* held-out pairs judged against the implicit Phi_c  */
+    int epochs;
+    int batch;             /* pairs per Adam step                              */
+    double lr;             /* Adam learning rate (beta1 0.9, beta2 0.999, eps 1e-8) */
+    unsigned long long seed;
+    int ic_modes;          /* random initial values: sums of ic_modes product-sine */
+    int ic_fmax;           /* modes, N(0,1) amplitudes, frequencies 1..ic_fmax     */
+    int traj_len;          /* pairs taken along each fine trajectory           */
+    pit_solve_opts fine;   /* solver of the fine steps that make the targets   */
+    pit_solve_opts crs;    /* solver of the implicit Phi_c used as the judge   */
+} pit_train_opts;
+
+typedef struct {
+    double loss_first_epoch;     /* mean relative squared loss, first epoch */
+    double loss_last_epoch;      /* same, last epoch                         */
+    double holdout_err_learned;  /* mean ||Phi_hat u - Phi^m u|| / ||Phi^m u|| on held-out pairs */
+    double holdout_err_implicit; /* same for the implicit coarse step        */
+    int accepted;                /* 1 when the learned error is not larger  */
+    int adam_steps;
+    double ms_data;              /* generating the pairs                    */
+    double ms_train;             /* forward/backward/Adam                   */
+} pit_train_stats;
+
+/* Sets (host, n == PIT_NET_PARAMS floats; rounded to BF16 here) or reads the
+ * network parameters of the problem.  Setting marks the network accepted. */
+pit_status pit_net_set_params(pit_problem_t p, const float *w, int n);
+pit_status pit_net_get_params(pit_problem_t p, float *w, int n);
+
+/* out = Phi_hat(u) for n_batch packed states with coarse step dT.
+ * u, out: device, n_batch * n_total doubles, must not overlap. */
+pit_status pit_net_forward(pit_problem_t p, double dT, int n_batch, const double *u, double *out);
+
+/* Training loss sum over all (state, grid) items of ||Phi_hat(u) - y||^2 /
+ * ||y||^2 and its gradient with respect to the parameters (as used: BF16-
+ * rounded).  u, y: device, n_batch * n_total doubles; loss: host double;
+ * grad: host, PIT_NET_PARAMS floats. */
+pit_status pit_net_loss_grad(pit_problem_t p, double dT, int n_batch, const double *u, const double *y,
+                             double *loss, float *grad);
+
+/* Trains the network on the GPU: pairs (u, Phi^m u) from fine trajectories
+ * of seeded random initial values (training and held-out), Adam on FP32
+ * master weights with BF16 forward/backward weights, then judges it against
+ * the implicit coarse step on the held-out pairs.  The trained parameters are
+ * kept; MGRIT with PIT_COARSE_LEARNED uses them only when accepted. */
+pit_status pit_train_coarse(pit_problem_t p, const pit_train_opts *opts, pit_train_stats *stats);
 
 /* Creates a problem on the current CUDA device: enumerates the component
  * grids (Eq. "combination_technique_solution"; l >= level0 componentwise,
@@ -219,6 +289,7 @@ typedef struct {
     long long phi_items;
     long long point_iters;   /* sum over items of nodes x Krylov iterations       */
     long long point_passes;  /* sum over items of nodes x FP64 residual passes    */
+    long long point_steps;   /* sum over items of nodes x backward-Euler steps    */
 } pit_profile;
 
 pit_status pit_profile_enable(pit_problem_t p, int on);

@@ -33,7 +33,9 @@ PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
 
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
             "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",
-            "pit_profile_read", "pit_phi_batch_inplace_static", "pit_last_error"]
+            "pit_profile_read", "pit_phi_batch_inplace_static", "pit_net_set_params", "pit_net_get_params",
+            "pit_net_forward", "pit_net_loss_grad", "pit_train_coarse", "pit_last_error"]
+NET_PARAMS = 3094
 STATIC_SCRATCH_DOUBLES = 1 << 20
 
 
@@ -68,7 +70,22 @@ class pit_mgrit_stats(ctypes.Structure):
 
 class pit_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("phi_items", ctypes.c_longlong),
-                ("point_iters", ctypes.c_longlong), ("point_passes", ctypes.c_longlong)]
+                ("point_iters", ctypes.c_longlong), ("point_passes", ctypes.c_longlong),
+                ("point_steps", ctypes.c_longlong)]
+
+
+class pit_train_opts(ctypes.Structure):
+    _fields_ = [("dt_fine", ctypes.c_double), ("m", ctypes.c_int), ("n_pairs", ctypes.c_int),
+                ("n_holdout", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("ic_modes", ctypes.c_int), ("ic_fmax", ctypes.c_int),
+                ("traj_len", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts)]
+
+
+class pit_train_stats(ctypes.Structure):
+    _fields_ = [("loss_first_epoch", ctypes.c_double), ("loss_last_epoch", ctypes.c_double),
+                ("holdout_err_learned", ctypes.c_double), ("holdout_err_implicit", ctypes.c_double),
+                ("accepted", ctypes.c_int), ("adam_steps", ctypes.c_int), ("ms_data", ctypes.c_double),
+                ("ms_train", ctypes.c_double)]
 
 
 _lib = None
@@ -99,6 +116,11 @@ def load(path: str = LIB_PATH):
         L.pit_profile_enable.argtypes = [vp, ci]
         L.pit_profile_read.argtypes = [vp, P(pit_profile)]
         L.pit_phi_batch_inplace_static.argtypes = [vp, cd, ci, vp, vp, P(pit_solve_opts), P(pit_phi_stats)]
+        L.pit_net_set_params.argtypes = [vp, vp, ci]
+        L.pit_net_get_params.argtypes = [vp, vp, ci]
+        L.pit_net_forward.argtypes = [vp, cd, ci, vp, vp]
+        L.pit_net_loss_grad.argtypes = [vp, cd, ci, vp, vp, P(cd), vp]
+        L.pit_train_coarse.argtypes = [vp, P(pit_train_opts), P(pit_train_stats)]
         L.pit_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name != "pit_last_error":
@@ -132,6 +154,21 @@ def _ptr(x):
 
 def solve_opts(prec=PIT_PREC_FP64, rtol=1e-10, maxit=10000, inner_rtol=1e-4, ir_maxit=12) -> pit_solve_opts:
     return pit_solve_opts(prec, rtol, maxit, inner_rtol, ir_maxit)
+
+
+def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=1e-3, seed=0, ic_modes=8,
+               ic_fmax=4, traj_len=8, fine=None, crs=None) -> pit_train_opts:
+    fine = fine or solve_opts(PIT_PREC_MIXED, rtol=1e-10)
+    crs = crs or fine
+    return pit_train_opts(dt_fine, m, n_pairs, n_holdout, epochs, batch, lr, seed, ic_modes, ic_fmax, traj_len,
+                          fine, crs)
+
+
+def bf16_round(w) -> np.ndarray:
+    """Round float32 values to BF16 (nearest even), returned as float32."""
+    b = np.ascontiguousarray(w, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
@@ -220,6 +257,34 @@ class Problem:
         if check:
             _check(rc, "pit_mgrit_solve")
         return st if check else (st, rc)
+
+    # learned coarse propagator
+    def net_set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().pit_net_set_params(self._h, ctypes.c_void_p(w.ctypes.data), w.size), "pit_net_set_params")
+
+    def net_get_params(self) -> np.ndarray:
+        w = np.empty(NET_PARAMS, dtype=np.float32)
+        _check(load().pit_net_get_params(self._h, ctypes.c_void_p(w.ctypes.data), w.size), "pit_net_get_params")
+        return w
+
+    def net_forward(self, dT, u, out, n_batch=None):
+        nb = n_batch if n_batch is not None else u.numel() // self.n_total
+        _check(load().pit_net_forward(self._h, dT, nb, _ptr(u), _ptr(out)), "pit_net_forward")
+        return out
+
+    def net_loss_grad(self, dT, u, y, n_batch=None):
+        nb = n_batch if n_batch is not None else u.numel() // self.n_total
+        loss = ctypes.c_double()
+        grad = np.empty(NET_PARAMS, dtype=np.float32)
+        _check(load().pit_net_loss_grad(self._h, dT, nb, _ptr(u), _ptr(y), ctypes.byref(loss),
+                                        ctypes.c_void_p(grad.ctypes.data)), "pit_net_loss_grad")
+        return loss.value, grad
+
+    def train_coarse(self, opts) -> pit_train_stats:
+        st = pit_train_stats()
+        _check(load().pit_train_coarse(self._h, ctypes.byref(opts), ctypes.byref(st)), "pit_train_coarse")
+        return st
 
     def profile_enable(self, on=True):
         _check(load().pit_profile_enable(self._h, 1 if on else 0), "pit_profile_enable")

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpit.so")
-SOURCES = ["pit_phi.cu", "pit_aux.cu", "pit_api.cu"]
+SOURCES = ["pit_phi_heat.cu", "pit_phi_varheat.cu", "pit_phi_ou.cu", "pit_phi.cu", "pit_net.cu", "pit_aux.cu", "pit_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +37,8 @@ def _stale(obj: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
-    headers = [os.path.join(CSRC, "pit_internal.cuh"), os.path.join(ROOT, "include", "pit.h")]
+    headers = [os.path.join(CSRC, "pit_internal.cuh"), os.path.join(CSRC, "pit_phi.cuh"),
+               os.path.join(ROOT, "include", "pit.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                     "-I", os.path.join(ROOT, "include")] + (extra or [])
     procs, objs = [], []

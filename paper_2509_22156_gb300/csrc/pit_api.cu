@@ -101,12 +101,16 @@ struct pit_problem {
     std::vector<double> h_res;
     double *h_rmax = nullptr;  // pinned, G
     int *h_act = nullptr;      // pinned, G
+    // learned coarse propagator
+    bool have_net = false, net_accepted = false;
+    NetWeights h_net;  // BF16-rounded parameters as used by the kernels
+    DBuf n_master, n_m, n_v, n_w, n_rows, n_loss, n_act, n_items, n_U, n_Y, n_grad, n_tmp, n_prm;
     // kernel timing (pit_profile_enable / pit_profile_read)
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> prof_recs;  // (family, first event index)
-    long long prof_items = 0, prof_point_iters = 0, prof_point_passes = 0;
+    long long prof_items = 0, prof_point_iters = 0, prof_point_passes = 0, prof_point_steps = 0;
 };
 
 namespace {
@@ -240,11 +244,14 @@ struct StepCall {
     const double *cmp = nullptr;
     long long cs = 0;
     double *norms = nullptr;
+    const double *guess = nullptr;
+    long long gus = 0, gust = 0;
 };
 
 StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
 {
     StepArgs a;
+    a.item0 = 0;
     a.grids = P->d_grids;
     a.masks = P->d_masks;
     a.order = P->d_order;
@@ -270,6 +277,9 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.cmp = c.cmp;
     a.cmp_stride = c.cs;
     a.norms = c.norms;
+    a.guess = c.guess;
+    a.guess_stride = c.gus;
+    a.guess_step = c.gust;
     a.active = active;
     a.faces = P->d_faces;
     a.op = P->op;
@@ -339,6 +349,36 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     return PIT_OK;
 }
 
+// Network application with StepArgs semantics; activations in shared memory
+// when the largest grid fits, else in per-CTA global slabs (launch split into
+// chunks of CTAs so that the slabs stay below 4 GiB).
+pit_status run_net(pit_problem *P, const StepCall &c, const int *active)
+{
+    if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
+    pit_solve_opts dummy{PIT_PREC_FP64, 0.0, 1, 0.5, 1};
+    StepArgs a = make_args(P, dummy, c, active);
+    int nmax = 0;
+    for (const GridInfo &I : P->info) nmax = I.n > nmax ? I.n : nmax;
+    const long long items = (long long)c.nb * P->G;
+    size_t smem = net_smem_bytes(nmax);
+    ProfScope ps(P, 0);
+    if (smem <= P->max_smem) {
+        CU(launch_net_steps(a, P->h_net, nullptr, 0, smem, P->stream, (int)items));
+        return PIT_OK;
+    }
+    const long long slab = (long long)net_act_floats(nmax, false);
+    const long long limit = (4LL << 30) / (long long)(slab * sizeof(float));
+    const long long chunk = items < limit ? items : (limit > 0 ? limit : 1);
+    CU(P->n_act.ensure(sizeof(float) * (size_t)(slab * chunk)));
+    smem = (size_t)((nmax + 3) & ~3) * 12 + 16;
+    for (long long k0 = 0; k0 < items; k0 += chunk) {
+        a.item0 = (int)k0;
+        const long long cnt = (items - k0) < chunk ? (items - k0) : chunk;
+        CU(launch_net_steps(a, P->h_net, (float *)P->n_act.p, slab, smem, P->stream, (int)cnt));
+    }
+    return PIT_OK;
+}
+
 pit_status reset_stats(pit_problem *P)
 {
     CU(cudaMemsetAsync(P->d_stats, 0, sizeof(DevStats), P->stream));
@@ -354,6 +394,7 @@ pit_status read_stats(pit_problem *P, DevStats &s)
         P->prof_items += (long long)s.items;
         P->prof_point_iters += (long long)s.point_iters;
         P->prof_point_passes += (long long)s.point_passes;
+        P->prof_point_steps += (long long)s.point_steps;
     }
     return PIT_OK;
 }
@@ -474,6 +515,7 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
                              cudaGetErrorString(e_)));                                              \
     } while (0)
     CUB(phi_kernels_init(P->max_smem));
+    CUB(net_kernels_init(P->max_smem));
     CUB(cudaMalloc(&P->d_grids, sizeof(GridInfo) * P->G));
     CUB(cudaMemcpy(P->d_grids, P->info.data(), sizeof(GridInfo) * P->G, cudaMemcpyHostToDevice));
     CUB(cudaMalloc(&P->d_coef, sizeof(double) * P->G));
@@ -521,8 +563,10 @@ pit_status pit_problem_destroy(pit_problem_t P)
     if (P->h_stats) cudaFreeHost(P->h_stats);
     if (P->h_rmax) cudaFreeHost(P->h_rmax);
     if (P->h_act) cudaFreeHost(P->h_act);
-    DBuf *bufs[] = {&P->w_in, &P->w_out, &P->w_pts, &P->w_u,   &P->w_prm, &P->m_U,  &P->m_R, &P->m_UT,
-                    &P->m_GC, &P->m_res, &P->m_UT1, &P->m_GC1, &P->m_T0,  &P->m_act, &P->w_tune};
+    DBuf *bufs[] = {&P->w_in,     &P->w_out,  &P->w_pts, &P->w_u,     &P->w_prm,  &P->m_U,     &P->m_R,
+                    &P->m_UT,     &P->m_GC,   &P->m_res, &P->m_UT1,   &P->m_GC1,  &P->m_T0,    &P->m_act,
+                    &P->w_tune,   &P->n_master, &P->n_m, &P->n_v,     &P->n_w,    &P->n_rows,  &P->n_loss,
+                    &P->n_act,    &P->n_items, &P->n_U,  &P->n_Y,     &P->n_grad, &P->n_tmp,   &P->n_prm};
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     delete P;
@@ -689,6 +733,7 @@ struct Mg {
     double dt;
     long long nt;
     const int *active;
+    bool learned;  // level-1 coarse propagator is the network
 };
 
 // Coarse propagator of level 1: backward Euler with m dt, or m fine steps.
@@ -704,6 +749,17 @@ void coarse_call(Mg &M, StepCall &c, int level)
     }
 }
 
+// Runs one call with the coarse propagator of `level` (1: Phi_c, 2: Phi_cc).
+pit_status run_coarse(Mg &M, StepCall c, int level)
+{
+    if (level == 1 && M.learned) {
+        c.dt = M.dt * M.o->m;
+        return run_net(M.P, c, M.active);
+    }
+    coarse_call(M, c, level);
+    return run_steps(M.P, M.o->crs, c, M.active);
+}
+
 // Two-level cycle of level 1 in a three-level hierarchy: level-1 points are V
 // (read) -> W (written), Nc1 = N1/m intervals, forcing of level-1 point k is
 // F[k-1]; the level-2 problem is solved by a sequential sweep.
@@ -712,15 +768,12 @@ pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const doub
     pit_problem *P = M.P;
     const int m = M.o->m, Nc = N1 / m;
     const long long nt = M.nt, sm = (long long)m * nt;
-    const pit_solve_opts &so = M.o->crs;
     CU(P->m_UT1.ensure(sizeof(double) * nt * Nc));
     CU(P->m_GC1.ensure(sizeof(double) * nt * Nc));
     double *UT1 = P->m_UT1.d(), *GC1 = P->m_GC1.d();
     if (W != V) CU(cudaMemcpyAsync(W, V, sizeof(double) * nt, cudaMemcpyDeviceToDevice, P->stream));
-    const double dt1 = M.dt * m;
     // FC: F-points and C-point of every interval from the old C-points
     StepCall fc;
-    fc.dt = dt1;
     fc.nb = Nc;
     fc.nsteps = m;
     fc.in = V;
@@ -733,16 +786,15 @@ pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const doub
     fc.osst = nt;
     fc.out_last = W + sm;
     fc.ols = sm;
-    TRY(run_steps(P, so, fc, M.active));
+    TRY(run_coarse(M, fc, 1));
     // F-relaxation from the new C-points (F-points in place) and utilde
     StepCall fr = fc;
     fr.in = W;
     fr.out_last = UT1;
     fr.ols = nt;
-    TRY(run_steps(P, so, fr, M.active));
+    TRY(run_coarse(M, fr, 1));
     // coarse right-hand side and the level-2 sweep into the C-points of W
     StepCall gc;
-    gc.dt = M.dt * m * m;
     gc.nb = Nc;
     gc.nsteps = 1;
     gc.in = W;
@@ -752,20 +804,21 @@ pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const doub
     gc.scale = -1.0;
     gc.h = UT1;
     gc.hs = nt;
-    TRY(run_steps(P, so, gc, M.active));
+    TRY(run_coarse(M, gc, 2));
     StepCall sw;
-    sw.dt = M.dt * m * m;
     sw.nb = 1;
     sw.nsteps = Nc;
     sw.in = W;
     sw.is = nt;
     sw.g = GC1;
     sw.gst = nt;
+    sw.guess = UT1;  // Phi_2 of the relaxed level-1 C-points, as in the two-level sweep
+    sw.gust = nt;
     sw.out_steps = W + sm;
     sw.osst = sm;
     sw.out_last = W + (long long)Nc * sm;
     sw.ols = nt;
-    TRY(run_steps(P, so, sw, M.active));
+    TRY(run_coarse(M, sw, 2));
     return PIT_OK;
 }
 
@@ -781,8 +834,11 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     if (o->m < 2 || o->levels < 2 || o->levels > 3 || o->nsteps < 1 || o->maxit < 1 || !(o->tol >= 0.0) ||
         !(o->t1 > o->t0))
         return fail(PIT_ERR_INVALID_ARG, "need m >= 2, levels in {2,3}, nsteps >= 1, maxit >= 1, tol >= 0, t1 > t0");
-    if (o->coarse != PIT_COARSE_IMPLICIT && o->coarse != PIT_COARSE_EXACT)
-        return fail(PIT_ERR_UNSUPPORTED, "coarse propagator %d is not available", o->coarse);
+    if (o->coarse != PIT_COARSE_IMPLICIT && o->coarse != PIT_COARSE_EXACT && o->coarse != PIT_COARSE_LEARNED)
+        return fail(PIT_ERR_INVALID_ARG, "unknown coarse propagator %d", o->coarse);
+    if (o->coarse == PIT_COARSE_LEARNED && !P->have_net)
+        return fail(PIT_ERR_INVALID_ARG, "the learned coarse propagator has no parameters (pit_train_coarse or "
+                                         "pit_net_set_params)");
     long long div = o->m;
     if (o->levels == 3) div *= o->m;
     if (o->nsteps % div != 0) return fail(PIT_ERR_INVALID_ARG, "nsteps must be a multiple of m^(levels-1)");
@@ -809,9 +865,12 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     CU(cudaMemcpyAsync(act, P->h_act, sizeof(int) * G, cudaMemcpyHostToDevice, P->stream));
     TRY(reset_stats(P));
 
-    Mg M{P, o, (o->t1 - o->t0) / o->nsteps, nt, act};
+    Mg M{P, o, (o->t1 - o->t0) / o->nsteps, nt, act, o->coarse == PIT_COARSE_LEARNED && P->net_accepted};
     pit_mgrit_stats st;
     memset(&st, 0, sizeof(st));
+    st.learned_used = M.learned ? 1 : 0;
+    st.fallback = (o->coarse == PIT_COARSE_LEARNED && !M.learned) ? 1 : 0;
+    double r_prev = -1.0;
     int n_active = G, it = 0;
     while (n_active > 0 && it < o->maxit) {
         StepCall fc;  // FC relaxation
@@ -841,8 +900,7 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
         gc.scale = -1.0;
         gc.h = UT;
         gc.hs = nt;
-        coarse_call(M, gc, 1);
-        TRY(run_steps(P, o->crs, gc, act));
+        TRY(run_coarse(M, gc, 1));
         if (o->levels == 3) {
             TRY(mg_level1_cycle(M, R, U, Nc, GC));
         } else if (o->coarse == PIT_COARSE_EXACT) {
@@ -867,12 +925,17 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
             sw.is = nt;
             sw.g = GC;
             sw.gst = nt;
+            // Krylov initial guess of Phi_c(u_j): Phi_c(r_j) = UT[j] - GC[j],
+            // computed by the FAS launch (r_j = relaxed C-point; equal to u_j
+            // once MGRIT has converged there)
+            sw.guess = UT;
+            sw.gust = nt;
             sw.out_steps = U + nt;
             sw.osst = nt;
             sw.out_last = U + (long long)Nc * nt;
             sw.ols = nt;
-            coarse_call(M, sw, 1);
-            TRY(run_steps(P, o->crs, sw, act));
+            if (M.learned) sw.guess = nullptr;  // explicit: no Krylov guess
+            TRY(run_coarse(M, sw, 1));
         }
         CU(cudaStreamSynchronize(P->stream));
         double rmax = 0.0;
@@ -890,6 +953,13 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
         }
         if (it < PIT_MAX_HIST) st.res_hist[it] = rmax;
         ++it;
+        // runtime judge of the learned coarse propagator: fall back to the
+        // implicit step when a cycle does not reduce the residual enough
+        if (M.learned && n_active > 0 && (!(rmax == rmax) || (r_prev > 0.0 && rmax > 0.9 * r_prev))) {
+            M.learned = false;
+            st.fallback = 1;
+        }
+        r_prev = rmax;
         if (n_active > 0) CU(cudaMemcpyAsync(act, P->h_act, sizeof(int) * G, cudaMemcpyHostToDevice, P->stream));
         if (!(rmax == rmax)) break;  // NaN: stop at once
     }
@@ -940,7 +1010,7 @@ extern "C" pit_status pit_profile_enable(pit_problem_t P, int on)
     P->prof_on = on != 0;
     P->ev_used = 0;
     P->prof_recs.clear();
-    P->prof_items = P->prof_point_iters = P->prof_point_passes = 0;
+    P->prof_items = P->prof_point_iters = P->prof_point_passes = P->prof_point_steps = 0;
     return PIT_OK;
 }
 
@@ -958,6 +1028,7 @@ extern "C" pit_status pit_profile_read(pit_problem_t P, pit_profile *out)
     out->phi_items = P->prof_items;
     out->point_iters = P->prof_point_iters;
     out->point_passes = P->prof_point_passes;
+    out->point_steps = P->prof_point_steps;
     return PIT_OK;
 }
 
@@ -1032,5 +1103,323 @@ extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, i
         fill_phi_stats(s, stats);
         TRY(status_of(s));
     }
+    return PIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned coarse propagator: parameters, forward, loss gradient, training.
+namespace {
+
+float bf16_round_host(float v)
+{
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    if ((b & 0x7f800000u) == 0x7f800000u) return v;
+    b += 0x7fffu + ((b >> 16) & 1u);
+    b &= 0xffff0000u;
+    float r;
+    memcpy(&r, &b, 4);
+    return r;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) and Box-Muller normals for the seeded
+// training data.
+struct Rng {
+    uint64_t s;
+    uint64_t next()
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+    double normal()
+    {
+        const double u1 = 1.0 - uniform(), u2 = uniform();
+        return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    }
+};
+
+pit_status net_loss_grad_dev(pit_problem *P, double dT, int n_batch, const double *u, const double *y,
+                             const NetTrainItem *items_host, int n_items, const float *w_dev, float *grad_dev,
+                             double *loss_host)
+{
+    int nmax = 0;
+    for (const GridInfo &I : P->info) nmax = I.n > nmax ? I.n : nmax;
+    (void)n_batch;
+    const long long slab = (long long)net_act_floats(nmax, true);
+    CU(P->n_act.ensure(sizeof(float) * (size_t)(slab * n_items)));
+    CU(P->n_rows.ensure(sizeof(float) * (size_t)PIT_NET_PARAMS * n_items));
+    CU(P->n_loss.ensure(sizeof(double) * n_items));
+    CU(P->n_items.ensure(sizeof(NetTrainItem) * n_items));
+    CU(cudaMemcpyAsync(P->n_items.p, items_host, sizeof(NetTrainItem) * n_items, cudaMemcpyHostToDevice, P->stream));
+    {
+        ProfScope ps(P, 3);
+        CU(launch_net_train(P->d_grids, (const NetTrainItem *)P->n_items.p, n_items, u, y, dT, w_dev,
+                            (float *)P->n_act.p, slab, (float *)P->n_rows.p, P->n_loss.d(), P->op, P->stream));
+    }
+    if (grad_dev)
+        CU(launch_net_adam((const float *)P->n_rows.p, n_items, 1.0f, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0, 0,
+                           grad_dev, P->stream));
+    if (loss_host) {
+        std::vector<double> l(n_items);
+        CU(cudaMemcpyAsync(l.data(), P->n_loss.p, sizeof(double) * n_items, cudaMemcpyDeviceToHost, P->stream));
+        CU(cudaStreamSynchronize(P->stream));
+        double s = 0.0;
+        for (int k = 0; k < n_items; ++k) s += l[k];
+        *loss_host = s;
+    }
+    return PIT_OK;
+}
+
+}  // namespace
+
+extern "C" pit_status pit_net_set_params(pit_problem_t P, const float *w, int n)
+{
+    if (!P || !w) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
+    if (n != PIT_NET_PARAMS) return fail(PIT_ERR_INVALID_ARG, "expected %d parameters, got %d", PIT_NET_PARAMS, n);
+    for (int k = 0; k < n; ++k) {
+        if (!std::isfinite(w[k])) return fail(PIT_ERR_NONFINITE, "parameter %d is not finite", k);
+        P->h_net.w[k] = bf16_round_host(w[k]);
+    }
+    CU(P->n_master.ensure(sizeof(float) * n));
+    CU(P->n_w.ensure(sizeof(float) * n));
+    CU(cudaMemcpyAsync(P->n_master.p, w, sizeof(float) * n, cudaMemcpyHostToDevice, P->stream));
+    CU(cudaMemcpyAsync(P->n_w.p, P->h_net.w, sizeof(float) * n, cudaMemcpyHostToDevice, P->stream));
+    CU(cudaStreamSynchronize(P->stream));
+    P->have_net = true;
+    P->net_accepted = true;
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_get_params(pit_problem_t P, float *w, int n)
+{
+    if (!P || !w) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
+    if (n != PIT_NET_PARAMS) return fail(PIT_ERR_INVALID_ARG, "expected %d parameters, got %d", PIT_NET_PARAMS, n);
+    if (!P->have_net) return fail(PIT_ERR_INVALID_ARG, "the network has no parameters yet");
+    memcpy(w, P->h_net.w, sizeof(float) * n);
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_net_forward(pit_problem_t P, double dT, int n_batch, const double *u, double *out)
+{
+    if (!P || !u || !out || n_batch < 0) return fail(PIT_ERR_INVALID_ARG, "bad argument");
+    if (!P->have_net) return fail(PIT_ERR_INVALID_ARG, "the network has no parameters yet");
+    if (!(dT > 0.0) || !std::isfinite(dT)) return fail(PIT_ERR_INVALID_ARG, "dT must be finite and > 0");
+    if (!ptr_is_device(u) || !ptr_is_device(out)) return fail(PIT_ERR_INVALID_ARG, "u and out must be device memory");
+    StepCall c;
+    c.dt = dT;
+    c.nb = n_batch;
+    c.nsteps = 1;
+    c.in = u;
+    c.is = P->ntot;
+    c.out_last = out;
+    c.ols = P->ntot;
+    return run_net(P, c, nullptr);
+}
+
+extern "C" pit_status pit_net_loss_grad(pit_problem_t P, double dT, int n_batch, const double *u, const double *y,
+                                        double *loss, float *grad)
+{
+    if (!P || !u || !y || !loss || !grad || n_batch < 1) return fail(PIT_ERR_INVALID_ARG, "bad argument");
+    if (!P->have_net) return fail(PIT_ERR_INVALID_ARG, "the network has no parameters yet");
+    if (!(dT > 0.0) || !std::isfinite(dT)) return fail(PIT_ERR_INVALID_ARG, "dT must be finite and > 0");
+    if (!ptr_is_device(u) || !ptr_is_device(y)) return fail(PIT_ERR_INVALID_ARG, "u and y must be device memory");
+    std::vector<NetTrainItem> items;
+    for (int b = 0; b < n_batch; ++b)
+        for (int g = 0; g < P->G; ++g) items.push_back({g, 0, (long long)b * P->ntot + P->off[g]});
+    CU(P->n_grad.ensure(sizeof(float) * PIT_NET_PARAMS));
+    TRY(net_loss_grad_dev(P, dT, n_batch, u, y, items.data(), (int)items.size(), (const float *)P->n_w.p,
+                          (float *)P->n_grad.p, loss));
+    CU(cudaMemcpyAsync(grad, P->n_grad.p, sizeof(float) * PIT_NET_PARAMS, cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaStreamSynchronize(P->stream));
+    return PIT_OK;
+}
+
+extern "C" pit_status pit_train_coarse(pit_problem_t P, const pit_train_opts *o, pit_train_stats *stats)
+{
+    if (!P || !o) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
+    TRY(check_solve_opts(&o->fine));
+    TRY(check_solve_opts(&o->crs));
+    if (!(o->dt_fine > 0.0) || o->m < 1 || o->n_pairs < 1 || o->n_holdout < 1 || o->epochs < 1 || o->batch < 1 ||
+        !(o->lr > 0.0) || o->ic_modes < 1 || o->ic_fmax < 1 || o->traj_len < 1)
+        return fail(PIT_ERR_INVALID_ARG, "invalid training options");
+    auto t0 = std::chrono::steady_clock::now();
+    const int G = P->G, d = P->desc.d;
+    const long long nt = P->ntot;
+    const double dT = o->dt_fine * o->m;
+    // --- data: n_states packed pair states (training, then held-out)
+    const int n_train_states = (o->n_pairs + G - 1) / G;
+    const int n_hold_states = (o->n_holdout + G - 1) / G;
+    const int n_states = n_train_states + n_hold_states;
+    const int n_traj = (n_states + o->traj_len - 1) / o->traj_len;
+    CU(P->n_U.ensure(sizeof(double) * nt * (size_t)n_traj * o->traj_len));
+    CU(P->n_Y.ensure(sizeof(double) * nt * (size_t)n_traj * o->traj_len));
+    double *Ud = P->n_U.d(), *Yd = P->n_Y.d();
+    Rng rng{o->seed};
+    std::vector<double> prm(1 + o->ic_modes * (d + 1));
+    CU(P->n_prm.ensure(sizeof(double) * prm.size()));
+    TRY(reset_stats(P));
+    for (int tr = 0; tr < n_traj; ++tr) {
+        // seeded random initial value: sum of product-sine modes
+        prm[0] = o->ic_modes;
+        for (int k = 0; k < o->ic_modes; ++k) {
+            prm[1 + k * (d + 1)] = rng.normal();
+            for (int i = 0; i < d; ++i)
+                prm[2 + k * (d + 1) + i] = 1 + (int)(rng.uniform() * o->ic_fmax) % o->ic_fmax;
+        }
+        CU(cudaMemcpyAsync(P->n_prm.p, prm.data(), sizeof(double) * prm.size(), cudaMemcpyHostToDevice, P->stream));
+        double *u0 = Ud + (long long)tr * o->traj_len * nt;
+        CU(launch_initial(P->d_grids, G, P->op, P->d_hi, 0, P->n_prm.d(), (int)prm.size(), u0, P->stream));
+        // pair k: (u_k, u_{k+1} = Phi^m u_k), u_{k+1} also the input of pair k+1
+        for (int k = 0; k < o->traj_len; ++k) {
+            StepCall c;
+            c.dt = o->dt_fine;
+            c.nb = 1;
+            c.nsteps = o->m;
+            c.in = u0 + (long long)k * nt;
+            c.is = nt;
+            c.out_last = Yd + ((long long)tr * o->traj_len + k) * nt;
+            c.ols = nt;
+            TRY(run_steps(P, o->fine, c, nullptr));
+            if (k + 1 < o->traj_len)
+                CU(cudaMemcpyAsync(u0 + (long long)(k + 1) * nt, c.out_last, sizeof(double) * nt,
+                                   cudaMemcpyDeviceToDevice, P->stream));
+        }
+    }
+    DevStats ds;
+    TRY(read_stats(P, ds));
+    TRY(status_of(ds));
+    auto t1 = std::chrono::steady_clock::now();
+    // training and held-out items: state p < n_train_states is training
+    std::vector<NetTrainItem> train, hold;
+    for (int p = 0; p < n_states; ++p)
+        for (int g = 0; g < G; ++g) {
+            NetTrainItem it{g, 0, (long long)p * nt + P->off[g]};
+            if (p < n_train_states) train.push_back(it);
+            else hold.push_back(it);
+        }
+    if ((int)train.size() > o->n_pairs) train.resize(o->n_pairs);
+    if ((int)hold.size() > o->n_holdout) hold.resize(o->n_holdout);
+    // --- parameters: FP32 master weights, He-scaled normals, last layer zero
+    //     (the network starts as the identity map)
+    std::vector<float> w0(PIT_NET_PARAMS, 0.0f);
+    {
+        int pos = 0;
+        const int cin[4] = {3, 17, 17, 17}, cout[4] = {16, 16, 16, 1};
+        for (int k = 0; k < 4; ++k) {
+            const int nw = cout[k] * cin[k] * 5;
+            const double sd = (k == 3) ? 0.0 : sqrt(2.0 / (cin[k] * 5.0 * d));
+            for (int q = 0; q < nw; ++q) w0[pos + q] = (float)(sd * rng.normal());
+            pos += nw + cout[k];
+        }
+    }
+    CU(P->n_master.ensure(sizeof(float) * PIT_NET_PARAMS));
+    CU(P->n_w.ensure(sizeof(float) * PIT_NET_PARAMS));
+    CU(P->n_m.ensure(sizeof(float) * PIT_NET_PARAMS));
+    CU(P->n_v.ensure(sizeof(float) * PIT_NET_PARAMS));
+    std::vector<float> wr(PIT_NET_PARAMS);
+    for (int k = 0; k < PIT_NET_PARAMS; ++k) wr[k] = bf16_round_host(w0[k]);
+    CU(cudaMemcpyAsync(P->n_master.p, w0.data(), sizeof(float) * PIT_NET_PARAMS, cudaMemcpyHostToDevice, P->stream));
+    CU(cudaMemcpyAsync(P->n_w.p, wr.data(), sizeof(float) * PIT_NET_PARAMS, cudaMemcpyHostToDevice, P->stream));
+    CU(cudaMemsetAsync(P->n_m.p, 0, sizeof(float) * PIT_NET_PARAMS, P->stream));
+    CU(cudaMemsetAsync(P->n_v.p, 0, sizeof(float) * PIT_NET_PARAMS, P->stream));
+    int nmax = 0;
+    for (const GridInfo &I : P->info) nmax = I.n > nmax ? I.n : nmax;
+    const long long slab = (long long)net_act_floats(nmax, true);
+    const int B = o->batch < (int)train.size() ? o->batch : (int)train.size();
+    CU(P->n_act.ensure(sizeof(float) * (size_t)(slab * B)));
+    CU(P->n_rows.ensure(sizeof(float) * (size_t)PIT_NET_PARAMS * B));
+    const int steps_per_epoch = ((int)train.size() + B - 1) / B;
+    CU(P->n_loss.ensure(sizeof(double) * (size_t)B * steps_per_epoch));
+    CU(P->n_items.ensure(sizeof(NetTrainItem) * (size_t)B * steps_per_epoch));
+    std::vector<double> losses((size_t)B * steps_per_epoch);
+    pit_train_stats st;
+    memset(&st, 0, sizeof(st));
+    int t = 0;
+    std::vector<NetTrainItem> order(train);
+    for (int ep = 0; ep < o->epochs; ++ep) {
+        for (int k = (int)order.size() - 1; k > 0; --k) std::swap(order[k], order[rng.next() % (uint64_t)(k + 1)]);
+        CU(cudaMemcpyAsync(P->n_items.p, order.data(), sizeof(NetTrainItem) * order.size(), cudaMemcpyHostToDevice,
+                           P->stream));
+        int n_loss = 0;
+        for (int s0 = 0; s0 < (int)order.size(); s0 += B) {
+            const int nb = ((int)order.size() - s0) < B ? ((int)order.size() - s0) : B;
+            {
+                ProfScope ps(P, 3);
+                CU(launch_net_train(P->d_grids, (const NetTrainItem *)P->n_items.p + s0, nb, Ud, Yd, dT,
+                                    (const float *)P->n_w.p, (float *)P->n_act.p, slab, (float *)P->n_rows.p,
+                                    P->n_loss.d() + s0, P->op, P->stream));
+            }
+            ++t;
+            CU(launch_net_adam((const float *)P->n_rows.p, nb, 1.0f / nb, (float *)P->n_master.p, (float *)P->n_m.p,
+                               (float *)P->n_v.p, (float *)P->n_w.p, (float)o->lr, 0.9f, 0.999f, 1e-8f, t, nullptr,
+                               P->stream));
+            n_loss += nb;
+        }
+        if (ep == 0 || ep == o->epochs - 1) {
+            CU(cudaMemcpyAsync(losses.data(), P->n_loss.p, sizeof(double) * n_loss, cudaMemcpyDeviceToHost, P->stream));
+            CU(cudaStreamSynchronize(P->stream));
+            double sum = 0.0;
+            for (int k = 0; k < n_loss; ++k) sum += losses[k];
+            const double mean = sum / n_loss;
+            if (!std::isfinite(mean)) return fail(PIT_ERR_NONFINITE, "training loss is not finite (epoch %d)", ep);
+            if (ep == 0) st.loss_first_epoch = mean;
+            st.loss_last_epoch = mean;
+        }
+    }
+    CU(cudaMemcpyAsync(P->h_net.w, P->n_w.p, sizeof(float) * PIT_NET_PARAMS, cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaStreamSynchronize(P->stream));
+    P->have_net = true;
+    st.adam_steps = t;
+    auto t2 = std::chrono::steady_clock::now();
+    // --- judge on the held-out pairs: learned vs implicit coarse step
+    const int n_hold_states_used = n_hold_states;
+    const double *Uh = Ud + (long long)n_train_states * nt, *Yh = Yd + (long long)n_train_states * nt;
+    CU(P->n_tmp.ensure(sizeof(double) * nt * (size_t)n_hold_states_used * 2));
+    double *Ln = P->n_tmp.d(), *Li = Ln + (long long)n_hold_states_used * nt;
+    StepCall c;
+    c.dt = dT;
+    c.nb = n_hold_states_used;
+    c.nsteps = 1;
+    c.in = Uh;
+    c.is = nt;
+    c.out_last = Ln;
+    c.ols = nt;
+    TRY(run_net(P, c, nullptr));
+    c.out_last = Li;
+    TRY(reset_stats(P));
+    TRY(run_steps(P, o->crs, c, nullptr));
+    TRY(read_stats(P, ds));
+    TRY(status_of(ds));
+    std::vector<double> hy((size_t)nt * n_hold_states_used), hn(hy.size()), hi(hy.size());
+    CU(cudaMemcpyAsync(hy.data(), Yh, sizeof(double) * hy.size(), cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaMemcpyAsync(hn.data(), Ln, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaMemcpyAsync(hi.data(), Li, sizeof(double) * hi.size(), cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaStreamSynchronize(P->stream));
+    double el = 0.0, ei = 0.0;
+    for (const NetTrainItem &it : hold) {
+        const long long off = it.off - (long long)n_train_states * nt;
+        const int n = P->info[it.g].n;
+        double yy = 0.0, dl = 0.0, di = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double yv = hy[off + j];
+            yy += yv * yv;
+            dl += (hn[off + j] - yv) * (hn[off + j] - yv);
+            di += (hi[off + j] - yv) * (hi[off + j] - yv);
+        }
+        if (yy > 0.0) {
+            el += sqrt(dl / yy);
+            ei += sqrt(di / yy);
+        }
+    }
+    st.holdout_err_learned = el / hold.size();
+    st.holdout_err_implicit = ei / hold.size();
+    st.accepted = (st.holdout_err_learned <= st.holdout_err_implicit) ? 1 : 0;
+    P->net_accepted = st.accepted != 0;
+    st.ms_data = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    st.ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    if (stats) *stats = st;
     return PIT_OK;
 }

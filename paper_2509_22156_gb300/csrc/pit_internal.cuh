@@ -36,22 +36,27 @@ struct DevStats {
     unsigned long long items;
     unsigned long long point_iters;   // sum of nodes x Krylov iterations
     unsigned long long point_passes;  // sum of nodes x FP64 residual passes
+    unsigned long long point_steps;   // sum of nodes x backward-Euler steps
     int max_iters;
     int n_failed;
     int max_refine;
     int worst;          // largest pit_status code seen
 };
 
-// Arguments of one multi-step backward-Euler launch.  Item k of the launch
-// is grid order[k / n_batch] of batch entry b = k % n_batch.  Entry b starts
+// Arguments of one multi-step backward-Euler launch.  Item k = item0 +
+// blockIdx.x is grid order[k / n_batch] of batch entry b = k % n_batch.  Entry b starts
 // from in + b*in_stride (+ grid offset) and takes nsteps steps of size dt;
 // after step s (1-based) x <- x + g_s with g_s = g + b*g_stride + (s-1)*g_step
 // (g may be NULL); states after steps 1..nsteps-1 are written to out_steps +
 // b*os_stride + (s-1)*os_step when out_steps is non-NULL; the final state x is
 // written as out_scale * x + h_b to out_last + b*ol_stride, and, when cmp is
-// non-NULL, norms[b*n_grids + g] = ||x - cmp_b||_2.  No output may overlap the
-// input of the same item.
+// non-NULL, norms[b*n_grids + g] = ||x - cmp_b||_2.  When guess is non-NULL
+// the Krylov solve of step s starts from guess_s - g_s instead of x_{s-1}
+// (guess_s = guess + b*guess_stride + (s-1)*guess_step); the right-hand side is
+// unchanged, so only the iteration count depends on it.  No output may overlap
+// the input of the same item.
 struct StepArgs {
+    int item0;              // first item of this launch (launches may be split in chunks)
     const GridInfo *grids;
     const uint16_t *masks;  // neighbour mask of every node, packed like a state
     const int *order;       // grids by decreasing size
@@ -68,6 +73,7 @@ struct StepArgs {
     const double *h;         long long h_stride;
     const double *cmp;       long long cmp_stride;
     double *norms;
+    const double *guess;     long long guess_stride, guess_step;
     const int *active;       // per grid, NULL = all active
     const double *faces;     // variable coefficient at the 2d faces of every node, or NULL
     OpParams op;
@@ -79,6 +85,33 @@ struct StepArgs {
 };
 
 enum Prec { PLAIN = 0, MIXED = 1 };
+
+// Learned coarse propagator: parameter block (BF16-rounded values held as
+// FP32) passed by value to the inference kernel, and one training item.
+struct NetWeights {
+    float w[PIT_NET_PARAMS];
+};
+struct NetTrainItem {
+    int g;          // grid
+    int pad;
+    long long off;  // offset of the grid's values in the packed u and y arrays
+};
+
+size_t net_smem_bytes(int n);
+size_t net_act_floats(int n, bool train);
+cudaError_t net_kernels_init(size_t max_smem);
+// Launches items a.item0 .. a.item0 + n_items - 1.
+cudaError_t launch_net_steps(const StepArgs &a, const NetWeights &W, float *act, long long act_stride, size_t smem,
+                             cudaStream_t s, int n_items);
+cudaError_t launch_net_train(const GridInfo *grids, const NetTrainItem *items, int n_items, const double *u,
+                             const double *y, double dT, const float *w, float *act, long long act_stride,
+                             float *grad_rows, double *loss_items, OpParams op, cudaStream_t s);
+// Sums n_rows gradient rows (item order) into grad_out (if non-NULL) and, when
+// master is non-NULL, takes one Adam step on the master weights (gradient
+// scaled by `scale`) and writes their BF16 rounding to w_bf16.
+cudaError_t launch_net_adam(const float *grad_rows, int n_rows, float scale, float *master, float *m, float *v,
+                            float *w_bf16, float lr, float b1, float b2, float eps, int t, float *grad_out,
+                            cudaStream_t s);
 
 // Shared-memory bytes a backward-Euler item of n nodes needs.
 size_t phi_smem_bytes(int prec, int op, int d, int n);

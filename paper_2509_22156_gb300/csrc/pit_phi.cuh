@@ -1,0 +1,650 @@
+// Device code of the batched multi-step backward-Euler propagator
+// (Sec. 2, Eq. "parabolic_problem_time_propagation"): every (batch entry,
+// component grid) item is advanced by nsteps backward-Euler steps
+//     (I + dt L_l) x_s = x_{s-1} + dt f,   x_s <- x_s + g_s (optional forcing),
+// each solved matrix-free with CG (symmetric operators) or BiCGStab (drift
+// operator, Sec. 4.1), initial guess x_{s-1}.
+//
+// Design (grid-resident, multi-step): one CTA owns one item for all its
+// steps.  The FP64 state, the Krylov vectors and the neighbour masks live in
+// shared memory; dot products are reduced with warp shuffles and one block
+// barrier.  A whole F-relaxation interval or a sequential coarse sweep is one
+// launch; HBM is touched once to read the start state and once per stored
+// output state; the intermediate F-values never leave the SM (the C-point-only
+// storage of Sec. 3.3.2).  Kernels are instantiated per dimension D so that
+// every per-axis loop is unrolled and per-axis constants stay in registers.
+//
+// Precision forms:
+//   PLAIN  Krylov in FP64 until ||b - A x|| <= rtol ||b||.
+//   MIXED  FP64 iterative refinement around an FP32 Krylov solve: residual
+//          b - A x formed in FP64 from the FP64 state, the correction equation
+//          solved in FP32, the correction added in FP64; same FP64 stopping
+//          rule.  The FP32 target of each correction solve is the looser of
+//          inner_rtol and half of what the FP64 tolerance still asks for.  On
+//          GB300 FP64 arithmetic runs at 1/58 of FP32, so the FP64 stencil
+//          passes bound the kernel: when a step has no forcing, the FP64 pass
+//          that verifies step s also yields x_s - A x_s, which is exactly the
+//          initial residual of step s+1 (b = x_s, x_0 = x_s), so each step
+//          costs one FP64 stencil pass per correction.
+// CG is the single-reduction (Chronopoulos-Gear) form: one fused block
+// reduction of (r,r) and (Ar,r) per iteration and two barriers.
+#pragma once
+
+#include <type_traits>
+
+#include "pit_internal.cuh"
+
+namespace pit {
+
+#define PIT_FULL_MASK 0xffffffffu
+
+// ----------------------------------------------------------------------------
+// Operator coefficients of node j in FP64: (A p)_j = diag p_j + sum_i cm_i
+// p_{j-e_i} + cp_i p_{j+e_i}, zero towards boundary nodes (zero Dirichlet):
+//   heat    L p = sum_i (2 p_j - p_- - p_+) / h_i^2
+//   varheat L p = sum_i [a_+ (p_j - p_+) + a_- (p_j - p_-)] / h_i^2
+//   OU      L p = sum_i (F_+ - F_-) / h_i + (sigma^2/2)(2 p_j - p_- - p_+) / h_i^2,
+//           F_+ = max(v_+,0) p_j + min(v_+,0) p_+,  v_+ = -theta (x_i + h_i/2).
+template <int D>
+__device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, const double *faces, int j,
+                                        double dt, double &diag, double *cm, double *cp)
+{
+    diag = 1.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const int c = (j / G.S[i]) % G.N[i];
+        const double h = G.h[i];
+        const double ih2 = 1.0 / (h * h);
+        double dd, dm, dp;
+        if (op.op == PIT_OP_HEAT) {
+            dd = 2.0 * ih2; dm = -ih2; dp = -ih2;
+        } else if (op.op == PIT_OP_VARHEAT) {
+            const double am = faces[(G.off + j) * (2 * D) + 2 * i];
+            const double ap = faces[(G.off + j) * (2 * D) + 2 * i + 1];
+            dd = (am + ap) * ih2; dm = -am * ih2; dp = -ap * ih2;
+        } else {
+            const double x = op.lo[i] + (double)(c + 1) * h;
+            const double vp = -op.theta * (x + 0.5 * h);
+            const double vm = -op.theta * (x - 0.5 * h);
+            const double s2 = 0.5 * op.sigma * op.sigma * ih2;
+            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
+            dm = -fmax(vm, 0.0) / h - s2;
+            dp = fmin(vp, 0.0) / h - s2;
+        }
+        diag += dt * dd;
+        cm[i] = (c > 0) ? dt * dm : 0.0;
+        cp[i] = (c < G.N[i] - 1) ? dt * dp : 0.0;
+    }
+}
+
+// Constant-coefficient heat stencil with a per-node neighbour mask
+// (bit 2i: interior neighbour at -e_i, bit 2i+1: at +e_i).
+template <typename T, int D>
+struct HeatSt {
+    const uint16_t *mask;
+    int S[D];
+    T diag;
+    T off[D];
+    __device__ __forceinline__ T operator()(const T *p, int j) const
+    {
+        const unsigned mk = mask[j];
+        T s = diag * p[j];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T pm = ((mk >> (2 * i)) & 1u) ? p[j - S[i]] : T(0);
+            const T pp = ((mk >> (2 * i + 1)) & 1u) ? p[j + S[i]] : T(0);
+            s += off[i] * (pm + pp);
+        }
+        return s;
+    }
+};
+
+// Variable-coefficient stencil from a per-node table in shared memory
+// (structure of arrays: tab[k*ld + j], k = 0 diagonal, 1+2i minus, 2+2i plus;
+// zero coefficients towards the boundary).
+template <typename T, int D>
+struct TabSt {
+    const uint16_t *mask;
+    const T *tab;
+    int ld;
+    int S[D];
+    __device__ __forceinline__ T operator()(const T *p, int j) const
+    {
+        const unsigned mk = mask[j];
+        T s = tab[j] * p[j];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int jm = ((mk >> (2 * i)) & 1u) ? j - S[i] : j;
+            const int jp = ((mk >> (2 * i + 1)) & 1u) ? j + S[i] : j;
+            s += tab[(1 + 2 * i) * ld + j] * p[jm] + tab[(2 + 2 * i) * ld + j] * p[jp];
+        }
+        return s;
+    }
+};
+
+// ----------------------------------------------------------------------------
+// Block reductions: warp shuffles, one partial per warp in a 32-slot buffer,
+// one barrier, then every warp reduces the partials with the same shuffle
+// tree and broadcasts lane 0: all threads hold the bitwise same value,
+// independent of scheduling.  Consecutive reductions alternate two buffers,
+// so one barrier per reduction suffices (a warp can only reuse a buffer after
+// every warp passed the barrier of the reduction in between).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(PIT_FULL_MASK, v, o);
+    return v;
+}
+
+template <typename T>
+struct Reducer {
+    T *buf;    // two halves of 4 x 32 slots
+    int slot;
+    template <int K>
+    __device__ __forceinline__ void sum(T *v)
+    {
+        static_assert(K <= 4, "at most four values per reduction");
+        T *red = buf + (slot & 1) * 128;
+        ++slot;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T x = warp_sum(v[k]);
+            if (lane == 0) red[k * 32 + w] = x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            T x = (lane < nw) ? red[k * 32 + lane] : T(0);
+            x = warp_sum(x);
+            v[k] = __shfl_sync(PIT_FULL_MASK, x, 0);
+        }
+    }
+};
+
+__device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
+__device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
+
+// ----------------------------------------------------------------------------
+// Single-reduction CG (Chronopoulos & Gear 1989) on A e = r0: r holds r0 on
+// entry (own nodes written by the caller), the iterate is accumulated into X
+// (FP64 state or FP32 correction).  Stops when (r,r) <= stop2.
+template <typename T, typename TX, class ST>
+__device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reducer<T> &R, T stop2, int maxit,
+                       int &status)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    status = PIT_OK;
+    __syncthreads();  // r complete
+    T v[2] = {T(0), T(0)};
+    for (int j = tid; j < n; j += nt) {
+        const T wj = A(r, j);
+        w[j] = wj;
+        const T rj = r[j];
+        v[0] += rj * rj;
+        v[1] += wj * rj;
+    }
+    R.template sum<2>(v);
+    T gam = v[0];
+    if (!(gam > stop2)) {
+        if (gam != gam) status = PIT_ERR_NONFINITE;
+        return 0;
+    }
+    if (!finite_pos(v[1])) {
+        status = (v[1] != v[1]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+        return 0;
+    }
+    T alpha = gam / v[1], beta = T(0);
+    bool first = true;
+    int k = 0;
+    for (;;) {
+        if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+        for (int j = tid; j < n; j += nt) {
+            const T pj = first ? r[j] : r[j] + beta * p[j];
+            const T sj = first ? w[j] : w[j] + beta * s[j];
+            p[j] = pj;
+            s[j] = sj;
+            X[j] += (TX)(alpha * pj);
+            r[j] -= alpha * sj;
+        }
+        first = false;
+        ++k;
+        __syncthreads();
+        T u[2] = {T(0), T(0)};
+        for (int j = tid; j < n; j += nt) {
+            const T wj = A(r, j);
+            w[j] = wj;
+            const T rj = r[j];
+            u[0] += rj * rj;
+            u[1] += wj * rj;
+        }
+        R.template sum<2>(u);
+        if (!(u[0] > stop2)) {
+            if (u[0] != u[0]) status = PIT_ERR_NONFINITE;
+            break;
+        }
+        beta = u[0] / gam;
+        const T den = u[1] - beta * u[0] / alpha;
+        if (!finite_pos(den)) { status = (den != den) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        alpha = u[0] / den;
+        gam = u[0];
+    }
+    return k;
+}
+
+// BiCGStab (van der Vorst 1992) on A e = r0: r holds r0 on entry; rh, p, v
+// are initialised here; s shares r's storage.
+template <typename T, typename TX, class ST>
+__device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v, T *t, Reducer<T> &R, T stop2,
+                             int maxit, int &status)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    T rr[1] = {T(0)};
+    for (int j = tid; j < n; j += nt) {
+        const T rj = r[j];
+        rh[j] = rj;
+        p[j] = T(0);
+        v[j] = T(0);
+        rr[0] += rj * rj;
+    }
+    R.template sum<1>(rr);
+    T rho = T(1), alpha = T(1), omega = T(1), rrv = rr[0];
+    int k = 0;
+    status = PIT_OK;
+    for (;;) {
+        if (!(rrv > stop2)) {
+            if (rrv != rrv) status = PIT_ERR_NONFINITE;
+            break;
+        }
+        if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+        T rho_n[1] = {T(0)};
+        for (int j = tid; j < n; j += nt) rho_n[0] += rh[j] * r[j];
+        R.template sum<1>(rho_n);
+        if (rho_n[0] == T(0) || omega == T(0) || rho_n[0] != rho_n[0]) {
+            status = (rho_n[0] != rho_n[0]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+            break;
+        }
+        const T beta = (rho_n[0] / rho) * (alpha / omega);
+        for (int j = tid; j < n; j += nt) p[j] = r[j] + beta * (p[j] - omega * v[j]);
+        __syncthreads();
+        T rhv[1] = {T(0)};
+        for (int j = tid; j < n; j += nt) {
+            const T vj = A(p, j);
+            v[j] = vj;
+            rhv[0] += rh[j] * vj;
+        }
+        R.template sum<1>(rhv);
+        if (rhv[0] == T(0) || rhv[0] != rhv[0]) {
+            status = (rhv[0] != rhv[0]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+            break;
+        }
+        alpha = rho_n[0] / rhv[0];
+        for (int j = tid; j < n; j += nt) r[j] = r[j] - alpha * v[j];  // s
+        __syncthreads();
+        T tt[2] = {T(0), T(0)};
+        for (int j = tid; j < n; j += nt) {
+            const T tj = A(r, j);
+            t[j] = tj;
+            tt[0] += tj * tj;
+            tt[1] += tj * r[j];
+        }
+        R.template sum<2>(tt);
+        omega = (tt[0] > T(0)) ? tt[1] / tt[0] : T(0);
+        T rn[1] = {T(0)};
+        for (int j = tid; j < n; j += nt) {
+            X[j] += (TX)(alpha * p[j] + omega * r[j]);
+            const T rj = r[j] - omega * t[j];
+            r[j] = rj;
+            rn[0] += rj * rj;
+        }
+        R.template sum<1>(rn);
+        rho = rho_n[0];
+        rrv = rn[0];
+        ++k;
+        if (omega == T(0) && rrv > stop2) { status = PIT_ERR_BREAKDOWN; break; }
+    }
+    return k;
+}
+
+// ----------------------------------------------------------------------------
+// Shared-memory layout of one item (ld = n rounded up to 4):
+//   FP64 arrays: x, [b (MIXED)], [Krylov vectors (PLAIN)], [table (var. coef.)]
+//   FP32 arrays: [Krylov vectors + table (MIXED)]
+//   u16 mask
+__host__ __device__ inline int krylov_vecs(int op, int prec)
+{
+    if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e)
+    return prec == PLAIN ? 4 : 5;                        // r p s w (+ e)
+}
+__host__ __device__ inline int n_tab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
+__host__ __device__ inline int n_f64(int op, int prec, int d)
+{
+    return (prec == PLAIN ? 1 + krylov_vecs(op, prec) : 2) + n_tab(op, d);
+}
+__host__ __device__ inline int n_f32(int op, int prec, int d)
+{
+    return prec == MIXED ? krylov_vecs(op, prec) + n_tab(op, d) : 0;
+}
+
+template <int OP, int PREC, int D>
+__global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
+{
+    typedef typename std::conditional<PREC == PLAIN, double, float>::type T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ GridInfo GI;
+    __shared__ double red64[2 * 128];
+    __shared__ float red32[2 * 128];
+
+    const int item = a.item0 + (int)blockIdx.x;
+    const int g = a.order[item / a.n_batch];
+    const int b = item % a.n_batch;
+    if (a.active && !a.active[g]) return;  // uniform over the block
+    if (threadIdx.x == 0) GI = a.grids[g];
+    __syncthreads();
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = GI.n;
+    const int ld = (n + 3) & ~3;
+    const double dt = a.dt;
+    constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
+    constexpr int NF64 = (PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
+    constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6) : (PREC == PLAIN ? 4 : 5);
+    constexpr int NF32 = (PREC == MIXED) ? NKV + K : 0;
+
+    double *x = reinterpret_cast<double *>(smem);
+    double *bvec = x + ld;  // MIXED: right-hand side of the current step
+    double *v64 = x + ld;   // PLAIN: Krylov vectors
+    double *tab64 = x + (size_t)(NF64 - K) * ld;
+    float *f32 = reinterpret_cast<float *>(x + (size_t)NF64 * ld);
+    float *tab32 = f32 + (size_t)NKV * ld;
+    uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
+
+    const double *in = a.in + (long long)b * a.in_stride + GI.off;
+    const double *f = a.f ? a.f + (long long)b * a.f_stride + GI.off : nullptr;
+    const uint16_t *gmask = a.masks + GI.off;
+
+    for (int j = tid; j < n; j += nt) {
+        mask[j] = gmask[j];
+        x[j] = in[j];
+    }
+    if constexpr (OP != PIT_OP_HEAT) {
+        for (int j = tid; j < n; j += nt) {
+            double diag, cm[D], cp[D];
+            op_coef<D>(a.op, GI, a.faces, j, dt, diag, cm, cp);
+            tab64[j] = diag;
+            if constexpr (PREC == MIXED) tab32[j] = (float)diag;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                tab64[(1 + 2 * i) * ld + j] = cm[i];
+                tab64[(2 + 2 * i) * ld + j] = cp[i];
+                if constexpr (PREC == MIXED) {
+                    tab32[(1 + 2 * i) * ld + j] = (float)cm[i];
+                    tab32[(2 + 2 * i) * ld + j] = (float)cp[i];
+                }
+            }
+        }
+    }
+    // stencils in FP64 and in the working precision
+    HeatSt<double, D> H64;
+    HeatSt<T, D> HT;
+    TabSt<double, D> T64;
+    TabSt<float, D> T32;
+    H64.mask = HT.mask = T64.mask = T32.mask = mask;
+    T64.tab = tab64;
+    T32.tab = tab32;
+    T64.ld = T32.ld = ld;
+    {
+        double diag = 1.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const double ih2 = 1.0 / (GI.h[i] * GI.h[i]);
+            H64.S[i] = HT.S[i] = T64.S[i] = T32.S[i] = GI.S[i];
+            H64.off[i] = -dt * ih2;
+            HT.off[i] = (T)(-dt * ih2);
+            diag += 2.0 * dt * ih2;
+        }
+        H64.diag = diag;
+        HT.diag = (T)diag;
+    }
+    auto A64 = [&](const double *v, int j) -> double {
+        if constexpr (OP == PIT_OP_HEAT) return H64(v, j);
+        else return T64(v, j);
+    };
+
+    Reducer<double> R64{red64, 0};
+    Reducer<float> R32{red32, 0};
+    int status = PIT_OK, iters = 0, passes = 0;
+    const bool carry_ok = (f == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
+    // MIXED: carried initial residual of the next step (see the file comment)
+    bool have_r0 = false;
+    double rn0_c = 0.0, bb_c = 0.0;
+    float *rv = f32 + ld, *pv = f32 + 2 * ld, *sv = f32 + 3 * ld, *wv = f32 + 4 * ld, *tv = f32 + 5 * ld;
+
+    for (int step = 1; step <= a.nsteps; ++step) {
+        __syncthreads();  // state complete
+        if constexpr (PREC == PLAIN) {
+            double *r = v64, *q1 = v64 + ld, *q2 = v64 + 2 * ld, *q3 = v64 + 3 * ld, *q4 = v64 + 4 * ld;
+            double bb[1] = {0.0};
+            if (a.guess) {
+                // right-hand side kept in r, iterate replaced by the guess
+                const long long sb0 = (long long)(step - 1);
+                const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
+                const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
+                for (int j = tid; j < n; j += nt) {
+                    const double bj = f ? x[j] + dt * f[j] : x[j];
+                    r[j] = bj;
+                    bb[0] += bj * bj;
+                    x[j] = gf ? gu[j] - gf[j] : gu[j];
+                }
+                __syncthreads();
+                for (int j = tid; j < n; j += nt) r[j] -= A64(x, j);
+            } else {
+                for (int j = tid; j < n; j += nt) {
+                    const double bj = f ? x[j] + dt * f[j] : x[j];
+                    r[j] = bj - A64(x, j);
+                    bb[0] += bj * bj;
+                }
+            }
+            R64.template sum<1>(bb);  // also orders the residual before x changes
+            ++passes;
+            const double stop2 = a.rtol * a.rtol * bb[0];
+            int st, k;
+            if constexpr (OP == PIT_OP_OU) k = bicgstab_core<double, double>(T64, n, x, r, q1, q2, q3, q4, R64, stop2, a.maxit, st);
+            else if constexpr (OP == PIT_OP_HEAT) k = cg_core<double, double>(H64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
+            else k = cg_core<double, double>(T64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
+            iters += k;
+            if (st > status) status = st;
+        } else {
+            float *e = f32;
+            // right-hand side b = x_{s-1} + dt f; optional initial guess
+            if (a.guess) {
+                const long long sb0 = (long long)(step - 1);
+                const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
+                const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
+                for (int j = tid; j < n; j += nt) {
+                    bvec[j] = f ? x[j] + dt * f[j] : x[j];
+                    x[j] = gf ? gu[j] - gf[j] : gu[j];
+                }
+            } else {
+                for (int j = tid; j < n; j += nt) bvec[j] = f ? x[j] + dt * f[j] : x[j];
+            }
+            double rn2, bb;
+            if (have_r0) {
+                // r0 = x_{s-1} - A x_{s-1}, computed by the last check of the
+                // previous step into wv (OU: tv)
+                if constexpr (OP == PIT_OP_OU) { float *t_ = rv; rv = tv; tv = t_; }
+                else { float *t_ = rv; rv = wv; wv = t_; }
+                rn2 = rn0_c;
+                bb = bb_c;
+            } else {
+                __syncthreads();  // bvec complete (read only by the owner; x unchanged)
+                double acc[2] = {0.0, 0.0};
+                for (int j = tid; j < n; j += nt) {
+                    const double bj = bvec[j];
+                    const double rj = bj - A64(x, j);
+                    rv[j] = (float)rj;
+                    acc[0] += rj * rj;
+                    acc[1] += bj * bj;
+                }
+                R64.template sum<2>(acc);
+                ++passes;
+                rn2 = acc[0];
+                bb = acc[1];
+            }
+            have_r0 = false;
+            const double stop2 = a.rtol * a.rtol * bb;
+            int st_step = PIT_OK;
+            bool carried = false;
+            for (int pass = 0;; ++pass) {
+                if (!(rn2 > stop2)) {
+                    if (rn2 != rn2) st_step = PIT_ERR_NONFINITE;
+                    else if (carry_ok && pass == 0) {
+                        // x unchanged: its residual is the next step's r0
+                        if constexpr (OP == PIT_OP_OU) { float *t_ = rv; rv = tv; tv = t_; }
+                        else { float *t_ = rv; rv = wv; wv = t_; }
+                        rn0_c = rn2;
+                        bb_c = bb;
+                        carried = true;
+                    }
+                    break;
+                }
+                if (pass >= a.ir_maxit) { st_step = PIT_ERR_NOCONV; break; }
+                const double rnorm = sqrt(rn2);
+                const float inv = (float)(1.0 / rnorm);
+                for (int j = tid; j < n; j += nt) {
+                    rv[j] *= inv;
+                    e[j] = 0.0f;
+                }
+                const double want = 0.5 * sqrt(stop2 / rn2);
+                const float tgt = (float)(want > (double)a.inner_rtol ? want : (double)a.inner_rtol);
+                const float stop32 = tgt * tgt;
+                int st, k;
+                if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, e, rv, pv, sv, wv, tv, R32, stop32, a.maxit, st);
+                else if constexpr (OP == PIT_OP_HEAT) k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                else k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                iters += k;
+                if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
+                // a stalled or broken-down inner solve still gives a usable
+                // correction; the FP64 residual decides
+                for (int j = tid; j < n; j += nt) x[j] += (double)e[j] * rnorm;
+                __syncthreads();  // x complete
+                // FP64 check: r = b - A x, and (no forcing) the next step's r0 = x - A x
+                float *cv = (OP == PIT_OP_OU) ? tv : wv;
+                double acc[3] = {0.0, 0.0, 0.0};
+                for (int j = tid; j < n; j += nt) {
+                    const double xj = x[j];
+                    const double Ax = A64(x, j);
+                    const double rj = bvec[j] - Ax;
+                    rv[j] = (float)rj;
+                    acc[0] += rj * rj;
+                    if (carry_ok) {
+                        const double cj = xj - Ax;
+                        cv[j] = (float)cj;
+                        acc[1] += cj * cj;
+                        acc[2] += xj * xj;
+                    }
+                }
+                R64.template sum<3>(acc);
+                ++passes;
+                rn2 = acc[0];
+                if (carry_ok) {
+                    rn0_c = acc[1];
+                    bb_c = acc[2];
+                    carried = true;
+                }
+            }
+            if (st_step > status) status = st_step;
+            have_r0 = carried && st_step == PIT_OK && step < a.nsteps;
+        }
+        // forcing of this step and the stored outputs (own nodes only)
+        const long long sb = (long long)(step - 1);
+        if (a.g) {
+            const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
+            for (int j = tid; j < n; j += nt) x[j] += gs[j];
+        }
+        if (step < a.nsteps) {
+            if (a.out_steps) {
+                double *os = a.out_steps + (long long)b * a.os_stride + sb * a.os_step + GI.off;
+                for (int j = tid; j < n; j += nt) os[j] = x[j];
+            }
+        } else {
+            double *ol = a.out_last + (long long)b * a.ol_stride + GI.off;
+            const double *h = a.h ? a.h + (long long)b * a.h_stride + GI.off : nullptr;
+            const double *cmp = a.cmp ? a.cmp + (long long)b * a.cmp_stride + GI.off : nullptr;
+            double acc[1] = {0.0};
+            for (int j = tid; j < n; j += nt) {
+                const double xj = x[j];
+                if (cmp) {
+                    const double dlt = xj - cmp[j];
+                    acc[0] += dlt * dlt;
+                }
+                ol[j] = a.out_scale * xj + (h ? h[j] : 0.0);
+            }
+            if (cmp) {
+                R64.template sum<1>(acc);
+                if (tid == 0) a.norms[(long long)b * a.n_grids + g] = sqrt(acc[0]);
+            }
+        }
+    }
+    if (tid == 0 && a.stats) {
+        atomicAdd(&a.stats->sum_iters, (unsigned long long)iters);
+        atomicAdd(&a.stats->items, (unsigned long long)a.nsteps);
+        atomicAdd(&a.stats->point_iters, (unsigned long long)iters * (unsigned long long)n);
+        atomicAdd(&a.stats->point_passes, (unsigned long long)passes * (unsigned long long)n);
+        atomicAdd(&a.stats->point_steps, (unsigned long long)a.nsteps * (unsigned long long)n);
+        atomicMax(&a.stats->max_iters, iters);
+        atomicMax(&a.stats->max_refine, passes);
+        if (status != PIT_OK) {
+            atomicAdd(&a.stats->n_failed, 1);
+            atomicMax(&a.stats->worst, status);
+        }
+    }
+}
+
+// Per-operator launchers (one translation unit each).
+cudaError_t steps_init_heat(int bytes);
+cudaError_t steps_init_varheat(int bytes);
+cudaError_t steps_init_ou(int bytes);
+cudaError_t steps_launch_heat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s);
+cudaError_t steps_launch_varheat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s);
+cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s);
+
+// Instantiates the launcher and attribute setter of one operator for D = 1..6.
+#define PIT_STEPS_OP(NAME, OPV)                                                                                   \
+    cudaError_t steps_init_##NAME(int bytes)                                                                      \
+    {                                                                                                             \
+        cudaError_t e = cudaSuccess;                                                                              \
+        auto set = [&](const void *fn) {                                                                          \
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+        };                                                                                                        \
+        set((const void *)steps_kernel<OPV, PLAIN, 1>); set((const void *)steps_kernel<OPV, MIXED, 1>);           \
+        set((const void *)steps_kernel<OPV, PLAIN, 2>); set((const void *)steps_kernel<OPV, MIXED, 2>);           \
+        set((const void *)steps_kernel<OPV, PLAIN, 3>); set((const void *)steps_kernel<OPV, MIXED, 3>);           \
+        set((const void *)steps_kernel<OPV, PLAIN, 4>); set((const void *)steps_kernel<OPV, MIXED, 4>);           \
+        set((const void *)steps_kernel<OPV, PLAIN, 5>); set((const void *)steps_kernel<OPV, MIXED, 5>);           \
+        set((const void *)steps_kernel<OPV, PLAIN, 6>); set((const void *)steps_kernel<OPV, MIXED, 6>);           \
+        return e;                                                                                                 \
+    }                                                                                                             \
+    cudaError_t steps_launch_##NAME(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,       \
+                                    cudaStream_t s)                                                               \
+    {                                                                                                             \
+        switch (d * 2 + prec) {                                                                                   \
+        case 1 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 1><<<grid, block, smem, s>>>(a); break;                      \
+        case 1 * 2 + MIXED: steps_kernel<OPV, MIXED, 1><<<grid, block, smem, s>>>(a); break;                      \
+        case 2 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 2><<<grid, block, smem, s>>>(a); break;                      \
+        case 2 * 2 + MIXED: steps_kernel<OPV, MIXED, 2><<<grid, block, smem, s>>>(a); break;                      \
+        case 3 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 3><<<grid, block, smem, s>>>(a); break;                      \
+        case 3 * 2 + MIXED: steps_kernel<OPV, MIXED, 3><<<grid, block, smem, s>>>(a); break;                      \
+        case 4 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 4><<<grid, block, smem, s>>>(a); break;                      \
+        case 4 * 2 + MIXED: steps_kernel<OPV, MIXED, 4><<<grid, block, smem, s>>>(a); break;                      \
+        case 5 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 5><<<grid, block, smem, s>>>(a); break;                      \
+        case 5 * 2 + MIXED: steps_kernel<OPV, MIXED, 5><<<grid, block, smem, s>>>(a); break;                      \
+        case 6 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 6><<<grid, block, smem, s>>>(a); break;                      \
+        case 6 * 2 + MIXED: steps_kernel<OPV, MIXED, 6><<<grid, block, smem, s>>>(a); break;                      \
+        default: return cudaErrorInvalidValue;                                                                    \
+        }                                                                                                         \
+        return cudaGetLastError();                                                                                \
+    }
+
+}  // namespace pit

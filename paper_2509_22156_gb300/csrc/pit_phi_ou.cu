@@ -1,0 +1,7 @@
+// Multi-step backward-Euler kernels of one operator, instantiated for d = 1..6
+// and both precision forms (device code in pit_phi.cuh).
+#include "pit_phi.cuh"
+
+namespace pit {
+PIT_STEPS_OP(ou, PIT_OP_OU)
+}  // namespace pit

@@ -1,0 +1,163 @@
+"""GPU parity of the learned coarse propagator against the oracle's FP64
+restatement of the network (same BF16-rounded parameters), its training on
+the GPU, and MGRIT with the learned coarse propagator.
+
+Tolerances: the GPU network accumulates in FP32 with FP32 activations, the
+oracle in FP64: forward 2e-5 relative L2 per state; loss 1e-4 relative;
+gradient 1e-3 relative L2 with cosine >= 0.99999.  MGRIT with any coarse
+propagator converges to the fine (sequential) solution (Alg. 2), so the
+learned run is checked against the oracle's sequential solution at the MGRIT
+tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_22156_gb300 import binding as B
+from paper_2509_22156_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_22156_gb300 import build
+    build.build()
+    B.load()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def random_params(seed, scale=0.3):
+    w = (scale * W.normal(seed, B.NET_PARAMS)).astype(np.float32)
+    return B.bf16_round(w)
+
+
+CASES = [
+    (3, 4, W.OP_VARHEAT, [0.0] * 3, [1.0] * 3),
+    (2, 5, W.OP_HEAT, [0.0] * 2, [1.0] * 2),
+    (4, 3, W.OP_OU, [-6.0] * 4, [6.0] * 4),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=["varheat3d", "heat2d", "ou4d"])
+def test_forward_matches_oracle(case):
+    d, n, op, lo, hi = case
+    P = B.Problem(d, n, 1, op, lo, hi)
+    O = oracle.Problem(d, n, 1, op, lo, hi)
+    w = random_params(31)
+    P.net_set_params(w)
+    np.testing.assert_array_equal(P.net_get_params(), w)
+    dT = 0.01
+    u = W.random_vector(32, 3 * P.n_total)
+    out = torch.empty(3 * P.n_total, dtype=torch.float64, device="cuda")
+    P.net_forward(dT, cuda(u), out)
+    ref = O.net_forward(dT, w.astype(np.float64), u)
+    got = host(out)
+    for b in range(3):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < 2e-5, (b, g)
+
+
+def test_set_params_rounds_to_bf16():
+    P = B.Problem(2, 3, 1, B.PIT_OP_HEAT)
+    w = (0.37 * W.normal(5, B.NET_PARAMS)).astype(np.float32)
+    P.net_set_params(w)
+    np.testing.assert_array_equal(P.net_get_params(), B.bf16_round(w))
+    with pytest.raises(B.PitError):
+        P.net_set_params(w[:-1])
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=["varheat3d", "heat2d"])
+def test_loss_gradient_matches_oracle(case):
+    d, n, op, lo, hi = case
+    P = B.Problem(d, n, 1, op, lo, hi)
+    O = oracle.Problem(d, n, 1, op, lo, hi)
+    w = random_params(41, 0.2)
+    P.net_set_params(w)
+    dT = 0.02
+    u = W.random_vector(42, 2 * P.n_total)
+    y = W.random_vector(43, 2 * P.n_total)
+    loss, grad = P.net_loss_grad(dT, cuda(u), cuda(y))
+    lref, gref = O.net_loss_grad(dT, w.astype(np.float64), u, y)
+    assert abs(loss - lref) <= 1e-4 * abs(lref)
+    assert rel(grad, gref) < 1e-3
+    cos = float(np.dot(grad, gref) / (np.linalg.norm(grad) * np.linalg.norm(gref)))
+    assert cos > 0.99999
+
+
+def test_mgrit_with_learned_coarse_matches_fine_solution():
+    wl = W.workload(4)
+    n, N, m = 4, 128, 8
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    dt = (wl.t1 - wl.t0) / N
+    # a small untrained network: MGRIT must still converge to the fine solution
+    w = random_params(51, 0.02)
+    w[-86:] = 0.0  # output layer off: identity coarse map
+    w[-86 + 17 * 2 + 2] = B.bf16_round(np.float32([-0.05]))[0]
+    P.net_set_params(w)
+    tol = 1e-11 * np.abs(u0).max()
+    fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=50000)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, 2, tol=tol, maxit=40, coarse=B.PIT_COARSE_LEARNED, fine=fine)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st, rc = P.mgrit_solve(cuda(u0), opts, uT, check=False)
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    if st.fallback:
+        assert rc == 0 and st.learned_used == 1
+    assert rc == 0
+    assert rel(host(uT), seq) < 1e-9
+    # the oracle's MGRIT with the same parameters reaches the same fixed point
+    ref, its, _, _ = O.mgrit(u0, dt, N, m, 2, tol=tol, maxit=40, coarse_kind=W.COARSE_LEARNED,
+                             theta=w.astype(np.float64), rtol=1e-15)
+    assert rel(host(uT), ref) < 1e-9
+
+
+def test_learned_requires_parameters():
+    P = B.Problem(2, 4, 1, B.PIT_OP_HEAT)
+    u0 = torch.zeros(P.n_total, dtype=torch.float64, device="cuda")
+    uT = torch.empty_like(u0)
+    opts = B.mgrit_opts(0.0, 0.1, 16, 4, 2, coarse=B.PIT_COARSE_LEARNED)
+    st, rc = P.mgrit_solve(u0, opts, uT, check=False)
+    assert rc == B.PIT_ERR_INVALID_ARG
+
+
+def test_training_reduces_loss_and_is_judged():
+    wl = W.workload(4)
+    n, N, m = 5, 256, 8
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    dt = (wl.t1 - wl.t0) / N
+    mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-11, inner_rtol=1e-5, ir_maxit=20)
+    topts = B.train_opts(dt, m, n_pairs=512, n_holdout=64, epochs=6, batch=32, lr=2e-3, seed=3, traj_len=6,
+                         fine=mixed, crs=mixed)
+    st = P.train_coarse(topts)
+    assert st.adam_steps > 0 and np.isfinite(st.loss_last_epoch)
+    assert st.loss_last_epoch < st.loss_first_epoch
+    assert st.holdout_err_learned > 0 and st.holdout_err_implicit > 0
+    assert st.accepted == (1 if st.holdout_err_learned <= st.holdout_err_implicit else 0)
+    # whatever the judge said, MGRIT with the coarse choice reaches the fine solution
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    tol = 1e-10 * np.abs(u0).max()
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, 2, tol=tol, maxit=60, coarse=B.PIT_COARSE_LEARNED, fine=mixed,
+                        crs=mixed)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    stm = P.mgrit_solve(cuda(u0), opts, uT)
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert rel(host(uT), seq) < 1e-8
+    assert stm.learned_used == st.accepted
