@@ -130,6 +130,10 @@ typedef struct {
     double tol;
     int maxit;            /* MGRIT cycle cap */
     int coarse;           /* pit_coarse */
+    int fas;              /* 1: FAS form of Alg. 2 as printed; 0: with a linear coarse
+                             propagator (implicit), solve the coarse problem for the
+                             correction (Sec. 3.3.1 notes this for linear problems), so
+                             that crs.rtol is relative to the correction            */
     pit_solve_opts fine;  /* options of every fine-level Phi solve   */
     pit_solve_opts crs;   /* options of every coarse-level Phi solve */
 } pit_mgrit_opts;

@@ -58,7 +58,7 @@ class pit_phi_stats(ctypes.Structure):
 class pit_mgrit_opts(ctypes.Structure):
     _fields_ = [("t0", ctypes.c_double), ("t1", ctypes.c_double), ("nsteps", ctypes.c_int), ("m", ctypes.c_int),
                 ("levels", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("coarse", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts)]
+                ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts)]
 
 
 class pit_mgrit_stats(ctypes.Structure):
@@ -172,10 +172,10 @@ def bf16_round(w) -> np.ndarray:
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
-               crs=None) -> pit_mgrit_opts:
+               crs=None, fas=False) -> pit_mgrit_opts:
     fine = fine or solve_opts()
     crs = crs or fine
-    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, fine, crs)
+    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs)
 
 
 class Problem:

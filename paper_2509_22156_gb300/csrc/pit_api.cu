@@ -91,13 +91,21 @@ struct pit_problem {
     DevStats *h_stats = nullptr;  // pinned
     int *d_order = nullptr;          // grids by decreasing size
     uint16_t *d_masks = nullptr;     // neighbour masks, packed like a state
-    size_t smem_need[2] = {0, 0};    // per precision form
+    // launch plan per precision form: class 0 = grids whose FP64 state fits in
+    // shared memory, class 1 = larger grids (MIXED only: state in global memory)
     bool planned[2] = {false, false};
-    int threads[2][2] = {{0, 0}, {0, 0}};  // [prec][wide batch]; 0 = not tuned yet
-    int forced_threads[2] = {0, 0};        // pit_tune override [wide batch]
+    int n_cls[2][2] = {{0, 0}, {0, 0}};
+    int *d_order_cls[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    size_t smem_cls[2][2] = {{0, 0}, {0, 0}};
+    size_t smem_need[2] = {0, 0};    // class 0 (used by the allocation-free step)
+    int threads[2][2][2] = {};       // [prec][wide batch][class]; 0 = not tuned yet
+    int forced_threads[2] = {0, 0};  // override [wide batch]
+    cudaStream_t side = nullptr;     // second stream: the large-grid class runs beside class 0
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    DBuf w_xg;                       // FP64 state of class-1 items
     // workspaces
     DBuf w_in, w_out, w_pts, w_u, w_prm;
-    DBuf m_U, m_R, m_UT, m_GC, m_res, m_UT1, m_GC1, m_T0, m_act, w_tune;
+    DBuf m_U, m_R, m_UT, m_GC, m_res, m_UT1, m_GC1, m_T0, m_act, w_tune, m_Z, m_E;
     std::vector<double> h_res;
     double *h_rmax = nullptr;  // pinned, G
     int *h_act = nullptr;      // pinned, G
@@ -203,22 +211,43 @@ pit_status check_solve_opts(const pit_solve_opts *o)
     return PIT_OK;
 }
 
-// Shared memory the multi-step kernel needs for the largest grid.
+// Launch plan of a precision form: grids whose on-chip state fits in shared
+// memory form class 0; the others (MIXED) keep their FP64 state in global
+// memory (class 1).  Each class lists its grids by decreasing size.
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
-    size_t need = 0;
-    int gmax = 0;
-    for (int g = 0; g < P->G; ++g) {
-        const size_t bytes = phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[g].n);
-        if (bytes > need) { need = bytes; gmax = g; }
+    std::vector<int> order(P->G);
+    for (int g = 0; g < P->G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P->info[a].n > P->info[b].n; });
+    std::vector<int> cls[2];
+    size_t need[2] = {0, 0};
+    for (int g : order) {
+        const int n = P->info[g].n;
+        const size_t bytes = phi_smem_bytes(prec, P->desc.op, P->desc.d, n);
+        if (bytes <= P->max_smem) {
+            cls[0].push_back(g);
+            need[0] = bytes > need[0] ? bytes : need[0];
+            continue;
+        }
+        const size_t bx = prec == MIXED ? phi_smem_bytes_xg(P->desc.op, P->desc.d, n) : (size_t)-1;
+        if (bx > P->max_smem)
+            return fail(PIT_ERR_UNSUPPORTED,
+                        "grid %d (%d nodes) needs %zu bytes of shared memory for the on-chip solve in this precision "
+                        "form; the device offers %zu",
+                        g, n, prec == MIXED ? bx : bytes, P->max_smem);
+        cls[1].push_back(g);
+        need[1] = bx > need[1] ? bx : need[1];
     }
-    if (need > P->max_smem)
-        return fail(PIT_ERR_UNSUPPORTED,
-                    "grid %d (%d nodes) needs %zu bytes of shared memory for the on-chip solve in this precision "
-                    "form; the device offers %zu",
-                    gmax, P->info[gmax].n, need, P->max_smem);
-    P->smem_need[prec] = need;
+    for (int c = 0; c < 2; ++c) {
+        P->n_cls[prec][c] = (int)cls[c].size();
+        P->smem_cls[prec][c] = need[c];
+        if (!cls[c].empty()) {
+            CU(cudaMalloc(&P->d_order_cls[prec][c], sizeof(int) * cls[c].size()));
+            CU(cudaMemcpy(P->d_order_cls[prec][c], cls[c].data(), sizeof(int) * cls[c].size(), cudaMemcpyHostToDevice));
+        }
+    }
+    P->smem_need[prec] = need[0];
     P->planned[prec] = true;
     return PIT_OK;
 }
@@ -239,8 +268,11 @@ struct StepCall {
     double *out_last = nullptr;
     long long ols = 0;
     double scale = 1.0;
+    double hscale = 1.0;
     const double *h = nullptr;
     long long hs = 0;
+    const double *hstep = nullptr;  // added to every stored state (per-step stride hsst)
+    long long hss = 0, hsst = 0;
     const double *cmp = nullptr;
     long long cs = 0;
     double *norms = nullptr;
@@ -255,7 +287,11 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.grids = P->d_grids;
     a.masks = P->d_masks;
     a.order = P->d_order;
+    a.n_order = P->G;
     a.n_grids = P->G;
+    a.n_total = P->ntot;
+    a.xg = nullptr;
+    a.bg = nullptr;
     a.n_batch = c.nb;
     a.nsteps = c.nsteps;
     a.dt = c.dt;
@@ -272,8 +308,12 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.out_last = c.out_last;
     a.ol_stride = c.ols;
     a.out_scale = c.scale;
+    a.out_hscale = c.hscale;
     a.h = c.h;
     a.h_stride = c.hs;
+    a.hs = c.hstep;
+    a.hs_stride = c.hss;
+    a.hs_step = c.hsst;
     a.cmp = c.cmp;
     a.cmp_stride = c.cs;
     a.norms = c.norms;
@@ -292,11 +332,13 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
 }
 
 // Autotuner: the CTA size of a launch class (precision form x wide/narrow
-// batch) is chosen once per problem by timing one backward-Euler step of the
-// first real call of that class with every candidate, output to scratch.
-pit_status tune(pit_problem *P, int prec, bool wide, const pit_solve_opts &o, const StepCall &c, const int *active)
+// batch x grid class) is chosen once per problem by timing one backward-Euler
+// step of the first real call of that class with every candidate, output to
+// scratch.
+pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_opts &o, const StepCall &c,
+                const int *active)
 {
-    int &slot = P->threads[prec][wide ? 1 : 0];
+    int &slot = P->threads[prec][wide ? 1 : 0][cls];
     if (slot) return PIT_OK;
     if (P->forced_threads[wide ? 1 : 0]) {
         slot = P->forced_threads[wide ? 1 : 0];
@@ -314,6 +356,12 @@ pit_status tune(pit_problem *P, int prec, bool wide, const pit_solve_opts &o, co
     t.ols = P->ntot;
     StepArgs a = make_args(P, o, t, active);
     a.stats = nullptr;
+    a.order = P->d_order_cls[prec][cls];
+    a.n_order = P->n_cls[prec][cls];
+    if (cls == 1) {
+        a.xg = P->w_xg.d();
+        a.bg = a.xg + (long long)c.nb * P->ntot;
+    }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
@@ -322,7 +370,7 @@ pit_status tune(pit_problem *P, int prec, bool wide, const pit_solve_opts &o, co
     for (int k = 0; k < 4; ++k) {
         for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
             CU(cudaEventRecord(e0, P->stream));
-            CU(launch_steps(prec, a, cand[k], P->smem_need[prec], P->stream));
+            CU(launch_steps(prec, a, cand[k], P->smem_cls[prec][cls], P->stream, cls == 1));
             CU(cudaEventRecord(e1, P->stream));
         }
         CU(cudaEventSynchronize(e1));
@@ -336,16 +384,40 @@ pit_status tune(pit_problem *P, int prec, bool wide, const pit_solve_opts &o, co
     return PIT_OK;
 }
 
+// One multi-step launch of every grid: class 0 on the problem's stream and,
+// when present, class 1 (state in global memory) concurrently on the side
+// stream, joined before returning.
 pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
 {
     const int prec = o.prec == PIT_PREC_MIXED ? MIXED : PLAIN;
     TRY(plan(P, prec));
     if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
     const bool wide = c.nb >= 8;
-    TRY(tune(P, prec, wide, o, c, active));
+    const bool two = P->n_cls[prec][1] > 0;
+    if (two) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * 2));
+    for (int cls = 0; cls < 2; ++cls)
+        if (P->n_cls[prec][cls] > 0) TRY(tune(P, prec, wide, cls, o, c, active));
     StepArgs a = make_args(P, o, c, active);
     ProfScope ps(P, 0);
-    CU(launch_steps(prec, a, P->threads[prec][wide ? 1 : 0], P->smem_need[prec], P->stream));
+    if (two) {
+        CU(cudaEventRecord(P->ev_fork, P->stream));
+        CU(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+        StepArgs b = a;
+        b.order = P->d_order_cls[prec][1];
+        b.n_order = P->n_cls[prec][1];
+        b.xg = P->w_xg.d();
+        b.bg = b.xg + (long long)c.nb * P->ntot;
+        CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][1], P->smem_cls[prec][1], P->side, true));
+    }
+    if (P->n_cls[prec][0] > 0) {
+        a.order = P->d_order_cls[prec][0];
+        a.n_order = P->n_cls[prec][0];
+        CU(launch_steps(prec, a, P->threads[prec][wide ? 1 : 0][0], P->smem_cls[prec][0], P->stream, false));
+    }
+    if (two) {
+        CU(cudaEventRecord(P->ev_join, P->side));
+        CU(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+    }
     return PIT_OK;
 }
 
@@ -514,6 +586,9 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
             return bail(fail(e_ == cudaErrorMemoryAllocation ? PIT_ERR_OOM : PIT_ERR_CUDA, "%s: %s", #call, \
                              cudaGetErrorString(e_)));                                              \
     } while (0)
+    CUB(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+    CUB(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    CUB(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     CUB(phi_kernels_init(P->max_smem));
     CUB(net_kernels_init(P->max_smem));
     CUB(cudaMalloc(&P->d_grids, sizeof(GridInfo) * P->G));
@@ -554,6 +629,14 @@ pit_status pit_problem_destroy(pit_problem_t P)
     cudaStreamSynchronize(P->stream);
     cudaFree(P->d_order);
     cudaFree(P->d_masks);
+    for (int p = 0; p < 2; ++p)
+        for (int c = 0; c < 2; ++c) cudaFree(P->d_order_cls[p][c]);
+    if (P->side) {
+        cudaStreamSynchronize(P->side);
+        cudaStreamDestroy(P->side);
+    }
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
     cudaFree(P->d_grids);
     cudaFree(P->d_coef);
     cudaFree(P->d_levels);
@@ -566,7 +649,8 @@ pit_status pit_problem_destroy(pit_problem_t P)
     DBuf *bufs[] = {&P->w_in,     &P->w_out,  &P->w_pts, &P->w_u,     &P->w_prm,  &P->m_U,     &P->m_R,
                     &P->m_UT,     &P->m_GC,   &P->m_res, &P->m_UT1,   &P->m_GC1,  &P->m_T0,    &P->m_act,
                     &P->w_tune,   &P->n_master, &P->n_m, &P->n_v,     &P->n_w,    &P->n_rows,  &P->n_loss,
-                    &P->n_act,    &P->n_items, &P->n_U,  &P->n_Y,     &P->n_grad, &P->n_tmp,   &P->n_prm};
+                    &P->n_act,    &P->n_items, &P->n_U,  &P->n_Y,     &P->n_grad, &P->n_tmp,   &P->n_prm,
+                    &P->w_xg,     &P->m_Z,     &P->m_E};
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     delete P;
@@ -761,9 +845,10 @@ pit_status run_coarse(Mg &M, StepCall c, int level)
 }
 
 // Two-level cycle of level 1 in a three-level hierarchy: level-1 points are V
-// (read) -> W (written), Nc1 = N1/m intervals, forcing of level-1 point k is
-// F[k-1]; the level-2 problem is solved by a sequential sweep.
-pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const double *F)
+// (read; stride vstride, 0 for a constant initial guess) -> W (written),
+// Nc1 = N1/m intervals, forcing of level-1 point k is F[k-1]; the level-2
+// problem is solved by a sequential sweep.
+pit_status mg_level1_cycle(Mg &M, const double *V, long long vstride, double *W, int N1, const double *F)
 {
     pit_problem *P = M.P;
     const int m = M.o->m, Nc = N1 / m;
@@ -777,7 +862,7 @@ pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const doub
     fc.nb = Nc;
     fc.nsteps = m;
     fc.in = V;
-    fc.is = sm;
+    fc.is = vstride * m;
     fc.g = F;
     fc.gs = sm;
     fc.gst = nt;
@@ -790,6 +875,7 @@ pit_status mg_level1_cycle(Mg &M, const double *V, double *W, int N1, const doub
     // F-relaxation from the new C-points (F-points in place) and utilde
     StepCall fr = fc;
     fr.in = W;
+    fr.is = sm;
     fr.out_last = UT1;
     fr.ols = nt;
     TRY(run_coarse(M, fr, 1));
@@ -853,6 +939,9 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     CU(P->m_GC.ensure(vb * Nc));
     CU(P->m_res.ensure(sizeof(double) * G * Nc));
     CU(P->m_act.ensure(sizeof(int) * G));
+    CU(P->m_Z.ensure(vb));
+    CU(cudaMemsetAsync(P->m_Z.p, 0, vb, P->stream));
+    if (o->levels == 3) CU(P->m_E.ensure(vb * (Nc + 1)));
     P->h_res.resize((size_t)G * Nc);
     double *U = P->m_U.d(), *R = P->m_R.d(), *UT = P->m_UT.d(), *GC = P->m_GC.d(), *res = P->m_res.d();
     int *act = (int *)P->m_act.p;
@@ -882,14 +971,49 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
         fc.out_last = R + nt;
         fc.ols = nt;
         TRY(run_steps(P, o->fine, fc, act));
+        // linear coarse propagator: solve the coarse problem for the correction
+        // (Sec. 3.3.1: Alg. 2's coarse system is linear here), so the coarse
+        // tolerance is relative to the correction, which vanishes as MGRIT
+        // converges; the learned one is nonlinear and keeps the FAS form
+        const bool corr = !M.learned && o->coarse != PIT_COARSE_EXACT && !o->fas;
         StepCall fr = fc;  // F relaxation, utilde and the C-point residuals
         fr.in = R;
-        fr.out_last = UT;
         fr.cmp = R + nt;
         fr.cs = nt;
         fr.norms = res;
+        if (corr) {
+            fr.out_last = GC;  // r_{j+1} = utilde_{j+1} - u_{(j+1)m}
+            fr.h = R + nt;
+            fr.hs = nt;
+            fr.hscale = -1.0;
+        } else {
+            fr.out_last = UT;
+        }
         TRY(run_steps(P, o->fine, fr, act));
         CU(cudaMemcpyAsync(P->h_res.data(), res, sizeof(double) * G * Nc, cudaMemcpyDeviceToHost, P->stream));
+        if (corr) {
+            if (o->levels == 3) {
+                // level-1 problem e_k = Phi_c(e_{k-1}) + r_k, e_0 = 0, by one
+                // two-level cycle from e = 0; then u_{jm} = relaxed + e_j
+                TRY(mg_level1_cycle(M, P->m_Z.d(), 0, P->m_E.d(), Nc, GC));
+                CU(launch_add_states(P->d_grids, G, nt, Nc, R + nt, P->m_E.d() + nt, U + nt, act, P->stream));
+            } else {
+                StepCall sw;  // e_{j+1} = Phi_c(e_j) + r_{j+1}; stored as u = relaxed + e
+                sw.nb = 1;
+                sw.nsteps = Nc;
+                sw.in = P->m_Z.d();
+                sw.is = nt;
+                sw.g = GC;
+                sw.gst = nt;
+                sw.hstep = R + nt;
+                sw.hsst = nt;
+                sw.out_steps = U + nt;
+                sw.osst = nt;
+                sw.out_last = U + (long long)Nc * nt;
+                sw.ols = nt;
+                TRY(run_coarse(M, sw, 1));
+            }
+        } else {
         StepCall gc;  // coarse right-hand side
         gc.nb = Nc;
         gc.nsteps = 1;
@@ -902,7 +1026,7 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
         gc.hs = nt;
         TRY(run_coarse(M, gc, 1));
         if (o->levels == 3) {
-            TRY(mg_level1_cycle(M, R, U, Nc, GC));
+            TRY(mg_level1_cycle(M, R, nt, U, Nc, GC));
         } else if (o->coarse == PIT_COARSE_EXACT) {
             for (int j = 0; j < Nc; ++j) {
                 StepCall sw;
@@ -936,6 +1060,7 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
             sw.ols = nt;
             if (M.learned) sw.guess = nullptr;  // explicit: no Krylov guess
             TRY(run_coarse(M, sw, 1));
+        }
         }
         CU(cudaStreamSynchronize(P->stream));
         double rmax = 0.0;
@@ -1079,8 +1204,11 @@ extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, i
     }
     const int prec = opts->prec == PIT_PREC_MIXED ? MIXED : PLAIN;
     TRY(plan(P, prec));
+    if (P->n_cls[prec][1] > 0)
+        return fail(PIT_ERR_UNSUPPORTED, "this problem has grids whose solver state needs global scratch; "
+                                         "pit_phi_batch_inplace_static cannot serve it");
     const bool wide = n_batch >= 8;
-    const int threads = P->threads[prec][wide ? 1 : 0] ? P->threads[prec][wide ? 1 : 0] : 128;
+    const int threads = P->threads[prec][wide ? 1 : 0][0] ? P->threads[prec][wide ? 1 : 0][0] : 128;
     StepCall c;
     c.dt = dt;
     c.nb = n_batch;
@@ -1092,6 +1220,8 @@ extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, i
     c.out_last = scratch;  // every node of every item is written: nothing needs clearing
     c.ols = P->ntot;
     StepArgs a = make_args(P, *opts, c, nullptr);
+    a.order = P->d_order_cls[prec][0];
+    a.n_order = P->n_cls[prec][0];
     if (stats) CU(cudaMemsetAsync(P->d_stats, 0, sizeof(DevStats), P->stream));
     else a.stats = nullptr;
     CU(launch_steps(prec, a, threads, P->smem_need[prec], P->stream));

@@ -235,6 +235,26 @@ cudaError_t launch_resid_norms(const GridInfo *grids, int G, long long ntot, int
     return cudaGetLastError();
 }
 
+// out_k = x_k + y_k on the active grids of nb consecutive states.
+__global__ void add_states_kernel(const GridInfo *grids, int G, long long ntot, const double *x, const double *y,
+                                  double *out, const int *active)
+{
+    const int g = blockIdx.x % G, k = blockIdx.x / G;
+    if (active && !active[g]) return;
+    const GridInfo GI = grids[g];
+    const long long o = (long long)k * ntot + GI.off;
+    for (int j = threadIdx.x; j < GI.n; j += blockDim.x) out[o + j] = x[o + j] + y[o + j];
+}
+
+cudaError_t launch_add_states(const GridInfo *grids, int G, long long ntot, int nb, const double *x, const double *y,
+                              double *out, const int *active, cudaStream_t s)
+{
+    const long long blocks = (long long)nb * G;
+    if (blocks == 0) return cudaSuccess;
+    add_states_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, G, ntot, x, y, out, active);
+    return cudaGetLastError();
+}
+
 __global__ void resid_max_kernel(int G, int nb, const double *resid, const int *active, double *rmax)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;

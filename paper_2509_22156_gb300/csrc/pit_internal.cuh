@@ -49,7 +49,9 @@ struct DevStats {
 // after step s (1-based) x <- x + g_s with g_s = g + b*g_stride + (s-1)*g_step
 // (g may be NULL); states after steps 1..nsteps-1 are written to out_steps +
 // b*os_stride + (s-1)*os_step when out_steps is non-NULL; the final state x is
-// written as out_scale * x + h_b to out_last + b*ol_stride, and, when cmp is
+// written as out_scale * x + out_hscale * h_b to out_last + b*ol_stride; when
+// hs is non-NULL every stored state (steps and last) also gets hs_s =
+// hs + b*hs_stride + (s-1)*hs_step added; when cmp is
 // non-NULL, norms[b*n_grids + g] = ||x - cmp_b||_2.  When guess is non-NULL
 // the Krylov solve of step s starts from guess_s - g_s instead of x_{s-1}
 // (guess_s = guess + b*guess_stride + (s-1)*guess_step); the right-hand side is
@@ -59,8 +61,9 @@ struct StepArgs {
     int item0;              // first item of this launch (launches may be split in chunks)
     const GridInfo *grids;
     const uint16_t *masks;  // neighbour mask of every node, packed like a state
-    const int *order;       // grids by decreasing size
-    int n_grids;
+    const int *order;       // the launch's grids, by decreasing size
+    int n_order;            // grids in order
+    int n_grids;            // all grids of the problem (row length of norms)
     int n_batch;
     int nsteps;
     double dt;
@@ -70,10 +73,15 @@ struct StepArgs {
     double *out_steps;       long long os_stride, os_step;
     double *out_last;        long long ol_stride;
     double out_scale;
+    double out_hscale;
     const double *h;         long long h_stride;
+    const double *hs;        long long hs_stride, hs_step;
     const double *cmp;       long long cmp_stride;
     double *norms;
     const double *guess;     long long guess_stride, guess_step;
+    double *xg;              // state in global memory (MIXED, grids too large for shared memory):
+    double *bg;              //   x and b of entry b at xg/bg + b*n_total + grid offset
+    long long n_total;
     const int *active;       // per grid, NULL = all active
     const double *faces;     // variable coefficient at the 2d faces of every node, or NULL
     OpParams op;
@@ -115,8 +123,11 @@ cudaError_t launch_net_adam(const float *grad_rows, int n_rows, float scale, flo
 
 // Shared-memory bytes a backward-Euler item of n nodes needs.
 size_t phi_smem_bytes(int prec, int op, int d, int n);
-// Launch one multi-step batch (grid-per-CTA, every Krylov solve on chip).
-cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s);
+// Launch one multi-step batch (grid-per-CTA, every Krylov solve on chip);
+// xg selects the variant whose FP64 state lives in global memory.
+cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s, bool xg = false);
+// Shared memory per item; xg: FP64 state in global memory (MIXED only).
+size_t phi_smem_bytes_xg(int op, int d, int n);
 // Raise the dynamic shared-memory limit of every backward-Euler kernel.
 cudaError_t phi_kernels_init(size_t max_smem);
 // Neighbour masks of every node (bit 2i: interior neighbour at -e_i, 2i+1: at +e_i).
@@ -134,6 +145,9 @@ cudaError_t launch_resid_norms(const GridInfo *grids, int G, long long ntot, int
                                long long a_stride, const double *b, long long b_stride, const int *active,
                                double *resid, cudaStream_t s);
 // rmax[g] = max_j resid[j*G + g] (NaN propagates), active grids only.
+// out_k = x_k + y_k on the active grids of nb consecutive states.
+cudaError_t launch_add_states(const GridInfo *grids, int G, long long ntot, int nb, const double *x, const double *y,
+                              double *out, const int *active, cudaStream_t s);
 cudaError_t launch_resid_max(int G, int nb, const double *resid, const int *active, double *rmax,
                              cudaStream_t s);
 

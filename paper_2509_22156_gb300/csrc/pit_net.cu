@@ -197,15 +197,17 @@ __global__ void __launch_bounds__(256) net_steps_kernel(StepArgs a, const __grid
             const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
             for (int j = tid; j < n; j += nt) x[j] += gs[j];
         }
+        const double *hs = a.hs ? a.hs + (long long)b * a.hs_stride + sb * a.hs_step + GI.off : nullptr;
         if (step < a.nsteps) {
             if (a.out_steps) {
                 double *os = a.out_steps + (long long)b * a.os_stride + sb * a.os_step + GI.off;
-                for (int j = tid; j < n; j += nt) os[j] = x[j];
+                for (int j = tid; j < n; j += nt) os[j] = hs ? x[j] + hs[j] : x[j];
             }
         } else {
             double *ol = a.out_last + (long long)b * a.ol_stride + GI.off;
             const double *h = a.h ? a.h + (long long)b * a.h_stride + GI.off : nullptr;
-            for (int j = tid; j < n; j += nt) ol[j] = a.out_scale * x[j] + (h ? h[j] : 0.0);
+            for (int j = tid; j < n; j += nt)
+                ol[j] = a.out_scale * x[j] + (h ? a.out_hscale * h[j] : 0.0) + (hs ? hs[j] : 0.0);
         }
     }
     if (tid == 0 && a.stats) {

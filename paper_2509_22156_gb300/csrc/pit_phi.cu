@@ -11,6 +11,12 @@ size_t phi_smem_bytes(int prec, int op, int d, int n)
     return (size_t)n_f64(op, prec, d) * ld * 8 + (size_t)n_f32(op, prec, d) * ld * 4 + ld * 2 + 16;
 }
 
+size_t phi_smem_bytes_xg(int op, int d, int n)
+{
+    const size_t ld = (size_t)((n + 3) & ~3);
+    return (size_t)n_tab(op, d) * ld * 8 + (size_t)n_f32(op, MIXED, d) * ld * 4 + ld * 2 + 16;
+}
+
 static size_t g_max_smem = 0;
 
 cudaError_t phi_kernels_init(size_t max_smem)
@@ -23,17 +29,17 @@ cudaError_t phi_kernels_init(size_t max_smem)
     return e;
 }
 
-cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s)
+cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s, bool xg)
 {
-    const long long blocks = (long long)a.n_batch * a.n_grids;
+    const long long blocks = (long long)a.n_batch * a.n_order;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL || smem > g_max_smem || threads < 32 || threads > 512 || (threads & 31))
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)blocks), block(threads);
     switch (a.op.op) {
-    case PIT_OP_HEAT: return steps_launch_heat(prec, a.op.d, a, grid, block, smem, s);
-    case PIT_OP_VARHEAT: return steps_launch_varheat(prec, a.op.d, a, grid, block, smem, s);
-    case PIT_OP_OU: return steps_launch_ou(prec, a.op.d, a, grid, block, smem, s);
+    case PIT_OP_HEAT: return steps_launch_heat(prec, a.op.d, a, grid, block, smem, s, xg);
+    case PIT_OP_VARHEAT: return steps_launch_varheat(prec, a.op.d, a, grid, block, smem, s, xg);
+    case PIT_OP_OU: return steps_launch_ou(prec, a.op.d, a, grid, block, smem, s, xg);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -327,7 +327,7 @@ __host__ __device__ inline int n_f32(int op, int prec, int d)
     return prec == MIXED ? krylov_vecs(op, prec) + n_tab(op, d) : 0;
 }
 
-template <int OP, int PREC, int D>
+template <int OP, int PREC, int D, bool XG = false>
 __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
 {
     typedef typename std::conditional<PREC == PLAIN, double, float>::type T;
@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
     __shared__ double red64[2 * 128];
     __shared__ float red32[2 * 128];
 
+    static_assert(!XG || PREC == MIXED, "global-state variant is MIXED only");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -348,15 +349,16 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
     const int ld = (n + 3) & ~3;
     const double dt = a.dt;
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
-    constexpr int NF64 = (PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
+    constexpr int NF64 = (PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : (XG ? 0 : 2)) + K;
     constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6) : (PREC == PLAIN ? 4 : 5);
     constexpr int NF32 = (PREC == MIXED) ? NKV + K : 0;
 
-    double *x = reinterpret_cast<double *>(smem);
-    double *bvec = x + ld;  // MIXED: right-hand side of the current step
-    double *v64 = x + ld;   // PLAIN: Krylov vectors
-    double *tab64 = x + (size_t)(NF64 - K) * ld;
-    float *f32 = reinterpret_cast<float *>(x + (size_t)NF64 * ld);
+    double *s64 = reinterpret_cast<double *>(smem);
+    double *x = XG ? a.xg + (long long)b * a.n_total + GI.off : s64;
+    double *bvec = XG ? a.bg + (long long)b * a.n_total + GI.off : s64 + ld;  // MIXED: right-hand side
+    double *v64 = s64 + ld;  // PLAIN: Krylov vectors
+    double *tab64 = s64 + (size_t)(NF64 - K) * ld;
+    float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
     float *tab32 = f32 + (size_t)NKV * ld;
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
 
@@ -563,10 +565,11 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
             const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
             for (int j = tid; j < n; j += nt) x[j] += gs[j];
         }
+        const double *hs = a.hs ? a.hs + (long long)b * a.hs_stride + sb * a.hs_step + GI.off : nullptr;
         if (step < a.nsteps) {
             if (a.out_steps) {
                 double *os = a.out_steps + (long long)b * a.os_stride + sb * a.os_step + GI.off;
-                for (int j = tid; j < n; j += nt) os[j] = x[j];
+                for (int j = tid; j < n; j += nt) os[j] = hs ? x[j] + hs[j] : x[j];
             }
         } else {
             double *ol = a.out_last + (long long)b * a.ol_stride + GI.off;
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
                     const double dlt = xj - cmp[j];
                     acc[0] += dlt * dlt;
                 }
-                ol[j] = a.out_scale * xj + (h ? h[j] : 0.0);
+                ol[j] = a.out_scale * xj + (h ? a.out_hscale * h[j] : 0.0) + (hs ? hs[j] : 0.0);
             }
             if (cmp) {
                 R64.template sum<1>(acc);
@@ -606,9 +609,12 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
 cudaError_t steps_init_heat(int bytes);
 cudaError_t steps_init_varheat(int bytes);
 cudaError_t steps_init_ou(int bytes);
-cudaError_t steps_launch_heat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s);
-cudaError_t steps_launch_varheat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s);
-cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s);
+cudaError_t steps_launch_heat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              bool xg);
+cudaError_t steps_launch_varheat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t s, bool xg);
+cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            bool xg);
 
 // Instantiates the launcher and attribute setter of one operator for D = 1..6.
 #define PIT_STEPS_OP(NAME, OPV)                                                                                   \
@@ -624,11 +630,27 @@ cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 
         set((const void *)steps_kernel<OPV, PLAIN, 4>); set((const void *)steps_kernel<OPV, MIXED, 4>);           \
         set((const void *)steps_kernel<OPV, PLAIN, 5>); set((const void *)steps_kernel<OPV, MIXED, 5>);           \
         set((const void *)steps_kernel<OPV, PLAIN, 6>); set((const void *)steps_kernel<OPV, MIXED, 6>);           \
+        set((const void *)steps_kernel<OPV, MIXED, 1, true>); set((const void *)steps_kernel<OPV, MIXED, 2, true>); \
+        set((const void *)steps_kernel<OPV, MIXED, 3, true>); set((const void *)steps_kernel<OPV, MIXED, 4, true>); \
+        set((const void *)steps_kernel<OPV, MIXED, 5, true>); set((const void *)steps_kernel<OPV, MIXED, 6, true>); \
         return e;                                                                                                 \
     }                                                                                                             \
     cudaError_t steps_launch_##NAME(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,       \
-                                    cudaStream_t s)                                                               \
+                                    cudaStream_t s, bool xg)                                                      \
     {                                                                                                             \
+        if (xg) {                                                                                                 \
+            if (prec != MIXED) return cudaErrorInvalidValue;                                                      \
+            switch (d) {                                                                                          \
+            case 1: steps_kernel<OPV, MIXED, 1, true><<<grid, block, smem, s>>>(a); break;                        \
+            case 2: steps_kernel<OPV, MIXED, 2, true><<<grid, block, smem, s>>>(a); break;                        \
+            case 3: steps_kernel<OPV, MIXED, 3, true><<<grid, block, smem, s>>>(a); break;                        \
+            case 4: steps_kernel<OPV, MIXED, 4, true><<<grid, block, smem, s>>>(a); break;                        \
+            case 5: steps_kernel<OPV, MIXED, 5, true><<<grid, block, smem, s>>>(a); break;                        \
+            case 6: steps_kernel<OPV, MIXED, 6, true><<<grid, block, smem, s>>>(a); break;                        \
+            default: return cudaErrorInvalidValue;                                                                \
+            }                                                                                                     \
+            return cudaGetLastError();                                                                            \
+        }                                                                                                         \
         switch (d * 2 + prec) {                                                                                   \
         case 1 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 1><<<grid, block, smem, s>>>(a); break;                      \
         case 1 * 2 + MIXED: steps_kernel<OPV, MIXED, 1><<<grid, block, smem, s>>>(a); break;                      \

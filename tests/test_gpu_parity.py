@@ -191,8 +191,11 @@ def test_mgrit_matches_oracle(name, prec):
     assert rel(got, ref) < (1e-10 if prec == B.PIT_PREC_FP64 else 1e-9)
     assert st.n_converged == P.G
     # same number of cycles as the oracle on the slowest grid (converged-grid
-    # masking follows the per-grid stopping rule)
-    assert abs(st.max_cycles - int(its.max())) <= (0 if prec == B.PIT_PREC_FP64 else 1)
+    # masking follows the per-grid stopping rule); the GPU solves the linear
+    # coarse problem for the correction, the oracle in the FAS form of Alg. 2
+    # (equal in exact arithmetic), so a residual at the tolerance may tip one
+    # cycle either way
+    assert abs(st.max_cycles - int(its.max())) <= 1
     # and the fixed point is the sequential solution
     seq = O.sequential(u0, dt, N, rtol=1e-15)
     assert rel(got, seq) < 1e-7
@@ -215,3 +218,40 @@ def test_combine_matches_oracle(name):
     assert rel(outh, ref) < 1e-13
     # empty point set
     P.combine(u, pts[:0].copy(), outh[:0].copy())
+
+
+def test_large_grids_keep_their_state_in_global_memory():
+    """d = 2, level 12: grids (6, 7) and (7, 6) hold 8001 nodes, more than the
+    shared-memory solver state allows; the mixed form keeps their FP64 state in
+    global memory and runs them beside the other grids.  The FP64 form has no
+    such variant and refuses."""
+    P = B.Problem(2, 12, 1, B.PIT_OP_HEAT)
+    O = oracle.Problem(2, 12, 1, W.OP_HEAT)
+    assert int(np.diff(P.offsets).max()) == 127 * 63
+    dt = 1e-4
+    nb = 2
+    u = W.random_vector(505, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    opts = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-12, maxit=20000, inner_rtol=1e-5, ir_maxit=30)
+    st = P.phi_batch(dt, cuda(u), out, opts)
+    assert st.n_items == nb * P.G and st.n_failed == 0
+    ref = O.phi(dt, u, rtol=1e-15)
+    got = host(out)
+    for b in range(nb):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < 1e-9, (b, g)
+    with pytest.raises(B.PitError) as e:
+        P.phi_batch(dt, cuda(u), out, B.solve_opts(B.PIT_PREC_FP64))
+    assert e.value.status == B.PIT_ERR_UNSUPPORTED
+    # MGRIT over both classes.  The coarse systems have dT/h^2 up to 6700, so a
+    # true FP64 residual cannot go much below 1e-12 relative: Krylov 1e-10.
+    u0 = O.initial(W.IC_SINES, W.sine_modes(2, [(1.0, [1, 1]), (0.3, [2, 3])]))
+    N, m = 32, 4
+    tol = 1e-9 * np.abs(u0).max()
+    mo = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-10, maxit=20000, inner_rtol=1e-5, ir_maxit=30)
+    mopts = B.mgrit_opts(0.0, N * dt, N, m, 2, tol=tol, maxit=40, fine=mo)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    P.mgrit_solve(cuda(u0), mopts, uT)
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert rel(host(uT), seq) < 1e-7
