@@ -149,17 +149,26 @@ def ncu_traffic():
 # cpu_baseline leg).  The paper's own tolerances (1e-8 absolute, Sec. 4.1) are
 # timed as an extra form.
 MGRIT_TOL, KRYLOV_RTOL = 1e-7, 1e-10
+# per workload: the solution of the variable-coefficient workload decays about
+# 20-fold and its combination cancels strongly, so its tolerances are tighter
+# (checked the same way)
+MGRIT_TOL_BY_WORKLOAD = {1: 1e-8, 2: 1e-7, 3: 1e-8, 4: 1e-10, 5: 5e-9}
+# the d = 6 combination sums 4921 grids with coefficients up to C(5, 2) = 10,
+# which amplifies per-grid errors a few hundred times: tighter Krylov there
+KRYLOV_RTOL_BY_WORKLOAD = {4: 1e-11, 5: 1e-11}
 PAPER_TOL, PAPER_RTOL = 1e-8, 1e-10
 
 
 COARSE_RTOL = 1e-3  # coarse solves for the correction: relative to the correction
 
 
-def solver_setup(wl, B, tol=MGRIT_TOL, rtol=KRYLOV_RTOL, coarse=None):
+def solver_setup(wl, B, tol=None, rtol=None, coarse=None):
     """Options of the chosen form (FP32 Krylov in FP64 refinement, learned
     coarse propagator or the implicit one solved for the correction with a
     loose tolerance) and of the plain FP64 form (the paper's algorithm: FAS
     form of Alg. 2, FP64 Krylov, one tolerance for every solve)."""
+    tol = MGRIT_TOL_BY_WORKLOAD.get(wl_index(wl), MGRIT_TOL) if tol is None else tol
+    rtol = KRYLOV_RTOL_BY_WORKLOAD.get(wl_index(wl), KRYLOV_RTOL) if rtol is None else rtol
     mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=rtol, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     mixed_c = B.solve_opts(B.PIT_PREC_MIXED, rtol=COARSE_RTOL, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     plain = B.solve_opts(B.PIT_PREC_FP64, rtol=rtol, maxit=8000)
@@ -170,6 +179,14 @@ def solver_setup(wl, B, tol=MGRIT_TOL, rtol=KRYLOV_RTOL, coarse=None):
     fp64 = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=plain, crs=plain,
                         fas=True)
     return chosen, fp64, mixed, plain
+
+
+def wl_index(wl):
+    from paper_2509_22156_gb300 import workloads as W
+    for k in range(1, 6):
+        if W.workload(k).name == wl.name:
+            return k
+    return 0
 
 
 def train_network(P, wl, B, mixed, seed=0):
@@ -202,7 +219,9 @@ def run_pit(args, rank, world, local):
     training = train_network(P, wl, B, mixed)
     u0 = torch.empty(P.n_total, dtype=torch.float64, device=dev)
     P.sample_initial(wl.ic_kind, wl.ic_params, u0)
-    pts_h = W.eval_points(wl.d, wl.lo, wl.hi)
+    # 65,536 uniform points (4096 for d = 6, where the oracle's combination of
+    # 4921 grids is the slow part of the accuracy check), diagonal and centre
+    pts_h = W.eval_points(wl.d, wl.lo, wl.hi, n_uniform=65536 if wl.d < 6 else 4096)
     pts = torch.from_numpy(pts_h).to(dev)
     uT = torch.empty_like(u0)
     out = torch.empty(pts_h.shape[0], dtype=torch.float64, device=dev)
@@ -330,19 +349,26 @@ def run_pit(args, rank, world, local):
     out_fp64 = None
     if not args.no_forms and rank == 0:
         forms = {}
-        # plain FP64 MGRIT (same workload, FP64 Krylov)
-        step(fp64, u0, out)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        st = step(fp64, u0, out)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        forms["plain_fp64_mgrit"] = {"ms": ms, "value": dofsteps / (ms / 1e3), "cycles": st.max_cycles}
-        uT_fp64 = uT.cpu().numpy().copy()
-        out_fp64 = out.cpu().numpy().copy()
+        # plain FP64 MGRIT (same workload, FP64 Krylov, FAS form)
+        uT_fp64 = None
+        try:
+            step(fp64, u0, out)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st = step(fp64, u0, out)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            forms["plain_fp64_mgrit"] = {"ms": ms, "value": dofsteps / (ms / 1e3), "cycles": st.max_cycles}
+            uT_fp64 = uT.cpu().numpy().copy()
+            out_fp64 = out.cpu().numpy().copy()
+        except B.PitError as err:
+            forms["plain_fp64_mgrit"] = {"unavailable": str(err)}
         def timed(o):
-            step(o, u0, out)
+            try:
+                step(o, u0, out)
+            except B.PitError as err:
+                return {"unavailable": str(err)}
             torch.cuda.synchronize()
             e0.record(stream)
             st = step(o, u0, out)
@@ -355,18 +381,21 @@ def run_pit(args, rank, world, local):
         mi, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT)
         forms["mixed_implicit_coarse_mgrit"] = timed(mi)
         # the paper's algorithm (FAS form, one tolerance) in mixed precision
-        mf = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=MGRIT_TOL, maxit=64, fine=mixed, crs=mixed,
+        mf = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64, fine=mixed, crs=mixed,
                           fas=True)
         forms["mixed_fas_mgrit"] = timed(mf)
         # time-sequential stepping on the GPU, FP64 and mixed
         for name, so in (("sequential_fp64", plain), ("sequential_mixed", mixed)):
-            e0.record(stream)
-            P.sequential_solve(u0, wl.dt, wl.nsteps, uT, so)
-            P.combine(uT, pts, out)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3)}
+            try:
+                e0.record(stream)
+                P.sequential_solve(u0, wl.dt, wl.nsteps, uT, so)
+                P.combine(uT, pts, out)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3)}
+            except B.PitError as err:
+                forms[name] = {"unavailable": str(err)}
         # the paper's algorithm at the paper's tolerances (MGRIT 1e-8 absolute,
         # Krylov 1e-10 for every solve), both precision forms
         _, pfp, pmx, _ = solver_setup(wl, B, PAPER_TOL, PAPER_RTOL, coarse=B.PIT_COARSE_IMPLICIT)
@@ -374,8 +403,9 @@ def run_pit(args, rank, world, local):
                           fas=True)
         forms["paper_tol_mixed_fas_mgrit"] = timed(pm)
         forms["paper_tol_fp64_fas_mgrit"] = timed(pfp)
-        forms["chosen_vs_plain_fp64_speedup"] = forms["plain_fp64_mgrit"]["ms"] / ms_step
-        forms["chosen_vs_mixed_minus_fp64_rel_l2"] = float(np.linalg.norm(uT_h - uT_fp64) / np.linalg.norm(uT_fp64))
+        if uT_fp64 is not None:
+            forms["chosen_vs_plain_fp64_speedup"] = forms["plain_fp64_mgrit"]["ms"] / ms_step
+            forms["chosen_vs_mixed_minus_fp64_rel_l2"] = float(np.linalg.norm(uT_h - uT_fp64) / np.linalg.norm(uT_fp64))
         result["forms"] = forms
 
     if not args.no_cpu and rank == 0 and world == 1:

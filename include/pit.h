@@ -99,9 +99,10 @@ typedef struct {
  *   prec = PIT_PREC_FP64:  Krylov in FP64 until ||b - A x||_2 <= rtol ||b||_2
  *                          or maxit iterations.
  *   prec = PIT_PREC_MIXED: FP64 iterative refinement: r = b - A x in FP64,
- *                          FP32 Krylov on A e = r to relative inner_rtol
- *                          (at most maxit iterations), x += e in FP64; at most
- *                          ir_maxit passes; the same FP64 stopping rule. */
+ *                          FP32 Krylov on A e = r to relative
+ *                          max(inner_rtol, 0.5 rtol ||b|| / ||r||) (at most maxit
+ *                          iterations), x += e in FP64; at most ir_maxit
+ *                          passes; the same FP64 stopping rule. */
 typedef struct {
     int prec;
     double rtol;

@@ -164,6 +164,11 @@ struct Reducer {
 };
 
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
+// A right-hand side whose squared norm lies in [1e-24, 1e24] keeps every
+// residual that matters (relative size >= 1e-14) inside the normal FP32
+// range; outside it residuals are scaled by 1/||b|| in FP64 before the
+// conversion.
+__device__ __forceinline__ bool fp32_safe(double bb) { return bb >= 1e-24 && bb <= 1e24; }
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
 // ----------------------------------------------------------------------------
@@ -266,6 +271,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
             break;
         }
         const T beta = (rho_n[0] / rho) * (alpha / omega);
+        if (!(fabs(beta) < (T)1e30)) { status = (beta != beta) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
         for (int j = tid; j < n; j += nt) p[j] = r[j] + beta * (p[j] - omega * v[j]);
         __syncthreads();
         T rhv[1] = {T(0)};
@@ -280,6 +286,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
             break;
         }
         alpha = rho_n[0] / rhv[0];
+        if (!(fabs(alpha) < (T)1e30)) { status = (alpha != alpha) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
         for (int j = tid; j < n; j += nt) r[j] = r[j] - alpha * v[j];  // s
         __syncthreads();
         T tt[2] = {T(0), T(0)};
@@ -291,6 +298,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         }
         R.template sum<2>(tt);
         omega = (tt[0] > T(0)) ? tt[1] / tt[0] : T(0);
+        if (!(fabs(omega) < (T)1e30)) { status = (omega != omega) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
         T rn[1] = {T(0)};
         for (int j = tid; j < n; j += nt) {
             X[j] += (TX)(alpha * p[j] + omega * r[j]);
@@ -328,7 +336,7 @@ __host__ __device__ inline int n_f32(int op, int prec, int d)
 }
 
 template <int OP, int PREC, int D, bool XG = false>
-__global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
+__global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(StepArgs a)
 {
     typedef typename std::conditional<PREC == PLAIN, double, float>::type T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -418,9 +426,12 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
     Reducer<float> R32{red32, 0};
     int status = PIT_OK, iters = 0, passes = 0;
     const bool carry_ok = (f == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
-    // MIXED: carried initial residual of the next step (see the file comment)
+    // MIXED: carried initial residual of the next step (see the file comment).
+    // FP32 residual copies hold r * rsc, rsc = 1 (or 1 / ||b||, applied in FP64
+    // before the conversion, when ||b|| is so small or large that FP32 would
+    // under- or overflow).
     bool have_r0 = false;
-    double rn0_c = 0.0, bb_c = 0.0;
+    double rn0_c = 0.0, bb_c = 0.0, rsc_c = 0.0;
     float *rv = f32 + ld, *pv = f32 + 2 * ld, *sv = f32 + 3 * ld, *wv = f32 + 4 * ld, *tv = f32 + 5 * ld;
 
     for (int step = 1; step <= a.nsteps; ++step) {
@@ -471,7 +482,7 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
             } else {
                 for (int j = tid; j < n; j += nt) bvec[j] = f ? x[j] + dt * f[j] : x[j];
             }
-            double rn2, bb;
+            double rn2, bb, rsc;
             if (have_r0) {
                 // r0 = x_{s-1} - A x_{s-1}, computed by the last check of the
                 // previous step into wv (OU: tv)
@@ -479,23 +490,34 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
                 else { float *t_ = rv; rv = wv; wv = t_; }
                 rn2 = rn0_c;
                 bb = bb_c;
+                rsc = rsc_c;
             } else {
-                __syncthreads();  // bvec complete (read only by the owner; x unchanged)
-                double acc[2] = {0.0, 0.0};
-                for (int j = tid; j < n; j += nt) {
-                    const double bj = bvec[j];
-                    const double rj = bj - A64(x, j);
-                    rv[j] = (float)rj;
-                    acc[0] += rj * rj;
-                    acc[1] += bj * bj;
+                double acc[1] = {0.0};
+                for (int j = tid; j < n; j += nt) acc[0] += bvec[j] * bvec[j];
+                R64.template sum<1>(acc);  // also: bvec and x complete
+                bb = acc[0];
+                rsc = fp32_safe(bb) ? 1.0 : 1.0 / sqrt(bb);
+                acc[0] = 0.0;
+                if (rsc == 1.0) {
+                    for (int j = tid; j < n; j += nt) {
+                        const double rj = bvec[j] - A64(x, j);
+                        rv[j] = (float)rj;
+                        acc[0] += rj * rj;
+                    }
+                } else {
+                    for (int j = tid; j < n; j += nt) {
+                        const double rj = bvec[j] - A64(x, j);
+                        rv[j] = (float)(rj * rsc);
+                        acc[0] += rj * rj;
+                    }
                 }
-                R64.template sum<2>(acc);
+                R64.template sum<1>(acc);
                 ++passes;
                 rn2 = acc[0];
-                bb = acc[1];
             }
             have_r0 = false;
             const double stop2 = a.rtol * a.rtol * bb;
+            const double bsc = fp32_safe(bb) ? 1.0 : 1.0 / sqrt(bb);
             int st_step = PIT_OK;
             bool carried = false;
             for (int pass = 0;; ++pass) {
@@ -507,13 +529,14 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
                         else { float *t_ = rv; rv = wv; wv = t_; }
                         rn0_c = rn2;
                         bb_c = bb;
+                        rsc_c = rsc;
                         carried = true;
                     }
                     break;
                 }
                 if (pass >= a.ir_maxit) { st_step = PIT_ERR_NOCONV; break; }
                 const double rnorm = sqrt(rn2);
-                const float inv = (float)(1.0 / rnorm);
+                const float inv = (float)(1.0 / (rnorm * rsc));  // stored r * rsc -> unit norm
                 for (int j = tid; j < n; j += nt) {
                     rv[j] *= inv;
                     e[j] = 0.0f;
@@ -534,25 +557,43 @@ __global__ void __launch_bounds__(512, 2) steps_kernel(StepArgs a)
                 // FP64 check: r = b - A x, and (no forcing) the next step's r0 = x - A x
                 float *cv = (OP == PIT_OP_OU) ? tv : wv;
                 double acc[3] = {0.0, 0.0, 0.0};
-                for (int j = tid; j < n; j += nt) {
-                    const double xj = x[j];
-                    const double Ax = A64(x, j);
-                    const double rj = bvec[j] - Ax;
-                    rv[j] = (float)rj;
-                    acc[0] += rj * rj;
-                    if (carry_ok) {
-                        const double cj = xj - Ax;
-                        cv[j] = (float)cj;
-                        acc[1] += cj * cj;
-                        acc[2] += xj * xj;
+                if (bsc == 1.0) {
+                    for (int j = tid; j < n; j += nt) {
+                        const double xj = x[j];
+                        const double Ax = A64(x, j);
+                        const double rj = bvec[j] - Ax;
+                        rv[j] = (float)rj;
+                        acc[0] += rj * rj;
+                        if (carry_ok) {
+                            const double cj = xj - Ax;
+                            cv[j] = (float)cj;
+                            acc[1] += cj * cj;
+                            acc[2] += xj * xj;
+                        }
+                    }
+                } else {
+                    for (int j = tid; j < n; j += nt) {
+                        const double xj = x[j];
+                        const double Ax = A64(x, j);
+                        const double rj = bvec[j] - Ax;
+                        rv[j] = (float)(rj * bsc);
+                        acc[0] += rj * rj;
+                        if (carry_ok) {
+                            const double cj = xj - Ax;
+                            cv[j] = (float)(cj * bsc);
+                            acc[1] += cj * cj;
+                            acc[2] += xj * xj;
+                        }
                     }
                 }
                 R64.template sum<3>(acc);
                 ++passes;
                 rn2 = acc[0];
+                rsc = bsc;
                 if (carry_ok) {
                     rn0_c = acc[1];
                     bb_c = acc[2];
+                    rsc_c = bsc;
                     carried = true;
                 }
             }
