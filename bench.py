@@ -216,7 +216,9 @@ def run_pit(args, rank, world, local):
     wl = W.workload(args.workload)
     P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi, wl.theta, wl.sigma, wl.vamp, stream=stream.cuda_stream)
     chosen, fp64, mixed, plain = solver_setup(wl, B)
+    torch.cuda.nvtx.range_push("train")
     training = train_network(P, wl, B, mixed)
+    torch.cuda.nvtx.range_pop()
     u0 = torch.empty(P.n_total, dtype=torch.float64, device=dev)
     P.sample_initial(wl.ic_kind, wl.ic_params, u0)
     # 65,536 uniform points (4096 for d = 6, where the oracle's combination of
@@ -240,10 +242,14 @@ def run_pit(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
 
+    nvtx = torch.cuda.nvtx
+    nvtx.range_push("warmup")
     for _ in range(args.warmup):
         step(chosen, u0, out)
+    nvtx.range_pop()
     barrier()
     clocks = Clocks(local)
+    nvtx.range_push("timed")
     P.profile_enable(True)
     total_ms, launches, stats = 0.0, 0, None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -255,6 +261,7 @@ def run_pit(args, rank, world, local):
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+    nvtx.range_pop()
     prof = P.profile_read()
     P.profile_enable(False)
     barrier()
