@@ -21,11 +21,16 @@
 //          solved in FP32, the correction added in FP64; same FP64 stopping
 //          rule.  The FP32 target of each correction solve is the looser of
 //          inner_rtol and half of what the FP64 tolerance still asks for.  On
-//          GB300 FP64 arithmetic runs at 1/58 of FP32, so the FP64 stencil
-//          passes bound the kernel: when a step has no forcing, the FP64 pass
+//          GB300 FP64 arithmetic (and the hardware FP64<->FP32 conversion)
+//          runs at 1/58 of the FP32 rate, so the FP64 stencil passes bound the
+//          kernel and are kept lean: when a step has no forcing, the FP64 pass
 //          that verifies step s also yields x_s - A x_s, which is exactly the
 //          initial residual of step s+1 (b = x_s, x_0 = x_s), so each step
-//          costs one FP64 stencil pass per correction.
+//          costs one FP64 stencil pass per correction; conversions run on the
+//          integer pipes with an exact power-of-two scale, and only ||r||^2
+//          of the FP64 residual is accumulated in FP64 (the norms of the
+//          carried residual and of the next right-hand side, which only set
+//          tolerances, come from their FP32 copies).
 // CG is the single-reduction (Chronopoulos-Gear) form: one fused block
 // reduction of (r,r) and (Ar,r) per iteration and two barriers.
 #pragma once
@@ -124,11 +129,11 @@ struct TabSt {
 
 // ----------------------------------------------------------------------------
 // Block reductions: warp shuffles, one partial per warp in a 32-slot buffer,
-// one barrier, then every warp reduces the partials with the same shuffle
-// tree and broadcasts lane 0: all threads hold the bitwise same value,
-// independent of scheduling.  Consecutive reductions alternate two buffers,
-// so one barrier per reduction suffices (a warp can only reuse a buffer after
-// every warp passed the barrier of the reduction in between).
+// one barrier, then every warp reduces the nw partials with the same shuffle
+// tree (log2 nw levels) and broadcasts lane 0: all threads hold the bitwise
+// same value, independent of scheduling.  Consecutive reductions alternate two
+// buffers, so one barrier per reduction suffices (a warp can only reuse a
+// buffer after every warp passed the barrier of the reduction in between).
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -141,34 +146,98 @@ template <typename T>
 struct Reducer {
     T *buf;    // two halves of 4 x 32 slots
     int slot;
+    // first stage: warp sums into the current half; returns that half
     template <int K>
-    __device__ __forceinline__ void sum(T *v)
+    __device__ __forceinline__ T *stage1(const T *v)
     {
         static_assert(K <= 4, "at most four values per reduction");
         T *red = buf + (slot & 1) * 128;
         ++slot;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const T x = warp_sum(v[k]);
             if (lane == 0) red[k * 32 + w] = x;
         }
-        __syncthreads();
+        return red;
+    }
+    // second stage, after the barrier: sum of the nw warp partials
+    template <int K>
+    __device__ __forceinline__ void stage2(const T *red, T *v)
+    {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const int top = 1 << (32 - __clz(nw - 1));  // nw rounded up to a power of two
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             T x = (lane < nw) ? red[k * 32 + lane] : T(0);
-            x = warp_sum(x);
+            for (int o = top >> 1; o > 0; o >>= 1) x += __shfl_down_sync(PIT_FULL_MASK, x, o);
             v[k] = __shfl_sync(PIT_FULL_MASK, x, 0);
         }
     }
+    template <int K>
+    __device__ __forceinline__ void sum(T *v)
+    {
+        const T *red = stage1<K>(v);
+        __syncthreads();
+        stage2<K>(red, v);
+    }
 };
 
+// KD FP64 and KF FP32 sums behind one barrier.
+template <int KD, int KF>
+__device__ __forceinline__ void sum_mixed(Reducer<double> &Rd, double *vd, Reducer<float> &Rf, float *vf)
+{
+    const double *rd = Rd.template stage1<KD>(vd);
+    const float *rf = Rf.template stage1<KF>(vf);
+    __syncthreads();
+    Rd.template stage2<KD>(rd, vd);
+    Rf.template stage2<KF>(rf, vf);
+}
+
+// ----------------------------------------------------------------------------
+// Conversions between FP64 and FP32 by IEEE-754 bit-field arithmetic on the
+// integer pipes, with an exact power-of-two scale folded into the exponent.
+// GB300 executes the hardware conversion instructions on its FP64 pipe at the
+// FP64 rate; these keep that pipe for the residual arithmetic.
+//   to_f32(v, k): v 2^k with the mantissa truncated to 24 bits (error below
+//     one FP32 ulp); zero when v 2^k is below the normal FP32 range, infinity
+//     or NaN when it is above it or v is not finite.
+//   to_f64(f, k): f 2^k exactly for normal f; zero for zero or subnormal f or
+//     when the result would be below the normal FP64 range.
+__device__ __forceinline__ float to_f32(double v, int k)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const int ex = (int)((hi >> 20) & 0x7ffu) - (1023 - 127) + k;  // FP32 biased exponent
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned bits = sign | ((unsigned)min(ex, 255) << 23) | mant;
+    return __uint_as_float(ex > 0 ? bits : sign);
+}
+__device__ __forceinline__ double to_f64(float f, int k)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const int ef = (int)((u >> 23) & 0xffu);
+    const unsigned m = u & 0x7fffffu;
+    const int ex = min(ef == 255 ? 2047 : ef + (1023 - 127) + k, 2047);
+    const bool zero = (ef == 0) || (ex <= 0);
+    const unsigned hi = zero ? sign : (sign | ((unsigned)ex << 20) | (m >> 3));
+    const unsigned lo = zero ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+// 2^k as FP64 for |k| <= 1022
+__device__ __forceinline__ double pow2d(int k) { return __hiloint2double((1023 + k) << 20, 0); }
+// k with ||b|| 2^k in [1, 2) from bb = ||b||^2 (0 for bb = 0 or not finite)
+__device__ __forceinline__ int scale_exp(double bb)
+{
+    const int eb = (int)(((unsigned)__double2hiint(bb) >> 20) & 0x7ffu);
+    if (eb == 0 || eb == 2047) return eb == 0 && bb != 0.0 ? 540 : 0;
+    const int e = eb - 1023;
+    const int half = (e >= 0) ? e / 2 : -((1 - e) / 2);  // floor(e / 2)
+    return -half;
+}
+
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
-// A right-hand side whose squared norm lies in [1e-24, 1e24] keeps every
-// residual that matters (relative size >= 1e-14) inside the normal FP32
-// range; outside it residuals are scaled by 1/||b|| in FP64 before the
-// conversion.
-__device__ __forceinline__ bool fp32_safe(double bb) { return bb >= 1e-24 && bb <= 1e24; }
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
 // ----------------------------------------------------------------------------
@@ -427,11 +496,12 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     int status = PIT_OK, iters = 0, passes = 0;
     const bool carry_ok = (f == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
     // MIXED: carried initial residual of the next step (see the file comment).
-    // FP32 residual copies hold r * rsc, rsc = 1 (or 1 / ||b||, applied in FP64
-    // before the conversion, when ||b|| is so small or large that FP32 would
-    // under- or overflow).
+    // FP32 copies of FP64 vectors are scaled by a power of two 2^k chosen from
+    // ||b|| (exact, folded into the conversion), so they stay inside the normal
+    // FP32 range for states of any magnitude.
     bool have_r0 = false;
-    double rn0_c = 0.0, bb_c = 0.0, rsc_c = 0.0;
+    double rn0_c = 0.0, bb_c = 0.0;
+    int kr_c = 0;
     float *rv = f32 + ld, *pv = f32 + 2 * ld, *sv = f32 + 3 * ld, *wv = f32 + 4 * ld, *tv = f32 + 5 * ld;
 
     for (int step = 1; step <= a.nsteps; ++step) {
@@ -482,7 +552,8 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
             } else {
                 for (int j = tid; j < n; j += nt) bvec[j] = f ? x[j] + dt * f[j] : x[j];
             }
-            double rn2, bb, rsc;
+            double rn2, bb;
+            int kr;  // the stored FP32 residual rv holds r 2^kr
             if (have_r0) {
                 // r0 = x_{s-1} - A x_{s-1}, computed by the last check of the
                 // previous step into wv (OU: tv)
@@ -490,26 +561,18 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 else { float *t_ = rv; rv = wv; wv = t_; }
                 rn2 = rn0_c;
                 bb = bb_c;
-                rsc = rsc_c;
+                kr = kr_c;
             } else {
                 double acc[1] = {0.0};
                 for (int j = tid; j < n; j += nt) acc[0] += bvec[j] * bvec[j];
                 R64.template sum<1>(acc);  // also: bvec and x complete
                 bb = acc[0];
-                rsc = fp32_safe(bb) ? 1.0 : 1.0 / sqrt(bb);
+                kr = scale_exp(bb);
                 acc[0] = 0.0;
-                if (rsc == 1.0) {
-                    for (int j = tid; j < n; j += nt) {
-                        const double rj = bvec[j] - A64(x, j);
-                        rv[j] = (float)rj;
-                        acc[0] += rj * rj;
-                    }
-                } else {
-                    for (int j = tid; j < n; j += nt) {
-                        const double rj = bvec[j] - A64(x, j);
-                        rv[j] = (float)(rj * rsc);
-                        acc[0] += rj * rj;
-                    }
+                for (int j = tid; j < n; j += nt) {
+                    const double rj = bvec[j] - A64(x, j);
+                    rv[j] = to_f32(rj, kr);
+                    acc[0] += rj * rj;
                 }
                 R64.template sum<1>(acc);
                 ++passes;
@@ -517,7 +580,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
             }
             have_r0 = false;
             const double stop2 = a.rtol * a.rtol * bb;
-            const double bsc = fp32_safe(bb) ? 1.0 : 1.0 / sqrt(bb);
+            const int ks = scale_exp(bb);  // FP32 copies of this step: value 2^ks, ||b|| 2^ks in [1, 2)
             int st_step = PIT_OK;
             bool carried = false;
             for (int pass = 0;; ++pass) {
@@ -529,21 +592,25 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                         else { float *t_ = rv; rv = wv; wv = t_; }
                         rn0_c = rn2;
                         bb_c = bb;
-                        rsc_c = rsc;
+                        kr_c = kr;
                         carried = true;
                     }
                     break;
                 }
                 if (pass >= a.ir_maxit) { st_step = PIT_ERR_NOCONV; break; }
-                const double rnorm = sqrt(rn2);
-                const float inv = (float)(1.0 / (rnorm * rsc));  // stored r * rsc -> unit norm
+                // Scalars in FP32 on the scaled residual: rv 2^-kn has squared
+                // norm R2n = ||r||^2 4^(kr - kn) in [1, 4); the power of two
+                // makes the rescaling of the correction exact.
+                const int kn = min(max(kr - scale_exp(rn2), -120), 120);
+                const float inv = __uint_as_float((unsigned)(127 - kn) << 23);  // 2^-kn
+                const float R2n = to_f32(rn2, 2 * (kr - kn));
+                const float want = 0.5f * sqrtf(to_f32(stop2, 2 * (kr - kn)) / R2n);
+                const float tgt = want > a.inner_rtol ? want : (float)a.inner_rtol;
+                const float stop32 = tgt * tgt * R2n;
                 for (int j = tid; j < n; j += nt) {
                     rv[j] *= inv;
                     e[j] = 0.0f;
                 }
-                const double want = 0.5 * sqrt(stop2 / rn2);
-                const float tgt = (float)(want > (double)a.inner_rtol ? want : (double)a.inner_rtol);
-                const float stop32 = tgt * tgt;
                 int st, k;
                 if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, e, rv, pv, sv, wv, tv, R32, stop32, a.maxit, st);
                 else if constexpr (OP == PIT_OP_HEAT) k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
@@ -551,49 +618,38 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 iters += k;
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
                 // a stalled or broken-down inner solve still gives a usable
-                // correction; the FP64 residual decides
-                for (int j = tid; j < n; j += nt) x[j] += (double)e[j] * rnorm;
+                // correction; the FP64 residual decides.  x += e 2^(kn - kr)
+                const double cs = pow2d(kn - kr);
+                for (int j = tid; j < n; j += nt) x[j] = fma(to_f64(e[j], 0), cs, x[j]);
                 __syncthreads();  // x complete
-                // FP64 check: r = b - A x, and (no forcing) the next step's r0 = x - A x
+                // FP64 check: r = b - A x (norm in FP64), and (no forcing) the
+                // next step's r0 = x - A x with the norms of r0 and of x (the
+                // next right-hand side) accumulated from their FP32 copies
                 float *cv = (OP == PIT_OP_OU) ? tv : wv;
-                double acc[3] = {0.0, 0.0, 0.0};
-                if (bsc == 1.0) {
-                    for (int j = tid; j < n; j += nt) {
-                        const double xj = x[j];
-                        const double Ax = A64(x, j);
-                        const double rj = bvec[j] - Ax;
-                        rv[j] = (float)rj;
-                        acc[0] += rj * rj;
-                        if (carry_ok) {
-                            const double cj = xj - Ax;
-                            cv[j] = (float)cj;
-                            acc[1] += cj * cj;
-                            acc[2] += xj * xj;
-                        }
-                    }
-                } else {
-                    for (int j = tid; j < n; j += nt) {
-                        const double xj = x[j];
-                        const double Ax = A64(x, j);
-                        const double rj = bvec[j] - Ax;
-                        rv[j] = (float)(rj * bsc);
-                        acc[0] += rj * rj;
-                        if (carry_ok) {
-                            const double cj = xj - Ax;
-                            cv[j] = (float)(cj * bsc);
-                            acc[1] += cj * cj;
-                            acc[2] += xj * xj;
-                        }
+                double accd[1] = {0.0};
+                float accf[2] = {0.0f, 0.0f};
+                for (int j = tid; j < n; j += nt) {
+                    const double xj = x[j];
+                    const double Ax = A64(x, j);
+                    const double rj = bvec[j] - Ax;
+                    rv[j] = to_f32(rj, ks);
+                    accd[0] += rj * rj;
+                    if (carry_ok) {
+                        const float cj = to_f32(xj - Ax, ks);
+                        const float xf = to_f32(xj, ks);
+                        cv[j] = cj;
+                        accf[0] += cj * cj;
+                        accf[1] += xf * xf;
                     }
                 }
-                R64.template sum<3>(acc);
+                sum_mixed<1, 2>(R64, accd, R32, accf);
                 ++passes;
-                rn2 = acc[0];
-                rsc = bsc;
+                rn2 = accd[0];
+                kr = ks;
                 if (carry_ok) {
-                    rn0_c = acc[1];
-                    bb_c = acc[2];
-                    rsc_c = bsc;
+                    rn0_c = to_f64(accf[0], -2 * ks);
+                    bb_c = to_f64(accf[1], -2 * ks);
+                    kr_c = ks;
                     carried = true;
                 }
             }

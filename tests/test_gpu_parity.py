@@ -160,6 +160,21 @@ def test_sequential_matches_oracle_workload1(prec):
     assert rel(uT, ref) < (1e-10 if prec == B.PIT_PREC_FP64 else 1e-9)
 
 
+@pytest.mark.parametrize("name", ["varheat3d", "ou4d"])
+@pytest.mark.parametrize("scale", [1e-120, 1e-30, 1e30, 1e120])
+def test_mixed_steps_scale_with_the_state(name, scale):
+    # Phi is linear: Phi^k(s u) = s Phi^k(u).  The mixed form keeps its FP32
+    # copies in range by power-of-two scaling, so states far outside the FP32
+    # range give the same relative accuracy as states of unit size.
+    P, O, dt = pair(name)
+    u0 = W.random_vector(303, P.n_total)
+    ref = O.sequential(u0, dt, 6, rtol=1e-15)
+    uT = np.empty(P.n_total)
+    P.sequential_solve(u0 * scale, dt, 6, uT, B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-12, ir_maxit=30))
+    assert np.all(np.isfinite(uT))
+    assert rel(uT / scale, ref) < 1e-9
+
+
 MG_CASES = {
     # name: (workload, n, nsteps, m, levels, coarse)
     "w1": (1, 5, 64, 4, 2, B.PIT_COARSE_IMPLICIT),
