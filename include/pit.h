@@ -120,8 +120,17 @@ typedef struct {
     int status;           /* worst item status as a pit_status                  */
 } pit_phi_stats;
 
-/* MGRIT options (Sec. 3.3, Alg. 2 with FCF relaxation; Sec. 4.1 stopping rule:
- * a grid stops when all its C-point residual l2 norms are <= tol).
+/* Relaxation of the finest MGRIT level (Sec. 3.3.1 defines F- and C-relaxation;
+ * the experiments of Sec. 4.1 use FCF).  Coarser levels of a three-level
+ * hierarchy always use FCF. */
+typedef enum {
+    PIT_RELAX_FCF = 0, /* F-, C- and F-relaxation before the residual (Sec. 4.1) */
+    PIT_RELAX_F = 1    /* F-relaxation only: half the fine steps per cycle, exactness
+                          advances one coarse interval per cycle instead of two    */
+} pit_relax;
+
+/* MGRIT options (Sec. 3.3, Alg. 2; Sec. 4.1 stopping rule: a grid stops when
+ * all its C-point residual l2 norms are <= tol).
  * nsteps must be a multiple of m^(levels-1). */
 typedef struct {
     double t0, t1;
@@ -137,6 +146,11 @@ typedef struct {
                              that crs.rtol is relative to the correction            */
     pit_solve_opts fine;  /* options of every fine-level Phi solve   */
     pit_solve_opts crs;   /* options of every coarse-level Phi solve */
+    int relax;            /* pit_relax of the finest level           */
+    int lanes;            /* concurrent grid groups (Alg. 3 runs MGRIT per grid): 0 = library
+                             default (6), 1 = all grids in lockstep; more than one lane is
+                             used with the correction form and the implicit coarse step only,
+                             other forms run as one lane                                    */
 } pit_mgrit_opts;
 
 typedef struct {
@@ -286,8 +300,10 @@ pit_status pit_combine(pit_problem_t p, const double *u, int n_pts, const double
  * pit_profile_read synchronises the stream and returns, since the last
  * enable, per kernel family: launches, summed device milliseconds, and for
  * the backward-Euler kernels the work done (Krylov iterations and refinement
- * passes weighted by grid nodes).  Family 0 = backward-Euler solver,
- * 1 = MGRIT residual norms, 2 = combination sum, 3 = other. */
+ * passes weighted by grid nodes).  Family 0 = backward-Euler solver on
+ * batches of 8 or more entries per grid (relaxation), 1 = backward-Euler
+ * solver on fewer (sequential sweeps, time stepping), 2 = combination sum,
+ * 3 = other. */
 typedef struct {
     long long launches[4];
     double ms[4];

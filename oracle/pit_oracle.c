@@ -26,7 +26,8 @@
  *   or_cg / or_bicgstab            dense direct solve (numpy) on tiny grids
  *   or_phi / or_sequential         heat closed form per mode; OU Gaussian trend
  *   or_mgrit                       converged = sequential; FCF exactness after
- *                                  ceil(Nc/2) cycles; one cycle with Phi^m
+ *                                  ceil(Nc/2) cycles, F exactness after Nc
+ *                                  cycles; one cycle with Phi^m
  *   or_combine                     interpolation property at sparse-grid nodes
  *   or_initial                     direct evaluation at node coordinates
  *   or_net_forward / backward      finite-difference gradient check; linear
@@ -705,6 +706,7 @@ typedef struct {
     int maxit;
     int coarse_kind;    /* 0 implicit BE, 1 m exact fine steps, 2 learned net */
     const double *theta;/* net parameters (coarse_kind 2) */
+    int relax_f;        /* 1: F-relaxation on the finest level, 0: FCF */
     int status;
 } mg_ctx;
 
@@ -747,11 +749,13 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
      * C-point jm over the F-points jm+1 .. jm+m-1. */
     for (int j = 0; j < Nc; ++j)
         for (int i = 1; i < m; ++i) mg_step(C, level, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
-    /* C-relaxation: one step into every C-point. */
-    for (int j = 1; j <= Nc; ++j) mg_step(C, level, V(j * m - 1), GF(j * m), V(j * m));
-    /* F-relaxation again. */
-    for (int j = 0; j < Nc; ++j)
-        for (int i = 1; i < m; ++i) mg_step(C, level, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
+    if (!(level == 0 && C->relax_f)) {
+        /* C-relaxation: one step into every C-point. */
+        for (int j = 1; j <= Nc; ++j) mg_step(C, level, V(j * m - 1), GF(j * m), V(j * m));
+        /* F-relaxation again (FCF, Sec. 4.1). */
+        for (int j = 0; j < Nc; ++j)
+            for (int i = 1; i < m; ++i) mg_step(C, level, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
+    }
     /* C-point residual r_j = Phi(v_{jm-1}) + g_{jm} - v_{jm}; utilde_j keeps
      * Phi(v_{jm-1}) + g_{jm}. */
     double *ut = malloc(sizeof(double) * (size_t)(Nc + 1) * n);
@@ -798,7 +802,8 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
  * = residual measured in cycle k (when non-NULL). */
 int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev, double tol,
              int maxit, int coarse_kind, const double *theta, double rtol, int krylov_maxit,
-             double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */)
+             double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */,
+             int relax_f /* 1: F-relaxation on the finest level instead of FCF */)
 {
     or_problem *P = (or_problem *)vp;
     if (m < 2 || nlev < 2) return OR_EINVAL;
@@ -812,7 +817,7 @@ int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev,
         long long n = P->off[g + 1] - P->off[g];
         double *v = malloc(sizeof(double) * (size_t)(nsteps + 1) * n);
         for (int k = 0; k <= nsteps; ++k) memcpy(v + (long long)k * n, u0 + P->off[g], sizeof(double) * n);
-        mg_ctx C = {P, g, dt, m, nlev, rtol, krylov_maxit, coarse_kind, theta, OR_OK};
+        mg_ctx C = {P, g, dt, m, nlev, rtol, krylov_maxit, coarse_kind, theta, relax_f, OR_OK};
         int it = 0, conv = 0;
         while (it < maxit) {
             double r = mg_cycle(&C, 0, nsteps, v, NULL);

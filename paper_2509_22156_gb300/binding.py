@@ -30,6 +30,7 @@ STATUS_NAMES = {0: "PIT_OK", 1: "PIT_ERR_INVALID_ARG", 2: "PIT_ERR_CUDA", 3: "PI
 PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU = 0, 1, 2
 PIT_PREC_FP64, PIT_PREC_MIXED = 0, 1
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
+PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
 
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
             "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",
@@ -58,7 +59,8 @@ class pit_phi_stats(ctypes.Structure):
 class pit_mgrit_opts(ctypes.Structure):
     _fields_ = [("t0", ctypes.c_double), ("t1", ctypes.c_double), ("nsteps", ctypes.c_int), ("m", ctypes.c_int),
                 ("levels", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts)]
+                ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts),
+                ("relax", ctypes.c_int), ("lanes", ctypes.c_int)]
 
 
 class pit_mgrit_stats(ctypes.Structure):
@@ -172,10 +174,11 @@ def bf16_round(w) -> np.ndarray:
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
-               crs=None, fas=False) -> pit_mgrit_opts:
+               crs=None, fas=False, relax=None, lanes=0) -> pit_mgrit_opts:
     fine = fine or solve_opts()
     crs = crs or fine
-    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs)
+    relax = PIT_RELAX_FCF if relax is None else relax
+    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes)
 
 
 class Problem:

@@ -70,6 +70,27 @@ struct DBuf {
 
 }  // namespace
 
+// A lane of the MGRIT driver: a subset of the grids with its own streams,
+// launch plan and convergence state.  Grids are independent until the
+// combination (Alg. 3), so the cycles of several lanes run concurrently and
+// the latency-bound coarse sweep of one lane overlaps the relaxation of the
+// others.
+struct pit_lane {
+    std::vector<int> grids;
+    cudaStream_t s = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
+    bool planned[2] = {false, false};
+    int n_cls[2][2] = {{0, 0}, {0, 0}};
+    int *d_order_cls[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int *d_act = nullptr;     // G flags, zero outside the lane
+    int *h_act = nullptr;     // pinned, G
+    double *h_res = nullptr;  // pinned, G x Nc
+    size_t h_res_cap = 0;
+    // per-solve state
+    int it = 0, n_active = 0;
+    bool busy = false;
+};
+
 struct pit_problem {
     pit_problem_desc desc;
     cudaStream_t stream = nullptr;
@@ -96,6 +117,7 @@ struct pit_problem {
     bool planned[2] = {false, false};
     int n_cls[2][2] = {{0, 0}, {0, 0}};
     int *d_order_cls[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    std::vector<int> h_order_cls[2][2];
     size_t smem_cls[2][2] = {{0, 0}, {0, 0}};
     size_t smem_need[2] = {0, 0};    // class 0 (used by the allocation-free step)
     int threads[2][2][2] = {};       // [prec][wide batch][class]; 0 = not tuned yet
@@ -103,6 +125,7 @@ struct pit_problem {
     cudaStream_t side = nullptr;     // second stream: the large-grid class runs beside class 0
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf w_xg;                       // FP64 state of class-1 items
+    std::vector<pit_lane> lanes;     // MGRIT lanes (built on first use)
     // workspaces
     DBuf w_in, w_out, w_pts, w_u, w_prm;
     DBuf m_U, m_R, m_UT, m_GC, m_res, m_UT1, m_GC1, m_T0, m_act, w_tune, m_Z, m_E;
@@ -137,8 +160,9 @@ int ptr_is_device(const void *p)
 // Records a CUDA event pair around the next launch when profiling is on.
 struct ProfScope {
     pit_problem *P;
+    cudaStream_t s;
     long long idx = -1;
-    ProfScope(pit_problem *P_, int family) : P(P_)
+    ProfScope(pit_problem *P_, int family, cudaStream_t s_ = nullptr) : P(P_), s(s_ ? s_ : P_->stream)
     {
         if (!P->prof_on) return;
         while (P->ev_pool.size() < P->ev_used + 2) {
@@ -149,11 +173,11 @@ struct ProfScope {
         idx = (long long)P->ev_used;
         P->ev_used += 2;
         P->prof_recs.push_back({family, (size_t)idx});
-        cudaEventRecord(P->ev_pool[idx], P->stream);
+        cudaEventRecord(P->ev_pool[idx], s);
     }
     ~ProfScope()
     {
-        if (idx >= 0) cudaEventRecord(P->ev_pool[idx + 1], P->stream);
+        if (idx >= 0) cudaEventRecord(P->ev_pool[idx + 1], s);
     }
 };
 
@@ -241,6 +265,7 @@ pit_status plan(pit_problem *P, int prec)
     }
     for (int c = 0; c < 2; ++c) {
         P->n_cls[prec][c] = (int)cls[c].size();
+        P->h_order_cls[prec][c] = cls[c];
         P->smem_cls[prec][c] = need[c];
         if (!cls[c].empty()) {
             CU(cudaMalloc(&P->d_order_cls[prec][c], sizeof(int) * cls[c].size()));
@@ -384,39 +409,46 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     return PIT_OK;
 }
 
-// One multi-step launch of every grid: class 0 on the problem's stream and,
-// when present, class 1 (state in global memory) concurrently on the side
-// stream, joined before returning.
-pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
+// One multi-step launch of every grid (of a lane, when given): class 0 on the
+// problem's (lane's) stream and, when present, class 1 (state in global
+// memory) concurrently on the side stream, joined before returning.
+pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active,
+                     const pit_lane *L = nullptr)
 {
     const int prec = o.prec == PIT_PREC_MIXED ? MIXED : PLAIN;
     TRY(plan(P, prec));
     if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
+    if (L && !L->planned[prec]) return fail(PIT_ERR_INVALID_ARG, "lane without a launch plan");
     const bool wide = c.nb >= 8;
-    const bool two = P->n_cls[prec][1] > 0;
-    if (two) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * 2));
+    const int n0 = L ? L->n_cls[prec][0] : P->n_cls[prec][0];
+    const int n1 = L ? L->n_cls[prec][1] : P->n_cls[prec][1];
+    const bool two = n1 > 0;
+    // (a lane's workspaces and CTA sizes are prepared before its first launch)
+    if (two && !L) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * 2));
     for (int cls = 0; cls < 2; ++cls)
-        if (P->n_cls[prec][cls] > 0) TRY(tune(P, prec, wide, cls, o, c, active));
+        if (P->n_cls[prec][cls] > 0 && !L) TRY(tune(P, prec, wide, cls, o, c, active));
+    cudaStream_t s0 = L ? L->s : P->stream, s1 = L ? L->side : P->side;
+    cudaEvent_t ef = L ? L->fork : P->ev_fork, ej = L ? L->join : P->ev_join;
     StepArgs a = make_args(P, o, c, active);
-    ProfScope ps(P, 0);
+    ProfScope ps(P, wide ? 0 : 1, s0);
     if (two) {
-        CU(cudaEventRecord(P->ev_fork, P->stream));
-        CU(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+        CU(cudaEventRecord(ef, s0));
+        CU(cudaStreamWaitEvent(s1, ef, 0));
         StepArgs b = a;
-        b.order = P->d_order_cls[prec][1];
-        b.n_order = P->n_cls[prec][1];
+        b.order = L ? L->d_order_cls[prec][1] : P->d_order_cls[prec][1];
+        b.n_order = n1;
         b.xg = P->w_xg.d();
         b.bg = b.xg + (long long)c.nb * P->ntot;
-        CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][1], P->smem_cls[prec][1], P->side, true));
+        CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][1], P->smem_cls[prec][1], s1, true));
     }
-    if (P->n_cls[prec][0] > 0) {
-        a.order = P->d_order_cls[prec][0];
-        a.n_order = P->n_cls[prec][0];
-        CU(launch_steps(prec, a, P->threads[prec][wide ? 1 : 0][0], P->smem_cls[prec][0], P->stream, false));
+    if (n0 > 0) {
+        a.order = L ? L->d_order_cls[prec][0] : P->d_order_cls[prec][0];
+        a.n_order = n0;
+        CU(launch_steps(prec, a, P->threads[prec][wide ? 1 : 0][0], P->smem_cls[prec][0], s0, false));
     }
     if (two) {
-        CU(cudaEventRecord(P->ev_join, P->side));
-        CU(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+        CU(cudaEventRecord(ej, s1));
+        CU(cudaStreamWaitEvent(s0, ej, 0));
     }
     return PIT_OK;
 }
@@ -627,6 +659,21 @@ pit_status pit_problem_destroy(pit_problem_t P)
 {
     if (!P) return PIT_OK;
     cudaStreamSynchronize(P->stream);
+    for (pit_lane &L : P->lanes) {
+        if (L.s) cudaStreamSynchronize(L.s);
+        if (L.side) cudaStreamSynchronize(L.side);
+        for (int p = 0; p < 2; ++p)
+            for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
+        cudaFree(L.d_act);
+        cudaFreeHost(L.h_act);
+        cudaFreeHost(L.h_res);
+        if (L.s) cudaStreamDestroy(L.s);
+        if (L.side) cudaStreamDestroy(L.side);
+        if (L.fork) cudaEventDestroy(L.fork);
+        if (L.join) cudaEventDestroy(L.join);
+        if (L.done) cudaEventDestroy(L.done);
+    }
+    P->lanes.clear();
     cudaFree(P->d_order);
     cudaFree(P->d_masks);
     for (int p = 0; p < 2; ++p)
@@ -796,19 +843,24 @@ pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, in
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// MGRIT driver (Sec. 3.3, Alg. 2 with FCF relaxation; Alg. 3 per grid).
+// MGRIT driver (Sec. 3.3, Alg. 2 with FCF or F relaxation; Alg. 3 per grid).
 //
 // Level 0 stores C-points only (Sec. 3.3.2): U[j] = u_{jm}, j = 0..Nc.  One
-// cycle is four launches of the multi-step kernel:
+// FCF cycle is three or four launches of the multi-step kernel:
 //   FC    R[j+1]  = Phi^m(U[j])            (F-relaxation + C-relaxation)
 //   F     UT[j]   = Phi^m(R[j]),  res[j] = ||UT[j] - R[j+1]||   (F-relaxation,
 //                  C-point residual r_{j+1} = Phi(u_{(j+1)m-1}) - u_{(j+1)m})
+// then, with a linear coarse propagator (correction form, the default):
+//   sweep E[j+1]  = Phi_c(E[j]) + r_{j+1}, E[0] = 0, U[j+1] = R[j+1] + E[j+1]
+//                  (the F launch writes r_{j+1} in place of UT[j])
+// or, in the FAS form of Alg. 2 as printed (learned or exact Phi_c):
 //   FAS   GC[j]   = UT[j] - Phi_c(R[j])    (restricted residual + Phi_c of the
 //                  restricted solution: the coarse right-hand side of Alg. 2)
 //   sweep U[j+1]  = Phi_c(U[j]) + GC[j]    (coarse solve; its result is the
-//                  corrected C-point, the F-points follow from the next FC)
-// R[0] = U[0] = u0.  With three levels the sweep is replaced by one two-level
-// cycle of the level-1 problem (points R[0..Nc], forcing GC), written into U.
+//                  corrected C-point, the F-points follow from the next cycle)
+// R[0] = U[0] = u0.  F-relaxation drops the FC launch: the relaxed C-points
+// are U itself.  With three levels the sweep is replaced by one two-level FCF
+// cycle of the level-1 problem, written into U.
 namespace {
 
 struct Mg {
@@ -817,7 +869,9 @@ struct Mg {
     double dt;
     long long nt;
     const int *active;
-    bool learned;  // level-1 coarse propagator is the network
+    bool learned;    // level-1 coarse propagator is the network
+    pit_lane *L;     // lane of the cycle; nullptr: every grid on the problem's stream
+    cudaStream_t s;  // stream of the cycle
 };
 
 // Coarse propagator of level 1: backward Euler with m dt, or m fine steps.
@@ -838,25 +892,24 @@ pit_status run_coarse(Mg &M, StepCall c, int level)
 {
     if (level == 1 && M.learned) {
         c.dt = M.dt * M.o->m;
-        return run_net(M.P, c, M.active);
+        return run_net(M.P, c, M.active);  // (the learned form runs without lanes)
     }
     coarse_call(M, c, level);
-    return run_steps(M.P, M.o->crs, c, M.active);
+    return run_steps(M.P, M.o->crs, c, M.active, M.L);
 }
 
 // Two-level cycle of level 1 in a three-level hierarchy: level-1 points are V
 // (read; stride vstride, 0 for a constant initial guess) -> W (written),
 // Nc1 = N1/m intervals, forcing of level-1 point k is F[k-1]; the level-2
-// problem is solved by a sequential sweep.
+// problem is solved by a sequential sweep.  W[0] must equal V[0] on entry
+// when the cycle runs on a lane (the copy below covers every grid).
 pit_status mg_level1_cycle(Mg &M, const double *V, long long vstride, double *W, int N1, const double *F)
 {
     pit_problem *P = M.P;
     const int m = M.o->m, Nc = N1 / m;
     const long long nt = M.nt, sm = (long long)m * nt;
-    CU(P->m_UT1.ensure(sizeof(double) * nt * Nc));
-    CU(P->m_GC1.ensure(sizeof(double) * nt * Nc));
     double *UT1 = P->m_UT1.d(), *GC1 = P->m_GC1.d();
-    if (W != V) CU(cudaMemcpyAsync(W, V, sizeof(double) * nt, cudaMemcpyDeviceToDevice, P->stream));
+    if (W != V && !M.L) CU(cudaMemcpyAsync(W, V, sizeof(double) * nt, cudaMemcpyDeviceToDevice, M.s));
     // FC: F-points and C-point of every interval from the old C-points
     StepCall fc;
     fc.nb = Nc;
@@ -908,6 +961,252 @@ pit_status mg_level1_cycle(Mg &M, const double *V, long long vstride, double *W,
     return PIT_OK;
 }
 
+// Enqueues one MGRIT cycle of the active grids (of the lane) on M.s:
+// relaxation, C-point residual norms (copied to h_res, G x Nc), coarse
+// correction of the C-points.  corr: linear coarse problem solved for the
+// correction; otherwise the FAS form of Alg. 2.
+pit_status mg_cycle(Mg &M, int Nc, bool corr, double *h_res)
+{
+    pit_problem *P = M.P;
+    const pit_mgrit_opts *o = M.o;
+    const int G = P->G, m = o->m;
+    const long long nt = M.nt;
+    const size_t vb = sizeof(double) * nt;
+    double *U = P->m_U.d(), *R = P->m_R.d(), *UT = P->m_UT.d(), *GC = P->m_GC.d(), *res = P->m_res.d();
+    // F-relaxation alone leaves the C-points as they are: the relaxed C-points
+    // are U itself, and the correction updates U in place
+    const bool relax_f = o->relax == PIT_RELAX_F;
+    double *Rx = relax_f ? U : R;
+    StepCall fc;  // FC relaxation
+    fc.dt = M.dt;
+    fc.nb = Nc;
+    fc.nsteps = m;
+    fc.in = U;
+    fc.is = nt;
+    fc.out_last = R + nt;
+    fc.ols = nt;
+    if (!relax_f) TRY(run_steps(P, o->fine, fc, M.active, M.L));
+    StepCall fr = fc;  // F relaxation, utilde and the C-point residuals
+    fr.in = Rx;
+    fr.cmp = Rx + nt;
+    fr.cs = nt;
+    fr.norms = res;
+    if (corr) {
+        fr.out_last = GC;  // r_{j+1} = utilde_{j+1} - u_{(j+1)m}
+        fr.h = Rx + nt;
+        fr.hs = nt;
+        fr.hscale = -1.0;
+    } else {
+        fr.out_last = UT;
+    }
+    TRY(run_steps(P, o->fine, fr, M.active, M.L));
+    CU(cudaMemcpyAsync(h_res, res, sizeof(double) * G * Nc, cudaMemcpyDeviceToHost, M.s));
+    if (corr) {
+        if (o->levels == 3) {
+            // level-1 problem e_k = Phi_c(e_{k-1}) + r_k, e_0 = 0, by one
+            // two-level cycle from e = 0; then u_{jm} = relaxed + e_j
+            TRY(mg_level1_cycle(M, P->m_Z.d(), 0, P->m_E.d(), Nc, GC));
+            CU(launch_add_states(P->d_grids, G, nt, Nc, Rx + nt, P->m_E.d() + nt, U + nt, M.active, M.s));
+        } else {
+            StepCall sw;  // e_{j+1} = Phi_c(e_j) + r_{j+1}; stored as u = relaxed + e
+            sw.nb = 1;
+            sw.nsteps = Nc;
+            sw.in = P->m_Z.d();
+            sw.is = nt;
+            sw.g = GC;
+            sw.gst = nt;
+            sw.hstep = Rx + nt;  // read and written by the same thread when Rx = U
+            sw.hsst = nt;
+            sw.out_steps = U + nt;
+            sw.osst = nt;
+            sw.out_last = U + (long long)Nc * nt;
+            sw.ols = nt;
+            TRY(run_coarse(M, sw, 1));
+        }
+        return PIT_OK;
+    }
+    StepCall gc;  // coarse right-hand side
+    gc.nb = Nc;
+    gc.nsteps = 1;
+    gc.in = Rx;
+    gc.is = nt;
+    gc.out_last = GC;
+    gc.ols = nt;
+    gc.scale = -1.0;
+    gc.h = UT;
+    gc.hs = nt;
+    TRY(run_coarse(M, gc, 1));
+    if (o->levels == 3) {
+        // the level-1 cycle reads the relaxed C-points while it writes U:
+        // with F-relaxation they are U itself, so take a copy
+        if (relax_f) CU(cudaMemcpyAsync(R + nt, U + nt, vb * Nc, cudaMemcpyDeviceToDevice, M.s));
+        TRY(mg_level1_cycle(M, R, nt, U, Nc, GC));
+    } else if (o->coarse == PIT_COARSE_EXACT) {
+        for (int j = 0; j < Nc; ++j) {
+            StepCall sw;
+            sw.nb = 1;
+            sw.nsteps = 1;
+            sw.in = U + (long long)j * nt;
+            sw.is = nt;
+            sw.out_last = U + (long long)(j + 1) * nt;
+            sw.ols = nt;
+            sw.h = GC + (long long)j * nt;
+            sw.hs = nt;
+            coarse_call(M, sw, 1);
+            TRY(run_steps(P, o->crs, sw, M.active, M.L));
+        }
+    } else {
+        StepCall sw;  // sequential coarse sweep, one CTA per grid
+        sw.nb = 1;
+        sw.nsteps = Nc;
+        sw.in = U;
+        sw.is = nt;
+        sw.g = GC;
+        sw.gst = nt;
+        // Krylov initial guess of Phi_c(u_j): Phi_c(r_j) = UT[j] - GC[j],
+        // computed by the FAS launch (r_j = relaxed C-point; equal to u_j
+        // once MGRIT has converged there)
+        sw.guess = UT;
+        sw.gust = nt;
+        sw.out_steps = U + nt;
+        sw.osst = nt;
+        sw.out_last = U + (long long)Nc * nt;
+        sw.ols = nt;
+        if (M.learned) sw.guess = nullptr;  // explicit: no Krylov guess
+        TRY(run_coarse(M, sw, 1));
+    }
+    return PIT_OK;
+}
+
+// Stopping rule of Sec. 4.1 per grid on one cycle's residual norms (h_res,
+// G x Nc): a grid whose largest C-point residual is <= tol leaves the active
+// set.  Returns the largest norm over the listed grids (NaN propagates).
+double mg_evaluate(const double *h_res, int G, int Nc, const int *grids, int n_grids, int *h_act, double tol,
+                   int &n_active)
+{
+    double rmax = 0.0;
+    n_active = 0;
+    for (int q = 0; q < n_grids; ++q) {
+        const int g = grids ? grids[q] : q;
+        if (!h_act[g]) continue;
+        double r = 0.0;
+        for (int j = 0; j < Nc; ++j) {
+            const double v = h_res[(size_t)j * G + g];
+            if (!(v <= r)) r = v;  // NaN propagates
+        }
+        if (!(r <= rmax)) rmax = r;
+        if (r <= tol) h_act[g] = 0;
+        else ++n_active;
+    }
+    return rmax;
+}
+
+// K lanes over the grids, balanced by nodes (largest grid first to the lane
+// with the fewest nodes); each lane keeps the class lists of both precision
+// forms in the problem's decreasing-size order.
+pit_status lanes_prepare(pit_problem *P, int K, int Nc)
+{
+    if ((int)P->lanes.size() != K) {
+        for (pit_lane &L : P->lanes) {
+            cudaStreamSynchronize(L.s);
+            cudaStreamSynchronize(L.side);
+            for (int p = 0; p < 2; ++p)
+                for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
+            cudaFree(L.d_act);
+            cudaFreeHost(L.h_act);
+            cudaFreeHost(L.h_res);
+            cudaStreamDestroy(L.s);
+            cudaStreamDestroy(L.side);
+            cudaEventDestroy(L.fork);
+            cudaEventDestroy(L.join);
+            cudaEventDestroy(L.done);
+        }
+        P->lanes.assign(K, pit_lane());
+        std::vector<int> order(P->G);
+        for (int g = 0; g < P->G; ++g) order[g] = g;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P->info[a].n > P->info[b].n; });
+        std::vector<long long> load(K, 0);
+        std::vector<int> lane_of(P->G, 0);
+        for (int g : order) {
+            int best = 0;
+            for (int k = 1; k < K; ++k)
+                if (load[k] < load[best]) best = k;
+            load[best] += P->info[g].n;
+            lane_of[g] = best;
+            P->lanes[best].grids.push_back(g);
+        }
+        for (pit_lane &L : P->lanes) {
+            CU(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
+            CU(cudaStreamCreateWithFlags(&L.side, cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+            CU(cudaMalloc(&L.d_act, sizeof(int) * P->G));
+            CU(cudaMallocHost(&L.h_act, sizeof(int) * P->G));
+        }
+    }
+    for (int prec = 0; prec < 2; ++prec) {
+        if (!P->planned[prec]) continue;
+        for (int k = 0; k < K; ++k) {
+            pit_lane &L = P->lanes[k];
+            if (L.planned[prec]) continue;
+            std::vector<char> mine(P->G, 0);
+            for (int g : L.grids) mine[g] = 1;
+            for (int c = 0; c < 2; ++c) {
+                std::vector<int> lst;
+                for (int g : P->h_order_cls[prec][c])
+                    if (mine[g]) lst.push_back(g);
+                L.n_cls[prec][c] = (int)lst.size();
+                if (!lst.empty()) {
+                    CU(cudaMalloc(&L.d_order_cls[prec][c], sizeof(int) * lst.size()));
+                    CU(cudaMemcpy(L.d_order_cls[prec][c], lst.data(), sizeof(int) * lst.size(),
+                                  cudaMemcpyHostToDevice));
+                }
+            }
+            L.planned[prec] = true;
+        }
+    }
+    for (pit_lane &L : P->lanes) {
+        const size_t want = (size_t)P->G * Nc;
+        if (L.h_res_cap < want) {
+            if (L.h_res) cudaFreeHost(L.h_res);
+            L.h_res = nullptr;
+            L.h_res_cap = 0;
+            CU(cudaMallocHost(&L.h_res, sizeof(double) * want));
+            L.h_res_cap = want;
+        }
+    }
+    return PIT_OK;
+}
+
+// Workspaces and CTA sizes of every launch class a lane cycle uses, prepared
+// on the problem's stream before the lanes start (the autotuner times its
+// trial launches on that stream).
+pit_status lanes_prime(Mg &M, int Nc)
+{
+    pit_problem *P = M.P;
+    const pit_mgrit_opts *o = M.o;
+    const long long nt = M.nt;
+    struct Rep { const pit_solve_opts *so; int nb; double dt; };
+    Rep reps[3] = {{&o->fine, Nc, M.dt}, {&o->crs, 1, M.dt * o->m}, {&o->crs, Nc / o->m, M.dt * o->m}};
+    const int n_reps = o->levels == 3 ? 3 : 2;
+    for (int r = 0; r < n_reps; ++r) {
+        const int prec = reps[r].so->prec == PIT_PREC_MIXED ? MIXED : PLAIN;
+        TRY(plan(P, prec));
+        if (reps[r].nb <= 0) continue;
+        StepCall c;
+        c.dt = reps[r].dt;
+        c.nb = reps[r].nb;
+        c.nsteps = 1;
+        c.in = P->m_U.d();
+        c.is = nt;
+        if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * 2));
+        for (int cls = 0; cls < 2; ++cls)
+            if (P->n_cls[prec][cls] > 0) TRY(tune(P, prec, c.nb >= 8, cls, *reps[r].so, c, M.active));
+    }
+    return PIT_OK;
+}
+
 }  // namespace
 
 extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const pit_mgrit_opts *o, double *uT,
@@ -930,6 +1229,9 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     if (o->nsteps % div != 0) return fail(PIT_ERR_INVALID_ARG, "nsteps must be a multiple of m^(levels-1)");
     if (o->levels == 3 && o->coarse == PIT_COARSE_EXACT)
         return fail(PIT_ERR_UNSUPPORTED, "the exact coarse propagator is a two-level option");
+    if (o->relax != PIT_RELAX_FCF && o->relax != PIT_RELAX_F)
+        return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
+    if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     const int G = P->G, m = o->m, Nc = o->nsteps / m;
     const long long nt = P->ntot;
     const size_t vb = sizeof(double) * nt;
@@ -941,9 +1243,15 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     CU(P->m_act.ensure(sizeof(int) * G));
     CU(P->m_Z.ensure(vb));
     CU(cudaMemsetAsync(P->m_Z.p, 0, vb, P->stream));
-    if (o->levels == 3) CU(P->m_E.ensure(vb * (Nc + 1)));
+    if (o->levels == 3) {
+        CU(P->m_E.ensure(vb * (Nc + 1)));
+        CU(cudaMemsetAsync(P->m_E.p, 0, vb, P->stream));  // e_0 = 0 of the level-1 correction problem
+        const int Nc1 = Nc / m;
+        CU(P->m_UT1.ensure(sizeof(double) * nt * Nc1));
+        CU(P->m_GC1.ensure(sizeof(double) * nt * Nc1));
+    }
     P->h_res.resize((size_t)G * Nc);
-    double *U = P->m_U.d(), *R = P->m_R.d(), *UT = P->m_UT.d(), *GC = P->m_GC.d(), *res = P->m_res.d();
+    double *U = P->m_U.d(), *R = P->m_R.d();
     int *act = (int *)P->m_act.p;
     const double *src;
     TRY(stage_in(P, P->w_in, u0, nt, &src));
@@ -954,139 +1262,92 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     CU(cudaMemcpyAsync(act, P->h_act, sizeof(int) * G, cudaMemcpyHostToDevice, P->stream));
     TRY(reset_stats(P));
 
-    Mg M{P, o, (o->t1 - o->t0) / o->nsteps, nt, act, o->coarse == PIT_COARSE_LEARNED && P->net_accepted};
+    Mg M{P, o, (o->t1 - o->t0) / o->nsteps, nt, act, o->coarse == PIT_COARSE_LEARNED && P->net_accepted, nullptr,
+         P->stream};
     pit_mgrit_stats st;
     memset(&st, 0, sizeof(st));
     st.learned_used = M.learned ? 1 : 0;
     st.fallback = (o->coarse == PIT_COARSE_LEARNED && !M.learned) ? 1 : 0;
-    double r_prev = -1.0;
-    int n_active = G, it = 0;
-    while (n_active > 0 && it < o->maxit) {
-        StepCall fc;  // FC relaxation
-        fc.dt = M.dt;
-        fc.nb = Nc;
-        fc.nsteps = m;
-        fc.in = U;
-        fc.is = nt;
-        fc.out_last = R + nt;
-        fc.ols = nt;
-        TRY(run_steps(P, o->fine, fc, act));
-        // linear coarse propagator: solve the coarse problem for the correction
-        // (Sec. 3.3.1: Alg. 2's coarse system is linear here), so the coarse
-        // tolerance is relative to the correction, which vanishes as MGRIT
-        // converges; the learned one is nonlinear and keeps the FAS form
-        const bool corr = !M.learned && o->coarse != PIT_COARSE_EXACT && !o->fas;
-        StepCall fr = fc;  // F relaxation, utilde and the C-point residuals
-        fr.in = R;
-        fr.cmp = R + nt;
-        fr.cs = nt;
-        fr.norms = res;
-        if (corr) {
-            fr.out_last = GC;  // r_{j+1} = utilde_{j+1} - u_{(j+1)m}
-            fr.h = R + nt;
-            fr.hs = nt;
-            fr.hscale = -1.0;
-        } else {
-            fr.out_last = UT;
+    // linear coarse propagator: solve the coarse problem for the correction
+    // (Sec. 3.3.1: Alg. 2's coarse system is linear here), so the coarse
+    // tolerance is relative to the correction, which vanishes as MGRIT
+    // converges; the learned one is nonlinear and keeps the FAS form
+    auto corr_form = [&]() { return !M.learned && o->coarse != PIT_COARSE_EXACT && !o->fas; };
+    // lanes: the correction form with the implicit coarse step (no runtime
+    // switch of the coarse propagator), default six
+    int K = o->lanes == 0 ? 6 : o->lanes;
+    if (!corr_form() || o->coarse != PIT_COARSE_IMPLICIT) K = 1;
+    if (K > G) K = G;
+    int it = 0, n_active = G;
+    if (K > 1) {
+        TRY(lanes_prime(M, Nc));
+        TRY(lanes_prepare(P, K, Nc));
+        CU(cudaEventRecord(P->ev_fork, P->stream));
+        for (pit_lane &L : P->lanes) {
+            CU(cudaStreamWaitEvent(L.s, P->ev_fork, 0));
+            memset(L.h_act, 0, sizeof(int) * G);
+            for (int g : L.grids) L.h_act[g] = 1;
+            CU(cudaMemcpyAsync(L.d_act, L.h_act, sizeof(int) * G, cudaMemcpyHostToDevice, L.s));
+            L.it = 0;
+            L.n_active = (int)L.grids.size();
+            L.busy = true;
         }
-        TRY(run_steps(P, o->fine, fr, act));
-        CU(cudaMemcpyAsync(P->h_res.data(), res, sizeof(double) * G * Nc, cudaMemcpyDeviceToHost, P->stream));
-        if (corr) {
-            if (o->levels == 3) {
-                // level-1 problem e_k = Phi_c(e_{k-1}) + r_k, e_0 = 0, by one
-                // two-level cycle from e = 0; then u_{jm} = relaxed + e_j
-                TRY(mg_level1_cycle(M, P->m_Z.d(), 0, P->m_E.d(), Nc, GC));
-                CU(launch_add_states(P->d_grids, G, nt, Nc, R + nt, P->m_E.d() + nt, U + nt, act, P->stream));
-            } else {
-                StepCall sw;  // e_{j+1} = Phi_c(e_j) + r_{j+1}; stored as u = relaxed + e
-                sw.nb = 1;
-                sw.nsteps = Nc;
-                sw.in = P->m_Z.d();
-                sw.is = nt;
-                sw.g = GC;
-                sw.gst = nt;
-                sw.hstep = R + nt;
-                sw.hsst = nt;
-                sw.out_steps = U + nt;
-                sw.osst = nt;
-                sw.out_last = U + (long long)Nc * nt;
-                sw.ols = nt;
-                TRY(run_coarse(M, sw, 1));
+        auto enqueue = [&](pit_lane &L) -> pit_status {
+            Mg ML = M;
+            ML.active = L.d_act;
+            ML.L = &L;
+            ML.s = L.s;
+            TRY(mg_cycle(ML, Nc, true, L.h_res));
+            CU(cudaEventRecord(L.done, L.s));
+            return PIT_OK;
+        };
+        for (pit_lane &L : P->lanes) TRY(enqueue(L));
+        bool any = true;
+        while (any) {
+            any = false;
+            for (pit_lane &L : P->lanes) {
+                if (!L.busy) continue;
+                CU(cudaEventSynchronize(L.done));
+                int na = 0;
+                const double rmax = mg_evaluate(L.h_res, G, Nc, L.grids.data(), (int)L.grids.size(), L.h_act,
+                                                o->tol, na);
+                if (L.it < PIT_MAX_HIST && !(rmax <= st.res_hist[L.it])) st.res_hist[L.it] = rmax;
+                ++L.it;
+                L.n_active = na;
+                if (na > 0 && L.it < o->maxit && rmax == rmax) {
+                    CU(cudaMemcpyAsync(L.d_act, L.h_act, sizeof(int) * G, cudaMemcpyHostToDevice, L.s));
+                    TRY(enqueue(L));
+                    any = true;
+                } else {
+                    L.busy = false;
+                }
             }
-        } else {
-        StepCall gc;  // coarse right-hand side
-        gc.nb = Nc;
-        gc.nsteps = 1;
-        gc.in = R;
-        gc.is = nt;
-        gc.out_last = GC;
-        gc.ols = nt;
-        gc.scale = -1.0;
-        gc.h = UT;
-        gc.hs = nt;
-        TRY(run_coarse(M, gc, 1));
-        if (o->levels == 3) {
-            TRY(mg_level1_cycle(M, R, nt, U, Nc, GC));
-        } else if (o->coarse == PIT_COARSE_EXACT) {
-            for (int j = 0; j < Nc; ++j) {
-                StepCall sw;
-                sw.nb = 1;
-                sw.nsteps = 1;
-                sw.in = U + (long long)j * nt;
-                sw.is = nt;
-                sw.out_last = U + (long long)(j + 1) * nt;
-                sw.ols = nt;
-                sw.h = GC + (long long)j * nt;
-                sw.hs = nt;
-                coarse_call(M, sw, 1);
-                TRY(run_steps(P, o->crs, sw, act));
-            }
-        } else {
-            StepCall sw;  // sequential coarse sweep, one CTA per grid
-            sw.nb = 1;
-            sw.nsteps = Nc;
-            sw.in = U;
-            sw.is = nt;
-            sw.g = GC;
-            sw.gst = nt;
-            // Krylov initial guess of Phi_c(u_j): Phi_c(r_j) = UT[j] - GC[j],
-            // computed by the FAS launch (r_j = relaxed C-point; equal to u_j
-            // once MGRIT has converged there)
-            sw.guess = UT;
-            sw.gust = nt;
-            sw.out_steps = U + nt;
-            sw.osst = nt;
-            sw.out_last = U + (long long)Nc * nt;
-            sw.ols = nt;
-            if (M.learned) sw.guess = nullptr;  // explicit: no Krylov guess
-            TRY(run_coarse(M, sw, 1));
         }
-        }
-        CU(cudaStreamSynchronize(P->stream));
-        double rmax = 0.0;
         n_active = 0;
-        for (int g = 0; g < G; ++g) {
-            if (!P->h_act[g]) continue;
-            double r = 0.0;
-            for (int j = 0; j < Nc; ++j) {
-                const double v = P->h_res[(size_t)j * G + g];
-                if (!(v <= r)) r = v;  // NaN propagates
+        for (pit_lane &L : P->lanes) {
+            CU(cudaEventRecord(L.done, L.s));
+            CU(cudaStreamWaitEvent(P->stream, L.done, 0));
+            it = L.it > it ? L.it : it;
+            n_active += L.n_active;
+        }
+    } else {
+        double r_prev = -1.0;
+        while (n_active > 0 && it < o->maxit) {
+            TRY(mg_cycle(M, Nc, corr_form(), P->h_res.data()));
+            CU(cudaStreamSynchronize(P->stream));
+            const double rmax = mg_evaluate(P->h_res.data(), G, Nc, nullptr, G, P->h_act, o->tol, n_active);
+            if (it < PIT_MAX_HIST) st.res_hist[it] = rmax;
+            ++it;
+            // runtime judge of the learned coarse propagator: fall back to the
+            // implicit step when a cycle does not reduce the residual enough
+            if (M.learned && n_active > 0 && (!(rmax == rmax) || (r_prev > 0.0 && rmax > 0.9 * r_prev))) {
+                M.learned = false;
+                st.fallback = 1;
             }
-            if (!(r <= rmax)) rmax = r;
-            if (r <= o->tol) P->h_act[g] = 0;
-            else ++n_active;
+            r_prev = rmax;
+            if (n_active > 0) CU(cudaMemcpyAsync(act, P->h_act, sizeof(int) * G, cudaMemcpyHostToDevice, P->stream));
+            if (!(rmax == rmax)) break;  // NaN: stop at once
         }
-        if (it < PIT_MAX_HIST) st.res_hist[it] = rmax;
-        ++it;
-        // runtime judge of the learned coarse propagator: fall back to the
-        // implicit step when a cycle does not reduce the residual enough
-        if (M.learned && n_active > 0 && (!(rmax == rmax) || (r_prev > 0.0 && rmax > 0.9 * r_prev))) {
-            M.learned = false;
-            st.fallback = 1;
-        }
-        r_prev = rmax;
-        if (n_active > 0) CU(cudaMemcpyAsync(act, P->h_act, sizeof(int) * G, cudaMemcpyHostToDevice, P->stream));
-        if (!(rmax == rmax)) break;  // NaN: stop at once
     }
     CU(cudaMemcpyAsync(uT, U + (long long)Nc * nt, vb,
                        ptr_is_device(uT) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream));

@@ -216,6 +216,83 @@ def test_mgrit_matches_oracle(name, prec):
     assert rel(got, seq) < 1e-7
 
 
+F_CASES = ["w1", "w2_small", "w2_3lev", "w3_small", "w4_small", "w5_small"]
+
+
+@pytest.mark.parametrize("fas", [False, True])
+@pytest.mark.parametrize("prec", [B.PIT_PREC_FP64, B.PIT_PREC_MIXED])
+@pytest.mark.parametrize("name", F_CASES)
+def test_mgrit_f_relaxation_matches_oracle(name, prec, fas):
+    k, n, N, m, lev, coarse = MG_CASES[name]
+    wl = W.workload(k)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    tol = 1e-10 * np.abs(u0).max()
+    fine = B.solve_opts(prec, rtol=1e-13, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, coarse=coarse, fine=fine, fas=fas,
+                        relax=B.PIT_RELAX_F)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    dt = (wl.t1 - wl.t0) / N
+    ref, its, hist, _ = O.mgrit(u0, dt, N, m, lev, tol=tol, maxit=60, coarse_kind=coarse, rtol=1e-15, relax="F")
+    got = host(uT)
+    assert rel(got, ref) < (1e-10 if prec == B.PIT_PREC_FP64 else 1e-9)
+    assert st.n_converged == P.G
+    assert abs(st.max_cycles - int(its.max())) <= 1
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert rel(got, seq) < 1e-7
+
+
+@pytest.mark.parametrize("name", ["w2_small", "w2_3lev", "w3_small", "w5_small"])
+@pytest.mark.parametrize("relax", [B.PIT_RELAX_FCF, B.PIT_RELAX_F])
+def test_mgrit_lanes_give_identical_results(name, relax):
+    # grids are independent until the combination (Alg. 3): running them in
+    # concurrent lanes changes neither the per-grid arithmetic nor the cycle
+    # counts, so every lane count gives the bitwise same result
+    k, n, N, m, lev, coarse = MG_CASES[name]
+    wl = W.workload(k)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = cuda(O.initial(wl.ic_kind, wl.ic_params))
+    tol = 1e-10 * float(u0.abs().max())
+    fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-12, maxit=50000, inner_rtol=1e-5, ir_maxit=40)
+    crs = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-2, maxit=50000, inner_rtol=1e-5, ir_maxit=40)
+    res = {}
+    for lanes in (1, 2, 3, P.G):
+        opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, coarse=coarse, fine=fine, crs=crs,
+                            relax=relax, lanes=lanes)
+        uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+        st = P.mgrit_solve(u0, opts, uT)
+        res[lanes] = (host(uT), st.max_cycles, [st.res_hist[i] for i in range(st.max_cycles)])
+    for lanes in (2, 3, P.G):
+        np.testing.assert_array_equal(res[lanes][0], res[1][0])
+        assert res[lanes][1] == res[1][1]
+        assert res[lanes][2] == res[1][2]
+    dt = (wl.t1 - wl.t0) / N
+    seq = O.sequential(host(u0), dt, N, rtol=1e-15)
+    assert rel(res[1][0], seq) < 1e-7
+
+
+@pytest.mark.parametrize("kc", [1, 2, 3])
+def test_mgrit_f_relaxation_exact_after_nc_cycles(kc):
+    # kc F-relaxation cycles on Nc = kc coarse intervals reproduce sequential
+    # stepping for any coarse propagator (exactness moves one interval per cycle)
+    wl = W.workload(1)
+    P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = W.random_vector(5, P.n_total)
+    m, dt = wl.m, wl.dt
+    N = m * kc
+    fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-14, maxit=50000)
+    opts = B.mgrit_opts(0.0, dt * N, N, m, 2, tol=0.0, maxit=kc, fine=fine, relax=B.PIT_RELAX_F)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st, rc = P.mgrit_solve(cuda(u0), opts, uT, check=False)
+    assert rc in (0, B.PIT_ERR_NOCONV) and st.max_cycles == kc
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert np.max(np.abs(host(uT) - seq)) < 1e-11
+
+
 @pytest.mark.parametrize("name", ["heat2d", "heat3d", "ou2d_l0", "heat6d"])
 def test_combine_matches_oracle(name):
     P, O, _ = pair(name)

@@ -133,6 +133,32 @@ def test_mgrit_fcf_exactness_after_half_nc_cycles():
         assert np.max(np.abs(uT - seq)) > 1e-8
 
 
+def test_mgrit_f_relaxation_exactness_after_nc_cycles():
+    # F-relaxation carries exactness one coarse interval per cycle (FCF: two),
+    # for any coarse propagator
+    wl = W.workload(1)
+    P = _problem(wl)
+    u0 = W.random_vector(5, P.n_total)
+    m, dt = wl.m, wl.dt
+    for k in (1, 2, 3):
+        N = m * k
+        seq = P.sequential(u0, dt, N, rtol=1e-15)
+        uT, its, hist, st = P.mgrit(u0, dt, N, m, 2, tol=0.0, maxit=k, rtol=1e-15, check=False, relax="F")
+        assert np.all(its == k)
+        np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-13)
+        # Nc = k + 1: not yet exact after k F cycles (FCF would be)
+        N = m * (k + 1)
+        seq = P.sequential(u0, dt, N, rtol=1e-15)
+        uT, *_ = P.mgrit(u0, dt, N, m, 2, tol=0.0, maxit=k, rtol=1e-15, check=False, relax="F")
+        assert np.max(np.abs(uT - seq)) > 1e-8
+    # converged F-relaxation MGRIT is sequential stepping, also with three levels
+    wl, P, u0, N, dt = _mgrit_case(2, n=4, nsteps=64)
+    seq = P.sequential(u0, dt, N, rtol=1e-15)
+    for levels, m in ((2, 8), (3, 4)):
+        uT, its, hist, st = P.mgrit(u0, dt, N, m, levels, tol=1e-13, maxit=60, rtol=1e-15, relax="F")
+        np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-11)
+
+
 def test_mgrit_exact_coarse_propagator_one_cycle():
     wl, P, u0, N, dt = _mgrit_case(1)
     uT, its, hist, st = P.mgrit(u0, dt, N, wl.m, 2, tol=0.0, maxit=3, coarse_kind=W.COARSE_EXACT,
