@@ -149,7 +149,8 @@ typedef struct {
     int relax;            /* pit_relax of the finest level           */
     int lanes;            /* concurrent grid groups (Alg. 3 runs MGRIT per grid): 0 = library
                              default (6), 1 = all grids in lockstep; more than one lane is
-                             used with the correction form and the implicit coarse step only,
+                             used with the correction form and the implicit coarse step only
+                             (a learned propagator that was not accepted counts as implicit),
                              other forms run as one lane                                    */
 } pit_mgrit_opts;
 

@@ -1273,10 +1273,12 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     // tolerance is relative to the correction, which vanishes as MGRIT
     // converges; the learned one is nonlinear and keeps the FAS form
     auto corr_form = [&]() { return !M.learned && o->coarse != PIT_COARSE_EXACT && !o->fas; };
-    // lanes: the correction form with the implicit coarse step (no runtime
-    // switch of the coarse propagator), default six
+    // lanes: the correction form with the implicit coarse step for the whole
+    // solve (also when a learned propagator was requested but not accepted:
+    // the runtime judge only ever switches from the network to the implicit
+    // step), default six
     int K = o->lanes == 0 ? 6 : o->lanes;
-    if (!corr_form() || o->coarse != PIT_COARSE_IMPLICIT) K = 1;
+    if (!corr_form()) K = 1;
     if (K > G) K = G;
     int it = 0, n_active = G;
     if (K > 1) {
