@@ -68,7 +68,7 @@ typedef enum {
                            donor-cell upwind drift + central diffusion; BiCGStab            */
 } pit_op;
 
-typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1 } pit_prec;
+typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2 } pit_prec;
 
 typedef enum {
     PIT_COARSE_IMPLICIT = 0, /* Phi_coarse = backward Euler with dT = m dt (Sec. 3.3.1)  */
@@ -102,7 +102,14 @@ typedef struct {
  *                          FP32 Krylov on A e = r to relative
  *                          max(inner_rtol, 0.5 rtol ||b|| / ||r||) (at most maxit
  *                          iterations), x += e in FP64; at most ir_maxit
- *                          passes; the same FP64 stopping rule. */
+ *                          passes; the same FP64 stopping rule.
+ *   prec = PIT_PREC_FP32:  Krylov in FP32 on a copy of the state scaled by a
+ *                          power of two (inputs and outputs stay FP64) until
+ *                          the FP32 recurrence residual meets rtol; for solves
+ *                          whose tolerance lies far above FP32 rounding, such
+ *                          as the coarse correction solves of MGRIT (rtol of
+ *                          1e-5 or looser).  Values below 2^-126 of the largest
+ *                          input are flushed to zero. */
 typedef struct {
     int prec;
     double rtol;

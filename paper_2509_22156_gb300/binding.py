@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "PIT_OK", 1: "PIT_ERR_INVALID_ARG", 2: "PIT_ERR_CUDA", 3: "PI
                 4: "PIT_ERR_NOCONV", 5: "PIT_ERR_BREAKDOWN", 6: "PIT_ERR_NONFINITE", 7: "PIT_ERR_TIMEOUT",
                 8: "PIT_ERR_UNSUPPORTED"}
 PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU = 0, 1, 2
-PIT_PREC_FP64, PIT_PREC_MIXED = 0, 1
+PIT_PREC_FP64, PIT_PREC_MIXED, PIT_PREC_FP32 = 0, 1, 2
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
 PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
 

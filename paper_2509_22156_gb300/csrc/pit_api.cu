@@ -79,9 +79,9 @@ struct pit_lane {
     std::vector<int> grids;
     cudaStream_t s = nullptr, side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
-    bool planned[2] = {false, false};
-    int n_cls[2][2] = {{0, 0}, {0, 0}};
-    int *d_order_cls[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool planned[NPREC] = {};
+    int n_cls[NPREC][2] = {};
+    int *d_order_cls[NPREC][2] = {};
     int *d_act = nullptr;     // G flags, zero outside the lane
     int *h_act = nullptr;     // pinned, G
     double *h_res = nullptr;  // pinned, G x Nc
@@ -114,13 +114,13 @@ struct pit_problem {
     uint16_t *d_masks = nullptr;     // neighbour masks, packed like a state
     // launch plan per precision form: class 0 = grids whose FP64 state fits in
     // shared memory, class 1 = larger grids (MIXED only: state in global memory)
-    bool planned[2] = {false, false};
-    int n_cls[2][2] = {{0, 0}, {0, 0}};
-    int *d_order_cls[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    std::vector<int> h_order_cls[2][2];
-    size_t smem_cls[2][2] = {{0, 0}, {0, 0}};
-    size_t smem_need[2] = {0, 0};    // class 0 (used by the allocation-free step)
-    int threads[2][2][2] = {};       // [prec][wide batch][class]; 0 = not tuned yet
+    bool planned[NPREC] = {};
+    int n_cls[NPREC][2] = {};
+    int *d_order_cls[NPREC][2] = {};
+    std::vector<int> h_order_cls[NPREC][2];
+    size_t smem_cls[NPREC][2] = {};
+    size_t smem_need[NPREC] = {};    // class 0 (used by the allocation-free step)
+    int threads[NPREC][2][2] = {};   // [prec][wide batch][class]; 0 = not tuned yet
     int forced_threads[2] = {0, 0};  // override [wide batch]
     cudaStream_t side = nullptr;     // second stream: the large-grid class runs beside class 0
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -227,7 +227,7 @@ double binomial(int a, int b)
 pit_status check_solve_opts(const pit_solve_opts *o)
 {
     if (!o) return fail(PIT_ERR_INVALID_ARG, "solve options are NULL");
-    if (o->prec != PIT_PREC_FP64 && o->prec != PIT_PREC_MIXED)
+    if (o->prec != PIT_PREC_FP64 && o->prec != PIT_PREC_MIXED && o->prec != PIT_PREC_FP32)
         return fail(PIT_ERR_INVALID_ARG, "unknown precision %d", o->prec);
     if (!(o->rtol >= 0.0) || o->maxit < 1) return fail(PIT_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
     if (o->prec == PIT_PREC_MIXED && (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->ir_maxit < 1))
@@ -415,7 +415,7 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
 pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active,
                      const pit_lane *L = nullptr)
 {
-    const int prec = o.prec == PIT_PREC_MIXED ? MIXED : PLAIN;
+    const int prec = prec_form(o.prec);
     TRY(plan(P, prec));
     if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
     if (L && !L->planned[prec]) return fail(PIT_ERR_INVALID_ARG, "lane without a launch plan");
@@ -662,7 +662,7 @@ pit_status pit_problem_destroy(pit_problem_t P)
     for (pit_lane &L : P->lanes) {
         if (L.s) cudaStreamSynchronize(L.s);
         if (L.side) cudaStreamSynchronize(L.side);
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < NPREC; ++p)
             for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
         cudaFree(L.d_act);
         cudaFreeHost(L.h_act);
@@ -676,7 +676,7 @@ pit_status pit_problem_destroy(pit_problem_t P)
     P->lanes.clear();
     cudaFree(P->d_order);
     cudaFree(P->d_masks);
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < NPREC; ++p)
         for (int c = 0; c < 2; ++c) cudaFree(P->d_order_cls[p][c]);
     if (P->side) {
         cudaStreamSynchronize(P->side);
@@ -1110,7 +1110,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
         for (pit_lane &L : P->lanes) {
             cudaStreamSynchronize(L.s);
             cudaStreamSynchronize(L.side);
-            for (int p = 0; p < 2; ++p)
+            for (int p = 0; p < NPREC; ++p)
                 for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
             cudaFree(L.d_act);
             cudaFreeHost(L.h_act);
@@ -1145,7 +1145,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
             CU(cudaMallocHost(&L.h_act, sizeof(int) * P->G));
         }
     }
-    for (int prec = 0; prec < 2; ++prec) {
+    for (int prec = 0; prec < NPREC; ++prec) {
         if (!P->planned[prec]) continue;
         for (int k = 0; k < K; ++k) {
             pit_lane &L = P->lanes[k];
@@ -1191,7 +1191,7 @@ pit_status lanes_prime(Mg &M, int Nc)
     Rep reps[3] = {{&o->fine, Nc, M.dt}, {&o->crs, 1, M.dt * o->m}, {&o->crs, Nc / o->m, M.dt * o->m}};
     const int n_reps = o->levels == 3 ? 3 : 2;
     for (int r = 0; r < n_reps; ++r) {
-        const int prec = reps[r].so->prec == PIT_PREC_MIXED ? MIXED : PLAIN;
+        const int prec = prec_form(reps[r].so->prec);
         TRY(plan(P, prec));
         if (reps[r].nb <= 0) continue;
         StepCall c;
@@ -1465,7 +1465,7 @@ extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, i
         }
         scratch = g_static_ptr[dev];
     }
-    const int prec = opts->prec == PIT_PREC_MIXED ? MIXED : PLAIN;
+    const int prec = prec_form(opts->prec);
     TRY(plan(P, prec));
     if (P->n_cls[prec][1] > 0)
         return fail(PIT_ERR_UNSUPPORTED, "this problem has grids whose solver state needs global scratch; "

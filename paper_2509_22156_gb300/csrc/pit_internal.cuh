@@ -92,7 +92,15 @@ struct StepArgs {
     DevStats *stats;
 };
 
-enum Prec { PLAIN = 0, MIXED = 1 };
+// Precision forms of the multi-step kernel: PLAIN = FP64 Krylov, MIXED = FP32
+// Krylov in FP64 refinement, SINGLE = FP32 Krylov on a power-of-two-scaled
+// FP32 copy of the state (FP64 input and output).
+enum Prec { PLAIN = 0, MIXED = 1, SINGLE = 2 };
+constexpr int NPREC = 3;
+inline int prec_form(int pit_prec)
+{
+    return pit_prec == PIT_PREC_MIXED ? MIXED : pit_prec == PIT_PREC_FP32 ? SINGLE : PLAIN;
+}
 
 // Learned coarse propagator: parameter block (BF16-rounded values held as
 // FP32) passed by value to the inference kernel, and one training item.

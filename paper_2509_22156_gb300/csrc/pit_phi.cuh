@@ -386,22 +386,24 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
 
 // ----------------------------------------------------------------------------
 // Shared-memory layout of one item (ld = n rounded up to 4):
-//   FP64 arrays: x, [b (MIXED)], [Krylov vectors (PLAIN)], [table (var. coef.)]
-//   FP32 arrays: [Krylov vectors + table (MIXED)]
+//   FP64 arrays: x, [b (MIXED)], [Krylov vectors (PLAIN)], [table (var. coef.,
+//                PLAIN and MIXED)]
+//   FP32 arrays: [e (MIXED) or x (SINGLE), Krylov vectors, table (var. coef.)]
 //   u16 mask
 __host__ __device__ inline int krylov_vecs(int op, int prec)
 {
-    if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e)
-    return prec == PLAIN ? 4 : 5;                        // r p s w (+ e)
+    if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e or x)
+    return prec == PLAIN ? 4 : 5;                        // r p s w (+ e or x)
 }
 __host__ __device__ inline int n_tab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
 __host__ __device__ inline int n_f64(int op, int prec, int d)
 {
+    if (prec == SINGLE) return 0;
     return (prec == PLAIN ? 1 + krylov_vecs(op, prec) : 2) + n_tab(op, d);
 }
 __host__ __device__ inline int n_f32(int op, int prec, int d)
 {
-    return prec == MIXED ? krylov_vecs(op, prec) + n_tab(op, d) : 0;
+    return prec != PLAIN ? krylov_vecs(op, prec) + n_tab(op, d) : 0;
 }
 
 template <int OP, int PREC, int D, bool XG = false>
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     __shared__ float red32[2 * 128];
 
     static_assert(!XG || PREC == MIXED, "global-state variant is MIXED only");
+    static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE, "unknown precision form");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -426,15 +429,15 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     const int ld = (n + 3) & ~3;
     const double dt = a.dt;
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
-    constexpr int NF64 = (PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : (XG ? 0 : 2)) + K;
+    constexpr int NF64 = PREC == SINGLE ? 0 : (PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : (XG ? 0 : 2)) + K;
     constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6) : (PREC == PLAIN ? 4 : 5);
-    constexpr int NF32 = (PREC == MIXED) ? NKV + K : 0;
+    constexpr int NF32 = (PREC != PLAIN) ? NKV + K : 0;
 
     double *s64 = reinterpret_cast<double *>(smem);
     double *x = XG ? a.xg + (long long)b * a.n_total + GI.off : s64;
     double *bvec = XG ? a.bg + (long long)b * a.n_total + GI.off : s64 + ld;  // MIXED: right-hand side
     double *v64 = s64 + ld;  // PLAIN: Krylov vectors
-    double *tab64 = s64 + (size_t)(NF64 - K) * ld;
+    double *tab64 = PREC == SINGLE ? nullptr : s64 + (size_t)(NF64 - K) * ld;
     float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
     float *tab32 = f32 + (size_t)NKV * ld;
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
@@ -443,21 +446,40 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     const double *f = a.f ? a.f + (long long)b * a.f_stride + GI.off : nullptr;
     const uint16_t *gmask = a.masks + GI.off;
 
+    Reducer<double> R64{red64, 0};
+    Reducer<float> R32{red32, 0};
+    // SINGLE: the state is held as x 2^ks in FP32, ks from the input state and
+    // the first forcing term (the correction sweep of MGRIT starts from zero)
+    int ks = 0;
+    if constexpr (PREC == SINGLE) {
+        const double *g0 = a.g ? a.g + (long long)b * a.g_stride + GI.off : nullptr;
+        double acc[1] = {0.0};
+        for (int j = tid; j < n; j += nt) {
+            const double v = in[j];
+            acc[0] += v * v;
+            if (g0) acc[0] += g0[j] * g0[j];
+        }
+        R64.template sum<1>(acc);
+        ks = scale_exp(acc[0]);
+    }
     for (int j = tid; j < n; j += nt) {
         mask[j] = gmask[j];
-        x[j] = in[j];
+        if constexpr (PREC == SINGLE) f32[j] = to_f32(in[j], ks);
+        else x[j] = in[j];
     }
     if constexpr (OP != PIT_OP_HEAT) {
         for (int j = tid; j < n; j += nt) {
             double diag, cm[D], cp[D];
             op_coef<D>(a.op, GI, a.faces, j, dt, diag, cm, cp);
-            tab64[j] = diag;
-            if constexpr (PREC == MIXED) tab32[j] = (float)diag;
+            if constexpr (PREC != SINGLE) tab64[j] = diag;
+            if constexpr (PREC != PLAIN) tab32[j] = (float)diag;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                tab64[(1 + 2 * i) * ld + j] = cm[i];
-                tab64[(2 + 2 * i) * ld + j] = cp[i];
-                if constexpr (PREC == MIXED) {
+                if constexpr (PREC != SINGLE) {
+                    tab64[(1 + 2 * i) * ld + j] = cm[i];
+                    tab64[(2 + 2 * i) * ld + j] = cp[i];
+                }
+                if constexpr (PREC != PLAIN) {
                     tab32[(1 + 2 * i) * ld + j] = (float)cm[i];
                     tab32[(2 + 2 * i) * ld + j] = (float)cp[i];
                 }
@@ -491,8 +513,6 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
         else return T64(v, j);
     };
 
-    Reducer<double> R64{red64, 0};
-    Reducer<float> R32{red32, 0};
     int status = PIT_OK, iters = 0, passes = 0;
     const bool carry_ok = (f == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
     // MIXED: carried initial residual of the next step (see the file comment).
@@ -538,6 +558,81 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
             else k = cg_core<double, double>(T64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
             iters += k;
             if (st > status) status = st;
+        } else if constexpr (PREC == SINGLE) {
+            // FP32 Krylov on the scaled FP32 state xs = x 2^ks
+            float *xs = f32, *r = f32 + ld, *q1 = f32 + 2 * ld, *q2 = f32 + 3 * ld, *q3 = f32 + 4 * ld,
+                  *q4 = f32 + 5 * ld;
+            const float dtf = (float)dt;
+            float bb[1] = {0.0f};
+            if (a.guess) {
+                const long long sb0 = (long long)(step - 1);
+                const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
+                const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
+                for (int j = tid; j < n; j += nt) {
+                    const float bj = f ? xs[j] + dtf * to_f32(f[j], ks) : xs[j];
+                    r[j] = bj;
+                    bb[0] += bj * bj;
+                    xs[j] = to_f32(gf ? gu[j] - gf[j] : gu[j], ks);
+                }
+                __syncthreads();
+                for (int j = tid; j < n; j += nt) {
+                    if constexpr (OP == PIT_OP_HEAT) r[j] -= HT(xs, j);
+                    else r[j] -= T32(xs, j);
+                }
+            } else {
+                for (int j = tid; j < n; j += nt) {
+                    const float bj = f ? xs[j] + dtf * to_f32(f[j], ks) : xs[j];
+                    float Ax;
+                    if constexpr (OP == PIT_OP_HEAT) Ax = HT(xs, j);
+                    else Ax = T32(xs, j);
+                    r[j] = bj - Ax;
+                    bb[0] += bj * bj;
+                }
+            }
+            R32.template sum<1>(bb);  // also orders the residual before xs changes
+            const float rt = (float)a.rtol;
+            const float stop2 = rt * rt * bb[0];
+            int st, k;
+            if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, xs, r, q1, q2, q3, q4, R32, stop2, a.maxit, st);
+            else if constexpr (OP == PIT_OP_HEAT) k = cg_core<float, float>(HT, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
+            else k = cg_core<float, float>(T32, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
+            iters += k;
+            if (st > status) status = st;
+            // forcing of this step and the stored outputs (FP64, own nodes only)
+            const long long sb = (long long)(step - 1);
+            __syncthreads();  // xs complete
+            if (a.g) {
+                const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
+                for (int j = tid; j < n; j += nt) xs[j] += to_f32(gs[j], ks);
+            }
+            const double *hs = a.hs ? a.hs + (long long)b * a.hs_stride + sb * a.hs_step + GI.off : nullptr;
+            if (step < a.nsteps) {
+                if (a.out_steps) {
+                    double *os = a.out_steps + (long long)b * a.os_stride + sb * a.os_step + GI.off;
+                    for (int j = tid; j < n; j += nt) {
+                        const double xj = to_f64(xs[j], -ks);
+                        os[j] = hs ? xj + hs[j] : xj;
+                    }
+                }
+            } else {
+                double *ol = a.out_last + (long long)b * a.ol_stride + GI.off;
+                const double *h = a.h ? a.h + (long long)b * a.h_stride + GI.off : nullptr;
+                const double *cmp = a.cmp ? a.cmp + (long long)b * a.cmp_stride + GI.off : nullptr;
+                double acc[1] = {0.0};
+                for (int j = tid; j < n; j += nt) {
+                    const double xj = to_f64(xs[j], -ks);
+                    if (cmp) {
+                        const double dlt = xj - cmp[j];
+                        acc[0] += dlt * dlt;
+                    }
+                    ol[j] = a.out_scale * xj + (h ? a.out_hscale * h[j] : 0.0) + (hs ? hs[j] : 0.0);
+                }
+                if (cmp) {
+                    R64.template sum<1>(acc);
+                    if (tid == 0) a.norms[(long long)b * a.n_grids + g] = sqrt(acc[0]);
+                }
+            }
+            continue;
         } else {
             float *e = f32;
             // right-hand side b = x_{s-1} + dt f; optional initial guess
@@ -714,6 +809,13 @@ cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 
                             bool xg);
 
 // Instantiates the launcher and attribute setter of one operator for D = 1..6.
+#define PIT_STEPS_SET3(OPV, D)                                                                                    \
+    set((const void *)steps_kernel<OPV, PLAIN, D>); set((const void *)steps_kernel<OPV, MIXED, D>);               \
+    set((const void *)steps_kernel<OPV, SINGLE, D>); set((const void *)steps_kernel<OPV, MIXED, D, true>);
+#define PIT_STEPS_CASE3(OPV, D)                                                                                   \
+    case D * 3 + PLAIN: steps_kernel<OPV, PLAIN, D><<<grid, block, smem, s>>>(a); break;                          \
+    case D * 3 + MIXED: steps_kernel<OPV, MIXED, D><<<grid, block, smem, s>>>(a); break;                          \
+    case D * 3 + SINGLE: steps_kernel<OPV, SINGLE, D><<<grid, block, smem, s>>>(a); break;
 #define PIT_STEPS_OP(NAME, OPV)                                                                                   \
     cudaError_t steps_init_##NAME(int bytes)                                                                      \
     {                                                                                                             \
@@ -721,15 +823,8 @@ cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 
         auto set = [&](const void *fn) {                                                                          \
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
         };                                                                                                        \
-        set((const void *)steps_kernel<OPV, PLAIN, 1>); set((const void *)steps_kernel<OPV, MIXED, 1>);           \
-        set((const void *)steps_kernel<OPV, PLAIN, 2>); set((const void *)steps_kernel<OPV, MIXED, 2>);           \
-        set((const void *)steps_kernel<OPV, PLAIN, 3>); set((const void *)steps_kernel<OPV, MIXED, 3>);           \
-        set((const void *)steps_kernel<OPV, PLAIN, 4>); set((const void *)steps_kernel<OPV, MIXED, 4>);           \
-        set((const void *)steps_kernel<OPV, PLAIN, 5>); set((const void *)steps_kernel<OPV, MIXED, 5>);           \
-        set((const void *)steps_kernel<OPV, PLAIN, 6>); set((const void *)steps_kernel<OPV, MIXED, 6>);           \
-        set((const void *)steps_kernel<OPV, MIXED, 1, true>); set((const void *)steps_kernel<OPV, MIXED, 2, true>); \
-        set((const void *)steps_kernel<OPV, MIXED, 3, true>); set((const void *)steps_kernel<OPV, MIXED, 4, true>); \
-        set((const void *)steps_kernel<OPV, MIXED, 5, true>); set((const void *)steps_kernel<OPV, MIXED, 6, true>); \
+        PIT_STEPS_SET3(OPV, 1) PIT_STEPS_SET3(OPV, 2) PIT_STEPS_SET3(OPV, 3)                                      \
+        PIT_STEPS_SET3(OPV, 4) PIT_STEPS_SET3(OPV, 5) PIT_STEPS_SET3(OPV, 6)                                      \
         return e;                                                                                                 \
     }                                                                                                             \
     cudaError_t steps_launch_##NAME(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,       \
@@ -748,19 +843,10 @@ cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 
             }                                                                                                     \
             return cudaGetLastError();                                                                            \
         }                                                                                                         \
-        switch (d * 2 + prec) {                                                                                   \
-        case 1 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 1><<<grid, block, smem, s>>>(a); break;                      \
-        case 1 * 2 + MIXED: steps_kernel<OPV, MIXED, 1><<<grid, block, smem, s>>>(a); break;                      \
-        case 2 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 2><<<grid, block, smem, s>>>(a); break;                      \
-        case 2 * 2 + MIXED: steps_kernel<OPV, MIXED, 2><<<grid, block, smem, s>>>(a); break;                      \
-        case 3 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 3><<<grid, block, smem, s>>>(a); break;                      \
-        case 3 * 2 + MIXED: steps_kernel<OPV, MIXED, 3><<<grid, block, smem, s>>>(a); break;                      \
-        case 4 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 4><<<grid, block, smem, s>>>(a); break;                      \
-        case 4 * 2 + MIXED: steps_kernel<OPV, MIXED, 4><<<grid, block, smem, s>>>(a); break;                      \
-        case 5 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 5><<<grid, block, smem, s>>>(a); break;                      \
-        case 5 * 2 + MIXED: steps_kernel<OPV, MIXED, 5><<<grid, block, smem, s>>>(a); break;                      \
-        case 6 * 2 + PLAIN: steps_kernel<OPV, PLAIN, 6><<<grid, block, smem, s>>>(a); break;                      \
-        case 6 * 2 + MIXED: steps_kernel<OPV, MIXED, 6><<<grid, block, smem, s>>>(a); break;                      \
+        if (prec < 0 || prec >= NPREC) return cudaErrorInvalidValue;                                              \
+        switch (d * 3 + prec) {                                                                                   \
+        PIT_STEPS_CASE3(OPV, 1) PIT_STEPS_CASE3(OPV, 2) PIT_STEPS_CASE3(OPV, 3)                                   \
+        PIT_STEPS_CASE3(OPV, 4) PIT_STEPS_CASE3(OPV, 5) PIT_STEPS_CASE3(OPV, 6)                                   \
         default: return cudaErrorInvalidValue;                                                                    \
         }                                                                                                         \
         return cudaGetLastError();                                                                                \

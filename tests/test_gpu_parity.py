@@ -117,6 +117,36 @@ def test_phi_batch_matches_oracle(name, prec):
         assert st.max_refine >= 1
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_phi_batch_fp32_form_matches_oracle(name):
+    # FP32 Krylov on the scaled FP32 state: accuracy set by rtol and FP32
+    # rounding (relative 1e-6 asked, 1e-4 allowed), with a forcing term
+    P, O, dt = pair(name)
+    nb = 3
+    u = W.random_vector(212, nb * P.n_total)
+    f = W.random_vector(213, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    st = P.phi_batch(dt, cuda(u), out, B.solve_opts(B.PIT_PREC_FP32, rtol=1e-6, maxit=20000), f=cuda(f))
+    assert st.n_items == nb * P.G and st.n_failed == 0
+    ref = O.phi(dt, u, f, rtol=1e-15)
+    got = host(out)
+    for b in range(nb):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < 1e-4, (b, g)
+
+
+@pytest.mark.parametrize("scale", [1e-100, 1e-20, 1e20, 1e100])
+def test_fp32_form_scales_with_the_state(scale):
+    P, O, dt = pair("varheat3d")
+    u0 = W.random_vector(304, P.n_total)
+    ref = O.sequential(u0, dt, 4, rtol=1e-15)
+    uT = np.empty(P.n_total)
+    P.sequential_solve(u0 * scale, dt, 4, uT, B.solve_opts(B.PIT_PREC_FP32, rtol=1e-6))
+    assert np.all(np.isfinite(uT))
+    assert rel(uT / scale, ref) < 1e-4
+
+
 def test_phi_in_place_forcing_and_empty_batch():
     P, O, dt = pair("heat3d")
     u = W.random_vector(5, 2 * P.n_total)
@@ -272,6 +302,31 @@ def test_mgrit_lanes_give_identical_results(name, relax):
     dt = (wl.t1 - wl.t0) / N
     seq = O.sequential(host(u0), dt, N, rtol=1e-15)
     assert rel(res[1][0], seq) < 1e-7
+
+
+@pytest.mark.parametrize("name", ["w1", "w2_small", "w3_small", "w4_small"])
+@pytest.mark.parametrize("relax", [B.PIT_RELAX_FCF, B.PIT_RELAX_F])
+def test_mgrit_fp32_coarse_correction_solves(name, relax):
+    # the correction equation only needs the coarse tolerance: FP32 coarse
+    # solves reach the same fixed point in (about) the same number of cycles
+    k, n, N, m, lev, coarse = MG_CASES[name]
+    wl = W.workload(k)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    tol = 1e-10 * np.abs(u0).max()
+    fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-13, maxit=50000, inner_rtol=1e-5, ir_maxit=40)
+    res = {}
+    for cp in (B.PIT_PREC_MIXED, B.PIT_PREC_FP32):
+        crs = B.solve_opts(cp, rtol=1e-2, maxit=50000, inner_rtol=1e-5, ir_maxit=40)
+        opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, fine=fine, crs=crs, relax=relax)
+        uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+        st = P.mgrit_solve(cuda(u0), opts, uT)
+        res[cp] = (host(uT), st.max_cycles)
+    dt = (wl.t1 - wl.t0) / N
+    seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert rel(res[B.PIT_PREC_FP32][0], seq) < 1e-8
+    assert abs(res[B.PIT_PREC_FP32][1] - res[B.PIT_PREC_MIXED][1]) <= 1
 
 
 @pytest.mark.parametrize("kc", [1, 2, 3])
