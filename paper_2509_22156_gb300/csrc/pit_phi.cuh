@@ -590,6 +590,19 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 }
             }
             R32.template sum<1>(bb);  // also orders the residual before xs changes
+            if (bb[0] > 0.0f && !(bb[0] >= 0x1p-60f && bb[0] <= 0x1p60f)) {
+                // keep the FP32 state near unit size (the sweep's state can
+                // start at zero and grow or fade by many orders): exact
+                // power-of-two rescale of the linear quantities xs, r and of ks
+                const int kq = scale_exp((double)bb[0]);
+                const float sc = __uint_as_float((unsigned)(127 + kq) << 23);
+                for (int j = tid; j < n; j += nt) {
+                    xs[j] *= sc;
+                    r[j] *= sc;
+                }
+                bb[0] = (bb[0] * sc) * sc;
+                ks += kq;
+            }
             const float rt = (float)a.rtol;
             const float stop2 = rt * rt * bb[0];
             int st, k;

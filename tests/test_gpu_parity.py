@@ -304,13 +304,19 @@ def test_mgrit_lanes_give_identical_results(name, relax):
     assert rel(res[1][0], seq) < 1e-7
 
 
-@pytest.mark.parametrize("name", ["w1", "w2_small", "w3_small", "w4_small"])
+@pytest.mark.parametrize("name", ["w1", "w2_small", "w3_small", "w4_small", "w3_full"])
 @pytest.mark.parametrize("relax", [B.PIT_RELAX_FCF, B.PIT_RELAX_F])
 def test_mgrit_fp32_coarse_correction_solves(name, relax):
     # the correction equation only needs the coarse tolerance: FP32 coarse
     # solves reach the same fixed point in (about) the same number of cycles
-    k, n, N, m, lev, coarse = MG_CASES[name]
-    wl = W.workload(k)
+    if name == "w3_full":
+        # the drift workload at its full size and tolerance (BiCGStab in FP32,
+        # residuals spanning many orders of magnitude across the intervals)
+        wl = W.workload(3)
+        k, n, N, m, lev = 3, wl.n, wl.nsteps, wl.m, 2
+    else:
+        k, n, N, m, lev, coarse = MG_CASES[name]
+        wl = W.workload(k)
     P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
     O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
     u0 = O.initial(wl.ic_kind, wl.ic_params)
