@@ -236,8 +236,10 @@ pit_status check_solve_opts(const pit_solve_opts *o)
 }
 
 // Launch plan of a precision form: grids whose on-chip state fits in shared
-// memory form class 0; the others (MIXED) keep their FP64 state in global
-// memory (class 1).  Each class lists its grids by decreasing size.
+// memory form class 0; the others keep their FP64 vectors in global memory
+// (class 1: the state x and b in the mixed form, x and the Krylov vectors in
+// the FP64 form; the FP32 form has no class 1).  Each class lists its grids by
+// decreasing size.
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
@@ -254,12 +256,12 @@ pit_status plan(pit_problem *P, int prec)
             need[0] = bytes > need[0] ? bytes : need[0];
             continue;
         }
-        const size_t bx = prec == MIXED ? phi_smem_bytes_xg(P->desc.op, P->desc.d, n) : (size_t)-1;
+        const size_t bx = prec != SINGLE ? phi_smem_bytes_xg(prec, P->desc.op, P->desc.d, n) : (size_t)-1;
         if (bx > P->max_smem)
             return fail(PIT_ERR_UNSUPPORTED,
                         "grid %d (%d nodes) needs %zu bytes of shared memory for the on-chip solve in this precision "
                         "form; the device offers %zu",
-                        g, n, prec == MIXED ? bx : bytes, P->max_smem);
+                        g, n, prec != SINGLE ? bx : bytes, P->max_smem);
         cls[1].push_back(g);
         need[1] = bx > need[1] ? bx : need[1];
     }
@@ -424,7 +426,7 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     const int n1 = L ? L->n_cls[prec][1] : P->n_cls[prec][1];
     const bool two = n1 > 0;
     // (a lane's workspaces and CTA sizes are prepared before its first launch)
-    if (two && !L) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * 2));
+    if (two && !L) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op)));
     for (int cls = 0; cls < 2; ++cls)
         if (P->n_cls[prec][cls] > 0 && !L) TRY(tune(P, prec, wide, cls, o, c, active));
     cudaStream_t s0 = L ? L->s : P->stream, s1 = L ? L->side : P->side;
@@ -1200,7 +1202,7 @@ pit_status lanes_prime(Mg &M, int Nc)
         c.nsteps = 1;
         c.in = P->m_U.d();
         c.is = nt;
-        if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * 2));
+        if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op)));
         for (int cls = 0; cls < 2; ++cls)
             if (P->n_cls[prec][cls] > 0) TRY(tune(P, prec, c.nb >= 8, cls, *reps[r].so, c, M.active));
     }

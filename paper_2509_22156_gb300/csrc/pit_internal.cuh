@@ -79,8 +79,9 @@ struct StepArgs {
     const double *cmp;       long long cmp_stride;
     double *norms;
     const double *guess;     long long guess_stride, guess_step;
-    double *xg;              // state in global memory (MIXED, grids too large for shared memory):
-    double *bg;              //   x and b of entry b at xg/bg + b*n_total + grid offset
+    double *xg;              // state in global memory (grids too large for shared memory):
+    double *bg;              //   x and b (MIXED) of entry b at xg/bg + b*n_total + grid offset;
+                             //   PLAIN: Krylov vector k at xg + ((1+k) n_batch + b) n_total + offset
     long long n_total;
     const int *active;       // per grid, NULL = all active
     const double *faces;     // variable coefficient at the 2d faces of every node, or NULL
@@ -134,8 +135,11 @@ size_t phi_smem_bytes(int prec, int op, int d, int n);
 // Launch one multi-step batch (grid-per-CTA, every Krylov solve on chip);
 // xg selects the variant whose FP64 state lives in global memory.
 cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s, bool xg = false);
-// Shared memory per item; xg: FP64 state in global memory (MIXED only).
-size_t phi_smem_bytes_xg(int op, int d, int n);
+// Shared memory per item of the global-state variant (PLAIN or MIXED), and
+// the number of n_batch x n_total FP64 slabs of global workspace it uses
+// (x and b for MIXED; x and the Krylov vectors for PLAIN).
+size_t phi_smem_bytes_xg(int prec, int op, int d, int n);
+int xg_slabs(int prec, int op);
 // Raise the dynamic shared-memory limit of every backward-Euler kernel.
 cudaError_t phi_kernels_init(size_t max_smem);
 // Neighbour masks of every node (bit 2i: interior neighbour at -e_i, 2i+1: at +e_i).

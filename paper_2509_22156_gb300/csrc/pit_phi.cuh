@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     __shared__ double red64[2 * 128];
     __shared__ float red32[2 * 128];
 
-    static_assert(!XG || PREC == MIXED, "global-state variant is MIXED only");
+    static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
     static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE, "unknown precision form");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
@@ -429,14 +429,17 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     const int ld = (n + 3) & ~3;
     const double dt = a.dt;
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
-    constexpr int NF64 = PREC == SINGLE ? 0 : (PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : (XG ? 0 : 2)) + K;
+    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
     constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6) : (PREC == PLAIN ? 4 : 5);
     constexpr int NF32 = (PREC != PLAIN) ? NKV + K : 0;
 
     double *s64 = reinterpret_cast<double *>(smem);
     double *x = XG ? a.xg + (long long)b * a.n_total + GI.off : s64;
     double *bvec = XG ? a.bg + (long long)b * a.n_total + GI.off : s64 + ld;  // MIXED: right-hand side
-    double *v64 = s64 + ld;  // PLAIN: Krylov vectors
+    // PLAIN: Krylov vectors, in shared memory (stride ld) or, for the
+    // global-state variant, in per-vector slabs of n_batch x n_total after x
+    double *v64 = XG ? a.xg + ((long long)a.n_batch + b) * a.n_total + GI.off : s64 + ld;
+    const long long vs = XG ? (long long)a.n_batch * a.n_total : (long long)ld;
     double *tab64 = PREC == SINGLE ? nullptr : s64 + (size_t)(NF64 - K) * ld;
     float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
     float *tab32 = f32 + (size_t)NKV * ld;
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     for (int step = 1; step <= a.nsteps; ++step) {
         __syncthreads();  // state complete
         if constexpr (PREC == PLAIN) {
-            double *r = v64, *q1 = v64 + ld, *q2 = v64 + 2 * ld, *q3 = v64 + 3 * ld, *q4 = v64 + 4 * ld;
+            double *r = v64, *q1 = v64 + vs, *q2 = v64 + 2 * vs, *q3 = v64 + 3 * vs, *q4 = v64 + 4 * vs;
             double bb[1] = {0.0};
             if (a.guess) {
                 // right-hand side kept in r, iterate replaced by the guess
@@ -824,11 +827,15 @@ cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 
 // Instantiates the launcher and attribute setter of one operator for D = 1..6.
 #define PIT_STEPS_SET3(OPV, D)                                                                                    \
     set((const void *)steps_kernel<OPV, PLAIN, D>); set((const void *)steps_kernel<OPV, MIXED, D>);               \
-    set((const void *)steps_kernel<OPV, SINGLE, D>); set((const void *)steps_kernel<OPV, MIXED, D, true>);
+    set((const void *)steps_kernel<OPV, SINGLE, D>); set((const void *)steps_kernel<OPV, MIXED, D, true>);        \
+    set((const void *)steps_kernel<OPV, PLAIN, D, true>);
 #define PIT_STEPS_CASE3(OPV, D)                                                                                   \
     case D * 3 + PLAIN: steps_kernel<OPV, PLAIN, D><<<grid, block, smem, s>>>(a); break;                          \
     case D * 3 + MIXED: steps_kernel<OPV, MIXED, D><<<grid, block, smem, s>>>(a); break;                          \
     case D * 3 + SINGLE: steps_kernel<OPV, SINGLE, D><<<grid, block, smem, s>>>(a); break;
+#define PIT_STEPS_CASE_XG(OPV, D)                                                                                 \
+    case D * 3 + PLAIN: steps_kernel<OPV, PLAIN, D, true><<<grid, block, smem, s>>>(a); break;                    \
+    case D * 3 + MIXED: steps_kernel<OPV, MIXED, D, true><<<grid, block, smem, s>>>(a); break;
 #define PIT_STEPS_OP(NAME, OPV)                                                                                   \
     cudaError_t steps_init_##NAME(int bytes)                                                                      \
     {                                                                                                             \
@@ -844,14 +851,10 @@ cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 
                                     cudaStream_t s, bool xg)                                                      \
     {                                                                                                             \
         if (xg) {                                                                                                 \
-            if (prec != MIXED) return cudaErrorInvalidValue;                                                      \
-            switch (d) {                                                                                          \
-            case 1: steps_kernel<OPV, MIXED, 1, true><<<grid, block, smem, s>>>(a); break;                        \
-            case 2: steps_kernel<OPV, MIXED, 2, true><<<grid, block, smem, s>>>(a); break;                        \
-            case 3: steps_kernel<OPV, MIXED, 3, true><<<grid, block, smem, s>>>(a); break;                        \
-            case 4: steps_kernel<OPV, MIXED, 4, true><<<grid, block, smem, s>>>(a); break;                        \
-            case 5: steps_kernel<OPV, MIXED, 5, true><<<grid, block, smem, s>>>(a); break;                        \
-            case 6: steps_kernel<OPV, MIXED, 6, true><<<grid, block, smem, s>>>(a); break;                        \
+            if (prec != MIXED && prec != PLAIN) return cudaErrorInvalidValue;                                     \
+            switch (d * 3 + prec) {                                                                               \
+            PIT_STEPS_CASE_XG(OPV, 1) PIT_STEPS_CASE_XG(OPV, 2) PIT_STEPS_CASE_XG(OPV, 3)                         \
+            PIT_STEPS_CASE_XG(OPV, 4) PIT_STEPS_CASE_XG(OPV, 5) PIT_STEPS_CASE_XG(OPV, 6)                         \
             default: return cudaErrorInvalidValue;                                                                \
             }                                                                                                     \
             return cudaGetLastError();                                                                            \

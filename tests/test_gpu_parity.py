@@ -375,9 +375,9 @@ def test_combine_matches_oracle(name):
 
 def test_large_grids_keep_their_state_in_global_memory():
     """d = 2, level 12: grids (6, 7) and (7, 6) hold 8001 nodes, more than the
-    shared-memory solver state allows; the mixed form keeps their FP64 state in
-    global memory and runs them beside the other grids.  The FP64 form has no
-    such variant and refuses."""
+    shared-memory solver state allows; the mixed form keeps their FP64 state,
+    the FP64 form its state and Krylov vectors in global memory, and both run
+    them beside the other grids."""
     P = B.Problem(2, 12, 1, B.PIT_OP_HEAT)
     O = oracle.Problem(2, 12, 1, W.OP_HEAT)
     assert int(np.diff(P.offsets).max()) == 127 * 63
@@ -394,9 +394,13 @@ def test_large_grids_keep_their_state_in_global_memory():
         for g in range(P.G):
             sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
             assert rel(got[sl], ref[sl]) < 1e-9, (b, g)
-    with pytest.raises(B.PitError) as e:
-        P.phi_batch(dt, cuda(u), out, B.solve_opts(B.PIT_PREC_FP64))
-    assert e.value.status == B.PIT_ERR_UNSUPPORTED
+    st = P.phi_batch(dt, cuda(u), out, B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=20000))
+    assert st.n_items == nb * P.G and st.n_failed == 0
+    got = host(out)
+    for b in range(nb):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < 1e-10, (b, g)
     # MGRIT over both classes.  The coarse systems have dT/h^2 up to 6700, so a
     # true FP64 residual cannot go much below 1e-12 relative: Krylov 1e-10.
     u0 = O.initial(W.IC_SINES, W.sine_modes(2, [(1.0, [1, 1]), (0.3, [2, 3])]))
@@ -407,4 +411,9 @@ def test_large_grids_keep_their_state_in_global_memory():
     uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
     P.mgrit_solve(cuda(u0), mopts, uT)
     seq = O.sequential(u0, dt, N, rtol=1e-15)
+    assert rel(host(uT), seq) < 1e-7
+    # the paper's form (FP64 Krylov, FAS, FCF) over both classes
+    fo = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-10, maxit=20000)
+    fopts = B.mgrit_opts(0.0, N * dt, N, m, 2, tol=tol, maxit=40, fine=fo, fas=True)
+    P.mgrit_solve(cuda(u0), fopts, uT)
     assert rel(host(uT), seq) < 1e-7
