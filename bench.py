@@ -312,18 +312,20 @@ def run_pit(args, rank, world, local):
     # roofline of the dominant kernel (steps_kernel<HEAT, MIXED, 3>).  ncu
     # shows it bound by the FP64 pipe (the refinement residual passes), so the
     # roofline is FP64 arithmetic: FP64 flops per node and residual pass =
-    # stencil diag x + sum_i off_i (x_-i + x_+i) (3d + 1), b - A x and x - A x
-    # (2), ||r||^2 (2) and the correction update (2) = 3d + 7, from the
-    # kernel's own work counters, over its event time (one profiled step with
-    # every grid in one lane), against GB300's nominal FP64 rate.  The shared-
-    # memory view of the FP32 inner iterations is reported beside it.
+    # stencil diag x + sum_i off_i (x_-i + x_+i) (3d + 1), b - A x (1) and the
+    # correction update (2) = 3d + 4, from the kernel's own work counters, over
+    # its event time (one profiled step with every grid in one lane; the
+    # relaxation launches alone when the coarse solves run in the FP32 form,
+    # which has no FP64 passes), against GB300's nominal FP64 rate.  The
+    # shared-memory view of the FP32 inner iterations is reported beside it.
     d = wl.d
     # family 0: relaxation launches (many entries per grid), 1: sequential sweeps
     phi_ms = prof.ms[0] + prof.ms[1]
     phi_launches = int(prof.launches[0] + prof.launches[1])
-    fp64_flops = prof.point_passes * (3 * d + 7)
+    fp64_ms = prof.ms[0] if chosen.crs.prec == B.PIT_PREC_FP32 else phi_ms
+    fp64_flops = prof.point_passes * (3 * d + 4)
     fp64_peak = FP64_PEAK_TFLOPS
-    achieved = fp64_flops / (phi_ms / 1e3) / 1e12 if phi_ms > 0 else None
+    achieved = fp64_flops / (fp64_ms / 1e3) / 1e12 if fp64_ms > 0 else None
     trf = ncu_traffic()
     items_per_launch = prof.phi_items / max(1, phi_launches)
     smem_bytes_per_point_iter = 2 + 4 * (2 * d + 1) + 4 + 16 + 8 + 8 + 4
@@ -333,12 +335,15 @@ def run_pit(args, rank, world, local):
     roofline = {"bound": "alu", "kernel": "steps_kernel<HEAT,MIXED,3> (grid-resident multi-step BE, FP32 CG in FP64 refinement)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp64_peak) if achieved else None,
-                "traffic": (trf * items_per_launch) if trf is not None else None,
+                "traffic": (trf * P.G * (wl.nsteps // wl.m)) if trf is not None else None,
+                "traffic_note": "DRAM bytes of one full relaxation launch (all grids x intervals) from the "
+                                "committed ncu summary, null when the kernel changed since",
                 "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s, profiling recipe table); an FMA "
-                               "micro-benchmark on this pool measured 1.20; the kernel's FP64 op mix (2d + 5 "
-                               "instructions for 3d + 7 flops) saturates the pipe at fp64_pipe_limit_of_mix of it",
-                "fp64_flops_per_node_pass": 3 * d + 7,
-                "fp64_pipe_limit_of_mix": (3 * d + 7) / (2.0 * (2 * d + 5)),
+                               "micro-benchmark on this pool measured 1.20; the kernel's FP64 op mix (2d + 3 "
+                               "instructions for 3d + 4 flops) saturates the pipe at fp64_pipe_limit_of_mix of it",
+                "fp64_flops_per_node_pass": 3 * d + 4,
+                "fp64_pipe_limit_of_mix": (3 * d + 4) / (2.0 * (2 * d + 3)),
+                "fp64_time_basis_ms": fp64_ms,
                 "phi_ms_one_lane": phi_ms, "phi_launches_per_step": phi_launches,
                 "relax_ms_one_lane": prof.ms[0], "sweep_ms_one_lane": prof.ms[1],
                 "relax_launches": int(prof.launches[0]), "sweep_launches": int(prof.launches[1]),

@@ -80,7 +80,8 @@ struct StepArgs {
     double *norms;
     const double *guess;     long long guess_stride, guess_step;
     double *xg;              // state in global memory (grids too large for shared memory):
-    double *bg;              //   x and b (MIXED) of entry b at xg/bg + b*n_total + grid offset;
+    double *bg;              //   x and b (MIXED) of entry b at xg/bg + b*n_total + grid offset, the
+                             //   FP32 step increment (MIXED) at slab 2;
                              //   PLAIN: Krylov vector k at xg + ((1+k) n_batch + b) n_total + offset
     long long n_total;
     const int *active;       // per grid, NULL = all active
@@ -137,7 +138,8 @@ size_t phi_smem_bytes(int prec, int op, int d, int n);
 cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s, bool xg = false);
 // Shared memory per item of the global-state variant (PLAIN or MIXED), and
 // the number of n_batch x n_total FP64 slabs of global workspace it uses
-// (x and b for MIXED; x and the Krylov vectors for PLAIN).
+// (x, b and the FP32 step increment for MIXED; x and the Krylov vectors for
+// PLAIN).
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n);
 int xg_slabs(int prec, int op);
 // Raise the dynamic shared-memory limit of every backward-Euler kernel.

@@ -14,10 +14,10 @@ size_t phi_smem_bytes(int prec, int op, int d, int n)
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n)
 {
     const size_t ld = (size_t)((n + 3) & ~3);
-    return (size_t)n_tab(op, d) * ld * 8 + (size_t)n_f32(op, prec, d) * ld * 4 + ld * 2 + 16;
+    return (size_t)n_tab(op, d) * ld * 8 + (size_t)n_f32(op, prec, d, true) * ld * 4 + ld * 2 + 16;
 }
 
-int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 2; }
+int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 3; }
 
 static size_t g_max_smem = 0;
 

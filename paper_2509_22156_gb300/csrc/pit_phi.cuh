@@ -26,11 +26,13 @@
 //          kernel and are kept lean: when a step has no forcing, the FP64 pass
 //          that verifies step s also yields x_s - A x_s, which is exactly the
 //          initial residual of step s+1 (b = x_s, x_0 = x_s), so each step
-//          costs one FP64 stencil pass per correction; conversions run on the
-//          integer pipes with an exact power-of-two scale, and only ||r||^2
-//          of the FP64 residual is accumulated in FP64 (the norms of the
-//          carried residual and of the next right-hand side, which only set
-//          tolerances, come from their FP32 copies).
+//          costs one FP64 stencil pass per correction.  The FP64 pipe does
+//          only what needs FP64 (the stencil on the FP64 state and b - A x):
+//          conversions run on the integer pipes with an exact power-of-two
+//          scale, the carried residual is r + (x - b) with the step increment
+//          accumulated in FP32, and the squared norms that feed the stopping
+//          test and the tolerances are summed from the FP32 copies (relative
+//          accuracy about 1e-7, far below what a stopping test resolves).
 // CG is the single-reduction (Chronopoulos-Gear) form: one fused block
 // reduction of (r,r) and (Ar,r) per iteration and two barriers.
 #pragma once
@@ -401,9 +403,12 @@ __host__ __device__ inline int n_f64(int op, int prec, int d)
     if (prec == SINGLE) return 0;
     return (prec == PLAIN ? 1 + krylov_vecs(op, prec) : 2) + n_tab(op, d);
 }
-__host__ __device__ inline int n_f32(int op, int prec, int d)
+// (MIXED keeps one more FP32 array in shared memory, the step increment dv;
+// its global-state variant keeps dv in global memory instead)
+__host__ __device__ inline int n_f32(int op, int prec, int d, bool xg = false)
 {
-    return prec != PLAIN ? krylov_vecs(op, prec) + n_tab(op, d) : 0;
+    if (prec == PLAIN) return 0;
+    return krylov_vecs(op, prec) + (prec == MIXED && !xg ? 1 : 0) + n_tab(op, d);
 }
 
 template <int OP, int PREC, int D, bool XG = false>
@@ -431,7 +436,8 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
     constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
     constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6) : (PREC == PLAIN ? 4 : 5);
-    constexpr int NF32 = (PREC != PLAIN) ? NKV + K : 0;
+    constexpr int NDV = (PREC == MIXED && !XG) ? 1 : 0;  // dv in shared memory
+    constexpr int NF32 = (PREC != PLAIN) ? NKV + NDV + K : 0;
 
     double *s64 = reinterpret_cast<double *>(smem);
     double *x = XG ? a.xg + (long long)b * a.n_total + GI.off : s64;
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     const long long vs = XG ? (long long)a.n_batch * a.n_total : (long long)ld;
     double *tab64 = PREC == SINGLE ? nullptr : s64 + (size_t)(NF64 - K) * ld;
     float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
-    float *tab32 = f32 + (size_t)NKV * ld;
+    float *tab32 = f32 + (size_t)(NKV + NDV) * ld;
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
 
     const double *in = a.in + (long long)b * a.in_stride + GI.off;
@@ -526,6 +532,10 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
     double rn0_c = 0.0, bb_c = 0.0;
     int kr_c = 0;
     float *rv = f32 + ld, *pv = f32 + 2 * ld, *sv = f32 + 3 * ld, *wv = f32 + 4 * ld, *tv = f32 + 5 * ld;
+    // MIXED: increment x - b of the current step, scaled by 2^ks, accumulated
+    // in FP32 from the corrections (the carried residual is r + dv)
+    float *dv = XG ? reinterpret_cast<float *>(a.xg + ((long long)2 * a.n_batch + b) * a.n_total + GI.off)
+                   : f32 + (size_t)NKV * ld;
 
     for (int step = 1; step <= a.nsteps; ++step) {
         __syncthreads();  // state complete
@@ -679,19 +689,21 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 R64.template sum<1>(acc);  // also: bvec and x complete
                 bb = acc[0];
                 kr = scale_exp(bb);
-                acc[0] = 0.0;
+                float accf[1] = {0.0f};
                 for (int j = tid; j < n; j += nt) {
-                    const double rj = bvec[j] - A64(x, j);
-                    rv[j] = to_f32(rj, kr);
-                    acc[0] += rj * rj;
+                    const float rf = to_f32(bvec[j] - A64(x, j), kr);
+                    rv[j] = rf;
+                    accf[0] += rf * rf;
                 }
-                R64.template sum<1>(acc);
+                R32.template sum<1>(accf);
                 ++passes;
-                rn2 = acc[0];
+                rn2 = to_f64(accf[0], -2 * kr);
             }
             have_r0 = false;
             const double stop2 = a.rtol * a.rtol * bb;
             const int ks = scale_exp(bb);  // FP32 copies of this step: value 2^ks, ||b|| 2^ks in [1, 2)
+            if (carry_ok)
+                for (int j = tid; j < n; j += nt) dv[j] = 0.0f;  // x = b at the start of the step
             int st_step = PIT_OK;
             bool carried = false;
             for (int pass = 0;; ++pass) {
@@ -730,36 +742,42 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
                 // a stalled or broken-down inner solve still gives a usable
                 // correction; the FP64 residual decides.  x += e 2^(kn - kr)
+                // (FP64), dv += e 2^(kn - kr + ks) (FP32, exact scaling)
                 const double cs = pow2d(kn - kr);
-                for (int j = tid; j < n; j += nt) x[j] = fma(to_f64(e[j], 0), cs, x[j]);
+                const int kd = min(max(kn - kr + ks, -120), 120);
+                const float csf = __uint_as_float((unsigned)(127 + kd) << 23);
+                for (int j = tid; j < n; j += nt) {
+                    const float ej = e[j];
+                    x[j] = fma(to_f64(ej, 0), cs, x[j]);
+                    if (carry_ok) dv[j] = fmaf(ej, csf, dv[j]);
+                }
                 __syncthreads();  // x complete
-                // FP64 check: r = b - A x (norm in FP64), and (no forcing) the
-                // next step's r0 = x - A x with the norms of r0 and of x (the
-                // next right-hand side) accumulated from their FP32 copies
+                // FP64 check: r = b - A x; the stopping test and the next
+                // step's r0 = x - A x = r + (x - b) work on the FP32 copies
+                // (their squared norms accumulated in FP32), as does ||x||^2,
+                // the next right-hand side's norm
                 float *cv = (OP == PIT_OP_OU) ? tv : wv;
-                double accd[1] = {0.0};
-                float accf[2] = {0.0f, 0.0f};
+                float accf[3] = {0.0f, 0.0f, 0.0f};
                 for (int j = tid; j < n; j += nt) {
                     const double xj = x[j];
-                    const double Ax = A64(x, j);
-                    const double rj = bvec[j] - Ax;
-                    rv[j] = to_f32(rj, ks);
-                    accd[0] += rj * rj;
+                    const float rf = to_f32(bvec[j] - A64(x, j), ks);
+                    rv[j] = rf;
+                    accf[0] += rf * rf;
                     if (carry_ok) {
-                        const float cj = to_f32(xj - Ax, ks);
+                        const float cj = rf + dv[j];
                         const float xf = to_f32(xj, ks);
                         cv[j] = cj;
-                        accf[0] += cj * cj;
-                        accf[1] += xf * xf;
+                        accf[1] += cj * cj;
+                        accf[2] += xf * xf;
                     }
                 }
-                sum_mixed<1, 2>(R64, accd, R32, accf);
+                R32.template sum<3>(accf);
                 ++passes;
-                rn2 = accd[0];
+                rn2 = to_f64(accf[0], -2 * ks);
                 kr = ks;
                 if (carry_ok) {
-                    rn0_c = to_f64(accf[0], -2 * ks);
-                    bb_c = to_f64(accf[1], -2 * ks);
+                    rn0_c = to_f64(accf[1], -2 * ks);
+                    bb_c = to_f64(accf[2], -2 * ks);
                     kr_c = ks;
                     carried = true;
                 }
