@@ -155,9 +155,11 @@ MGRIT_TOL, KRYLOV_RTOL = 1e-7, 1e-10
 # 20-fold and its combination cancels strongly, so its tolerances are tighter
 # (checked the same way)
 MGRIT_TOL_BY_WORKLOAD = {1: 1e-8, 2: 1e-7, 3: 2e-9, 4: 1e-10, 5: 5e-9}
-# the d = 6 combination sums 4921 grids with coefficients up to C(5, 2) = 10,
-# which amplifies per-grid errors a few hundred times: tighter Krylov there
-KRYLOV_RTOL_BY_WORKLOAD = {4: 1e-11, 5: 1e-11}
+# the combination sums grids with coefficients of both signs (d = 6: 4921
+# grids, coefficients up to C(5, 2) = 10), which amplifies correlated per-grid
+# errors up to sum |c_g| times; steps that stop just below a 1e-10 residual
+# leave the heat3d_n9 combination at 1e-6, so 1e-11 where measured necessary
+KRYLOV_RTOL_BY_WORKLOAD = {2: 1e-11, 4: 1e-11, 5: 1e-11}
 PAPER_TOL, PAPER_RTOL = 1e-8, 1e-10
 
 
