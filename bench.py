@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="pit", choices=["pit", "reference"])
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--relax", default="F", choices=["FCF", "F"], help="relaxation of the finest MGRIT level")
+    ap.add_argument("--lanes", type=int, default=0, help="MGRIT lanes (0: library default)")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain-FP64 and sequential forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -226,6 +227,7 @@ def run_pit(args, rank, world, local):
     wl = W.workload(args.workload)
     P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi, wl.theta, wl.sigma, wl.vamp, stream=stream.cuda_stream)
     chosen, fp64, mixed, plain = solver_setup(wl, B, relax=B.PIT_RELAX_F if args.relax == "F" else B.PIT_RELAX_FCF)
+    chosen.lanes = args.lanes
     torch.cuda.nvtx.range_push("train")
     training = train_network(P, wl, B, mixed)
     torch.cuda.nvtx.range_pop()
