@@ -373,12 +373,23 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     }
     const int cand[4] = {64, 128, 256, 512};
     CU(P->w_tune.ensure(sizeof(double) * P->ntot * c.nb));
+    // the trial keeps the call's inputs (a correction sweep starts from zero
+    // and is driven by its forcing) and writes only scratch; narrow batches
+    // (sequential sweeps, latency bound) are timed over several steps
     StepCall t;
     t.dt = c.dt;
     t.nb = c.nb;
-    t.nsteps = 1;
+    t.nsteps = wide ? 1 : (c.nsteps < 8 ? c.nsteps : 8);
     t.in = c.in;
     t.is = c.is;
+    t.f = c.f;
+    t.fs = c.fs;
+    t.g = c.g;
+    t.gs = c.gs;
+    t.gst = c.gst;
+    t.guess = c.guess;
+    t.gus = c.gus;
+    t.gust = c.gust;
     t.out_last = P->w_tune.d();
     t.ols = P->ntot;
     StepArgs a = make_args(P, o, t, active);
@@ -395,7 +406,7 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     float best = 1e30f;
     int best_t = 128;
     for (int k = 0; k < 4; ++k) {
-        for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
+        for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up; the last is timed
             CU(cudaEventRecord(e0, P->stream));
             CU(launch_steps(prec, a, cand[k], P->smem_cls[prec][cls], P->stream, cls == 1));
             CU(cudaEventRecord(e1, P->stream));
@@ -1189,8 +1200,9 @@ pit_status lanes_prime(Mg &M, int Nc)
     pit_problem *P = M.P;
     const pit_mgrit_opts *o = M.o;
     const long long nt = M.nt;
-    struct Rep { const pit_solve_opts *so; int nb; double dt; };
-    Rep reps[3] = {{&o->fine, Nc, M.dt}, {&o->crs, 1, M.dt * o->m}, {&o->crs, Nc / o->m, M.dt * o->m}};
+    struct Rep { const pit_solve_opts *so; int nb; double dt; int nsteps; };
+    Rep reps[3] = {{&o->fine, Nc, M.dt, o->m}, {&o->crs, 1, M.dt * o->m, Nc},
+                   {&o->crs, Nc / o->m, M.dt * o->m, o->m}};
     const int n_reps = o->levels == 3 ? 3 : 2;
     for (int r = 0; r < n_reps; ++r) {
         const int prec = prec_form(reps[r].so->prec);
@@ -1199,8 +1211,8 @@ pit_status lanes_prime(Mg &M, int Nc)
         StepCall c;
         c.dt = reps[r].dt;
         c.nb = reps[r].nb;
-        c.nsteps = 1;
-        c.in = P->m_U.d();
+        c.nsteps = reps[r].nsteps;
+        c.in = P->m_U.d();  // u0 at every C-point
         c.is = nt;
         if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op)));
         for (int cls = 0; cls < 2; ++cls)
