@@ -65,6 +65,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device=None):
+    """The slowest rank's time: every rank holds an independent replica of the
+    workload (weak scaling), the job finishes with the last one."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_step):
+    """Whole-job throughput: the units all ranks processed over the max time."""
+    return world * units_per_rank / (ms_step / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 class Clocks:
@@ -288,13 +305,8 @@ def run_pit(args, rank, world, local):
     step(one_lane, u0, out)
     prof = P.profile_read()
     P.profile_enable(False)
-    ms_step = total_ms / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * dofsteps / (ms_step / 1e3)
+    ms_step = max_over_ranks(total_ms / args.steps, world, dev)
+    value = job_value(dofsteps, world, ms_step)
     gpu_launches = int(sum(prof_chosen.launches)) * args.steps
 
     # end to end through the C ABI with host buffers (pinned): H2D of u0 and
