@@ -412,7 +412,7 @@ __host__ __device__ inline int n_f32(int op, int prec, int d, bool xg = false)
 }
 
 template <int OP, int PREC, int D, bool XG = false>
-__global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(StepArgs a)
+__global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 {
     typedef typename std::conditional<PREC == PLAIN, double, float>::type T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 bb = acc[0];
                 kr = scale_exp(bb);
                 float accf[1] = {0.0f};
+#pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
                     const float rf = to_f32(bvec[j] - A64(x, j), kr);
                     rv[j] = rf;
@@ -746,6 +747,7 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 const double cs = pow2d(kn - kr);
                 const int kd = min(max(kn - kr + ks, -120), 120);
                 const float csf = __uint_as_float((unsigned)(127 + kd) << 23);
+#pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
                     const float ej = e[j];
                     x[j] = fma(to_f64(ej, 0), cs, x[j]);
@@ -758,6 +760,9 @@ __global__ void __launch_bounds__(512, (D >= 5 || XG) ? 1 : 2) steps_kernel(Step
                 // the next right-hand side's norm
                 float *cv = (OP == PIT_OP_OU) ? tv : wv;
                 float accf[3] = {0.0f, 0.0f, 0.0f};
+                // (unrolled: independent nodes keep several FP64 stencil
+                // chains in flight, the FP64 latency is long on GB300)
+#pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
                     const double xj = x[j];
                     const float rf = to_f32(bvec[j] - A64(x, j), ks);
