@@ -77,10 +77,11 @@ struct DBuf {
 // others.
 struct pit_lane {
     std::vector<int> grids;
-    cudaStream_t s = nullptr, side = nullptr;
+    cudaStream_t s = nullptr, side = nullptr, side2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
     bool planned[NPREC] = {};
     int n_cls[NPREC][2] = {};
+    int split[NPREC] = {};  // class-0 position of the first small grid
     int *d_order_cls[NPREC][2] = {};
     int *d_act = nullptr;     // G flags, zero outside the lane
     int *h_act = nullptr;     // pinned, G
@@ -120,9 +121,15 @@ struct pit_problem {
     std::vector<int> h_order_cls[NPREC][2];
     size_t smem_cls[NPREC][2] = {};
     size_t smem_need[NPREC] = {};    // class 0 (used by the allocation-free step)
-    int threads[NPREC][2][2] = {};   // [prec][wide batch][class]; 0 = not tuned yet
+    // class 0 runs as two launches: grids needing more than half of the largest
+    // grid's shared memory, then (from position split) the smaller ones with
+    // their own, smaller allocation, so that more of their CTAs fit on an SM
+    int split[NPREC] = {};
+    size_t smem_small[NPREC] = {};
+    int threads[NPREC][2][3] = {};   // [prec][wide batch][part: 0 large, 1 global state, 2 small]; 0 = not tuned
     int forced_threads[2] = {0, 0};  // override [wide batch]
     cudaStream_t side = nullptr;     // second stream: the large-grid class runs beside class 0
+    cudaStream_t side2 = nullptr;    // third stream: the small grids of class 0
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf w_xg;                       // FP64 state of class-1 items
     std::vector<pit_lane> lanes;     // MGRIT lanes (built on first use)
@@ -265,6 +272,13 @@ pit_status plan(pit_problem *P, int prec)
         cls[1].push_back(g);
         need[1] = bx > need[1] ? bx : need[1];
     }
+    {
+        int k = 0;
+        const int n0 = (int)cls[0].size();
+        while (k < n0 && 2 * phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) > need[0]) ++k;
+        P->split[prec] = k;
+        P->smem_small[prec] = k < n0 ? phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) : 0;
+    }
     for (int c = 0; c < 2; ++c) {
         P->n_cls[prec][c] = (int)cls[c].size();
         P->h_order_cls[prec][c] = cls[c];
@@ -362,11 +376,33 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
 // batch x grid class) is chosen once per problem by timing one backward-Euler
 // step of the first real call of that class with every candidate, output to
 // scratch.
+// One launch part of a precision form (of a lane, when given): 0 = class-0
+// grids above half the largest shared-memory need, 2 = the other class-0
+// grids, 1 = class 1 (state in global memory).
+struct PartView {
+    const int *order;
+    int n;
+    size_t smem;
+    bool xg;
+};
+PartView part_view(const pit_problem *P, const pit_lane *L, int prec, int part)
+{
+    const int n0 = L ? L->n_cls[prec][0] : P->n_cls[prec][0];
+    const int k = L ? L->split[prec] : P->split[prec];
+    int *o0 = L ? L->d_order_cls[prec][0] : P->d_order_cls[prec][0];
+    if (part == 0) return {o0, k, P->smem_cls[prec][0], false};
+    if (part == 2) return {o0 ? o0 + k : nullptr, n0 - k, P->smem_small[prec], false};
+    return {L ? L->d_order_cls[prec][1] : P->d_order_cls[prec][1], L ? L->n_cls[prec][1] : P->n_cls[prec][1],
+            P->smem_cls[prec][1], true};
+}
+
 pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_opts &o, const StepCall &c,
                 const int *active)
 {
     int &slot = P->threads[prec][wide ? 1 : 0][cls];
     if (slot) return PIT_OK;
+    const PartView v = part_view(P, nullptr, prec, cls);
+    if (v.n <= 0) return PIT_OK;
     if (P->forced_threads[wide ? 1 : 0]) {
         slot = P->forced_threads[wide ? 1 : 0];
         return PIT_OK;
@@ -394,8 +430,8 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     t.ols = P->ntot;
     StepArgs a = make_args(P, o, t, active);
     a.stats = nullptr;
-    a.order = P->d_order_cls[prec][cls];
-    a.n_order = P->n_cls[prec][cls];
+    a.order = v.order;
+    a.n_order = v.n;
     if (cls == 1) {
         a.xg = P->w_xg.d();
         a.bg = a.xg + (long long)c.nb * P->ntot;
@@ -408,7 +444,7 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     for (int k = 0; k < 4; ++k) {
         for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up; the last is timed
             CU(cudaEventRecord(e0, P->stream));
-            CU(launch_steps(prec, a, cand[k], P->smem_cls[prec][cls], P->stream, cls == 1));
+            CU(launch_steps(prec, a, cand[k], v.smem, P->stream, v.xg));
             CU(cudaEventRecord(e1, P->stream));
         }
         CU(cudaEventSynchronize(e1));
@@ -433,35 +469,41 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
     if (L && !L->planned[prec]) return fail(PIT_ERR_INVALID_ARG, "lane without a launch plan");
     const bool wide = c.nb >= 8;
-    const int n0 = L ? L->n_cls[prec][0] : P->n_cls[prec][0];
-    const int n1 = L ? L->n_cls[prec][1] : P->n_cls[prec][1];
-    const bool two = n1 > 0;
+    PartView v[3];
+    for (int q = 0; q < 3; ++q) v[q] = part_view(P, L, prec, q);
     // (a lane's workspaces and CTA sizes are prepared before its first launch)
-    if (two && !L) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op)));
-    for (int cls = 0; cls < 2; ++cls)
-        if (P->n_cls[prec][cls] > 0 && !L) TRY(tune(P, prec, wide, cls, o, c, active));
-    cudaStream_t s0 = L ? L->s : P->stream, s1 = L ? L->side : P->side;
+    if (v[1].n > 0 && !L) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op)));
+    if (!L)
+        for (int q = 0; q < 3; ++q) TRY(tune(P, prec, wide, q, o, c, active));
+    cudaStream_t st[3] = {L ? L->s : P->stream, L ? L->side : P->side, L ? L->side2 : P->side2};
     cudaEvent_t ef = L ? L->fork : P->ev_fork, ej = L ? L->join : P->ev_join;
     StepArgs a = make_args(P, o, c, active);
-    ProfScope ps(P, wide ? 0 : 1, s0);
-    if (two) {
-        CU(cudaEventRecord(ef, s0));
-        CU(cudaStreamWaitEvent(s1, ef, 0));
+    ProfScope ps(P, wide ? 0 : 1, st[0]);
+    const bool fork = v[1].n > 0 || (v[0].n > 0 && v[2].n > 0);
+    if (fork) {
+        CU(cudaEventRecord(ef, st[0]));
+        CU(cudaStreamWaitEvent(st[1], ef, 0));
+        CU(cudaStreamWaitEvent(st[2], ef, 0));
+    }
+    // the part without others runs on the main stream; with others, large
+    // grids on the main stream, small grids and global-state grids beside it
+    for (int q = 0; q < 3; ++q) {
+        if (v[q].n <= 0) continue;
         StepArgs b = a;
-        b.order = L ? L->d_order_cls[prec][1] : P->d_order_cls[prec][1];
-        b.n_order = n1;
-        b.xg = P->w_xg.d();
-        b.bg = b.xg + (long long)c.nb * P->ntot;
-        CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][1], P->smem_cls[prec][1], s1, true));
+        b.order = v[q].order;
+        b.n_order = v[q].n;
+        if (v[q].xg) {
+            b.xg = P->w_xg.d();
+            b.bg = b.xg + (long long)c.nb * P->ntot;
+        }
+        cudaStream_t sq = fork ? st[q] : st[0];
+        CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][q], v[q].smem, sq, v[q].xg));
     }
-    if (n0 > 0) {
-        a.order = L ? L->d_order_cls[prec][0] : P->d_order_cls[prec][0];
-        a.n_order = n0;
-        CU(launch_steps(prec, a, P->threads[prec][wide ? 1 : 0][0], P->smem_cls[prec][0], s0, false));
-    }
-    if (two) {
-        CU(cudaEventRecord(ej, s1));
-        CU(cudaStreamWaitEvent(s0, ej, 0));
+    if (fork) {
+        for (int q = 1; q < 3; ++q) {
+            CU(cudaEventRecord(ej, st[q]));
+            CU(cudaStreamWaitEvent(st[0], ej, 0));
+        }
     }
     return PIT_OK;
 }
@@ -632,6 +674,7 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
                              cudaGetErrorString(e_)));                                              \
     } while (0)
     CUB(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+    CUB(cudaStreamCreateWithFlags(&P->side2, cudaStreamNonBlocking));
     CUB(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     CUB(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     CUB(phi_kernels_init(P->max_smem));
@@ -675,6 +718,7 @@ pit_status pit_problem_destroy(pit_problem_t P)
     for (pit_lane &L : P->lanes) {
         if (L.s) cudaStreamSynchronize(L.s);
         if (L.side) cudaStreamSynchronize(L.side);
+        if (L.side2) cudaStreamSynchronize(L.side2);
         for (int p = 0; p < NPREC; ++p)
             for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
         cudaFree(L.d_act);
@@ -682,6 +726,7 @@ pit_status pit_problem_destroy(pit_problem_t P)
         cudaFreeHost(L.h_res);
         if (L.s) cudaStreamDestroy(L.s);
         if (L.side) cudaStreamDestroy(L.side);
+        if (L.side2) cudaStreamDestroy(L.side2);
         if (L.fork) cudaEventDestroy(L.fork);
         if (L.join) cudaEventDestroy(L.join);
         if (L.done) cudaEventDestroy(L.done);
@@ -694,6 +739,10 @@ pit_status pit_problem_destroy(pit_problem_t P)
     if (P->side) {
         cudaStreamSynchronize(P->side);
         cudaStreamDestroy(P->side);
+    }
+    if (P->side2) {
+        cudaStreamSynchronize(P->side2);
+        cudaStreamDestroy(P->side2);
     }
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
@@ -1123,6 +1172,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
         for (pit_lane &L : P->lanes) {
             cudaStreamSynchronize(L.s);
             cudaStreamSynchronize(L.side);
+            cudaStreamSynchronize(L.side2);
             for (int p = 0; p < NPREC; ++p)
                 for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
             cudaFree(L.d_act);
@@ -1130,6 +1180,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
             cudaFreeHost(L.h_res);
             cudaStreamDestroy(L.s);
             cudaStreamDestroy(L.side);
+            cudaStreamDestroy(L.side2);
             cudaEventDestroy(L.fork);
             cudaEventDestroy(L.join);
             cudaEventDestroy(L.done);
@@ -1151,6 +1202,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
         for (pit_lane &L : P->lanes) {
             CU(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
             CU(cudaStreamCreateWithFlags(&L.side, cudaStreamNonBlocking));
+            CU(cudaStreamCreateWithFlags(&L.side2, cudaStreamNonBlocking));
             CU(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
@@ -1163,8 +1215,12 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
         for (int k = 0; k < K; ++k) {
             pit_lane &L = P->lanes[k];
             if (L.planned[prec]) continue;
-            std::vector<char> mine(P->G, 0);
+            std::vector<char> mine(P->G, 0), large(P->G, 0);
             for (int g : L.grids) mine[g] = 1;
+            for (int q = 0; q < P->split[prec]; ++q) large[P->h_order_cls[prec][0][q]] = 1;
+            L.split[prec] = 0;
+            for (int g : P->h_order_cls[prec][0])
+                if (mine[g] && large[g]) ++L.split[prec];
             for (int c = 0; c < 2; ++c) {
                 std::vector<int> lst;
                 for (int g : P->h_order_cls[prec][c])
@@ -1215,8 +1271,7 @@ pit_status lanes_prime(Mg &M, int Nc)
         c.in = P->m_U.d();  // u0 at every C-point
         c.is = nt;
         if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op)));
-        for (int cls = 0; cls < 2; ++cls)
-            if (P->n_cls[prec][cls] > 0) TRY(tune(P, prec, c.nb >= 8, cls, *reps[r].so, c, M.active));
+        for (int part = 0; part < 3; ++part) TRY(tune(P, prec, c.nb >= 8, part, *reps[r].so, c, M.active));
     }
     return PIT_OK;
 }

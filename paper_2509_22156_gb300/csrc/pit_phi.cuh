@@ -254,6 +254,7 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
     status = PIT_OK;
     __syncthreads();  // r complete
     T v[2] = {T(0), T(0)};
+#pragma unroll 4
     for (int j = tid; j < n; j += nt) {
         const T wj = A(r, j);
         w[j] = wj;
@@ -276,6 +277,7 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
     int k = 0;
     for (;;) {
         if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T pj = first ? r[j] : r[j] + beta * p[j];
             const T sj = first ? w[j] : w[j] + beta * s[j];
@@ -288,6 +290,7 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
         ++k;
         __syncthreads();
         T u[2] = {T(0), T(0)};
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T wj = A(r, j);
             w[j] = wj;
@@ -317,6 +320,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     T rr[1] = {T(0)};
+#pragma unroll 4
     for (int j = tid; j < n; j += nt) {
         const T rj = r[j];
         rh[j] = rj;
@@ -335,6 +339,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         }
         if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
         T rho_n[1] = {T(0)};
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) rho_n[0] += rh[j] * r[j];
         R.template sum<1>(rho_n);
         if (rho_n[0] == T(0) || omega == T(0) || rho_n[0] != rho_n[0]) {
@@ -343,9 +348,11 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         }
         const T beta = (rho_n[0] / rho) * (alpha / omega);
         if (!(fabs(beta) < (T)1e30)) { status = (beta != beta) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) p[j] = r[j] + beta * (p[j] - omega * v[j]);
         __syncthreads();
         T rhv[1] = {T(0)};
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T vj = A(p, j);
             v[j] = vj;
@@ -358,9 +365,11 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         }
         alpha = rho_n[0] / rhv[0];
         if (!(fabs(alpha) < (T)1e30)) { status = (alpha != alpha) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) r[j] = r[j] - alpha * v[j];  // s
         __syncthreads();
         T tt[2] = {T(0), T(0)};
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T tj = A(r, j);
             t[j] = tj;
@@ -371,6 +380,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         omega = (tt[0] > T(0)) ? tt[1] / tt[0] : T(0);
         if (!(fabs(omega) < (T)1e30)) { status = (omega != omega) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
         T rn[1] = {T(0)};
+#pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             X[j] += (TX)(alpha * p[j] + omega * r[j]);
             const T rj = r[j] - omega * t[j];
