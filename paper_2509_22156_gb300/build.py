@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpit.so")
-SOURCES = ["pit_phi_heat.cu", "pit_phi_varheat.cu", "pit_phi_ou.cu", "pit_phi.cu", "pit_net.cu", "pit_aux.cu", "pit_api.cu"]
+SOURCES = [f"pit_phi_{op}_{p}.cu" for op in ("heat", "varheat", "ou") for p in ("mixed", "fp64", "fp32")] + \
+    [f"pit_net_d{d}.cu" for d in range(1, 7)] + ["pit_phi.cu", "pit_net.cu", "pit_aux.cu", "pit_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,7 +39,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
     headers = [os.path.join(CSRC, "pit_internal.cuh"), os.path.join(CSRC, "pit_phi.cuh"),
-               os.path.join(ROOT, "include", "pit.h")]
+               os.path.join(CSRC, "pit_net.cuh"), os.path.join(ROOT, "include", "pit.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                     "-I", os.path.join(ROOT, "include")] + (extra or [])
     procs, objs = [], []

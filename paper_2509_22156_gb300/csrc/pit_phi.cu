@@ -24,9 +24,12 @@ static size_t g_max_smem = 0;
 cudaError_t phi_kernels_init(size_t max_smem)
 {
     const int bytes = (int)max_smem;
-    cudaError_t e = steps_init_heat(bytes);
-    if (e == cudaSuccess) e = steps_init_varheat(bytes);
-    if (e == cudaSuccess) e = steps_init_ou(bytes);
+    cudaError_t e = cudaSuccess;
+    cudaError_t (*inits[])(int) = {steps_init_heat_fp64,    steps_init_heat_mixed,    steps_init_heat_fp32,
+                                   steps_init_varheat_fp64, steps_init_varheat_mixed, steps_init_varheat_fp32,
+                                   steps_init_ou_fp64,      steps_init_ou_mixed,      steps_init_ou_fp32};
+    for (auto f : inits)
+        if (e == cudaSuccess) e = f(bytes);
     if (e == cudaSuccess) g_max_smem = max_smem;
     return e;
 }
@@ -39,9 +42,17 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)blocks), block(threads);
     switch (a.op.op) {
-    case PIT_OP_HEAT: return steps_launch_heat(prec, a.op.d, a, grid, block, smem, s, xg);
-    case PIT_OP_VARHEAT: return steps_launch_varheat(prec, a.op.d, a, grid, block, smem, s, xg);
-    case PIT_OP_OU: return steps_launch_ou(prec, a.op.d, a, grid, block, smem, s, xg);
+#define PIT_BY_PREC(OPN)                                                                                          \
+    switch (prec) {                                                                                               \
+    case PLAIN: return steps_launch_##OPN##_fp64(a.op.d, a, grid, block, smem, s, xg);                            \
+    case MIXED: return steps_launch_##OPN##_mixed(a.op.d, a, grid, block, smem, s, xg);                           \
+    case SINGLE: return steps_launch_##OPN##_fp32(a.op.d, a, grid, block, smem, s, xg);                           \
+    default: return cudaErrorInvalidValue;                                                                        \
+    }
+    case PIT_OP_HEAT: PIT_BY_PREC(heat)
+    case PIT_OP_VARHEAT: PIT_BY_PREC(varheat)
+    case PIT_OP_OU: PIT_BY_PREC(ou)
+#undef PIT_BY_PREC
     default: return cudaErrorInvalidValue;
     }
 }

@@ -846,56 +846,46 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     }
 }
 
-// Per-operator launchers (one translation unit each).
-cudaError_t steps_init_heat(int bytes);
-cudaError_t steps_init_varheat(int bytes);
-cudaError_t steps_init_ou(int bytes);
-cudaError_t steps_launch_heat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              bool xg);
-cudaError_t steps_launch_varheat(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,
-                                 cudaStream_t s, bool xg);
-cudaError_t steps_launch_ou(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                            bool xg);
+// Launchers, one translation unit per (operator, precision form): OPN names
+// the operator (heat, varheat, ou), PN the form (fp64, mixed, fp32).
+#define PIT_STEPS_DECL(OPN, PN)                                                                                   \
+    cudaError_t steps_init_##OPN##_##PN(int bytes);                                                               \
+    cudaError_t steps_launch_##OPN##_##PN(int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,           \
+                                          cudaStream_t s, bool xg);
+PIT_STEPS_DECL(heat, fp64) PIT_STEPS_DECL(heat, mixed) PIT_STEPS_DECL(heat, fp32)
+PIT_STEPS_DECL(varheat, fp64) PIT_STEPS_DECL(varheat, mixed) PIT_STEPS_DECL(varheat, fp32)
+PIT_STEPS_DECL(ou, fp64) PIT_STEPS_DECL(ou, mixed) PIT_STEPS_DECL(ou, fp32)
 
-// Instantiates the launcher and attribute setter of one operator for D = 1..6.
-#define PIT_STEPS_SET3(OPV, D)                                                                                    \
-    set((const void *)steps_kernel<OPV, PLAIN, D>); set((const void *)steps_kernel<OPV, MIXED, D>);               \
-    set((const void *)steps_kernel<OPV, SINGLE, D>); set((const void *)steps_kernel<OPV, MIXED, D, true>);        \
-    set((const void *)steps_kernel<OPV, PLAIN, D, true>);
-#define PIT_STEPS_CASE3(OPV, D)                                                                                   \
-    case D * 3 + PLAIN: steps_kernel<OPV, PLAIN, D><<<grid, block, smem, s>>>(a); break;                          \
-    case D * 3 + MIXED: steps_kernel<OPV, MIXED, D><<<grid, block, smem, s>>>(a); break;                          \
-    case D * 3 + SINGLE: steps_kernel<OPV, SINGLE, D><<<grid, block, smem, s>>>(a); break;
-#define PIT_STEPS_CASE_XG(OPV, D)                                                                                 \
-    case D * 3 + PLAIN: steps_kernel<OPV, PLAIN, D, true><<<grid, block, smem, s>>>(a); break;                    \
-    case D * 3 + MIXED: steps_kernel<OPV, MIXED, D, true><<<grid, block, smem, s>>>(a); break;
-#define PIT_STEPS_OP(NAME, OPV)                                                                                   \
-    cudaError_t steps_init_##NAME(int bytes)                                                                      \
+// Instantiates the attribute setter and launcher of one operator and form for
+// D = 1..6 (XGV: whether the form has the global-state variant).
+#define PIT_STEPS_SET1(OPV, PV, XGV, D)                                                                           \
+    set((const void *)steps_kernel<OPV, PV, D>);                                                                  \
+    if constexpr (XGV) set((const void *)steps_kernel<OPV, PV, D, XGV>);
+#define PIT_STEPS_CASE1(OPV, PV, XGV, D)                                                                          \
+    case D:                                                                                                       \
+        if constexpr (XGV) {                                                                                      \
+            if (xg) { steps_kernel<OPV, PV, D, XGV><<<grid, block, smem, s>>>(a); break; }                        \
+        }                                                                                                         \
+        steps_kernel<OPV, PV, D><<<grid, block, smem, s>>>(a);                                                    \
+        break;
+#define PIT_STEPS_OP_PREC(OPN, PN, OPV, PV, XGV)                                                                  \
+    cudaError_t steps_init_##OPN##_##PN(int bytes)                                                                \
     {                                                                                                             \
         cudaError_t e = cudaSuccess;                                                                              \
         auto set = [&](const void *fn) {                                                                          \
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
         };                                                                                                        \
-        PIT_STEPS_SET3(OPV, 1) PIT_STEPS_SET3(OPV, 2) PIT_STEPS_SET3(OPV, 3)                                      \
-        PIT_STEPS_SET3(OPV, 4) PIT_STEPS_SET3(OPV, 5) PIT_STEPS_SET3(OPV, 6)                                      \
+        PIT_STEPS_SET1(OPV, PV, XGV, 1) PIT_STEPS_SET1(OPV, PV, XGV, 2) PIT_STEPS_SET1(OPV, PV, XGV, 3)           \
+        PIT_STEPS_SET1(OPV, PV, XGV, 4) PIT_STEPS_SET1(OPV, PV, XGV, 5) PIT_STEPS_SET1(OPV, PV, XGV, 6)           \
         return e;                                                                                                 \
     }                                                                                                             \
-    cudaError_t steps_launch_##NAME(int prec, int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,       \
-                                    cudaStream_t s, bool xg)                                                      \
+    cudaError_t steps_launch_##OPN##_##PN(int d, const StepArgs &a, dim3 grid, dim3 block, size_t smem,           \
+                                          cudaStream_t s, bool xg)                                                \
     {                                                                                                             \
-        if (xg) {                                                                                                 \
-            if (prec != MIXED && prec != PLAIN) return cudaErrorInvalidValue;                                     \
-            switch (d * 3 + prec) {                                                                               \
-            PIT_STEPS_CASE_XG(OPV, 1) PIT_STEPS_CASE_XG(OPV, 2) PIT_STEPS_CASE_XG(OPV, 3)                         \
-            PIT_STEPS_CASE_XG(OPV, 4) PIT_STEPS_CASE_XG(OPV, 5) PIT_STEPS_CASE_XG(OPV, 6)                         \
-            default: return cudaErrorInvalidValue;                                                                \
-            }                                                                                                     \
-            return cudaGetLastError();                                                                            \
-        }                                                                                                         \
-        if (prec < 0 || prec >= NPREC) return cudaErrorInvalidValue;                                              \
-        switch (d * 3 + prec) {                                                                                   \
-        PIT_STEPS_CASE3(OPV, 1) PIT_STEPS_CASE3(OPV, 2) PIT_STEPS_CASE3(OPV, 3)                                   \
-        PIT_STEPS_CASE3(OPV, 4) PIT_STEPS_CASE3(OPV, 5) PIT_STEPS_CASE3(OPV, 6)                                   \
+        if (xg && !XGV) return cudaErrorInvalidValue;                                                             \
+        switch (d) {                                                                                              \
+        PIT_STEPS_CASE1(OPV, PV, XGV, 1) PIT_STEPS_CASE1(OPV, PV, XGV, 2) PIT_STEPS_CASE1(OPV, PV, XGV, 3)        \
+        PIT_STEPS_CASE1(OPV, PV, XGV, 4) PIT_STEPS_CASE1(OPV, PV, XGV, 5) PIT_STEPS_CASE1(OPV, PV, XGV, 6)        \
         default: return cudaErrorInvalidValue;                                                                    \
         }                                                                                                         \
         return cudaGetLastError();                                                                                \
