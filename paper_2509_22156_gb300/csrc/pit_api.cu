@@ -77,11 +77,12 @@ struct DBuf {
 // others.
 struct pit_lane {
     std::vector<int> grids;
-    cudaStream_t s = nullptr, side = nullptr, side2 = nullptr;
+    cudaStream_t s = nullptr;
+    cudaStream_t sides[NPART - 1] = {};  // the launch parts other than the first
     cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
     bool planned[NPREC] = {};
     int n_cls[NPREC][2] = {};
-    int split[NPREC] = {};  // class-0 position of the first small grid
+    int split[NPREC][NBKT + 1] = {};  // class-0 positions where the shared-memory buckets start
     int *d_order_cls[NPREC][2] = {};
     int *d_act = nullptr;     // G flags, zero outside the lane
     int *h_act = nullptr;     // pinned, G
@@ -121,15 +122,15 @@ struct pit_problem {
     std::vector<int> h_order_cls[NPREC][2];
     size_t smem_cls[NPREC][2] = {};
     size_t smem_need[NPREC] = {};    // class 0 (used by the allocation-free step)
-    // class 0 runs as two launches: grids needing more than half of the largest
-    // grid's shared memory, then (from position split) the smaller ones with
-    // their own, smaller allocation, so that more of their CTAs fit on an SM
-    int split[NPREC] = {};
-    size_t smem_small[NPREC] = {};
-    int threads[NPREC][2][3] = {};   // [prec][wide batch][part: 0 large, 1 global state, 2 small]; 0 = not tuned
+    // class 0 runs as up to NBKT launches, one per shared-memory bucket: grids
+    // needing more than half of the largest grid's shared memory, then more
+    // than a quarter, and so on, each launch with its own allocation, so that
+    // the CTAs of smaller grids pack more densely on an SM
+    int split[NPREC][NBKT + 1] = {};
+    size_t smem_bkt[NPREC][NBKT] = {};
+    int threads[NPREC][2][NPART] = {};  // [prec][wide batch][part: buckets, then global state]; 0 = not tuned
     int forced_threads[2] = {0, 0};  // override [wide batch]
-    cudaStream_t side = nullptr;     // second stream: the large-grid class runs beside class 0
-    cudaStream_t side2 = nullptr;    // third stream: the small grids of class 0
+    cudaStream_t sides[NPART - 1] = {};  // streams of the launch parts beside the first
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf w_xg;                       // FP64 state of class-1 items
     std::vector<pit_lane> lanes;     // MGRIT lanes (built on first use)
@@ -273,11 +274,18 @@ pit_status plan(pit_problem *P, int prec)
         need[1] = bx > need[1] ? bx : need[1];
     }
     {
-        int k = 0;
         const int n0 = (int)cls[0].size();
-        while (k < n0 && 2 * phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) > need[0]) ++k;
-        P->split[prec] = k;
-        P->smem_small[prec] = k < n0 ? phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) : 0;
+        int k = 0;
+        P->split[prec][0] = 0;
+        for (int q = 0; q < NBKT; ++q) {
+            P->smem_bkt[prec][q] = k < n0 ? phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) : 0;
+            if (q == NBKT - 1) k = n0;
+            else
+                while (k < n0 && (phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) << (q + 1)) >
+                                     need[0])
+                    ++k;
+            P->split[prec][q + 1] = k;
+        }
     }
     for (int c = 0; c < 2; ++c) {
         P->n_cls[prec][c] = (int)cls[c].size();
@@ -387,11 +395,11 @@ struct PartView {
 };
 PartView part_view(const pit_problem *P, const pit_lane *L, int prec, int part)
 {
-    const int n0 = L ? L->n_cls[prec][0] : P->n_cls[prec][0];
-    const int k = L ? L->split[prec] : P->split[prec];
-    int *o0 = L ? L->d_order_cls[prec][0] : P->d_order_cls[prec][0];
-    if (part == 0) return {o0, k, P->smem_cls[prec][0], false};
-    if (part == 2) return {o0 ? o0 + k : nullptr, n0 - k, P->smem_small[prec], false};
+    if (part < NBKT) {
+        const int *sp = L ? L->split[prec] : P->split[prec];
+        int *o0 = L ? L->d_order_cls[prec][0] : P->d_order_cls[prec][0];
+        return {o0 ? o0 + sp[part] : nullptr, sp[part + 1] - sp[part], P->smem_bkt[prec][part], false};
+    }
     return {L ? L->d_order_cls[prec][1] : P->d_order_cls[prec][1], L ? L->n_cls[prec][1] : P->n_cls[prec][1],
             P->smem_cls[prec][1], true};
 }
@@ -432,7 +440,7 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     a.stats = nullptr;
     a.order = v.order;
     a.n_order = v.n;
-    if (cls == 1) {
+    if (v.xg) {
         a.xg = P->w_xg.d();
         a.bg = a.xg + (long long)c.nb * P->ntot;
     }
@@ -469,25 +477,32 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
     if (L && !L->planned[prec]) return fail(PIT_ERR_INVALID_ARG, "lane without a launch plan");
     const bool wide = c.nb >= 8;
-    PartView v[3];
-    for (int q = 0; q < 3; ++q) v[q] = part_view(P, L, prec, q);
+    PartView v[NPART];
+    int n_parts = 0;
+    for (int q = 0; q < NPART; ++q) {
+        v[q] = part_view(P, L, prec, q);
+        if (v[q].n > 0) ++n_parts;
+    }
     // (a lane's workspaces and CTA sizes are prepared before its first launch)
-    if (v[1].n > 0 && !L) CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op)));
+    if (v[NBKT].n > 0 && !L)
+        CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op)));
     if (!L)
-        for (int q = 0; q < 3; ++q) TRY(tune(P, prec, wide, q, o, c, active));
-    cudaStream_t st[3] = {L ? L->s : P->stream, L ? L->side : P->side, L ? L->side2 : P->side2};
+        for (int q = 0; q < NPART; ++q) TRY(tune(P, prec, wide, q, o, c, active));
+    cudaStream_t st[NPART];
+    st[0] = L ? L->s : P->stream;
+    for (int q = 1; q < NPART; ++q) st[q] = L ? L->sides[q - 1] : P->sides[q - 1];
     cudaEvent_t ef = L ? L->fork : P->ev_fork, ej = L ? L->join : P->ev_join;
     StepArgs a = make_args(P, o, c, active);
     ProfScope ps(P, wide ? 0 : 1, st[0]);
-    const bool fork = v[1].n > 0 || (v[0].n > 0 && v[2].n > 0);
+    const bool fork = n_parts > 1;
     if (fork) {
         CU(cudaEventRecord(ef, st[0]));
-        CU(cudaStreamWaitEvent(st[1], ef, 0));
-        CU(cudaStreamWaitEvent(st[2], ef, 0));
+        for (int q = 1; q < NPART; ++q)
+            if (v[q].n > 0) CU(cudaStreamWaitEvent(st[q], ef, 0));
     }
-    // the part without others runs on the main stream; with others, large
-    // grids on the main stream, small grids and global-state grids beside it
-    for (int q = 0; q < 3; ++q) {
+    // a single part runs on the main stream; several run concurrently, the
+    // largest grids on the main stream, the other parts each on its own stream
+    for (int q = 0; q < NPART; ++q) {
         if (v[q].n <= 0) continue;
         StepArgs b = a;
         b.order = v[q].order;
@@ -500,7 +515,8 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
         CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][q], v[q].smem, sq, v[q].xg));
     }
     if (fork) {
-        for (int q = 1; q < 3; ++q) {
+        for (int q = 1; q < NPART; ++q) {
+            if (v[q].n <= 0) continue;
             CU(cudaEventRecord(ej, st[q]));
             CU(cudaStreamWaitEvent(st[0], ej, 0));
         }
@@ -673,8 +689,7 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
             return bail(fail(e_ == cudaErrorMemoryAllocation ? PIT_ERR_OOM : PIT_ERR_CUDA, "%s: %s", #call, \
                              cudaGetErrorString(e_)));                                              \
     } while (0)
-    CUB(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
-    CUB(cudaStreamCreateWithFlags(&P->side2, cudaStreamNonBlocking));
+    for (auto &sq : P->sides) CUB(cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking));
     CUB(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     CUB(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     CUB(phi_kernels_init(P->max_smem));
@@ -717,16 +732,16 @@ pit_status pit_problem_destroy(pit_problem_t P)
     cudaStreamSynchronize(P->stream);
     for (pit_lane &L : P->lanes) {
         if (L.s) cudaStreamSynchronize(L.s);
-        if (L.side) cudaStreamSynchronize(L.side);
-        if (L.side2) cudaStreamSynchronize(L.side2);
+        for (auto sq : L.sides)
+            if (sq) cudaStreamSynchronize(sq);
         for (int p = 0; p < NPREC; ++p)
             for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
         cudaFree(L.d_act);
         cudaFreeHost(L.h_act);
         cudaFreeHost(L.h_res);
         if (L.s) cudaStreamDestroy(L.s);
-        if (L.side) cudaStreamDestroy(L.side);
-        if (L.side2) cudaStreamDestroy(L.side2);
+        for (auto sq : L.sides)
+            if (sq) cudaStreamDestroy(sq);
         if (L.fork) cudaEventDestroy(L.fork);
         if (L.join) cudaEventDestroy(L.join);
         if (L.done) cudaEventDestroy(L.done);
@@ -736,14 +751,11 @@ pit_status pit_problem_destroy(pit_problem_t P)
     cudaFree(P->d_masks);
     for (int p = 0; p < NPREC; ++p)
         for (int c = 0; c < 2; ++c) cudaFree(P->d_order_cls[p][c]);
-    if (P->side) {
-        cudaStreamSynchronize(P->side);
-        cudaStreamDestroy(P->side);
-    }
-    if (P->side2) {
-        cudaStreamSynchronize(P->side2);
-        cudaStreamDestroy(P->side2);
-    }
+    for (auto sq : P->sides)
+        if (sq) {
+            cudaStreamSynchronize(sq);
+            cudaStreamDestroy(sq);
+        }
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     cudaFree(P->d_grids);
@@ -1171,16 +1183,14 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
     if ((int)P->lanes.size() != K) {
         for (pit_lane &L : P->lanes) {
             cudaStreamSynchronize(L.s);
-            cudaStreamSynchronize(L.side);
-            cudaStreamSynchronize(L.side2);
+            for (auto sq : L.sides) cudaStreamSynchronize(sq);
             for (int p = 0; p < NPREC; ++p)
                 for (int c = 0; c < 2; ++c) cudaFree(L.d_order_cls[p][c]);
             cudaFree(L.d_act);
             cudaFreeHost(L.h_act);
             cudaFreeHost(L.h_res);
             cudaStreamDestroy(L.s);
-            cudaStreamDestroy(L.side);
-            cudaStreamDestroy(L.side2);
+            for (auto sq : L.sides) cudaStreamDestroy(sq);
             cudaEventDestroy(L.fork);
             cudaEventDestroy(L.join);
             cudaEventDestroy(L.done);
@@ -1201,8 +1211,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
         }
         for (pit_lane &L : P->lanes) {
             CU(cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking));
-            CU(cudaStreamCreateWithFlags(&L.side, cudaStreamNonBlocking));
-            CU(cudaStreamCreateWithFlags(&L.side2, cudaStreamNonBlocking));
+            for (auto &sq : L.sides) CU(cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking));
             CU(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
@@ -1215,12 +1224,18 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
         for (int k = 0; k < K; ++k) {
             pit_lane &L = P->lanes[k];
             if (L.planned[prec]) continue;
-            std::vector<char> mine(P->G, 0), large(P->G, 0);
+            std::vector<char> mine(P->G, 0);
+            std::vector<int> bkt(P->G, 0);
             for (int g : L.grids) mine[g] = 1;
-            for (int q = 0; q < P->split[prec]; ++q) large[P->h_order_cls[prec][0][q]] = 1;
-            L.split[prec] = 0;
+            for (int q = 0; q < NBKT; ++q)
+                for (int k = P->split[prec][q]; k < P->split[prec][q + 1]; ++k) bkt[P->h_order_cls[prec][0][k]] = q;
+            // the lane's class-0 list keeps the problem's order, so its buckets
+            // are consecutive too
+            int cnt[NBKT] = {};
             for (int g : P->h_order_cls[prec][0])
-                if (mine[g] && large[g]) ++L.split[prec];
+                if (mine[g]) ++cnt[bkt[g]];
+            L.split[prec][0] = 0;
+            for (int q = 0; q < NBKT; ++q) L.split[prec][q + 1] = L.split[prec][q] + cnt[q];
             for (int c = 0; c < 2; ++c) {
                 std::vector<int> lst;
                 for (int g : P->h_order_cls[prec][c])
@@ -1271,7 +1286,7 @@ pit_status lanes_prime(Mg &M, int Nc)
         c.in = P->m_U.d();  // u0 at every C-point
         c.is = nt;
         if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op)));
-        for (int part = 0; part < 3; ++part) TRY(tune(P, prec, c.nb >= 8, part, *reps[r].so, c, M.active));
+        for (int part = 0; part < NPART; ++part) TRY(tune(P, prec, c.nb >= 8, part, *reps[r].so, c, M.active));
     }
     return PIT_OK;
 }

@@ -99,6 +99,10 @@ struct StepArgs {
 // FP32 copy of the state (FP64 input and output).
 enum Prec { PLAIN = 0, MIXED = 1, SINGLE = 2 };
 constexpr int NPREC = 3;
+// Launch parts of one multi-step call: NBKT shared-memory buckets of the
+// grids whose state fits on chip, then the grids with global-memory state.
+constexpr int NBKT = 4;
+constexpr int NPART = NBKT + 1;
 inline int prec_form(int pit_prec)
 {
     return pit_prec == PIT_PREC_MIXED ? MIXED : pit_prec == PIT_PREC_FP32 ? SINGLE : PLAIN;
