@@ -246,8 +246,16 @@ pit_status check_solve_opts(const pit_solve_opts *o)
 // Launch plan of a precision form: grids whose on-chip state fits in shared
 // memory form class 0; the others keep their FP64 vectors in global memory
 // (class 1: the state x and b in the mixed form, x and the Krylov vectors in
-// the FP64 form; the FP32 form has no class 1).  Each class lists its grids by
-// decreasing size.
+// the FP64 form; the FP32 form has no class 1).  Class 0 lists its grids by
+// decreasing shared-memory need, class 1 by decreasing size.
+size_t grid_smem_bytes(const pit_problem *P, int prec, int g)
+{
+    const GridInfo &I = P->info[g];
+    int na = 1;
+    for (int i = 0; i < P->desc.d; ++i) na = I.N[i] > na ? I.N[i] : na;
+    return phi_smem_bytes(prec, P->desc.op, P->desc.d, I.n, na);
+}
+
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
@@ -258,7 +266,7 @@ pit_status plan(pit_problem *P, int prec)
     size_t need[2] = {0, 0};
     for (int g : order) {
         const int n = P->info[g].n;
-        const size_t bytes = phi_smem_bytes(prec, P->desc.op, P->desc.d, n);
+        const size_t bytes = grid_smem_bytes(P, prec, g);
         if (bytes <= P->max_smem) {
             cls[0].push_back(g);
             need[0] = bytes > need[0] ? bytes : need[0];
@@ -274,16 +282,18 @@ pit_status plan(pit_problem *P, int prec)
         need[1] = bx > need[1] ? bx : need[1];
     }
     {
+        // buckets over class 0 in decreasing order of shared-memory need
+        std::stable_sort(cls[0].begin(), cls[0].end(), [&](int a, int b) {
+            return grid_smem_bytes(P, prec, a) > grid_smem_bytes(P, prec, b);
+        });
         const int n0 = (int)cls[0].size();
         int k = 0;
         P->split[prec][0] = 0;
         for (int q = 0; q < NBKT; ++q) {
-            P->smem_bkt[prec][q] = k < n0 ? phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) : 0;
+            P->smem_bkt[prec][q] = k < n0 ? grid_smem_bytes(P, prec, cls[0][k]) : 0;
             if (q == NBKT - 1) k = n0;
             else
-                while (k < n0 && (phi_smem_bytes(prec, P->desc.op, P->desc.d, P->info[cls[0][k]].n) << (q + 1)) >
-                                     need[0])
-                    ++k;
+                while (k < n0 && (grid_smem_bytes(P, prec, cls[0][k]) << (q + 1)) > need[0]) ++k;
             P->split[prec][q + 1] = k;
         }
     }

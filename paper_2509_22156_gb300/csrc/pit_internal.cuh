@@ -136,7 +136,8 @@ cudaError_t launch_net_adam(const float *grad_rows, int n_rows, float scale, flo
                             cudaStream_t s);
 
 // Shared-memory bytes a backward-Euler item of n nodes needs.
-size_t phi_smem_bytes(int prec, int op, int d, int n);
+// (na: nodes of the grid's longest axis, for the heat line preconditioner)
+size_t phi_smem_bytes(int prec, int op, int d, int n, int na);
 // Launch one multi-step batch (grid-per-CTA, every Krylov solve on chip);
 // xg selects the variant whose FP64 state lives in global memory.
 cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s, bool xg = false);

@@ -5,10 +5,11 @@
 
 namespace pit {
 
-size_t phi_smem_bytes(int prec, int op, int d, int n)
+size_t phi_smem_bytes(int prec, int op, int d, int n, int na)
 {
     const size_t ld = (size_t)((n + 3) & ~3);
-    return (size_t)n_f64(op, prec, d) * ld * 8 + (size_t)n_f32(op, prec, d) * ld * 4 + ld * 2 + 16;
+    return (size_t)n_f64(op, prec, d) * ld * 8 + (size_t)n_f32(op, prec, d) * ld * 4 + ld * 2 + 16 +
+           (size_t)line_pc_bytes(op, prec, false, na);
 }
 
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n)

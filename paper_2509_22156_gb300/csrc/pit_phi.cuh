@@ -312,6 +312,119 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
     return k;
 }
 
+// Line preconditioner of the constant-coefficient heat operator: M keeps the
+// full diagonal of A = I + dt L and the couplings along one axis a (the
+// finest), so M is a tridiagonal matrix on every grid line along a, the same
+// on every line (zero Dirichlet values, constant coefficients).  M^{-1} r is a
+// Thomas solve per line with the LU factors of that matrix precomputed per
+// position k along the line: piv[k] = 1 / (diag - off c[k-1]), c[k] = off
+// piv[k].  For a grid whose axis a is much finer than the others, M captures
+// the stiff part of A and the preconditioned CG needs a few iterations where
+// the plain one needs tens (the anisotropic grids of the combination
+// technique).  Lines are distributed over the threads; node j of line l =
+// hi S_a + lo is at hi S_a N_a + lo + k S_a.
+template <typename T>
+struct LineM {
+    const T *c, *piv;
+    T off;
+    int Na, Sa, nlines;
+    __device__ __forceinline__ void operator()(const T *r, T *u) const
+    {
+        for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
+            const int hi = l / Sa, lo = l - hi * Sa;
+            const int j0 = hi * Sa * Na + lo;
+            T y = r[j0] * piv[0];
+            u[j0] = y;
+            for (int k = 1; k < Na; ++k) {
+                const int j = j0 + k * Sa;
+                y = (r[j] - off * y) * piv[k];
+                u[j] = y;
+            }
+            for (int k = Na - 2; k >= 0; --k) {
+                const int j = j0 + k * Sa;
+                y = u[j] - c[k] * y;
+                u[j] = y;
+            }
+        }
+    }
+};
+
+// Preconditioned single-reduction CG (the Chronopoulos-Gear recurrences with
+// u = M^{-1} r): one fused reduction of (r,r), (r,u), (Au,u) per iteration
+// and three barriers.  Stops when (r,r) <= stop2 (unpreconditioned norm, the
+// same test as cg_core).
+template <typename T, typename TX, class ST, class PC>
+__device__ int pcg_core(const ST &A, const PC &M, int n, TX *X, T *r, T *u, T *p, T *s, T *w, Reducer<T> &R,
+                        T stop2, int maxit, int &status)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    status = PIT_OK;
+    __syncthreads();  // r complete
+    M(r, u);
+    __syncthreads();  // u complete
+    T v[3] = {T(0), T(0), T(0)};
+#pragma unroll 4
+    for (int j = tid; j < n; j += nt) {
+        const T wj = A(u, j);
+        w[j] = wj;
+        const T rj = r[j], uj = u[j];
+        v[0] += rj * rj;
+        v[1] += rj * uj;
+        v[2] += wj * uj;
+    }
+    R.template sum<3>(v);
+    if (!(v[0] > stop2)) {
+        if (v[0] != v[0]) status = PIT_ERR_NONFINITE;
+        return 0;
+    }
+    if (!finite_pos(v[1]) || !finite_pos(v[2])) {
+        status = (v[1] != v[1] || v[2] != v[2]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+        return 0;
+    }
+    T gam = v[1], alpha = v[1] / v[2], beta = T(0);
+    bool first = true;
+    int k = 0;
+    for (;;) {
+        if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+#pragma unroll 4
+        for (int j = tid; j < n; j += nt) {
+            const T pj = first ? u[j] : u[j] + beta * p[j];
+            const T sj = first ? w[j] : w[j] + beta * s[j];
+            p[j] = pj;
+            s[j] = sj;
+            X[j] += (TX)(alpha * pj);
+            r[j] -= alpha * sj;
+        }
+        first = false;
+        ++k;
+        __syncthreads();  // r complete
+        M(r, u);
+        __syncthreads();  // u complete
+        T q[3] = {T(0), T(0), T(0)};
+#pragma unroll 4
+        for (int j = tid; j < n; j += nt) {
+            const T wj = A(u, j);
+            w[j] = wj;
+            const T rj = r[j], uj = u[j];
+            q[0] += rj * rj;
+            q[1] += rj * uj;
+            q[2] += wj * uj;
+        }
+        R.template sum<3>(q);
+        if (!(q[0] > stop2)) {
+            if (q[0] != q[0]) status = PIT_ERR_NONFINITE;
+            break;
+        }
+        if (!finite_pos(q[1])) { status = (q[1] != q[1]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        beta = q[1] / gam;
+        const T den = q[2] - beta * q[1] / alpha;
+        if (!finite_pos(den)) { status = (den != den) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        alpha = q[1] / den;
+        gam = q[1];
+    }
+    return k;
+}
+
 // BiCGStab (van der Vorst 1992) on A e = r0: r holds r0 on entry; rh, p, v
 // are initialised here; s shares r's storage.
 template <typename T, typename TX, class ST>
@@ -402,11 +515,20 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
 //                PLAIN and MIXED)]
 //   FP32 arrays: [e (MIXED) or x (SINGLE), Krylov vectors, table (var. coef.)]
 //   u16 mask
-__host__ __device__ inline int krylov_vecs(int op, int prec)
+__host__ __device__ inline bool line_pc_form(int op, int prec, bool xg) { return op == PIT_OP_HEAT && prec != PLAIN && !xg; }
+__host__ __device__ inline int krylov_vecs(int op, int prec, bool xg = false)
 {
     if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e or x)
+    if (line_pc_form(op, prec, xg)) return 6;           // r p s w u (+ e or x): u for the line preconditioner
     return prec == PLAIN ? 4 : 5;                        // r p s w (+ e or x)
 }
+// bytes after the mask: the line preconditioner's factors, 2 N_a floats
+// (N_a = nodes of the grid's longest axis, an upper bound for the finest one)
+__host__ __device__ inline int line_pc_bytes(int op, int prec, bool xg, int na)
+{
+    return line_pc_form(op, prec, xg) ? 8 * na + 16 : 0;
+}
+
 __host__ __device__ inline int n_tab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
 __host__ __device__ inline int n_f64(int op, int prec, int d)
 {
@@ -418,7 +540,7 @@ __host__ __device__ inline int n_f64(int op, int prec, int d)
 __host__ __device__ inline int n_f32(int op, int prec, int d, bool xg = false)
 {
     if (prec == PLAIN) return 0;
-    return krylov_vecs(op, prec) + (prec == MIXED && !xg ? 1 : 0) + n_tab(op, d);
+    return krylov_vecs(op, prec, xg) + (prec == MIXED && !xg ? 1 : 0) + n_tab(op, d);
 }
 
 template <int OP, int PREC, int D, bool XG = false>
@@ -445,7 +567,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     const double dt = a.dt;
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
     constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
-    constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6) : (PREC == PLAIN ? 4 : 5);
+    constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6)
+                                          : (PREC == PLAIN ? 4 : (OP == PIT_OP_HEAT && !XG ? 6 : 5));
     constexpr int NDV = (PREC == MIXED && !XG) ? 1 : 0;  // dv in shared memory
     constexpr int NF32 = (PREC != PLAIN) ? NKV + NDV + K : 0;
 
@@ -526,6 +649,44 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         }
         H64.diag = diag;
         HT.diag = (T)diag;
+    }
+    // Line preconditioner (heat, FP32 Krylov, state on chip) along the finest
+    // axis a, used when a is at least twice as fine as every other axis and
+    // stiff at this step size (4 dt / h_a^2 >= 2).  Its factors are computed
+    // once per launch; the barrier at the top of the step loop orders them.
+    bool use_pc = false;
+    LineM<float> LM{};
+    if constexpr (OP == PIT_OP_HEAT && PREC != PLAIN && !XG) {
+        int ax = 0;
+#pragma unroll
+        for (int i = 1; i < D; ++i)
+            if (GI.h[i] < GI.h[ax]) ax = i;
+        double h2 = 1e300;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+            if (i != ax && GI.h[i] < h2) h2 = GI.h[i];
+        const double ha = GI.h[ax];
+        const int Na = GI.N[ax];
+        use_pc = Na >= 3 && 2.0 * ha <= h2 * (1.0 + 1e-12) && 4.0 * dt / (ha * ha) >= 2.0;
+        if (use_pc) {
+            float *lf = reinterpret_cast<float *>(mask + ld);
+            if (tid == 0) {
+                const float dg = HT.diag, of = HT.off[ax];
+                float cprev = 0.0f;
+                for (int k = 0; k < Na; ++k) {
+                    const float pv = 1.0f / (dg - of * cprev);
+                    lf[Na + k] = pv;
+                    cprev = of * pv;
+                    lf[k] = cprev;
+                }
+            }
+            LM.c = lf;
+            LM.piv = lf + Na;
+            LM.off = HT.off[ax];
+            LM.Na = Na;
+            LM.Sa = GI.S[ax];
+            LM.nlines = n / Na;
+        }
     }
     auto A64 = [&](const double *v, int j) -> double {
         if constexpr (OP == PIT_OP_HEAT) return H64(v, j);
@@ -630,7 +791,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             const float stop2 = rt * rt * bb[0];
             int st, k;
             if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, xs, r, q1, q2, q3, q4, R32, stop2, a.maxit, st);
-            else if constexpr (OP == PIT_OP_HEAT) k = cg_core<float, float>(HT, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
+            else if constexpr (OP == PIT_OP_HEAT) {
+                if (use_pc) k = pcg_core<float, float>(HT, LM, n, xs, r, q4, q1, q2, q3, R32, stop2, a.maxit, st);
+                else k = cg_core<float, float>(HT, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
+            }
             else k = cg_core<float, float>(T32, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
             iters += k;
             if (st > status) status = st;
@@ -747,7 +911,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 }
                 int st, k;
                 if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, e, rv, pv, sv, wv, tv, R32, stop32, a.maxit, st);
-                else if constexpr (OP == PIT_OP_HEAT) k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                else if constexpr (OP == PIT_OP_HEAT) {
+                    if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
+                    else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                }
                 else k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
                 iters += k;
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }

@@ -147,6 +147,53 @@ def test_fp32_form_scales_with_the_state(scale):
     assert rel(uT / scale, ref) < 1e-4
 
 
+@pytest.mark.parametrize("d, n, dt", [(2, 6, 0.1), (3, 6, 0.01), (3, 5, 0.2), (4, 5, 0.05)])
+@pytest.mark.parametrize("prec", [B.PIT_PREC_MIXED, B.PIT_PREC_FP32])
+def test_stiff_anisotropic_heat_steps_match_oracle(d, n, dt, prec):
+    # large steps on grids whose finest axis is at least twice as fine as the
+    # others: the FP32 Krylov solves of the heat operator use the line
+    # preconditioner along that axis there; the solution is the same
+    P = B.Problem(d, n, 1, B.PIT_OP_HEAT)
+    O = oracle.Problem(d, n, 1, W.OP_HEAT)
+    nb = 2
+    u = W.random_vector(606 + d, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    rtol = 1e-12 if prec == B.PIT_PREC_MIXED else 1e-6
+    st = P.phi_batch(dt, cuda(u), out, B.solve_opts(prec, rtol=rtol, maxit=20000, inner_rtol=1e-5, ir_maxit=40))
+    assert st.n_failed == 0
+    ref = O.phi(dt, u, rtol=1e-15)
+    got = host(out)
+    tol = 1e-9 if prec == B.PIT_PREC_MIXED else 1e-4
+    for b in range(nb):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < tol, (b, g, P.levels[g])
+    # several steps in one launch (carried residual, preconditioner reused)
+    u0 = W.random_vector(707 + d, P.n_total)
+    uT = np.empty(P.n_total)
+    P.sequential_solve(u0, dt, 5, uT, B.solve_opts(prec, rtol=rtol, maxit=20000, inner_rtol=1e-5, ir_maxit=40))
+    assert rel(uT, O.sequential(u0, dt, 5, rtol=1e-15)) < tol
+
+
+def test_stiff_heat_mgrit_with_preconditioned_sweeps():
+    # coarse steps of 1/8 on level-5 grids in d = 3: the FP32 coarse
+    # correction sweep and the mixed fine steps run preconditioned on the
+    # anisotropic grids; MGRIT still reaches the oracle's fixed point
+    d, n, N, m = 3, 5, 64, 8
+    P = B.Problem(d, n, 1, B.PIT_OP_HEAT)
+    O = oracle.Problem(d, n, 1, W.OP_HEAT)
+    u0 = O.initial(W.IC_SINES, W.sine_modes(d, [(1.0, [1, 1, 1]), (0.5, [1, 2, 3])]))
+    fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-13, maxit=50000, inner_rtol=1e-5, ir_maxit=40)
+    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=50000)
+    tol = 1e-11 * np.abs(u0).max()
+    opts = B.mgrit_opts(0.0, 1.0, N, m, 2, tol=tol, maxit=60, fine=fine, crs=crs, relax=B.PIT_RELAX_F)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    seq = O.sequential(u0, 1.0 / N, N, rtol=1e-15)
+    assert st.n_converged == P.G
+    assert rel(host(uT), seq) < 1e-9
+
+
 def test_phi_in_place_forcing_and_empty_batch():
     P, O, dt = pair("heat3d")
     u = W.random_vector(5, 2 * P.n_total)
