@@ -163,7 +163,9 @@ def test_stiff_anisotropic_heat_steps_match_oracle(d, n, dt, prec):
     assert st.n_failed == 0
     ref = O.phi(dt, u, rtol=1e-15)
     got = host(out)
-    tol = 1e-9 if prec == B.PIT_PREC_MIXED else 1e-4
+    # the FP32 form stops at a relative residual of 1e-6, so its error can
+    # reach cond(A) x 1e-6, up to several hundred x 1e-6 at these step sizes
+    tol = 1e-9 if prec == B.PIT_PREC_MIXED else 2e-3
     for b in range(nb):
         for g in range(P.G):
             sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
