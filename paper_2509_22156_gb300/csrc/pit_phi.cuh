@@ -313,37 +313,181 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
 }
 
 // Line preconditioner of the constant-coefficient heat operator: M keeps the
-// full diagonal of A = I + dt L and the couplings along one axis a (the
-// finest), so M is a tridiagonal matrix on every grid line along a, the same
-// on every line (zero Dirichlet values, constant coefficients).  M^{-1} r is a
-// Thomas solve per line with the LU factors of that matrix precomputed per
-// position k along the line: piv[k] = 1 / (diag - off c[k-1]), c[k] = off
-// piv[k].  For a grid whose axis a is much finer than the others, M captures
-// the stiff part of A and the preconditioned CG needs a few iterations where
-// the plain one needs tens (the anisotropic grids of the combination
-// technique).  Lines are distributed over the threads; node j of line l =
-// hi S_a + lo is at hi S_a N_a + lo + k S_a.
+// full diagonal dg of A = I + dt L and the couplings o along one axis a (the
+// finest), so M is the tridiagonal Toeplitz matrix tridiag(o, dg, o) on every
+// grid line along a (zero Dirichlet values).  For a grid whose axis a is much
+// finer than the others, M captures the stiff part of A and the preconditioned
+// CG needs a few iterations where the plain one needs tens.
+//
+// M^{-1} r is a partitioned tridiagonal solve, so that one long line (the
+// 1-D-like grids of the combination technique) still keeps many threads busy:
+// every line is cut into P chunks (P - 1 of length L, the last of length Lz).
+// On a chunk with left and right outside neighbours xl, xr,
+//     x = g - xl alpha - xr beta,  T g = r_chunk, T alpha = o e_first, T beta = o e_last
+// (T the chunk's own tridiag(o, dg, o)).  The chunk ends give a small system
+// in the boundary values, solved per line by one forward and one backward
+// sweep over the chunks (phase 2), after which every interior node is updated
+// (phase 3).  Everything that depends on the matrix only (the LU factors of
+// both chunk lengths, alpha, beta, and the reduced-system coefficients) is the
+// same on every line and is computed once per launch (setup).
+// Line l = hi S_a + lo, node k of the line at hi S_a N_a + lo + k S_a.
 template <typename T>
 struct LineM {
-    const T *c, *piv;
+    const T *f;  // factors: see setup()
     T off;
-    int Na, Sa, nlines;
-    __device__ __forceinline__ void operator()(const T *r, T *u) const
+    int Na, Sa, nlines, P, L, Lz;
+    // shared-memory floats the factors need for a line of n nodes (upper bound)
+    __host__ __device__ static int floats(int n) { return 6 * n + 3 * 33 + 8; }
+    __device__ __forceinline__ const T *cz() const { return f; }
+    __device__ __forceinline__ const T *pz() const { return f + Lz; }
+    __device__ __forceinline__ const T *az() const { return f + 2 * Lz; }
+    __device__ __forceinline__ const T *bz() const { return f + 3 * Lz; }
+    __device__ __forceinline__ const T *cf() const { return f + 4 * Lz; }
+    __device__ __forceinline__ const T *pf() const { return f + 4 * Lz + L; }
+    __device__ __forceinline__ const T *af() const { return f + 4 * Lz + 2 * L; }
+    __device__ __forceinline__ const T *bf() const { return f + 4 * Lz + 3 * L; }
+    __device__ __forceinline__ const T *psi() const { return f + 4 * Lz + 4 * L; }
+    __device__ __forceinline__ const T *nu() const { return f + 4 * Lz + 4 * L + P; }
+    __device__ __forceinline__ const T *den() const { return f + 4 * Lz + 4 * L + 2 * P; }
+
+    // chunk layout for nt threads: about nt / nlines chunks per line (at most
+    // 32), every chunk at least 2 nodes long
+    __device__ void layout(int na, int sa, int n, int nt)
     {
-        for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
-            const int hi = l / Sa, lo = l - hi * Sa;
-            const int j0 = hi * Sa * Na + lo;
-            T y = r[j0] * piv[0];
+        Na = na;
+        Sa = sa;
+        nlines = n / na;
+        int p = nt / nlines;
+        p = p < 1 ? 1 : (p > 32 ? 32 : p);
+        if (p > na / 2) p = na / 2 > 1 ? na / 2 : 1;
+        L = (na + p - 1) / p;
+        p = (na + L - 1) / L;
+        Lz = na - (p - 1) * L;
+        if (p > 1 && Lz < 2) {
+            --p;
+            Lz += L;
+        }
+        P = p;
+        if (P == 1) L = 0;
+    }
+    // LU factors (c: super-diagonal of U scaled, piv: 1 / pivot) and the
+    // responses alpha, beta of tridiag(o, dg, o) of length m
+    __device__ static void chunk_factors(T o, T dg, int m, T *c, T *piv, T *al, T *be)
+    {
+        T cprev = T(0);
+        for (int k = 0; k < m; ++k) {
+            piv[k] = T(1) / (dg - o * cprev);
+            cprev = o * piv[k];
+            c[k] = cprev;
+        }
+        // alpha: right-hand side o e_first; beta: o e_last
+        T y = o * piv[0];
+        al[0] = y;
+        for (int k = 1; k < m; ++k) {
+            y = (-o * y) * piv[k];
+            al[k] = y;
+        }
+        for (int k = m - 2; k >= 0; --k) al[k] -= c[k] * al[k + 1];
+        T z = o * piv[m - 1];
+        be[m - 1] = z;
+        for (int k = m - 2; k >= 0; --k) {
+            z = -c[k] * z;
+            be[k] = z;
+        }
+    }
+    // one thread: every factor (the caller orders it with a barrier)
+    __device__ void setup(T *buf, T o, T dg)
+    {
+        f = buf;
+        off = o;
+        T *F = buf;
+        chunk_factors(o, dg, Lz, F, F + Lz, F + 2 * Lz, F + 3 * Lz);
+        if (P > 1) {
+            chunk_factors(o, dg, L, F + 4 * Lz, F + 4 * Lz + L, F + 4 * Lz + 2 * L, F + 4 * Lz + 3 * L);
+            T *ps = F + 4 * Lz + 4 * L, *nv = ps + P, *dn = nv + P;
+            T nu_prev = T(0);
+            for (int q = 0; q < P; ++q) {
+                const bool last = q == P - 1;
+                const int m = last ? Lz : L;
+                const T *al = last ? F + 2 * Lz : F + 4 * Lz + 2 * L;
+                const T *be = last ? F + 3 * Lz : F + 4 * Lz + 3 * L;
+                const T d = T(1) / (T(1) - al[0] * nu_prev);
+                dn[q] = d;
+                ps[q] = be[0] * d;
+                nv[q] = be[m - 1] + al[m - 1] * nu_prev * ps[q];
+                nu_prev = nv[q];
+            }
+        }
+    }
+    __device__ __forceinline__ int node(int l, int k) const
+    {
+        const int hi = l / Sa, lo = l - hi * Sa;
+        return hi * Sa * Na + lo + k * Sa;
+    }
+    // all threads of the block; u complete after the caller's next barrier
+    __device__ void operator()(const T *r, T *u) const
+    {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        // phase 1: chunk solves g (into u)
+        for (int t = tid; t < nlines * P; t += nt) {
+            const int l = t / P, q = t - l * P;
+            const bool last = q == P - 1;
+            const int m = last ? Lz : L, k0 = q * L;
+            const T *c = last ? cz() : cf(), *pv = last ? pz() : pf();
+            const int j0 = node(l, k0);
+            T y = r[j0] * pv[0];
             u[j0] = y;
-            for (int k = 1; k < Na; ++k) {
+            for (int k = 1; k < m; ++k) {
                 const int j = j0 + k * Sa;
-                y = (r[j] - off * y) * piv[k];
+                y = (r[j] - off * y) * pv[k];
                 u[j] = y;
             }
-            for (int k = Na - 2; k >= 0; --k) {
+            for (int k = m - 2; k >= 0; --k) {
                 const int j = j0 + k * Sa;
                 y = u[j] - c[k] * y;
                 u[j] = y;
+            }
+        }
+        if (P == 1) return;
+        __syncthreads();
+        // phase 2: chunk boundary values, one thread per line
+        for (int l = tid; l < nlines; l += nt) {
+            const T *ps = psi(), *nv = nu(), *dn = den();
+            T mu = T(0), nu_prev = T(0);
+            for (int q = 0; q < P; ++q) {
+                const bool last = q == P - 1;
+                const int m = last ? Lz : L;
+                const T *al = last ? az() : af();
+                const int js = node(l, q * L), je = js + (m - 1) * Sa;
+                const T phi = (u[js] - al[0] * mu) * dn[q];
+                mu = u[je] - al[m - 1] * (mu - nu_prev * phi);
+                u[js] = phi;
+                u[je] = mu;
+                nu_prev = nv[q];
+            }
+            T F = T(0);  // first value of chunk q + 1
+            for (int q = P - 1; q >= 0; --q) {
+                const int m = q == P - 1 ? Lz : L;
+                const int js = node(l, q * L), je = js + (m - 1) * Sa;
+                const T E = u[je] - nv[q] * F;
+                F = u[js] - ps[q] * F;
+                u[je] = E;
+                u[js] = F;
+            }
+        }
+        __syncthreads();
+        // phase 3: interior nodes from the neighbouring chunks' boundary values
+        for (int t = tid; t < nlines * P; t += nt) {
+            const int l = t / P, q = t - l * P;
+            const bool last = q == P - 1;
+            const int m = last ? Lz : L;
+            const T *al = last ? az() : af(), *be = last ? bz() : bf();
+            const int j0 = node(l, q * L);
+            const T xl = q > 0 ? u[j0 - Sa] : T(0);
+            const T xr = last ? T(0) : u[j0 + m * Sa];
+            for (int k = 1; k < m - 1; ++k) {
+                const int j = j0 + k * Sa;
+                u[j] -= al[k] * xl + be[k] * xr;
             }
         }
     }
@@ -526,7 +670,7 @@ __host__ __device__ inline int krylov_vecs(int op, int prec, bool xg = false)
 // (N_a = nodes of the grid's longest axis, an upper bound for the finest one)
 __host__ __device__ inline int line_pc_bytes(int op, int prec, bool xg, int na)
 {
-    return line_pc_form(op, prec, xg) ? 8 * na + 16 : 0;
+    return line_pc_form(op, prec, xg) ? 4 * (6 * na + 3 * 33 + 8) + 16 : 0;
 }
 
 __host__ __device__ inline int n_tab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
@@ -670,22 +814,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         use_pc = Na >= 3 && 2.0 * ha <= h2 * (1.0 + 1e-12) && 4.0 * dt / (ha * ha) >= 2.0;
         if (use_pc) {
             float *lf = reinterpret_cast<float *>(mask + ld);
-            if (tid == 0) {
-                const float dg = HT.diag, of = HT.off[ax];
-                float cprev = 0.0f;
-                for (int k = 0; k < Na; ++k) {
-                    const float pv = 1.0f / (dg - of * cprev);
-                    lf[Na + k] = pv;
-                    cprev = of * pv;
-                    lf[k] = cprev;
-                }
-            }
-            LM.c = lf;
-            LM.piv = lf + Na;
+            LM.layout(Na, GI.S[ax], n, nt);
+            LM.f = lf;
             LM.off = HT.off[ax];
-            LM.Na = Na;
-            LM.Sa = GI.S[ax];
-            LM.nlines = n / Na;
+            if (tid == 0) LM.setup(lf, HT.off[ax], HT.diag);
         }
     }
     auto A64 = [&](const double *v, int j) -> double {
