@@ -149,12 +149,14 @@ def test_fp32_form_scales_with_the_state(scale):
 
 @pytest.mark.parametrize("d, n, dt", [(2, 6, 0.1), (3, 6, 0.01), (3, 5, 0.2), (4, 5, 0.05)])
 @pytest.mark.parametrize("prec", [B.PIT_PREC_MIXED, B.PIT_PREC_FP32])
-def test_stiff_anisotropic_heat_steps_match_oracle(d, n, dt, prec):
+@pytest.mark.parametrize("op", [B.PIT_OP_HEAT, B.PIT_OP_VARHEAT])
+def test_stiff_anisotropic_heat_steps_match_oracle(d, n, dt, prec, op):
     # large steps on grids whose finest axis is at least twice as fine as the
-    # others: the FP32 Krylov solves of the heat operator use the line
-    # preconditioner along that axis there; the solution is the same
-    P = B.Problem(d, n, 1, B.PIT_OP_HEAT)
-    O = oracle.Problem(d, n, 1, W.OP_HEAT)
+    # others: the FP32 Krylov solves of the (variable-coefficient) heat
+    # operator use the line preconditioner along that axis there; the solution
+    # is the same
+    P = B.Problem(d, n, 1, op)
+    O = oracle.Problem(d, n, 1, op)
     nb = 2
     u = W.random_vector(606 + d, nb * P.n_total)
     out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
