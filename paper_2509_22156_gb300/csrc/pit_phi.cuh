@@ -661,7 +661,7 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
 //   u16 mask
 __host__ __device__ inline bool line_pc_form(int op, int prec, bool xg)
 {
-    return (op == PIT_OP_HEAT || op == PIT_OP_VARHEAT) && prec != PLAIN && !xg;
+    return op == PIT_OP_HEAT && prec != PLAIN && !xg;
 }
 __host__ __device__ inline int krylov_vecs(int op, int prec, bool xg = false)
 {
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
     constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
     constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6)
-                                          : (PREC == PLAIN ? 4 : ((OP == PIT_OP_HEAT || OP == PIT_OP_VARHEAT) && !XG ? 6 : 5));
+                                          : (PREC == PLAIN ? 4 : (OP == PIT_OP_HEAT && !XG ? 6 : 5));
     constexpr int NDV = (PREC == MIXED && !XG) ? 1 : 0;  // dv in shared memory
     constexpr int NF32 = (PREC != PLAIN) ? NKV + NDV + K : 0;
 
@@ -797,27 +797,30 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         H64.diag = diag;
         HT.diag = (T)diag;
     }
-    // Line preconditioner (FP32 Krylov, state on chip) along the finest axis a,
-    // used when a is at least twice as fine as every other axis and stiff at
-    // this step size (4 dt / h_a^2 >= 2): the heat operator's line matrix; for
-    // the variable-coefficient operator the same matrix (coefficient 1, the
-    // mean of a), spectrally equivalent within max a / min a.  Its factors are
-    // computed once per launch; the barrier at the top of the step loop orders
-    // them.
+    // Line preconditioner (heat, FP32 Krylov, state on chip) along the finest
+    // axis a, used where it pays: when the condition number estimate
+    // 1 + 4 dt sum_i 1/h_i^2 of A is at least 16 times that of the part M
+    // leaves out, 1 + 4 dt sum_{i != a} 1/h_i^2 (a preconditioned iteration
+    // costs about two plain ones; the iteration counts scale with the square
+    // roots).  Its factors are computed once per launch; the barrier at the
+    // top of the step loop orders them.  (With the variable coefficient the
+    // constant-coefficient line matrix was measured slower than plain CG.)
     bool use_pc = false;
     LineM<float> LM{};
-    if constexpr ((OP == PIT_OP_HEAT || OP == PIT_OP_VARHEAT) && PREC != PLAIN && !XG) {
+    if constexpr (OP == PIT_OP_HEAT && PREC != PLAIN && !XG) {
         int ax = 0;
 #pragma unroll
         for (int i = 1; i < D; ++i)
             if (GI.h[i] < GI.h[ax]) ax = i;
-        double h2 = 1e300;
+        double kp = 1.0, kr = 1.0;
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-            if (i != ax && GI.h[i] < h2) h2 = GI.h[i];
-        const double ha = GI.h[ax];
+        for (int i = 0; i < D; ++i) {
+            const double t = 4.0 * dt / (GI.h[i] * GI.h[i]);
+            kp += t;
+            if (i != ax) kr += t;
+        }
         const int Na = GI.N[ax];
-        use_pc = Na >= 3 && 2.0 * ha <= h2 * (1.0 + 1e-12) && 4.0 * dt / (ha * ha) >= 2.0;
+        use_pc = Na >= 3 && kp >= 16.0 * kr;
         if (use_pc) {
             float *lf = reinterpret_cast<float *>(mask + ld);
             LM.layout(Na, GI.S[ax], n, nt);
@@ -933,10 +936,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 if (use_pc) k = pcg_core<float, float>(HT, LM, n, xs, r, q4, q1, q2, q3, R32, stop2, a.maxit, st);
                 else k = cg_core<float, float>(HT, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
             }
-            else {
-                if (use_pc) k = pcg_core<float, float>(T32, LM, n, xs, r, q4, q1, q2, q3, R32, stop2, a.maxit, st);
-                else k = cg_core<float, float>(T32, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
-            }
+            else k = cg_core<float, float>(T32, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
             iters += k;
             if (st > status) status = st;
             // forcing of this step and the stored outputs (FP64, own nodes only)
@@ -1056,10 +1056,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
                     else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
                 }
-                else {
-                    if (use_pc) k = pcg_core<float, float>(T32, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
-                    else k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
-                }
+                else k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
                 iters += k;
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
                 // a stalled or broken-down inner solve still gives a usable
