@@ -361,6 +361,7 @@ struct LineM {
         p = p < 1 ? 1 : (p > 32 ? 32 : p);
         if (p > na / 2) p = na / 2 > 1 ? na / 2 : 1;
         L = (na + p - 1) / p;
+        L |= 1;  // odd chunk length: the chunks of one line start in distinct banks
         p = (na + L - 1) / L;
         Lz = na - (p - 1) * L;
         if (p > 1 && Lz < 2) {
@@ -430,7 +431,7 @@ struct LineM {
         const int tid = threadIdx.x, nt = blockDim.x;
         // phase 1: chunk solves g (into u)
         for (int t = tid; t < nlines * P; t += nt) {
-            const int l = t / P, q = t - l * P;
+            const int q = t / nlines, l = t - q * nlines;  // neighbouring threads: neighbouring lines
             const bool last = q == P - 1;
             const int m = last ? Lz : L, k0 = q * L;
             const T *c = last ? cz() : cf(), *pv = last ? pz() : pf();
@@ -478,7 +479,7 @@ struct LineM {
         __syncthreads();
         // phase 3: interior nodes from the neighbouring chunks' boundary values
         for (int t = tid; t < nlines * P; t += nt) {
-            const int l = t / P, q = t - l * P;
+            const int q = t / nlines, l = t - q * nlines;  // neighbouring threads: neighbouring lines
             const bool last = q == P - 1;
             const int m = last ? Lz : L;
             const T *al = last ? az() : af(), *be = last ? bz() : bf();
