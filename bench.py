@@ -184,7 +184,7 @@ PAPER_TOL, PAPER_RTOL = 1e-8, 1e-10
 COARSE_RTOL = 1e-2  # coarse solves for the correction: relative to the correction
 
 
-def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None):
+def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None, init=True):
     """Options of the chosen form (FP32 Krylov in FP64 refinement, learned
     coarse propagator or the implicit one solved for the correction with a
     loose tolerance) and of the plain FP64 form (the paper's algorithm: FAS
@@ -203,7 +203,7 @@ def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_pre
     loose = wl.levels == 2
     relax = B.PIT_RELAX_FCF if relax is None else relax
     chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, coarse=coarse, fine=mixed,
-                          crs=mixed_c if loose else mixed, relax=relax)
+                          crs=mixed_c if loose else mixed, relax=relax, init=init)
     fp64 = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=plain, crs=plain,
                         fas=True)
     return chosen, fp64, mixed, plain
@@ -379,7 +379,8 @@ def run_pit(args, rank, world, local):
         "data": "synthetic (analytic initial value, seeded evaluation points)",
         "config": {"workload": wl.name, "d": wl.d, "level": wl.n, "grids": P.G, "n_total": P.n_total,
                    "accuracy_target": "relative L2 error <= 1e-6 of the combined solution vs the oracle's sequential solution",
-                   "nsteps": wl.nsteps, "t": [wl.t0, wl.t1], "mgrit": f"{wl.levels}-level, {'F' if chosen.relax == B.PIT_RELAX_F else 'FCF'} relaxation, m={wl.m}",
+                   "nsteps": wl.nsteps, "t": [wl.t0, wl.t1], "mgrit": f"{wl.levels}-level, {'F' if chosen.relax == B.PIT_RELAX_F else 'FCF'} relaxation, m={wl.m}"
+                            f"{', initial coarse sweep' if chosen.init else ''}",
                    "coarse": "learned network (implicit backward Euler dT = m dt when the judge rejects it)",
                    "mgrit_tol_abs": chosen.tol,
                    "krylov_rtol": chosen.fine.rtol, "inner_rtol": chosen.fine.inner_rtol,
@@ -439,6 +440,9 @@ def run_pit(args, rank, world, local):
                          ("mixed_implicit_coarse_mgrit_f", B.PIT_RELAX_F)):
             o_rx, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT, relax=rx)
             forms[name] = timed(o_rx)
+        # the chosen form started from u0 at every time point (no initial coarse sweep)
+        o_ni, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT, relax=chosen.relax, init=False)
+        forms["mixed_implicit_coarse_mgrit_no_initial_sweep"] = timed(o_ni)
         # the coarse correction solves in the mixed form instead of FP32
         o_mc, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT, relax=chosen.relax,
                                      coarse_prec=B.PIT_PREC_MIXED)
@@ -506,7 +510,8 @@ def cpu_baseline(wl, uT_gpu, out_gpu, pts, chosen, out_fp64=None, n_grids=12):
     t0 = time.perf_counter()
     relax = "F" if chosen.relax == 1 else "FCF"
     uT, its, _, st = O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64,
-                             rtol=chosen.fine.rtol, check=False, grids=grids, relax=relax)
+                             rtol=chosen.fine.rtol, check=False, grids=grids, relax=relax,
+                             init=bool(chosen.init))
     # (the oracle restates Alg. 2 in its FAS form with one Krylov tolerance)
     t_mg = time.perf_counter() - t0
     dof = sum(int(O.offsets[g + 1] - O.offsets[g]) for g in grids)
@@ -522,7 +527,8 @@ def cpu_baseline(wl, uT_gpu, out_gpu, pts, chosen, out_fp64=None, n_grids=12):
                      np.linalg.norm(uT[O.grid_slice(g)])) for g in grids]
     base = {"value": dof * wl.nsteps / t_mg, "unit": UNIT, "cores": min(cores, len(grids)), "kind": "oracle",
             "sample": f"{len(grids)} of {O.G} grids ({dof} of {O.n_total} nodes), all {wl.nsteps} steps, "
-                      f"{wl.levels}-level MGRIT ({relax} relaxation) m={wl.m} with the same tolerances, "
+                      f"{wl.levels}-level MGRIT ({relax} relaxation{', initial coarse sweep' if chosen.init else ''}) "
+                      f"m={wl.m} with the same tolerances, "
                       f"{t_mg:.1f} s",
             "seconds": t_mg,
             "oracle_sequential_all_grids": {"value": O.n_total * wl.nsteps / t_seq, "unit": UNIT, "cores": cores,

@@ -159,6 +159,9 @@ typedef struct {
                              used with the correction form and the implicit coarse step only
                              (a learned propagator that was not accepted counts as implicit),
                              other forms run as one lane                                    */
+    int init;             /* initial guess: 0 = u0 at every time point; 1 = one sweep of the
+                             level-1 coarse propagator from u0 over the C-points (the paper
+                             leaves the initial guess open; the fixed point is the same)   */
 } pit_mgrit_opts;
 
 typedef struct {

@@ -68,7 +68,7 @@ def lib():
             L.or_sequential.argtypes = [vp, vp, c_double, c_int, c_double, c_int, vp, vp]
             L.or_mgrit.restype = c_int
             L.or_mgrit.argtypes = [vp, vp, c_double, c_int, c_int, c_int, c_double, c_int, c_int,
-                                   vp, c_double, c_int, vp, vp, vp, vp, c_int]
+                                   vp, c_double, c_int, vp, vp, vp, vp, c_int, c_int]
             L.or_combine.argtypes = [vp, vp, c_int, vp, vp]
             L.or_interp.argtypes = [vp, c_int, vp, c_int, vp, vp]
             L.or_initial.restype = c_int
@@ -194,10 +194,11 @@ class Problem:
         return out
 
     def mgrit(self, u0, dt, nsteps, m, levels=2, tol=1e-10, maxit=100, coarse_kind=0,
-              theta=None, rtol=1e-14, krylov_maxit=100000, check=True, grids=None, relax="FCF"):
+              theta=None, rtol=1e-14, krylov_maxit=100000, check=True, grids=None, relax="FCF", init=False):
         """Returns (uT, cycles per grid, residual history G x maxit, status);
         with `grids`, only those grids are computed.  relax: "FCF" (Sec. 4.1)
-        or "F" (F-relaxation on the finest level)."""
+        or "F" (F-relaxation on the finest level).  init: start from one sweep
+        of the level-1 propagator over the C-points instead of u0 everywhere."""
         if relax not in ("FCF", "F"):
             raise ValueError("relax must be 'FCF' or 'F'")
         u0 = _f64(u0)
@@ -208,7 +209,7 @@ class Problem:
         th = _f64(theta) if theta is not None else None
         st = lib().or_mgrit(self._h, _p(u0), dt, nsteps, m, levels, tol, maxit, coarse_kind,
                             _p(th), rtol, krylov_maxit, _p(out), _p(its), _p(hist), _p(gm),
-                            1 if relax == "F" else 0)
+                            1 if relax == "F" else 0, 1 if init else 0)
         if check and st != 0:
             raise RuntimeError(f"oracle mgrit: {STATUS.get(st, st)}")
         return out, its, hist, st

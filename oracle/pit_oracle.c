@@ -797,13 +797,15 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
 
 /* CTMGRIT^loc with s = 1 (Alg. 3): independent MGRIT on every grid, each
  * stopping when all its C-point residual norms are <= tol (Sec. 4.1), then
- * the caller combines.  The initial guess is u0 at every time point.
+ * the caller combines.  The initial guess is u0 at every time point, or
+ * (init = 1) one sweep of the level-1 propagator over the C-points.
  * Returns u_N on every grid in uT; iters[g] = cycles used; res_hist[g*maxit+k]
  * = residual measured in cycle k (when non-NULL). */
 int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev, double tol,
              int maxit, int coarse_kind, const double *theta, double rtol, int krylov_maxit,
              double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */,
-             int relax_f /* 1: F-relaxation on the finest level instead of FCF */)
+             int relax_f /* 1: F-relaxation on the finest level instead of FCF */,
+             int init /* 1: initial C-points from one sweep of the level-1 propagator */)
 {
     or_problem *P = (or_problem *)vp;
     if (m < 2 || nlev < 2) return OR_EINVAL;
@@ -818,6 +820,12 @@ int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev,
         double *v = malloc(sizeof(double) * (size_t)(nsteps + 1) * n);
         for (int k = 0; k <= nsteps; ++k) memcpy(v + (long long)k * n, u0 + P->off[g], sizeof(double) * n);
         mg_ctx C = {P, g, dt, m, nlev, rtol, krylov_maxit, coarse_kind, theta, relax_f, OR_OK};
+        if (init) {
+            /* initial guess at the C-points: u_{jm} = Phi_c(u_{(j-1)m}); the
+             * F-points follow from the first relaxation */
+            for (int j = 1; j <= nsteps / m; ++j)
+                mg_step(&C, 1, v + (long long)(j - 1) * m * n, NULL, v + (long long)j * m * n);
+        }
         int it = 0, conv = 0;
         while (it < maxit) {
             double r = mg_cycle(&C, 0, nsteps, v, NULL);

@@ -60,7 +60,7 @@ class pit_mgrit_opts(ctypes.Structure):
     _fields_ = [("t0", ctypes.c_double), ("t1", ctypes.c_double), ("nsteps", ctypes.c_int), ("m", ctypes.c_int),
                 ("levels", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts),
-                ("relax", ctypes.c_int), ("lanes", ctypes.c_int)]
+                ("relax", ctypes.c_int), ("lanes", ctypes.c_int), ("init", ctypes.c_int)]
 
 
 class pit_mgrit_stats(ctypes.Structure):
@@ -174,11 +174,12 @@ def bf16_round(w) -> np.ndarray:
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
-               crs=None, fas=False, relax=None, lanes=0) -> pit_mgrit_opts:
+               crs=None, fas=False, relax=None, lanes=0, init=False) -> pit_mgrit_opts:
     fine = fine or solve_opts()
     crs = crs or fine
     relax = PIT_RELAX_FCF if relax is None else relax
-    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes)
+    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes,
+                          1 if init else 0)
 
 
 class Problem:

@@ -1326,6 +1326,7 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     if (o->relax != PIT_RELAX_FCF && o->relax != PIT_RELAX_F)
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
+    if (o->init != 0 && o->init != 1) return fail(PIT_ERR_INVALID_ARG, "init must be 0 or 1");
     const int G = P->G, m = o->m, Nc = o->nsteps / m;
     const long long nt = P->ntot;
     const size_t vb = sizeof(double) * nt;
@@ -1367,6 +1368,33 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     // tolerance is relative to the correction, which vanishes as MGRIT
     // converges; the learned one is nonlinear and keeps the FAS form
     auto corr_form = [&]() { return !M.learned && o->coarse != PIT_COARSE_EXACT && !o->fas; };
+    if (o->init) {
+        // initial C-points from one sweep of the level-1 propagator (the
+        // F-points follow from the first relaxation)
+        if (o->coarse == PIT_COARSE_EXACT) {
+            for (int j = 0; j < Nc; ++j) {
+                StepCall sw;
+                sw.nb = 1;
+                sw.nsteps = 1;
+                sw.in = U + (long long)j * nt;
+                sw.is = nt;
+                sw.out_last = U + (long long)(j + 1) * nt;
+                sw.ols = nt;
+                TRY(run_coarse(M, sw, 1));
+            }
+        } else {
+            StepCall sw;
+            sw.nb = 1;
+            sw.nsteps = Nc;
+            sw.in = U;
+            sw.is = nt;
+            sw.out_steps = U + nt;
+            sw.osst = nt;
+            sw.out_last = U + (long long)Nc * nt;
+            sw.ols = nt;
+            TRY(run_coarse(M, sw, 1));
+        }
+    }
     // lanes: the correction form with the implicit coarse step for the whole
     // solve (also when a learned propagator was requested but not accepted:
     // the runtime judge only ever switches from the network to the implicit

@@ -386,6 +386,43 @@ def test_mgrit_fp32_coarse_correction_solves(name, relax):
     assert abs(res[B.PIT_PREC_FP32][1] - res[B.PIT_PREC_MIXED][1]) <= 1
 
 
+@pytest.mark.parametrize("name", ["w1", "w2_small", "w2_3lev", "w3_small", "w5_small"])
+@pytest.mark.parametrize("relax", [B.PIT_RELAX_FCF, B.PIT_RELAX_F])
+def test_mgrit_coarse_sweep_initial_guess_matches_oracle(name, relax):
+    k, n, N, m, lev, coarse = MG_CASES[name]
+    wl = W.workload(k)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    tol = 1e-10 * np.abs(u0).max()
+    fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=50000)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, coarse=coarse, fine=fine, relax=relax,
+                        init=True)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    dt = (wl.t1 - wl.t0) / N
+    ref, its, hist, _ = O.mgrit(u0, dt, N, m, lev, tol=tol, maxit=60, coarse_kind=coarse, rtol=1e-15,
+                                relax="F" if relax == B.PIT_RELAX_F else "FCF", init=True)
+    got = host(uT)
+    assert rel(got, ref) < 1e-10
+    assert abs(st.max_cycles - int(its.max())) <= 1
+    assert rel(got, O.sequential(u0, dt, N, rtol=1e-15)) < 1e-7
+
+
+def test_mgrit_exact_coarse_sweep_start_is_converged():
+    # with Phi_c = Phi^m the initial sweep is sequential stepping at the
+    # C-points: the first cycle's residual is at round-off level
+    k, n, N, m, lev, _ = MG_CASES["w1"]
+    wl = W.workload(k)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = W.random_vector(9, P.n_total)
+    fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-14, maxit=50000)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, 2, tol=1e-9, maxit=5, coarse=B.PIT_COARSE_EXACT, fine=fine, init=True)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    assert st.max_cycles == 1 and st.res_hist[0] < 1e-9
+
+
 @pytest.mark.parametrize("kc", [1, 2, 3])
 def test_mgrit_f_relaxation_exact_after_nc_cycles(kc):
     # kc F-relaxation cycles on Nc = kc coarse intervals reproduce sequential

@@ -159,6 +159,24 @@ def test_mgrit_f_relaxation_exactness_after_nc_cycles():
         np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-11)
 
 
+def test_mgrit_coarse_sweep_initial_guess():
+    # with Phi_c = Phi^m the initial coarse sweep is already the sequential
+    # solution at every C-point: the first cycle sees no residual
+    wl, P, u0, N, dt = _mgrit_case(1)
+    seq = P.sequential(u0, dt, N, rtol=1e-15)
+    uT, its, hist, st = P.mgrit(u0, dt, N, wl.m, 2, tol=0.0, maxit=1, coarse_kind=W.COARSE_EXACT,
+                                rtol=1e-15, check=False, init=True)
+    assert np.all(hist[:, 0] < 1e-13 * max(1.0, np.abs(u0).max()))
+    np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-12)
+    # with the implicit coarse step it changes the iterates, not the fixed
+    # point, and converges in no more cycles than the plain start
+    for relax in ("FCF", "F"):
+        a, its_a, *_ = P.mgrit(u0, dt, N, wl.m, 2, tol=1e-12, maxit=60, rtol=1e-15, relax=relax)
+        b, its_b, *_ = P.mgrit(u0, dt, N, wl.m, 2, tol=1e-12, maxit=60, rtol=1e-15, relax=relax, init=True)
+        np.testing.assert_allclose(b, seq, rtol=0, atol=1e-10)
+        assert its_b.max() <= its_a.max()
+
+
 def test_mgrit_exact_coarse_propagator_one_cycle():
     wl, P, u0, N, dt = _mgrit_case(1)
     uT, its, hist, st = P.mgrit(u0, dt, N, wl.m, 2, tol=0.0, maxit=3, coarse_kind=W.COARSE_EXACT,
