@@ -171,8 +171,10 @@ def ncu_traffic():
 MGRIT_TOL, KRYLOV_RTOL = 1e-7, 1e-10
 # per workload: the solution of the variable-coefficient workload decays about
 # 20-fold and its combination cancels strongly, so its tolerances are tighter
-# (checked the same way)
-MGRIT_TOL_BY_WORKLOAD = {1: 1e-8, 2: 1e-7, 3: 2e-9, 4: 1e-10, 5: 5e-9}
+# (checked the same way).  heat3d_n9: the combined error stays near 0.4x the
+# last C-point residual (1.6e-8 after a 3.8e-8 residual), so 3e-7 stops one
+# cycle earlier with a 10x margin to 1e-6
+MGRIT_TOL_BY_WORKLOAD = {1: 1e-8, 2: 3e-7, 3: 2e-9, 4: 1e-10, 5: 5e-9}
 # the combination sums grids with coefficients of both signs (d = 6: 4921
 # grids, coefficients up to C(5, 2) = 10), which amplifies correlated per-grid
 # errors up to sum |c_g| times; steps that stop just below a 1e-10 residual
@@ -182,6 +184,7 @@ PAPER_TOL, PAPER_RTOL = 1e-8, 1e-10
 
 
 COARSE_RTOL = 1e-2  # coarse solves for the correction: relative to the correction
+COARSE_RTOL_3LEVEL = 1e-6  # coarse solves of a three-level hierarchy
 
 
 def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None, init=True):
@@ -198,12 +201,16 @@ def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_pre
                            maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     plain = B.solve_opts(B.PIT_PREC_FP64, rtol=rtol, maxit=8000)
     coarse = B.PIT_COARSE_LEARNED if coarse is None else coarse
-    # the level-1 cycle of three levels needs tight coarse solves to keep the
-    # two-level convergence rate (measured: 5 cycles instead of 11)
+    # the level-1 cycle of three levels needs tighter coarse solves to keep the
+    # two-level convergence rate (measured on heat6d_n10, F relaxation: FP32
+    # to 1e-2 11 cycles; mixed to 1e-11 4 cycles, 2824 ms; to 1e-6 5 cycles,
+    # 2698 ms; to 1e-4 8 cycles, 2882 ms)
+    mixed_c3 = B.solve_opts(B.PIT_PREC_MIXED if coarse_prec is None else coarse_prec, rtol=COARSE_RTOL_3LEVEL,
+                            maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     loose = wl.levels == 2
     relax = B.PIT_RELAX_FCF if relax is None else relax
     chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, coarse=coarse, fine=mixed,
-                          crs=mixed_c if loose else mixed, relax=relax, init=init)
+                          crs=mixed_c if loose else mixed_c3, relax=relax, init=init)
     fp64 = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=plain, crs=plain,
                         fas=True)
     return chosen, fp64, mixed, plain
@@ -307,7 +314,7 @@ def run_pit(args, rank, world, local):
     P.profile_enable(False)
     ms_step = max_over_ranks(total_ms / args.steps, world, dev)
     value = job_value(dofsteps, world, ms_step)
-    gpu_launches = int(sum(prof_chosen.launches)) * args.steps
+    gpu_launches = int(sum(prof_chosen.kernels)) * args.steps
 
     # end to end through the C ABI with host buffers (pinned): H2D of u0 and
     # D2H of the combined values inside the timed region
@@ -335,7 +342,8 @@ def run_pit(args, rank, world, local):
     # which has no FP64 passes), against GB300's nominal FP64 rate.  The
     # shared-memory view of the FP32 inner iterations is reported beside it.
     d = wl.d
-    # family 0: relaxation launches (many entries per grid), 1: sequential sweeps
+    # family 0: relaxation calls (many entries per grid), 1: sequential sweeps;
+    # one timed call launches one kernel per shared-memory bucket, concurrently
     phi_ms = prof.ms[0] + prof.ms[1]
     phi_launches = int(prof.launches[0] + prof.launches[1])
     fp64_ms = prof.ms[0] if chosen.crs.prec == B.PIT_PREC_FP32 else phi_ms
@@ -361,9 +369,10 @@ def run_pit(args, rank, world, local):
                 "fp64_flops_per_node_pass": 3 * d + 4,
                 "fp64_pipe_limit_of_mix": (3 * d + 4) / (2.0 * (2 * d + 3)),
                 "fp64_time_basis_ms": fp64_ms,
-                "phi_ms_one_lane": phi_ms, "phi_launches_per_step": phi_launches,
+                "phi_ms_one_lane": phi_ms, "phi_calls_per_step": phi_launches,
                 "relax_ms_one_lane": prof.ms[0], "sweep_ms_one_lane": prof.ms[1],
-                "relax_launches": int(prof.launches[0]), "sweep_launches": int(prof.launches[1]),
+                "relax_calls": int(prof.launches[0]), "sweep_calls": int(prof.launches[1]),
+                "relax_kernels": int(prof.kernels[0]), "sweep_kernels": int(prof.kernels[1]),
                 "phi_share_of_one_lane_step": phi_ms / max(1e-9, sum(prof.ms)),
                 "point_iters_per_step": prof.point_iters,
                 "fp64_passes_per_node_step": prof.point_passes / max(1, prof.point_steps),
@@ -406,31 +415,33 @@ def run_pit(args, rank, world, local):
         forms = {}
         # plain FP64 MGRIT (same workload, FP64 Krylov, FAS form)
         uT_fp64 = None
-        try:
-            step(fp64, u0, out)
+
+        def median_ms(run):
+            """One untimed run (first-call planning and launch-shape tuning),
+            then the median of three timed runs (one when a run takes over a
+            second); returns (ms, the last run's result)."""
+            run()
             torch.cuda.synchronize()
-            e0.record(stream)
-            st = step(fp64, u0, out)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            forms["plain_fp64_mgrit"] = {"ms": ms, "value": dofsteps / (ms / 1e3), "cycles": st.max_cycles}
-            uT_fp64 = uT.cpu().numpy().copy()
-            out_fp64 = out.cpu().numpy().copy()
-        except B.PitError as err:
-            forms["plain_fp64_mgrit"] = {"unavailable": str(err)}
+            times, res = [], None
+            while len(times) < 3 and (not times or times[-1] < 1e3):
+                e0.record(stream)
+                res = run()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            return float(np.median(times)), res
+
         def timed(o):
             try:
-                step(o, u0, out)
+                ms, st = median_ms(lambda: step(o, u0, out))
             except B.PitError as err:
                 return {"unavailable": str(err)}
-            torch.cuda.synchronize()
-            e0.record(stream)
-            st = step(o, u0, out)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
             return {"ms": ms, "value": dofsteps / (ms / 1e3), "cycles": st.max_cycles}
+
+        forms["plain_fp64_mgrit"] = timed(fp64)
+        if "ms" in forms["plain_fp64_mgrit"]:
+            uT_fp64 = uT.cpu().numpy().copy()
+            out_fp64 = out.cpu().numpy().copy()
 
         # the chosen form without the network (implicit coarse step solved for the correction)
         mi, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT)
@@ -455,12 +466,7 @@ def run_pit(args, rank, world, local):
         # time-sequential stepping on the GPU, FP64 and mixed
         for name, so in (("sequential_fp64", plain), ("sequential_mixed", mixed)):
             try:
-                e0.record(stream)
-                P.sequential_solve(u0, wl.dt, wl.nsteps, uT, so)
-                P.combine(uT, pts, out)
-                e1.record(stream)
-                e1.synchronize()
-                ms = e0.elapsed_time(e1)
+                ms, _ = median_ms(lambda: (P.sequential_solve(u0, wl.dt, wl.nsteps, uT, so), P.combine(uT, pts, out)))
                 forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3)}
             except B.PitError as err:
                 forms[name] = {"unavailable": str(err)}

@@ -306,22 +306,26 @@ pit_status pit_mgrit_solve(pit_problem_t p, const double *u0, const pit_mgrit_op
  * are clamped to its boundary cell. */
 pit_status pit_combine(pit_problem_t p, const double *u, int n_pts, const double *pts, double *out);
 
-/* Kernel timing of a problem: while enabled, every kernel the library
- * launches is bracketed by CUDA events recorded on the problem's stream.
- * pit_profile_read synchronises the stream and returns, since the last
- * enable, per kernel family: launches, summed device milliseconds, and for
- * the backward-Euler kernels the work done (Krylov iterations and refinement
- * passes weighted by grid nodes).  Family 0 = backward-Euler solver on
- * batches of 8 or more entries per grid (relaxation), 1 = backward-Euler
- * solver on fewer (sequential sweeps, time stepping), 2 = combination sum,
- * 3 = other. */
+/* Kernel timing of a problem: while enabled, every library call that launches
+ * device work is bracketed by CUDA events recorded on the problem's stream
+ * (one timed call may launch several kernels: a multi-step solve launches one
+ * kernel per shared-memory bucket, concurrently on forked streams, and the
+ * events span them all).  pit_profile_read synchronises the stream and
+ * returns, since the last enable, per kernel family: timed calls, their summed
+ * device milliseconds, the kernels launched, and for the backward-Euler
+ * kernels the work done (Krylov iterations and refinement passes weighted by
+ * grid nodes).  Family 0 = backward-Euler solver on batches of 8 or more
+ * entries per grid (relaxation), 1 = backward-Euler solver on fewer
+ * (sequential sweeps, time stepping), 2 = combination sum, 3 = other. */
 typedef struct {
-    long long launches[4];
-    double ms[4];
+    long long launches[4];   /* timed calls                                       */
+    double ms[4];            /* device time of the timed calls                    */
     long long phi_items;
     long long point_iters;   /* sum over items of nodes x Krylov iterations       */
     long long point_passes;  /* sum over items of nodes x FP64 residual passes    */
     long long point_steps;   /* sum over items of nodes x backward-Euler steps    */
+    long long kernels[4];    /* kernel launches, including those of the
+                                launch-shape tuner on a first call              */
 } pit_profile;
 
 pit_status pit_profile_enable(pit_problem_t p, int on);

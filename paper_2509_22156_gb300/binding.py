@@ -73,7 +73,7 @@ class pit_mgrit_stats(ctypes.Structure):
 class pit_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("phi_items", ctypes.c_longlong),
                 ("point_iters", ctypes.c_longlong), ("point_passes", ctypes.c_longlong),
-                ("point_steps", ctypes.c_longlong)]
+                ("point_steps", ctypes.c_longlong), ("kernels", ctypes.c_longlong * 4)]
 
 
 class pit_train_opts(ctypes.Structure):

@@ -150,6 +150,7 @@ struct pit_problem {
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> prof_recs;  // (family, first event index)
     long long prof_items = 0, prof_point_iters = 0, prof_point_passes = 0, prof_point_steps = 0;
+    long long prof_kernels[4] = {0, 0, 0, 0};  // kernel launches per profile family
 };
 
 namespace {
@@ -166,6 +167,12 @@ int ptr_is_device(const void *p)
 }
 
 // Records a CUDA event pair around the next launch when profiling is on.
+// Counts kernel launches per profile family while profiling is enabled.
+static inline void count_kernels(pit_problem *P, int family, long long n = 1)
+{
+    if (P->prof_on) P->prof_kernels[family] += n;
+}
+
 struct ProfScope {
     pit_problem *P;
     cudaStream_t s;
@@ -463,6 +470,7 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
         for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up; the last is timed
             CU(cudaEventRecord(e0, P->stream));
             CU(launch_steps(prec, a, cand[k], v.smem, P->stream, v.xg));
+            count_kernels(P, wide ? 0 : 1);
             CU(cudaEventRecord(e1, P->stream));
         }
         CU(cudaEventSynchronize(e1));
@@ -523,6 +531,7 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
         }
         cudaStream_t sq = fork ? st[q] : st[0];
         CU(launch_steps(prec, b, P->threads[prec][wide ? 1 : 0][q], v[q].smem, sq, v[q].xg));
+        count_kernels(P, wide ? 0 : 1);
     }
     if (fork) {
         for (int q = 1; q < NPART; ++q) {
@@ -549,6 +558,7 @@ pit_status run_net(pit_problem *P, const StepCall &c, const int *active)
     ProfScope ps(P, 0);
     if (smem <= P->max_smem) {
         CU(launch_net_steps(a, P->h_net, nullptr, 0, smem, P->stream, (int)items));
+        count_kernels(P, 0);
         return PIT_OK;
     }
     const long long slab = (long long)net_act_floats(nmax, false);
@@ -560,6 +570,7 @@ pit_status run_net(pit_problem *P, const StepCall &c, const int *active)
         a.item0 = (int)k0;
         const long long cnt = (items - k0) < chunk ? (items - k0) : chunk;
         CU(launch_net_steps(a, P->h_net, (float *)P->n_act.p, slab, smem, P->stream, (int)cnt));
+        count_kernels(P, 0);
     }
     return PIT_OK;
 }
@@ -826,6 +837,7 @@ pit_status pit_sample_initial(pit_problem_t P, int kind, const double *params, i
     {
         ProfScope ps(P, 3);
         CU(launch_initial(P->d_grids, P->G, P->op, P->d_hi, kind, P->w_prm.d(), n_params, target, P->stream));
+        count_kernels(P, 3);
     }
     if (!dev) CU(cudaMemcpyAsync(u0, target, sizeof(double) * P->ntot, cudaMemcpyDeviceToHost, P->stream));
     CU(cudaStreamSynchronize(P->stream));
@@ -838,6 +850,7 @@ pit_status pit_apply(pit_problem_t P, double dt, int n_batch, const double *pv, 
     if (!ptr_is_device(pv) || !ptr_is_device(qv)) return fail(PIT_ERR_INVALID_ARG, "p and q must be device memory");
     ProfScope ps(P, 3);
     CU(launch_apply(P->d_grids, P->G, P->ntot, n_batch, dt, pv, qv, P->d_faces, P->op, P->stream));
+    count_kernels(P, 3);
     return PIT_OK;
 }
 
@@ -1091,6 +1104,7 @@ pit_status mg_cycle(Mg &M, int Nc, bool corr, double *h_res)
             // two-level cycle from e = 0; then u_{jm} = relaxed + e_j
             TRY(mg_level1_cycle(M, P->m_Z.d(), 0, P->m_E.d(), Nc, GC));
             CU(launch_add_states(P->d_grids, G, nt, Nc, Rx + nt, P->m_E.d() + nt, U + nt, M.active, M.s));
+            count_kernels(P, 3);
         } else {
             StepCall sw;  // e_{j+1} = Phi_c(e_j) + r_{j+1}; stored as u = relaxed + e
             sw.nb = 1;
@@ -1505,6 +1519,7 @@ extern "C" pit_status pit_combine(pit_problem_t P, const double *u, int n_pts, c
     {
         ProfScope ps(P, 2);
         CU(launch_combine(P->d_grids, P->d_coef, P->d_levels, P->G, P->op, du, n_pts, dp, target, P->stream));
+        count_kernels(P, 2);
     }
     if (!dev_out) {
         CU(cudaMemcpyAsync(out, target, sizeof(double) * n_pts, cudaMemcpyDeviceToHost, P->stream));
@@ -1521,6 +1536,7 @@ extern "C" pit_status pit_profile_enable(pit_problem_t P, int on)
     P->ev_used = 0;
     P->prof_recs.clear();
     P->prof_items = P->prof_point_iters = P->prof_point_passes = P->prof_point_steps = 0;
+    for (long long &k : P->prof_kernels) k = 0;
     return PIT_OK;
 }
 
@@ -1535,6 +1551,7 @@ extern "C" pit_status pit_profile_read(pit_problem_t P, pit_profile *out)
         out->launches[r.first] += 1;
         out->ms[r.first] += ms;
     }
+    for (int f = 0; f < 4; ++f) out->kernels[f] = P->prof_kernels[f];
     out->phi_items = P->prof_items;
     out->point_iters = P->prof_point_iters;
     out->point_passes = P->prof_point_passes;
@@ -1673,10 +1690,12 @@ pit_status net_loss_grad_dev(pit_problem *P, double dT, int n_batch, const doubl
         ProfScope ps(P, 3);
         CU(launch_net_train(P->d_grids, (const NetTrainItem *)P->n_items.p, n_items, u, y, dT, w_dev,
                             (float *)P->n_act.p, slab, (float *)P->n_rows.p, P->n_loss.d(), P->op, P->stream));
+        count_kernels(P, 3);
     }
     if (grad_dev)
         CU(launch_net_adam((const float *)P->n_rows.p, n_items, 1.0f, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0, 0,
                            grad_dev, P->stream));
+        count_kernels(P, 3);
     if (loss_host) {
         std::vector<double> l(n_items);
         CU(cudaMemcpyAsync(l.data(), P->n_loss.p, sizeof(double) * n_items, cudaMemcpyDeviceToHost, P->stream));
@@ -1787,6 +1806,7 @@ extern "C" pit_status pit_train_coarse(pit_problem_t P, const pit_train_opts *o,
         CU(cudaMemcpyAsync(P->n_prm.p, prm.data(), sizeof(double) * prm.size(), cudaMemcpyHostToDevice, P->stream));
         double *u0 = Ud + (long long)tr * o->traj_len * nt;
         CU(launch_initial(P->d_grids, G, P->op, P->d_hi, 0, P->n_prm.d(), (int)prm.size(), u0, P->stream));
+        count_kernels(P, 3);
         // pair k: (u_k, u_{k+1} = Phi^m u_k), u_{k+1} also the input of pair k+1
         for (int k = 0; k < o->traj_len; ++k) {
             StepCall c;
@@ -1866,11 +1886,13 @@ extern "C" pit_status pit_train_coarse(pit_problem_t P, const pit_train_opts *o,
                 CU(launch_net_train(P->d_grids, (const NetTrainItem *)P->n_items.p + s0, nb, Ud, Yd, dT,
                                     (const float *)P->n_w.p, (float *)P->n_act.p, slab, (float *)P->n_rows.p,
                                     P->n_loss.d() + s0, P->op, P->stream));
+                count_kernels(P, 3);
             }
             ++t;
             CU(launch_net_adam((const float *)P->n_rows.p, nb, 1.0f / nb, (float *)P->n_master.p, (float *)P->n_m.p,
                                (float *)P->n_v.p, (float *)P->n_w.p, (float)o->lr, 0.9f, 0.999f, 1e-8f, t, nullptr,
                                P->stream));
+            count_kernels(P, 3);
             n_loss += nb;
         }
         if (ep == 0 || ep == o->epochs - 1) {
