@@ -42,6 +42,8 @@ UNIT = "DoF-steps/s"
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK = 128  # 32 banks x 4 B per SM and clock
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (non-tensor) rate
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 partitions x 32)
+PREC_NAMES = ["fp64", "mixed (FP64 refinement)", "fp32", "pair (FP32-pair refinement)"]
 
 
 def parse():
@@ -187,14 +189,24 @@ COARSE_RTOL = 1e-2  # coarse solves for the correction: relative to the correcti
 COARSE_RTOL_3LEVEL = 1e-6  # coarse solves of a three-level hierarchy
 
 
-def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None, init=True):
-    """Options of the chosen form (FP32 Krylov in FP64 refinement, learned
-    coarse propagator or the implicit one solved for the correction with a
-    loose tolerance) and of the plain FP64 form (the paper's algorithm: FAS
-    form of Alg. 2, FP64 Krylov, one tolerance for every solve)."""
+def fine_prec_of(wl, B):
+    """Precision form of the fine solves: the pair refinement for the heat
+    operator (the form it is implemented for), FP64 refinement otherwise."""
+    return B.PIT_PREC_MIXED_PAIR if wl.op == B.PIT_OP_HEAT else B.PIT_PREC_MIXED
+
+
+def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None, init=True, fine_prec=None):
+    """Options of the chosen form (FP32 Krylov in a refinement on FP32 pairs
+    (heat) or in FP64 refinement, learned coarse propagator or the implicit one
+    solved for the correction with a loose tolerance) and of the plain FP64
+    form (the paper's algorithm: FAS form of Alg. 2, FP64 Krylov, one tolerance
+    for every solve).  Returns (chosen, plain FP64 MGRIT, FP64-refinement
+    solve options, FP64 solve options)."""
     tol = MGRIT_TOL_BY_WORKLOAD.get(wl_index(wl), MGRIT_TOL) if tol is None else tol
     rtol = KRYLOV_RTOL_BY_WORKLOAD.get(wl_index(wl), KRYLOV_RTOL) if rtol is None else rtol
+    fine_prec = fine_prec_of(wl, B) if fine_prec is None else fine_prec
     mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=rtol, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+    fine = B.solve_opts(fine_prec, rtol=rtol, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     # coarse solves of the two-level correction form: FP32 Krylov to the coarse
     # tolerance (relative to the correction, far above FP32 rounding)
     mixed_c = B.solve_opts(B.PIT_PREC_FP32 if coarse_prec is None else coarse_prec, rtol=COARSE_RTOL,
@@ -205,11 +217,11 @@ def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_pre
     # two-level convergence rate (measured on heat6d_n10, F relaxation: FP32
     # to 1e-2 11 cycles; mixed to 1e-11 4 cycles, 2824 ms; to 1e-6 5 cycles,
     # 2698 ms; to 1e-4 8 cycles, 2882 ms)
-    mixed_c3 = B.solve_opts(B.PIT_PREC_MIXED if coarse_prec is None else coarse_prec, rtol=COARSE_RTOL_3LEVEL,
+    mixed_c3 = B.solve_opts(fine_prec if coarse_prec is None else coarse_prec, rtol=COARSE_RTOL_3LEVEL,
                             maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     loose = wl.levels == 2
     relax = B.PIT_RELAX_FCF if relax is None else relax
-    chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, coarse=coarse, fine=mixed,
+    chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, coarse=coarse, fine=fine,
                           crs=mixed_c if loose else mixed_c3, relax=relax, init=init)
     fp64 = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, fine=plain, crs=plain,
                         fas=True)
@@ -332,51 +344,72 @@ def run_pit(args, rank, world, local):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step = sum(e2e_ms) / len(e2e_ms)
 
-    # roofline of the dominant kernel (steps_kernel<HEAT, MIXED, 3>).  ncu
-    # shows it bound by the FP64 pipe (the refinement residual passes), so the
-    # roofline is FP64 arithmetic: FP64 flops per node and residual pass =
-    # stencil diag x + sum_i off_i (x_-i + x_+i) (3d + 1), b - A x (1) and the
-    # correction update (2) = 3d + 4, from the kernel's own work counters, over
-    # its event time (one profiled step with every grid in one lane; the
-    # relaxation launches alone when the coarse solves run in the FP32 form,
-    # which has no FP64 passes), against GB300's nominal FP64 rate.  The
-    # shared-memory view of the FP32 inner iterations is reported beside it.
+    # roofline of the dominant kernel: the relaxation launches (family 0: many
+    # entries per grid), from the kernel's own work counters of one profiled
+    # step with every grid in one lane, over those launches' event time.
+    #   pair form (heat): bound by FP32 arithmetic issue, no FP64 work.  FP32
+    #     operations per node, counted from the kernel source: refinement pass
+    #     = correction added to the pairs (14) + residual check (39 d + 17) =
+    #     39 d + 31; CG iteration = stencil (3 d + 1) + two dot products (4) +
+    #     four vector updates (8) = 3 d + 13 (the line-preconditioned
+    #     iterations do more, so the count is a lower bound); peak = 152 SMs x
+    #     128 FP32 lanes x 2 (FMA) x SM clock.
+    #   FP64-refinement form: bound by the FP64 pipe; FP64 flops per node and
+    #     residual pass = stencil diag x + sum_i off_i (x_-i + x_+i) (3d + 1),
+    #     b - A x (1) and the correction update (2) = 3d + 4, against GB300's
+    #     nominal FP64 rate.
+    # The shared-memory view of the FP32 inner iterations is reported beside it.
     d = wl.d
     # family 0: relaxation calls (many entries per grid), 1: sequential sweeps;
     # one timed call launches one kernel per shared-memory bucket, concurrently
     phi_ms = prof.ms[0] + prof.ms[1]
     phi_launches = int(prof.launches[0] + prof.launches[1])
-    fp64_ms = prof.ms[0] if chosen.crs.prec == B.PIT_PREC_FP32 else phi_ms
-    fp64_flops = prof.point_passes * (3 * d + 4)
-    fp64_peak = FP64_PEAK_TFLOPS
-    achieved = fp64_flops / (fp64_ms / 1e3) / 1e12 if fp64_ms > 0 else None
+    relax_ms = prof.ms[0]
+    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    pair = chosen.fine.prec == B.PIT_PREC_MIXED_PAIR
+    if pair:
+        flops_pass, flops_iter = 39 * d + 31, 3 * d + 13
+        flops = prof.point_passes_f[0] * flops_pass + prof.point_iters_f[0] * flops_iter
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        kernel = f"steps_kernel<HEAT,PAIR,{d}> (grid-resident multi-step BE, FP32 CG in a refinement on FP32 pairs)"
+        peak_source = (f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops (FMA) x {sm_mhz:.0f} MHz "
+                       "(GB300 unit counts and maximum SM clock)")
+        extra = {"fp32_flops_per_node_pass": flops_pass, "fp32_flops_per_node_krylov_iter": flops_iter,
+                 "flop_count_note": "per-node FP32 operation counts of the kernel source; the line-preconditioned "
+                                    "Krylov iterations do more, so achieved is a lower bound"}
+    else:
+        flops = prof.point_passes_f[0] * (3 * d + 4)
+        peak = FP64_PEAK_TFLOPS
+        opname = {B.PIT_OP_HEAT: "HEAT", B.PIT_OP_VARHEAT: "VARHEAT", B.PIT_OP_OU: "OU"}[wl.op]
+        kernel = f"steps_kernel<{opname},MIXED,{d}> (grid-resident multi-step BE, FP32 Krylov in FP64 refinement)"
+        peak_source = ("GB300 nominal FP64 rate (1.25 TFLOP/s, profiling recipe table); an FMA micro-benchmark on "
+                       "this pool measured 1.20; the kernel's FP64 op mix (2d + 3 instructions for 3d + 4 flops) "
+                       "saturates the pipe at fp64_pipe_limit_of_mix of it")
+        extra = {"fp64_flops_per_node_pass": 3 * d + 4,
+                 "fp64_pipe_limit_of_mix": (3 * d + 4) / (2.0 * (2 * d + 3))}
+    achieved = flops / (relax_ms / 1e3) / 1e12 if relax_ms > 0 else None
     # (the committed ncu summary covers the heat3d_n9 workload only)
     trf = ncu_traffic() if wl_index(wl) == 2 else None
-    items_per_launch = prof.phi_items / max(1, phi_launches)
     smem_bytes_per_point_iter = 2 + 4 * (2 * d + 1) + 4 + 16 + 8 + 8 + 4
-    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
     peak_smem = SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9  # GB/s
-    smem_achieved = prof.point_iters * smem_bytes_per_point_iter / (phi_ms / 1e3) / 1e9 if phi_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": "steps_kernel<HEAT,MIXED,3> (grid-resident multi-step BE, FP32 CG in FP64 refinement)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp64_peak) if achieved else None,
+    smem_achieved = (prof.point_iters_f[0] * smem_bytes_per_point_iter / (relax_ms / 1e3) / 1e9
+                     if relax_ms > 0 else None)
+    roofline = {"bound": "alu", "kernel": kernel,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
                 "traffic": (trf * P.G * (wl.nsteps // wl.m)) if trf is not None else None,
                 "traffic_note": "DRAM bytes of one full relaxation launch (all grids x intervals) from the "
                                 "committed ncu summary, null when the kernel changed since",
-                "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s, profiling recipe table); an FMA "
-                               "micro-benchmark on this pool measured 1.20; the kernel's FP64 op mix (2d + 3 "
-                               "instructions for 3d + 4 flops) saturates the pipe at fp64_pipe_limit_of_mix of it",
-                "fp64_flops_per_node_pass": 3 * d + 4,
-                "fp64_pipe_limit_of_mix": (3 * d + 4) / (2.0 * (2 * d + 3)),
-                "fp64_time_basis_ms": fp64_ms,
+                "peak_source": peak_source, **extra,
+                "time_basis_ms": relax_ms,
                 "phi_ms_one_lane": phi_ms, "phi_calls_per_step": phi_launches,
                 "relax_ms_one_lane": prof.ms[0], "sweep_ms_one_lane": prof.ms[1],
                 "relax_calls": int(prof.launches[0]), "sweep_calls": int(prof.launches[1]),
                 "relax_kernels": int(prof.kernels[0]), "sweep_kernels": int(prof.kernels[1]),
                 "phi_share_of_one_lane_step": phi_ms / max(1e-9, sum(prof.ms)),
-                "point_iters_per_step": prof.point_iters,
-                "fp64_passes_per_node_step": prof.point_passes / max(1, prof.point_steps),
-                "krylov_iters_per_node_step": prof.point_iters / max(1, prof.point_steps),
+                "relax_node_steps": prof.point_steps_f[0],
+                "relax_passes_per_node_step": prof.point_passes_f[0] / max(1, prof.point_steps_f[0]),
+                "relax_krylov_iters_per_node_step": prof.point_iters_f[0] / max(1, prof.point_steps_f[0]),
                 "smem_view": {"achieved": smem_achieved, "peak": peak_smem, "unit": "GB/s",
                               "frac": (smem_achieved / peak_smem) if smem_achieved else None,
                               "bytes_per_node_iter": smem_bytes_per_point_iter,
@@ -385,7 +418,9 @@ def run_pit(args, rank, world, local):
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 (FP32 inner Krylov inside FP64 refinement; BF16-weight coarse network)",
+        "vs_baseline": None,
+        "dtype": ("f64 in/out (state and residual as FP32 pairs, ~48-bit; FP32 inner Krylov; BF16-weight coarse network)"
+                  if pair else "f64 (FP32 inner Krylov inside FP64 refinement; BF16-weight coarse network)"),
         "data": "synthetic (analytic initial value, seeded evaluation points)",
         "config": {"workload": wl.name, "d": wl.d, "level": wl.n, "grids": P.G, "n_total": P.n_total,
                    "accuracy_target": "relative L2 error <= 1e-6 of the combined solution vs the oracle's sequential solution",
@@ -394,7 +429,8 @@ def run_pit(args, rank, world, local):
                    "coarse": "learned network (implicit backward Euler dT = m dt when the judge rejects it)",
                    "mgrit_tol_abs": chosen.tol,
                    "krylov_rtol": chosen.fine.rtol, "inner_rtol": chosen.fine.inner_rtol,
-                   "coarse_solves": {"prec": ["fp64", "mixed", "fp32"][chosen.crs.prec], "rtol": chosen.crs.rtol},
+                   "fine_solves": {"prec": PREC_NAMES[chosen.fine.prec]},
+                   "coarse_solves": {"prec": PREC_NAMES[chosen.crs.prec], "rtol": chosen.crs.rtol},
                    "eval_points": int(pts_h.shape[0]), "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "time_to_tol_ms": ms_step, "mgrit_cycles": stats.max_cycles,
@@ -459,12 +495,20 @@ def run_pit(args, rank, world, local):
         o_mc, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT, relax=chosen.relax,
                                      coarse_prec=B.PIT_PREC_MIXED)
         forms["mixed_implicit_coarse_mgrit_mixed_coarse_solves"] = timed(o_mc)
+        if fine_prec_of(wl, B) != B.PIT_PREC_MIXED:
+            # the chosen form with the fine solves in FP64 refinement instead of FP32 pairs
+            o_fr, _, _, _ = solver_setup(wl, B, coarse=B.PIT_COARSE_IMPLICIT, relax=chosen.relax,
+                                         fine_prec=B.PIT_PREC_MIXED)
+            forms["mixed_implicit_coarse_mgrit_fp64_refinement"] = timed(o_fr)
         # the paper's algorithm (FAS form, one tolerance) in mixed precision
         mf = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64, fine=mixed, crs=mixed,
                           fas=True)
         forms["mixed_fas_mgrit"] = timed(mf)
-        # time-sequential stepping on the GPU, FP64 and mixed
-        for name, so in (("sequential_fp64", plain), ("sequential_mixed", mixed)):
+        # time-sequential stepping on the GPU: FP64, FP64 refinement and (heat) pair refinement
+        seq_forms = [("sequential_fp64", plain), ("sequential_mixed", mixed)]
+        if fine_prec_of(wl, B) != B.PIT_PREC_MIXED:
+            seq_forms.append(("sequential_pair", chosen.fine))
+        for name, so in seq_forms:
             try:
                 ms, _ = median_ms(lambda: (P.sequential_solve(u0, wl.dt, wl.nsteps, uT, so), P.combine(uT, pts, out)))
                 forms[name] = {"ms": ms, "value": dofsteps / (ms / 1e3)}

@@ -68,7 +68,7 @@ typedef enum {
                            donor-cell upwind drift + central diffusion; BiCGStab            */
 } pit_op;
 
-typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2 } pit_prec;
+typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2, PIT_PREC_MIXED_PAIR = 3 } pit_prec;
 
 typedef enum {
     PIT_COARSE_IMPLICIT = 0, /* Phi_coarse = backward Euler with dT = m dt (Sec. 3.3.1)  */
@@ -109,7 +109,21 @@ typedef struct {
  *                          whose tolerance lies far above FP32 rounding, such
  *                          as the coarse correction solves of MGRIT (rtol of
  *                          1e-5 or looser).  Values below 2^-126 of the largest
- *                          input are flushed to zero. */
+ *                          input are flushed to zero.
+ *   prec = PIT_PREC_MIXED_PAIR: the refinement of PIT_PREC_MIXED with the
+ *                          state held as pairs of FP32 numbers (hi + lo, about
+ *                          48 significant bits, scaled by a power of two) and
+ *                          the residual b - A x formed from the pairs by
+ *                          error-free FP32 transformations (two-sum, two-product
+ *                          by FMA) with one compensation term: the accuracy of
+ *                          the FP64 residual to about 1e-14 relative, without
+ *                          FP64 arithmetic (which GB300 runs at 1/58 of the FP32
+ *                          rate).  Same options and stopping rule as
+ *                          PIT_PREC_MIXED.  Heat operator only (other operators:
+ *                          PIT_ERR_UNSUPPORTED); grids whose state does not fit
+ *                          in shared memory are solved in the PIT_PREC_MIXED
+ *                          form.  Inputs and outputs stay FP64; values below
+ *                          2^-102 of the state's norm lose their low part. */
 typedef struct {
     int prec;
     double rtol;
@@ -322,10 +336,13 @@ typedef struct {
     double ms[4];            /* device time of the timed calls                    */
     long long phi_items;
     long long point_iters;   /* sum over items of nodes x Krylov iterations       */
-    long long point_passes;  /* sum over items of nodes x FP64 residual passes    */
+    long long point_passes;  /* sum over items of nodes x refinement residual passes */
     long long point_steps;   /* sum over items of nodes x backward-Euler steps    */
     long long kernels[4];    /* kernel launches, including those of the
                                 launch-shape tuner on a first call              */
+    long long point_iters_f[2];   /* point_iters of family 0 and of family 1     */
+    long long point_passes_f[2];  /* point_passes of family 0 and of family 1    */
+    long long point_steps_f[2];   /* point_steps of family 0 and of family 1     */
 } pit_profile;
 
 pit_status pit_profile_enable(pit_problem_t p, int on);

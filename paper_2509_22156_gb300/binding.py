@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "PIT_OK", 1: "PIT_ERR_INVALID_ARG", 2: "PIT_ERR_CUDA", 3: "PI
                 4: "PIT_ERR_NOCONV", 5: "PIT_ERR_BREAKDOWN", 6: "PIT_ERR_NONFINITE", 7: "PIT_ERR_TIMEOUT",
                 8: "PIT_ERR_UNSUPPORTED"}
 PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU = 0, 1, 2
-PIT_PREC_FP64, PIT_PREC_MIXED, PIT_PREC_FP32 = 0, 1, 2
+PIT_PREC_FP64, PIT_PREC_MIXED, PIT_PREC_FP32, PIT_PREC_MIXED_PAIR = 0, 1, 2, 3
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
 PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
 
@@ -73,7 +73,9 @@ class pit_mgrit_stats(ctypes.Structure):
 class pit_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4), ("phi_items", ctypes.c_longlong),
                 ("point_iters", ctypes.c_longlong), ("point_passes", ctypes.c_longlong),
-                ("point_steps", ctypes.c_longlong), ("kernels", ctypes.c_longlong * 4)]
+                ("point_steps", ctypes.c_longlong), ("kernels", ctypes.c_longlong * 4),
+                ("point_iters_f", ctypes.c_longlong * 2), ("point_passes_f", ctypes.c_longlong * 2),
+                ("point_steps_f", ctypes.c_longlong * 2)]
 
 
 class pit_train_opts(ctypes.Structure):

@@ -110,8 +110,8 @@ struct pit_problem {
     int *d_levels = nullptr;
     double *d_hi = nullptr;
     double *d_faces = nullptr;
-    DevStats *d_stats = nullptr;
-    DevStats *h_stats = nullptr;  // pinned
+    DevStats *d_stats = nullptr;  // [0]: batches of 8 or more entries per grid, [1]: fewer
+    DevStats *h_stats = nullptr;  // pinned, the same two
     int *d_order = nullptr;          // grids by decreasing size
     uint16_t *d_masks = nullptr;     // neighbour masks, packed like a state
     // launch plan per precision form: class 0 = grids whose FP64 state fits in
@@ -151,6 +151,7 @@ struct pit_problem {
     std::vector<std::pair<int, size_t>> prof_recs;  // (family, first event index)
     long long prof_items = 0, prof_point_iters = 0, prof_point_passes = 0, prof_point_steps = 0;
     long long prof_kernels[4] = {0, 0, 0, 0};  // kernel launches per profile family
+    long long prof_fam_iters[2] = {0, 0}, prof_fam_passes[2] = {0, 0}, prof_fam_steps[2] = {0, 0};
 };
 
 namespace {
@@ -242,10 +243,12 @@ double binomial(int a, int b)
 pit_status check_solve_opts(const pit_solve_opts *o)
 {
     if (!o) return fail(PIT_ERR_INVALID_ARG, "solve options are NULL");
-    if (o->prec != PIT_PREC_FP64 && o->prec != PIT_PREC_MIXED && o->prec != PIT_PREC_FP32)
+    if (o->prec != PIT_PREC_FP64 && o->prec != PIT_PREC_MIXED && o->prec != PIT_PREC_FP32 &&
+        o->prec != PIT_PREC_MIXED_PAIR)
         return fail(PIT_ERR_INVALID_ARG, "unknown precision %d", o->prec);
     if (!(o->rtol >= 0.0) || o->maxit < 1) return fail(PIT_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
-    if (o->prec == PIT_PREC_MIXED && (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->ir_maxit < 1))
+    if ((o->prec == PIT_PREC_MIXED || o->prec == PIT_PREC_MIXED_PAIR) &&
+        (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->ir_maxit < 1))
         return fail(PIT_ERR_INVALID_ARG, "mixed precision needs 0 < inner_rtol < 1 and ir_maxit >= 1");
     return PIT_OK;
 }
@@ -266,6 +269,8 @@ size_t grid_smem_bytes(const pit_problem *P, int prec, int g)
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
+    if (prec == PAIR && P->desc.op != PIT_OP_HEAT)
+        return fail(PIT_ERR_UNSUPPORTED, "the pair precision form is implemented for the heat operator only");
     std::vector<int> order(P->G);
     for (int g = 0; g < P->G; ++g) order[g] = g;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P->info[a].n > P->info[b].n; });
@@ -511,6 +516,7 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     for (int q = 1; q < NPART; ++q) st[q] = L ? L->sides[q - 1] : P->sides[q - 1];
     cudaEvent_t ef = L ? L->fork : P->ev_fork, ej = L ? L->join : P->ev_join;
     StepArgs a = make_args(P, o, c, active);
+    a.stats = P->d_stats + (wide ? 0 : 1);  // counters per kernel family
     ProfScope ps(P, wide ? 0 : 1, st[0]);
     const bool fork = n_parts > 1;
     if (fork) {
@@ -577,20 +583,36 @@ pit_status run_net(pit_problem *P, const StepCall &c, const int *active)
 
 pit_status reset_stats(pit_problem *P)
 {
-    CU(cudaMemsetAsync(P->d_stats, 0, sizeof(DevStats), P->stream));
+    CU(cudaMemsetAsync(P->d_stats, 0, 2 * sizeof(DevStats), P->stream));
     return PIT_OK;
 }
 
+// Counters of both kernel families since the last reset, merged.
 pit_status read_stats(pit_problem *P, DevStats &s)
 {
-    CU(cudaMemcpyAsync(P->h_stats, P->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaMemcpyAsync(P->h_stats, P->d_stats, 2 * sizeof(DevStats), cudaMemcpyDeviceToHost, P->stream));
     CU(cudaStreamSynchronize(P->stream));
-    s = *P->h_stats;
+    const DevStats &a = P->h_stats[0], &b = P->h_stats[1];
+    s = a;
+    s.sum_iters += b.sum_iters;
+    s.items += b.items;
+    s.point_iters += b.point_iters;
+    s.point_passes += b.point_passes;
+    s.point_steps += b.point_steps;
+    s.max_iters = b.max_iters > s.max_iters ? b.max_iters : s.max_iters;
+    s.n_failed += b.n_failed;
+    s.max_refine = b.max_refine > s.max_refine ? b.max_refine : s.max_refine;
+    s.worst = b.worst > s.worst ? b.worst : s.worst;
     if (P->prof_on) {
         P->prof_items += (long long)s.items;
         P->prof_point_iters += (long long)s.point_iters;
         P->prof_point_passes += (long long)s.point_passes;
         P->prof_point_steps += (long long)s.point_steps;
+        for (int f = 0; f < 2; ++f) {
+            P->prof_fam_iters[f] += (long long)P->h_stats[f].point_iters;
+            P->prof_fam_passes[f] += (long long)P->h_stats[f].point_passes;
+            P->prof_fam_steps[f] += (long long)P->h_stats[f].point_steps;
+        }
     }
     return PIT_OK;
 }
@@ -723,8 +745,8 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     CUB(cudaMemcpy(P->d_levels, P->levels.data(), sizeof(int) * P->G * d, cudaMemcpyHostToDevice));
     CUB(cudaMalloc(&P->d_hi, sizeof(double) * PIT_MAX_DIM));
     CUB(cudaMemcpy(P->d_hi, desc->hi, sizeof(double) * PIT_MAX_DIM, cudaMemcpyHostToDevice));
-    CUB(cudaMalloc(&P->d_stats, sizeof(DevStats)));
-    CUB(cudaMallocHost(&P->h_stats, sizeof(DevStats)));
+    CUB(cudaMalloc(&P->d_stats, 2 * sizeof(DevStats)));
+    CUB(cudaMallocHost(&P->h_stats, 2 * sizeof(DevStats)));
     CUB(cudaMallocHost(&P->h_rmax, sizeof(double) * P->G));
     CUB(cudaMallocHost(&P->h_act, sizeof(int) * P->G));
     {
@@ -1537,6 +1559,7 @@ extern "C" pit_status pit_profile_enable(pit_problem_t P, int on)
     P->prof_recs.clear();
     P->prof_items = P->prof_point_iters = P->prof_point_passes = P->prof_point_steps = 0;
     for (long long &k : P->prof_kernels) k = 0;
+    for (int f = 0; f < 2; ++f) P->prof_fam_iters[f] = P->prof_fam_passes[f] = P->prof_fam_steps[f] = 0;
     return PIT_OK;
 }
 
@@ -1552,6 +1575,11 @@ extern "C" pit_status pit_profile_read(pit_problem_t P, pit_profile *out)
         out->ms[r.first] += ms;
     }
     for (int f = 0; f < 4; ++f) out->kernels[f] = P->prof_kernels[f];
+    for (int f = 0; f < 2; ++f) {
+        out->point_iters_f[f] = P->prof_fam_iters[f];
+        out->point_passes_f[f] = P->prof_fam_passes[f];
+        out->point_steps_f[f] = P->prof_fam_steps[f];
+    }
     out->phi_items = P->prof_items;
     out->point_iters = P->prof_point_iters;
     out->point_passes = P->prof_point_passes;

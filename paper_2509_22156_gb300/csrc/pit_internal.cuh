@@ -35,7 +35,7 @@ struct DevStats {
     unsigned long long sum_iters;
     unsigned long long items;
     unsigned long long point_iters;   // sum of nodes x Krylov iterations
-    unsigned long long point_passes;  // sum of nodes x FP64 residual passes
+    unsigned long long point_passes;  // sum of nodes x refinement residual passes
     unsigned long long point_steps;   // sum of nodes x backward-Euler steps
     int max_iters;
     int n_failed;
@@ -96,16 +96,21 @@ struct StepArgs {
 
 // Precision forms of the multi-step kernel: PLAIN = FP64 Krylov, MIXED = FP32
 // Krylov in FP64 refinement, SINGLE = FP32 Krylov on a power-of-two-scaled
-// FP32 copy of the state (FP64 input and output).
-enum Prec { PLAIN = 0, MIXED = 1, SINGLE = 2 };
-constexpr int NPREC = 3;
+// FP32 copy of the state (FP64 input and output), PAIR = FP32 Krylov in a
+// refinement whose state and residual are FP32 pairs (heat operator; grids
+// whose state does not fit on chip run the MIXED kernel).
+enum Prec { PLAIN = 0, MIXED = 1, SINGLE = 2, PAIR = 3 };
+constexpr int NPREC = 4;
 // Launch parts of one multi-step call: NBKT shared-memory buckets of the
 // grids whose state fits on chip, then the grids with global-memory state.
 constexpr int NBKT = 4;
 constexpr int NPART = NBKT + 1;
 inline int prec_form(int pit_prec)
 {
-    return pit_prec == PIT_PREC_MIXED ? MIXED : pit_prec == PIT_PREC_FP32 ? SINGLE : PLAIN;
+    return pit_prec == PIT_PREC_MIXED        ? MIXED
+           : pit_prec == PIT_PREC_FP32       ? SINGLE
+           : pit_prec == PIT_PREC_MIXED_PAIR ? PAIR
+                                             : PLAIN;
 }
 
 // Learned coarse propagator: parameter block (BF16-rounded values held as

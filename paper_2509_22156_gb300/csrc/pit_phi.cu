@@ -12,13 +12,15 @@ size_t phi_smem_bytes(int prec, int op, int d, int n, int na)
            (size_t)line_pc_bytes(op, prec, false, na);
 }
 
+// (the pair form runs its global-state grids in the mixed form)
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n)
 {
+    if (prec == PAIR) prec = MIXED;
     const size_t ld = (size_t)((n + 3) & ~3);
     return (size_t)n_tab(op, d) * ld * 8 + (size_t)n_f32(op, prec, d, true) * ld * 4 + ld * 2 + 16;
 }
 
-int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 3; }
+int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 3; }  // PAIR: as MIXED
 
 static size_t g_max_smem = 0;
 
@@ -28,7 +30,8 @@ cudaError_t phi_kernels_init(size_t max_smem)
     cudaError_t e = cudaSuccess;
     cudaError_t (*inits[])(int) = {steps_init_heat_fp64,    steps_init_heat_mixed,    steps_init_heat_fp32,
                                    steps_init_varheat_fp64, steps_init_varheat_mixed, steps_init_varheat_fp32,
-                                   steps_init_ou_fp64,      steps_init_ou_mixed,      steps_init_ou_fp32};
+                                   steps_init_ou_fp64,      steps_init_ou_mixed,      steps_init_ou_fp32,
+                                   steps_init_heat_pair};
     for (auto f : inits)
         if (e == cudaSuccess) e = f(bytes);
     if (e == cudaSuccess) g_max_smem = max_smem;
@@ -42,6 +45,13 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
     if (blocks > 0x7fffffffLL || smem > g_max_smem || threads < 32 || threads > 512 || (threads & 31))
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)blocks), block(threads);
+    if (prec == PAIR) {
+        // heat only (the plan rejects other operators); global-state grids
+        // run the mixed form
+        if (a.op.op != PIT_OP_HEAT) return cudaErrorInvalidValue;
+        if (xg) return steps_launch_heat_mixed(a.op.d, a, grid, block, smem, s, true);
+        return steps_launch_heat_pair(a.op.d, a, grid, block, smem, s, false);
+    }
     switch (a.op.op) {
 #define PIT_BY_PREC(OPN)                                                                                          \
     switch (prec) {                                                                                               \

@@ -239,6 +239,88 @@ __device__ __forceinline__ int scale_exp(double bb)
     return -half;
 }
 
+// ----------------------------------------------------------------------------
+// FP32 pairs: a value held as hi + lo with |lo| <= ulp(hi) / 2 carries about 48
+// significant bits (Dekker 1971).  two_sum is Knuth's error-free addition
+// (s + e = a + b exactly, no ordering of |a| and |b| needed); the error of a
+// product comes from one FMA (p = fl(a b), e = a b - p exactly).  The
+// round-to-nearest intrinsics keep the compiler from contracting these
+// operations into FMAs, which would break the exactness.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+// v 2^k as a pair: hi = v 2^k truncated to 24 bits; lo = the next 24 bits of
+// the remainder v - hi 2^-k (exact in FP64: the low bits of v).  One FP64
+// subtraction; the scale is exact.
+__device__ __forceinline__ float2 split_pair(double v, int k)
+{
+    const float hi = to_f32(v, k);
+    return make_float2(hi, to_f32(v - to_f64(hi, -k), k));
+}
+// (hi + lo) 2^-k in FP64: both parts convert exactly, one FP64 addition rounds
+__device__ __forceinline__ double pair_to_f64(float2 p, int k) { return to_f64(p.x, -k) + to_f64(p.y, -k); }
+// pair + FP32 value, renormalised
+__device__ __forceinline__ float2 pair_add(float2 x, float v)
+{
+    float s, e, h, l;
+    two_sum(x.x, v, s, e);
+    two_sum(s, __fadd_rn(e, x.y), h, l);
+    return make_float2(h, l);
+}
+// pair + pair, renormalised (relative error about 2^-47 of the larger operand)
+__device__ __forceinline__ float2 pair_add(float2 x, float2 y)
+{
+    float s, e, h, l;
+    two_sum(x.x, y.x, s, e);
+    two_sum(s, __fadd_rn(e, __fadd_rn(x.y, y.y)), h, l);
+    return make_float2(h, l);
+}
+
+// b_j - (A x)_j of the constant-coefficient heat stencil on pairs (state and
+// right-hand side scaled by the same power of two), rounded once to FP32:
+//     A x = x + sum_i c_i (2 x_j - x_{j-e_i} - x_{j+e_i}),  c_i = dt / h_i^2,
+// with zero neighbours towards the boundary (the same operator as HeatSt).
+// The hi parts of b - x and of the neighbour differences are formed with
+// two_sum, c_i (a pair) times the difference with the FMA product error, and
+// the big terms are summed with two_sum; every rounding error, the lo parts
+// and the small cross products go to one FP32 compensation term.  What is
+// lost is second order (about 2^-48 of |x| + sum_i c_i |2 x_j - x_m - x_p|),
+// so the residual keeps FP64-like accuracy when b - A x cancels to 1e-11 of b.
+// Also yields x_j - b_j rounded to FP32.
+template <int D>
+struct PairHeat {
+    const uint16_t *mask;
+    int S[D];
+    float ch[D], cl[D];
+    __device__ __forceinline__ float operator()(const float2 *x, const float2 *bv, int j, float &xmb) const
+    {
+        const unsigned mk = mask[j];
+        const float2 xj = x[j], bj = bv[j];
+        float s, comp;
+        two_sum(bj.x, -xj.x, s, comp);
+        comp = __fadd_rn(comp, __fsub_rn(bj.y, xj.y));
+        xmb = -__fadd_rn(s, comp);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float2 xm = ((mk >> (2 * i)) & 1u) ? x[j - S[i]] : make_float2(0.0f, 0.0f);
+            const float2 xq = ((mk >> (2 * i + 1)) & 1u) ? x[j + S[i]] : make_float2(0.0f, 0.0f);
+            float a1, e1, a2, e2, t, e3, e4;
+            two_sum(xj.x, -xm.x, a1, e1);
+            two_sum(xj.x, -xq.x, a2, e2);
+            two_sum(a1, a2, t, e3);
+            const float tl = ((e1 + e2) + e3) + ((2.0f * xj.y - xm.y) - xq.y);
+            const float p = __fmul_rn(ch[i], t);
+            const float q = __fmaf_rn(ch[i], t, -p) + (ch[i] * tl + cl[i] * t);
+            two_sum(s, -p, s, e4);
+            comp = comp + (e4 - q);
+        }
+        return __fadd_rn(s, comp);
+    }
+};
+
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
@@ -701,7 +783,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     __shared__ float red32[2 * 128];
 
     static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
-    static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE, "unknown precision form");
+    static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE || PREC == PAIR, "unknown precision form");
+    static_assert(PREC != PAIR || (OP == PIT_OP_HEAT && !XG), "the pair form is for the heat operator on chip");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -738,10 +821,11 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     Reducer<double> R64{red64, 0};
     Reducer<float> R32{red32, 0};
-    // SINGLE: the state is held as x 2^ks in FP32, ks from the input state and
-    // the first forcing term (the correction sweep of MGRIT starts from zero)
+    // SINGLE: the state is held as x 2^ks in FP32 (PAIR: as FP32 pairs), ks
+    // from the input state and the first forcing term (the correction sweep of
+    // MGRIT starts from zero)
     int ks = 0;
-    if constexpr (PREC == SINGLE) {
+    if constexpr (PREC == SINGLE || PREC == PAIR) {
         const double *g0 = a.g ? a.g + (long long)b * a.g_stride + GI.off : nullptr;
         double acc[1] = {0.0};
         for (int j = tid; j < n; j += nt) {
@@ -755,6 +839,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     for (int j = tid; j < n; j += nt) {
         mask[j] = gmask[j];
         if constexpr (PREC == SINGLE) f32[j] = to_f32(in[j], ks);
+        else if constexpr (PREC == PAIR) reinterpret_cast<float2 *>(s64)[j] = split_pair(in[j], ks);
         else x[j] = in[j];
     }
     if constexpr (OP != PIT_OP_HEAT) {
@@ -797,6 +882,17 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         }
         H64.diag = diag;
         HT.diag = (T)diag;
+    }
+    PairHeat<D> PH;
+    if constexpr (PREC == PAIR) {
+        PH.mask = mask;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const double c = dt / (GI.h[i] * GI.h[i]);
+            PH.S[i] = GI.S[i];
+            PH.ch[i] = to_f32(c, 0);
+            PH.cl[i] = to_f32(c - to_f64(PH.ch[i], 0), 0);
+        }
     }
     // Line preconditioner (heat, FP32 Krylov, state on chip) along the finest
     // axis a, used when a is at least twice as fine as every other axis and
@@ -960,6 +1056,161 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 double acc[1] = {0.0};
                 for (int j = tid; j < n; j += nt) {
                     const double xj = to_f64(xs[j], -ks);
+                    if (cmp) {
+                        const double dlt = xj - cmp[j];
+                        acc[0] += dlt * dlt;
+                    }
+                    ol[j] = a.out_scale * xj + (h ? a.out_hscale * h[j] : 0.0) + (hs ? hs[j] : 0.0);
+                }
+                if (cmp) {
+                    R64.template sum<1>(acc);
+                    if (tid == 0) a.norms[(long long)b * a.n_grids + g] = sqrt(acc[0]);
+                }
+            }
+            continue;
+        } else if constexpr (PREC == PAIR) {
+            // Refinement on FP32 pairs of the state scaled by 2^ks: b - A x
+            // from PairHeat, the correction equation solved in FP32 as in
+            // MIXED, the correction added to the pairs.  The residual copies
+            // are in the state's scale (its norm is kept in [2^-10, 2^10]), so
+            // no per-step rescaling of them is needed.
+            float2 *xp = reinterpret_cast<float2 *>(s64), *bp = xp + ld;
+            float *e = f32;
+            if (a.guess) {
+                const long long sb0 = (long long)(step - 1);
+                const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
+                const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
+                for (int j = tid; j < n; j += nt) {
+                    bp[j] = f ? pair_add(xp[j], split_pair(dt * f[j], ks)) : xp[j];
+                    xp[j] = split_pair(gf ? gu[j] - gf[j] : gu[j], ks);
+                }
+            } else {
+                for (int j = tid; j < n; j += nt) bp[j] = f ? pair_add(xp[j], split_pair(dt * f[j], ks)) : xp[j];
+            }
+            double rn2, bb;
+            if (have_r0 && bb_c >= 0x1p-20 && bb_c <= 0x1p20) {
+                // r0 = x_{s-1} - A x_{s-1}, from the last check of the previous step (in wv)
+                float *t_ = rv; rv = wv; wv = t_;
+                rn2 = rn0_c;
+                bb = bb_c;
+            } else {
+                float acc[1] = {0.0f};
+                for (int j = tid; j < n; j += nt) acc[0] += bp[j].x * bp[j].x;
+                R32.template sum<1>(acc);  // also: bp and xp complete
+                bb = to_f64(acc[0], 0);
+                if (bb > 0.0 && !(bb >= 0x1p-20 && bb <= 0x1p20)) {
+                    // exact power-of-two rescale of the state (it can fade or
+                    // grow by many orders over a long sweep)
+                    const int kq = scale_exp(bb);
+                    const float sc = __uint_as_float((unsigned)(127 + kq) << 23);
+                    for (int j = tid; j < n; j += nt) {
+                        const float2 xj = xp[j], bj = bp[j];
+                        xp[j] = make_float2(xj.x * sc, xj.y * sc);
+                        bp[j] = make_float2(bj.x * sc, bj.y * sc);
+                    }
+                    bb = bb * pow2d(2 * kq);
+                    ks += kq;
+                    __syncthreads();
+                }
+                float accf[1] = {0.0f};
+#pragma unroll 4
+                for (int j = tid; j < n; j += nt) {
+                    float xmb;
+                    const float rf = PH(xp, bp, j, xmb);
+                    rv[j] = rf;
+                    accf[0] += rf * rf;
+                }
+                R32.template sum<1>(accf);
+                ++passes;
+                rn2 = to_f64(accf[0], 0);
+            }
+            have_r0 = false;
+            const double stop2 = a.rtol * a.rtol * bb;
+            int st_step = PIT_OK;
+            bool carried = false;
+            for (int pass = 0;; ++pass) {
+                if (!(rn2 > stop2)) {
+                    if (rn2 != rn2) st_step = PIT_ERR_NONFINITE;
+                    else if (carry_ok && pass == 0) {
+                        // x unchanged: its residual is the next step's r0
+                        float *t_ = rv; rv = wv; wv = t_;
+                        rn0_c = rn2;
+                        bb_c = bb;
+                        carried = true;
+                    }
+                    break;
+                }
+                if (pass >= a.ir_maxit) { st_step = PIT_ERR_NOCONV; break; }
+                // the correction equation on rv 2^-kn (squared norm in [1, 4))
+                const int kn = min(max(-scale_exp(rn2), -120), 120);
+                const float inv = __uint_as_float((unsigned)(127 - kn) << 23);  // 2^-kn
+                const float R2n = to_f32(rn2, -2 * kn);
+                const float want = 0.5f * sqrtf(to_f32(stop2, -2 * kn) / R2n);
+                const float tgt = want > a.inner_rtol ? want : (float)a.inner_rtol;
+                const float stop32 = tgt * tgt * R2n;
+                for (int j = tid; j < n; j += nt) {
+                    rv[j] *= inv;
+                    e[j] = 0.0f;
+                }
+                int st, k;
+                if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
+                else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                iters += k;
+                if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
+                // x += e 2^kn on the pairs (the scaling is exact)
+                const float csf = __uint_as_float((unsigned)(127 + kn) << 23);
+#pragma unroll 4
+                for (int j = tid; j < n; j += nt) xp[j] = pair_add(xp[j], e[j] * csf);
+                __syncthreads();  // x complete
+                // check: r = b - A x; the next step's r0 = x - A x = r + (x - b)
+                float accf[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+                for (int j = tid; j < n; j += nt) {
+                    float xmb;
+                    const float rf = PH(xp, bp, j, xmb);
+                    rv[j] = rf;
+                    accf[0] += rf * rf;
+                    if (carry_ok) {
+                        const float cj = rf + xmb;
+                        const float xf = xp[j].x;
+                        wv[j] = cj;
+                        accf[1] += cj * cj;
+                        accf[2] += xf * xf;
+                    }
+                }
+                R32.template sum<3>(accf);
+                ++passes;
+                rn2 = to_f64(accf[0], 0);
+                if (carry_ok) {
+                    rn0_c = to_f64(accf[1], 0);
+                    bb_c = to_f64(accf[2], 0);
+                    carried = true;
+                }
+            }
+            if (st_step > status) status = st_step;
+            have_r0 = carried && st_step == PIT_OK && step < a.nsteps;
+            // forcing of this step and the stored outputs (FP64, own nodes only)
+            const long long sb = (long long)(step - 1);
+            if (a.g) {
+                const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
+                for (int j = tid; j < n; j += nt) xp[j] = pair_add(xp[j], split_pair(gs[j], ks));
+            }
+            const double *hs = a.hs ? a.hs + (long long)b * a.hs_stride + sb * a.hs_step + GI.off : nullptr;
+            if (step < a.nsteps) {
+                if (a.out_steps) {
+                    double *os = a.out_steps + (long long)b * a.os_stride + sb * a.os_step + GI.off;
+                    for (int j = tid; j < n; j += nt) {
+                        const double xj = pair_to_f64(xp[j], ks);
+                        os[j] = hs ? xj + hs[j] : xj;
+                    }
+                }
+            } else {
+                double *ol = a.out_last + (long long)b * a.ol_stride + GI.off;
+                const double *h = a.h ? a.h + (long long)b * a.h_stride + GI.off : nullptr;
+                const double *cmp = a.cmp ? a.cmp + (long long)b * a.cmp_stride + GI.off : nullptr;
+                double acc[1] = {0.0};
+                for (int j = tid; j < n; j += nt) {
+                    const double xj = pair_to_f64(xp[j], ks);
                     if (cmp) {
                         const double dlt = xj - cmp[j];
                         acc[0] += dlt * dlt;
@@ -1161,6 +1412,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 PIT_STEPS_DECL(heat, fp64) PIT_STEPS_DECL(heat, mixed) PIT_STEPS_DECL(heat, fp32)
 PIT_STEPS_DECL(varheat, fp64) PIT_STEPS_DECL(varheat, mixed) PIT_STEPS_DECL(varheat, fp32)
 PIT_STEPS_DECL(ou, fp64) PIT_STEPS_DECL(ou, mixed) PIT_STEPS_DECL(ou, fp32)
+PIT_STEPS_DECL(heat, pair)
 
 // Instantiates the attribute setter and launcher of one operator and form for
 // D = 1..6 (XGV: whether the form has the global-state variant).

@@ -55,3 +55,25 @@ def test_profile_counts_calls_and_kernels():
     pr2 = P.profile_read()
     P.profile_enable(False)
     assert sum(pr2.launches) == 0 and sum(pr2.kernels) == 0
+
+
+def test_profile_splits_work_counters_by_family():
+    wl = W.workload(2)
+    P = B.Problem(wl.d, 5, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    P.sample_initial(wl.ic_kind, wl.ic_params, u0)
+    uT = torch.empty_like(u0)
+    fine = B.solve_opts(B.PIT_PREC_MIXED_PAIR, rtol=1e-11, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=4000)
+    opts = B.mgrit_opts(wl.t0, wl.t1, 256, 16, 2, tol=1e-9, maxit=20, fine=fine, crs=crs, relax=B.PIT_RELAX_F)
+    P.mgrit_solve(u0, opts, uT)
+    P.profile_enable(True)
+    P.mgrit_solve(u0, opts, uT)
+    pr = P.profile_read()
+    P.profile_enable(False)
+    assert pr.point_iters_f[0] + pr.point_iters_f[1] == pr.point_iters
+    assert pr.point_passes_f[0] + pr.point_passes_f[1] == pr.point_passes
+    assert pr.point_steps_f[0] + pr.point_steps_f[1] == pr.point_steps
+    # relaxation in the pair refinement: residual passes; FP32 coarse sweeps: none
+    assert pr.point_passes_f[0] > 0 and pr.point_passes_f[1] == 0
+    assert pr.point_iters_f[1] > 0
