@@ -101,6 +101,14 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        # start timing only once the sampler reports (its start-up holds the
+        # driver for a moment)
+        t0 = time.time()
+        while self.p is not None and time.time() - t0 < 5.0:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self) -> dict:
         if self.p is None:
@@ -150,7 +158,7 @@ def phi_source_hash() -> str:
 def ncu_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "steps_kernel_heat_mixed_heat3d_n9.txt")
+    path = os.path.join(ROOT, "profiles", "steps_kernel_heat_pair_heat3d_n9.txt")
     try:
         kv = {}
         for line in open(path):

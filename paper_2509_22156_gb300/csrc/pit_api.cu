@@ -98,6 +98,7 @@ struct pit_problem {
     cudaStream_t stream = nullptr;
     int device = 0;
     size_t max_smem = 0;
+    int n_sm = 0;  // streaming multiprocessors of the device
     int G = 0;
     long long ntot = 0;
     std::vector<int> levels;      // G*d
@@ -136,6 +137,7 @@ struct pit_problem {
     std::vector<pit_lane> lanes;     // MGRIT lanes (built on first use)
     // workspaces
     DBuf w_in, w_out, w_pts, w_u, w_prm;
+    DBuf w_part;  // partial sums of the chunked combination sum
     DBuf m_U, m_R, m_UT, m_GC, m_res, m_UT1, m_GC1, m_T0, m_act, w_tune, m_Z, m_E;
     std::vector<double> h_res;
     double *h_rmax = nullptr;  // pinned, G
@@ -676,6 +678,7 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     // static shared memory of the kernels (grid record, reduction buffers) is reserved
     P->max_smem = smem_optin > 4096 ? (size_t)smem_optin - 4096 : 0;
+    cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, P->device);
 
     std::vector<int> layer;
     enumerate_levels(d, desc->level_n, desc->level0, P->levels, layer);
@@ -814,7 +817,7 @@ pit_status pit_problem_destroy(pit_problem_t P)
                     &P->m_UT,     &P->m_GC,   &P->m_res, &P->m_UT1,   &P->m_GC1,  &P->m_T0,    &P->m_act,
                     &P->w_tune,   &P->n_master, &P->n_m, &P->n_v,     &P->n_w,    &P->n_rows,  &P->n_loss,
                     &P->n_act,    &P->n_items, &P->n_U,  &P->n_Y,     &P->n_grad, &P->n_tmp,   &P->n_prm,
-                    &P->w_xg,     &P->m_Z,     &P->m_E};
+                    &P->w_xg,     &P->m_Z,     &P->m_E,   &P->w_part};
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     delete P;
@@ -1538,10 +1541,13 @@ extern "C" pit_status pit_combine(pit_problem_t P, const double *u, int n_pts, c
         CU(P->w_out.ensure(sizeof(double) * n_pts));
         target = P->w_out.d();
     }
+    const int chunks = combine_chunks(P->G, n_pts, P->n_sm);
+    if (chunks > 1) CU(P->w_part.ensure(sizeof(double) * (size_t)chunks * n_pts));
     {
         ProfScope ps(P, 2);
-        CU(launch_combine(P->d_grids, P->d_coef, P->d_levels, P->G, P->op, du, n_pts, dp, target, P->stream));
-        count_kernels(P, 2);
+        CU(launch_combine(P->d_grids, P->d_coef, P->d_levels, P->G, P->op, du, n_pts, dp, target, chunks,
+                          chunks > 1 ? P->w_part.d() : nullptr, P->stream));
+        count_kernels(P, 2, chunks > 1 ? 2 : 1);
     }
     if (!dev_out) {
         CU(cudaMemcpyAsync(out, target, sizeof(double) * n_pts, cudaMemcpyDeviceToHost, P->stream));

@@ -162,8 +162,13 @@ cudaError_t launch_apply(const GridInfo *grids, int G, long long ntot, int n_bat
 cudaError_t launch_initial(const GridInfo *grids, int G, OpParams op, const double *hi, int kind,
                            const double *params_dev, int n_params, double *u, cudaStream_t s);
 cudaError_t launch_faces(const GridInfo *grids, int G, OpParams op, double *faces, cudaStream_t s);
+// Number of grid chunks the combination sum splits into (one kernel per
+// chunk set, partial sums in part[chunk * n_pts + k], n_chunks x n_pts doubles,
+// then added in chunk order); 1 means a single kernel writing out directly.
+int combine_chunks(int G, int n_pts, int n_sm);
 cudaError_t launch_combine(const GridInfo *grids, const double *coef, const int *levels, int G, OpParams op,
-                           const double *u, int n_pts, const double *pts, double *out, cudaStream_t s);
+                           const double *u, int n_pts, const double *pts, double *out, int n_chunks, double *part,
+                           cudaStream_t s);
 // resid[j*G + g] = || a_j - b_j ||_2 on grid g, for active grids; j < nb.
 cudaError_t launch_resid_norms(const GridInfo *grids, int G, long long ntot, int nb, const double *a,
                                long long a_stride, const double *b, long long b_stride, const int *active,

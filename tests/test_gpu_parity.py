@@ -461,6 +461,20 @@ def test_combine_matches_oracle(name):
     P.combine(u, pts[:0].copy(), outh[:0].copy())
 
 
+@pytest.mark.parametrize("n_uniform", [1, 200, 20000, 90000])
+def test_combine_grid_chunks_match_oracle(n_uniform):
+    # the sum splits the grids into chunks when the points alone fill few
+    # SMs (one chunk for 90,000 points, several below); every split gives the
+    # oracle's values
+    P, O, _ = pair("heat6d")
+    lo, hi = CASES["heat6d"][4], CASES["heat6d"][5]
+    u = W.random_vector(808, P.n_total)
+    pts = W.eval_points(6, lo, hi, n_uniform=n_uniform, n_diag=5, seed=11)
+    out = torch.empty(pts.shape[0], dtype=torch.float64, device="cuda")
+    P.combine(cuda(u), cuda(pts), out)
+    assert rel(host(out), O.combine(u, pts)) < 1e-13
+
+
 def test_large_grids_keep_their_state_in_global_memory():
     """d = 2, level 12: grids (6, 7) and (7, 6) hold 8001 nodes, more than the
     shared-memory solver state allows; the mixed form keeps their FP64 state,

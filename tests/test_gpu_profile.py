@@ -45,8 +45,9 @@ def test_profile_counts_calls_and_kernels():
         assert pr.launches[f] > 0
         assert pr.kernels[f] >= pr.launches[f]
         assert pr.ms[f] > 0.0
-    # the combination sum is one call of one kernel
-    assert pr.launches[2] == 1 and pr.kernels[2] == 1
+    # the combination sum is one call: one kernel, or two when it splits the
+    # grids into chunks whose partial sums a second kernel adds
+    assert pr.launches[2] == 1 and pr.kernels[2] in (1, 2)
     assert pr.phi_items > 0 and pr.point_steps > 0
 
     # disabled profiling records nothing; enabling again starts from zero
