@@ -221,6 +221,9 @@ typedef struct {
     int traj_len;          /* pairs taken along each fine trajectory           */
     pit_solve_opts fine;   /* solver of the fine steps that make the targets   */
     pit_solve_opts crs;    /* solver of the implicit Phi_c used as the judge   */
+    double accept_ratio;   /* the network is accepted when its held-out error is
+                              at most accept_ratio x that of the implicit step
+                              (0 < accept_ratio <= 1; 1: not larger)          */
 } pit_train_opts;
 
 typedef struct {
@@ -228,7 +231,8 @@ typedef struct {
     double loss_last_epoch;      /* same, last epoch                         */
     double holdout_err_learned;  /* mean ||Phi_hat u - Phi^m u|| / ||Phi^m u|| on held-out pairs */
     double holdout_err_implicit; /* same for the implicit coarse step        */
-    int accepted;                /* 1 when the learned error is not larger  */
+    int accepted;                /* 1 when the learned error is at most
+                                    accept_ratio x the implicit one        */
     int adam_steps;
     double ms_data;              /* generating the pairs                    */
     double ms_train;             /* forward/backward/Adam                   */

@@ -82,7 +82,7 @@ class pit_train_opts(ctypes.Structure):
     _fields_ = [("dt_fine", ctypes.c_double), ("m", ctypes.c_int), ("n_pairs", ctypes.c_int),
                 ("n_holdout", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("ic_modes", ctypes.c_int), ("ic_fmax", ctypes.c_int),
-                ("traj_len", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts)]
+                ("traj_len", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts), ("accept_ratio", ctypes.c_double)]
 
 
 class pit_train_stats(ctypes.Structure):
@@ -161,11 +161,11 @@ def solve_opts(prec=PIT_PREC_FP64, rtol=1e-10, maxit=10000, inner_rtol=1e-4, ir_
 
 
 def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=1e-3, seed=0, ic_modes=8,
-               ic_fmax=4, traj_len=8, fine=None, crs=None) -> pit_train_opts:
+               ic_fmax=4, traj_len=8, fine=None, crs=None, accept_ratio=1.0) -> pit_train_opts:
     fine = fine or solve_opts(PIT_PREC_MIXED, rtol=1e-10)
     crs = crs or fine
     return pit_train_opts(dt_fine, m, n_pairs, n_holdout, epochs, batch, lr, seed, ic_modes, ic_fmax, traj_len,
-                          fine, crs)
+                          fine, crs, accept_ratio)
 
 
 def bf16_round(w) -> np.ndarray:

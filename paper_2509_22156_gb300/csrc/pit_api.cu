@@ -1811,7 +1811,8 @@ extern "C" pit_status pit_train_coarse(pit_problem_t P, const pit_train_opts *o,
     TRY(check_solve_opts(&o->fine));
     TRY(check_solve_opts(&o->crs));
     if (!(o->dt_fine > 0.0) || o->m < 1 || o->n_pairs < 1 || o->n_holdout < 1 || o->epochs < 1 || o->batch < 1 ||
-        !(o->lr > 0.0) || o->ic_modes < 1 || o->ic_fmax < 1 || o->traj_len < 1)
+        !(o->lr > 0.0) || o->ic_modes < 1 || o->ic_fmax < 1 || o->traj_len < 1 ||
+        !(o->accept_ratio > 0.0 && o->accept_ratio <= 1.0))
         return fail(PIT_ERR_INVALID_ARG, "invalid training options");
     auto t0 = std::chrono::steady_clock::now();
     const int G = P->G, d = P->desc.d;
@@ -1987,7 +1988,7 @@ extern "C" pit_status pit_train_coarse(pit_problem_t P, const pit_train_opts *o,
     }
     st.holdout_err_learned = el / hold.size();
     st.holdout_err_implicit = ei / hold.size();
-    st.accepted = (st.holdout_err_learned <= st.holdout_err_implicit) ? 1 : 0;
+    st.accepted = (st.holdout_err_learned <= o->accept_ratio * st.holdout_err_implicit) ? 1 : 0;
     P->net_accepted = st.accepted != 0;
     st.ms_data = std::chrono::duration<double, std::milli>(t1 - t0).count();
     st.ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count();

@@ -161,3 +161,24 @@ def test_training_reduces_loss_and_is_judged():
     seq = O.sequential(u0, dt, N, rtol=1e-15)
     assert rel(host(uT), seq) < 1e-8
     assert stm.learned_used == st.accepted
+
+
+def test_acceptance_ratio_of_the_holdout_judge():
+    wl = W.workload(1)
+    P = B.Problem(wl.d, 4, wl.L0, wl.op, wl.lo, wl.hi)
+    dt = (wl.t1 - wl.t0) / 64
+    mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-11, inner_rtol=1e-5, ir_maxit=20)
+    base = dict(n_pairs=128, n_holdout=32, epochs=1, batch=32, lr=1e-3, seed=5, traj_len=4, fine=mixed, crs=mixed)
+    for bad in (0.0, -1.0, 1.5):
+        with pytest.raises(B.PitError) as e:
+            P.train_coarse(B.train_opts(dt, 4, accept_ratio=bad, **base))
+        assert e.value.status == B.PIT_ERR_INVALID_ARG
+    # a ratio no network can meet: rejected, and MGRIT runs the implicit step
+    st = P.train_coarse(B.train_opts(dt, 4, accept_ratio=1e-9, **base))
+    assert st.accepted == 0
+    u0 = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    P.sample_initial(wl.ic_kind, wl.ic_params, u0)
+    uT = torch.empty_like(u0)
+    opts = B.mgrit_opts(wl.t0, wl.t1, 64, 4, 2, tol=1e-9, maxit=40, coarse=B.PIT_COARSE_LEARNED, fine=mixed, crs=mixed)
+    stm = P.mgrit_solve(u0, opts, uT)
+    assert stm.learned_used == 0
