@@ -115,15 +115,20 @@ typedef struct {
  *                          48 significant bits, scaled by a power of two) and
  *                          the residual b - A x formed from the pairs by
  *                          error-free FP32 transformations (two-sum, two-product
- *                          by FMA) with one compensation term: the accuracy of
- *                          the FP64 residual to about 1e-14 relative, without
- *                          FP64 arithmetic (which GB300 runs at 1/58 of the FP32
- *                          rate).  Same options and stopping rule as
+ *                          by FMA) with one compensation term, without FP64
+ *                          arithmetic (which GB300 runs at 1/58 of the FP32
+ *                          rate).  The residual's floor is about 2^-48 (|x| +
+ *                          sum_i (dt / h_i^2) |2 x_j - x_{j-e_i} - x_{j+e_i}|):
+ *                          about 1e-14 of ||b|| for smooth states, but for rough
+ *                          states on grids with dt / h^2 in the hundreds near
+ *                          1e-12, where FP64 reaches about 1e-13; choose rtol
+ *                          above it.  Same options and stopping rule as
  *                          PIT_PREC_MIXED.  Heat operator only (other operators:
  *                          PIT_ERR_UNSUPPORTED); grids whose state does not fit
- *                          in shared memory are solved in the PIT_PREC_MIXED
- *                          form.  Inputs and outputs stay FP64; values below
- *                          2^-102 of the state's norm lose their low part. */
+ *                          in shared memory keep their pairs in global memory,
+ *                          as PIT_PREC_MIXED keeps its FP64 state.  Inputs and
+ *                          outputs stay FP64; values below 2^-102 of the
+ *                          state's norm lose their low part. */
 typedef struct {
     int prec;
     double rtol;

@@ -12,15 +12,13 @@ size_t phi_smem_bytes(int prec, int op, int d, int n, int na)
            (size_t)line_pc_bytes(op, prec, false, na);
 }
 
-// (the pair form runs its global-state grids in the mixed form)
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n)
 {
-    if (prec == PAIR) prec = MIXED;
     const size_t ld = (size_t)((n + 3) & ~3);
     return (size_t)n_tab(op, d) * ld * 8 + (size_t)n_f32(op, prec, d, true) * ld * 4 + ld * 2 + 16;
 }
 
-int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 3; }  // PAIR: as MIXED
+int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 3; }  // PAIR uses two
 
 static size_t g_max_smem = 0;
 
@@ -46,11 +44,9 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)blocks), block(threads);
     if (prec == PAIR) {
-        // heat only (the plan rejects other operators); global-state grids
-        // run the mixed form
+        // heat only (the plan rejects other operators)
         if (a.op.op != PIT_OP_HEAT) return cudaErrorInvalidValue;
-        if (xg) return steps_launch_heat_mixed(a.op.d, a, grid, block, smem, s, true);
-        return steps_launch_heat_pair(a.op.d, a, grid, block, smem, s, false);
+        return steps_launch_heat_pair(a.op.d, a, grid, block, smem, s, xg);
     }
     switch (a.op.op) {
 #define PIT_BY_PREC(OPN)                                                                                          \

@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
     static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE || PREC == PAIR, "unknown precision form");
-    static_assert(PREC != PAIR || (OP == PIT_OP_HEAT && !XG), "the pair form is for the heat operator on chip");
+    static_assert(PREC != PAIR || OP == PIT_OP_HEAT, "the pair form is for the heat operator");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -806,6 +806,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     double *s64 = reinterpret_cast<double *>(smem);
     double *x = XG ? a.xg + (long long)b * a.n_total + GI.off : s64;
     double *bvec = XG ? a.bg + (long long)b * a.n_total + GI.off : s64 + ld;  // MIXED: right-hand side
+    // PAIR: the state and the right-hand side as FP32 pairs, in the places of x and bvec
+    float2 *xp = reinterpret_cast<float2 *>(x), *bp = reinterpret_cast<float2 *>(bvec);
     // PLAIN: Krylov vectors, in shared memory (stride ld) or, for the
     // global-state variant, in per-vector slabs of n_batch x n_total after x
     double *v64 = XG ? a.xg + ((long long)a.n_batch + b) * a.n_total + GI.off : s64 + ld;
@@ -839,7 +841,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     for (int j = tid; j < n; j += nt) {
         mask[j] = gmask[j];
         if constexpr (PREC == SINGLE) f32[j] = to_f32(in[j], ks);
-        else if constexpr (PREC == PAIR) reinterpret_cast<float2 *>(s64)[j] = split_pair(in[j], ks);
+        else if constexpr (PREC == PAIR) xp[j] = split_pair(in[j], ks);
         else x[j] = in[j];
     }
     if constexpr (OP != PIT_OP_HEAT) {
@@ -1074,7 +1076,6 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             // MIXED, the correction added to the pairs.  The residual copies
             // are in the state's scale (its norm is kept in [2^-10, 2^10]), so
             // no per-step rescaling of them is needed.
-            float2 *xp = reinterpret_cast<float2 *>(s64), *bp = xp + ld;
             float *e = f32;
             if (a.guess) {
                 const long long sb0 = (long long)(step - 1);

@@ -4,5 +4,5 @@
 #include "pit_phi.cuh"
 
 namespace pit {
-PIT_STEPS_OP_PREC(heat, pair, PIT_OP_HEAT, PAIR, false)
+PIT_STEPS_OP_PREC(heat, pair, PIT_OP_HEAT, PAIR, true)
 }  // namespace pit

@@ -203,11 +203,12 @@ def test_pair_mgrit_lanes_and_coarse_fp32_solves():
     assert rel(res[0], seq) < 1e-8
 
 
-def test_pair_large_grids_run_in_the_mixed_form():
-    # grids with 8001 nodes exceed the on-chip state: they run the
-    # global-state kernel of the FP64-refinement form beside the pair kernels
+def test_pair_large_grids_keep_their_pairs_in_global_memory():
+    # grids with 8001 nodes exceed the on-chip state: their pairs live in
+    # global memory (the Krylov vectors stay on chip), beside the on-chip items
     P = B.Problem(2, 12, 1, B.PIT_OP_HEAT)
     O = oracle.Problem(2, 12, 1, W.OP_HEAT)
+    assert int(np.diff(P.offsets).max()) == 127 * 63
     dt = 1e-4
     nb = 2
     u = W.random_vector(525, nb * P.n_total)
@@ -215,6 +216,25 @@ def test_pair_large_grids_run_in_the_mixed_form():
     st = P.phi_batch(dt, cuda(u), out, opts())
     assert st.n_items == nb * P.G and st.n_failed == 0
     per_grid(P, host(out), O.phi(dt, u, rtol=1e-15), nb, 1e-9)
+    # several steps in one launch, with a state scaled far outside FP32 (a
+    # smaller step: with dt / h^2 = 419 on the finest axis a random state
+    # puts the pair residual's floor, about 2^-48 x 4 dt / h^2, near 1e-12)
+    u0 = W.random_vector(526, P.n_total)
+    uT = np.empty(P.n_total)
+    P.sequential_solve(u0 * 1e-60, 1e-6, 6, uT, opts())
+    assert rel(uT * 1e60, O.sequential(u0, 1e-6, 6, rtol=1e-15)) < 1e-9
+    # MGRIT over both classes, F relaxation with FP32 coarse solves; Krylov
+    # 1e-10 as for the FP64-refinement form on these stiff grids
+    u0 = O.initial(W.IC_SINES, W.sine_modes(2, [(1.0, [1, 1]), (0.3, [2, 3])]))
+    N, m = 32, 4
+    tol = 1e-9 * np.abs(u0).max()
+    fine = B.solve_opts(PAIR, rtol=1e-10, maxit=20000, inner_rtol=1e-5, ir_maxit=30)
+    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=20000)
+    o = B.mgrit_opts(0.0, N * dt, N, m, 2, tol=tol, maxit=60, fine=fine, crs=crs, relax=B.PIT_RELAX_F)
+    uTd = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    stm = P.mgrit_solve(cuda(u0), o, uTd)
+    assert stm.n_converged == P.G
+    assert rel(host(uTd), O.sequential(u0, dt, N, rtol=1e-15)) < 1e-8
 
 
 def test_pair_rejects_other_operators_and_reports_errors():
