@@ -198,9 +198,10 @@ COARSE_RTOL_3LEVEL = 1e-6  # coarse solves of a three-level hierarchy
 
 
 def fine_prec_of(wl, B):
-    """Precision form of the fine solves: the pair refinement for the heat
-    operator (the form it is implemented for), FP64 refinement otherwise."""
-    return B.PIT_PREC_MIXED_PAIR if wl.op == B.PIT_OP_HEAT else B.PIT_PREC_MIXED
+    """Precision form of the fine solves: the pair refinement for the
+    symmetric operators (the ones it is implemented for), FP64 refinement for
+    the drift operator."""
+    return B.PIT_PREC_MIXED if wl.op == B.PIT_OP_OU else B.PIT_PREC_MIXED_PAIR
 
 
 def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None, init=True, fine_prec=None):
@@ -365,13 +366,14 @@ def run_pit(args, rank, world, local):
     # roofline of the dominant kernel: the relaxation launches (family 0: many
     # entries per grid), from the kernel's own work counters of one profiled
     # step with every grid in one lane, over those launches' event time.
-    #   pair form (heat): bound by FP32 arithmetic issue, no FP64 work.  FP32
-    #     operations per node, counted from the kernel source: refinement pass
-    #     = correction added to the pairs (14) + residual check (39 d + 17) =
-    #     39 d + 31; CG iteration = stencil (3 d + 1) + two dot products (4) +
-    #     four vector updates (8) = 3 d + 13 (the line-preconditioned
-    #     iterations do more, so the count is a lower bound); peak = 152 SMs x
-    #     128 FP32 lanes x 2 (FMA) x SM clock.
+    #   pair form (heat, variable coefficient): bound by FP32 arithmetic
+    #     issue, no FP64 work.  FP32 operations per node, counted from the
+    #     kernel source: refinement pass = correction added to the pairs (14)
+    #     + residual check (heat 39 d + 17, variable coefficient 46 d + 17);
+    #     CG iteration = stencil (heat 3 d + 1, variable coefficient 4 d + 1)
+    #     + two dot products (4) + four vector updates (8) (the
+    #     line-preconditioned iterations do more, so the count is a lower
+    #     bound); peak = 152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock.
     #   FP64-refinement form: bound by the FP64 pipe; FP64 flops per node and
     #     residual pass = stencil diag x + sum_i off_i (x_-i + x_+i) (3d + 1),
     #     b - A x (1) and the correction update (2) = 3d + 4, against GB300's
@@ -385,11 +387,15 @@ def run_pit(args, rank, world, local):
     relax_ms = prof.ms[0]
     sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
     pair = chosen.fine.prec == B.PIT_PREC_MIXED_PAIR
+    opname = {B.PIT_OP_HEAT: "HEAT", B.PIT_OP_VARHEAT: "VARHEAT", B.PIT_OP_OU: "OU"}[wl.op]
     if pair:
-        flops_pass, flops_iter = 39 * d + 31, 3 * d + 13
+        if wl.op == B.PIT_OP_HEAT:
+            flops_pass, flops_iter = 39 * d + 31, 3 * d + 13
+        else:
+            flops_pass, flops_iter = 46 * d + 31, 4 * d + 13
         flops = prof.point_passes_f[0] * flops_pass + prof.point_iters_f[0] * flops_iter
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        kernel = f"steps_kernel<HEAT,PAIR,{d}> (grid-resident multi-step BE, FP32 CG in a refinement on FP32 pairs)"
+        kernel = f"steps_kernel<{opname},PAIR,{d}> (grid-resident multi-step BE, FP32 CG in a refinement on FP32 pairs)"
         peak_source = (f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops (FMA) x {sm_mhz:.0f} MHz "
                        "(GB300 unit counts and maximum SM clock)")
         extra = {"fp32_flops_per_node_pass": flops_pass, "fp32_flops_per_node_krylov_iter": flops_iter,
@@ -398,7 +404,6 @@ def run_pit(args, rank, world, local):
     else:
         flops = prof.point_passes_f[0] * (3 * d + 4)
         peak = FP64_PEAK_TFLOPS
-        opname = {B.PIT_OP_HEAT: "HEAT", B.PIT_OP_VARHEAT: "VARHEAT", B.PIT_OP_OU: "OU"}[wl.op]
         kernel = f"steps_kernel<{opname},MIXED,{d}> (grid-resident multi-step BE, FP32 Krylov in FP64 refinement)"
         peak_source = ("GB300 nominal FP64 rate (1.25 TFLOP/s, profiling recipe table); an FMA micro-benchmark on "
                        "this pool measured 1.20; the kernel's FP64 op mix (2d + 3 instructions for 3d + 4 flops) "

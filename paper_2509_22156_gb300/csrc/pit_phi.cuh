@@ -321,6 +321,45 @@ struct PairHeat {
     }
 };
 
+// The same for the variable-coefficient operator, from the face
+// coefficients c = dt a / h_i^2 of every node held as pairs (zero neighbours
+// towards the boundary, whose face coefficient still counts):
+//     A x = x + sum_i c_{j-e_i/2} (x_j - x_{j-e_i}) + c_{j+e_i/2} (x_j - x_{j+e_i}).
+// Table layout: c[(2 i) ld + j] towards -e_i, c[(2 i + 1) ld + j] towards +e_i.
+template <int D>
+struct PairTab {
+    const uint16_t *mask;
+    const float2 *c;
+    int ld;
+    int S[D];
+    __device__ __forceinline__ float operator()(const float2 *x, const float2 *bv, int j, float &xmb) const
+    {
+        const unsigned mk = mask[j];
+        const float2 xj = x[j], bj = bv[j];
+        float s, comp;
+        two_sum(bj.x, -xj.x, s, comp);
+        comp = __fadd_rn(comp, __fsub_rn(bj.y, xj.y));
+        xmb = -__fadd_rn(s, comp);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const bool inner = (mk >> (2 * i + side)) & 1u;
+                const float2 xn = inner ? x[side ? j + S[i] : j - S[i]] : make_float2(0.0f, 0.0f);
+                const float2 cf = c[(2 * i + side) * ld + j];
+                float dh, e1, e2;
+                two_sum(xj.x, -xn.x, dh, e1);
+                const float dl = e1 + (xj.y - xn.y);
+                const float p = __fmul_rn(cf.x, dh);
+                const float q = __fmaf_rn(cf.x, dh, -p) + (cf.x * dl + cf.y * dh);
+                two_sum(s, -p, s, e2);
+                comp = comp + (e2 - q);
+            }
+        }
+        return __fadd_rn(s, comp);
+    }
+};
+
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
@@ -784,7 +823,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
     static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE || PREC == PAIR, "unknown precision form");
-    static_assert(PREC != PAIR || OP == PIT_OP_HEAT, "the pair form is for the heat operator");
+    static_assert(PREC != PAIR || OP != PIT_OP_OU, "the pair form is for the symmetric operators");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -848,13 +887,22 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         for (int j = tid; j < n; j += nt) {
             double diag, cm[D], cp[D];
             op_coef<D>(a.op, GI, a.faces, j, dt, diag, cm, cp);
-            if constexpr (PREC != SINGLE) tab64[j] = diag;
+            if constexpr (PREC != SINGLE && PREC != PAIR) tab64[j] = diag;
             if constexpr (PREC != PLAIN) tab32[j] = (float)diag;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                if constexpr (PREC != SINGLE) {
+                if constexpr (PREC != SINGLE && PREC != PAIR) {
                     tab64[(1 + 2 * i) * ld + j] = cm[i];
                     tab64[(2 + 2 * i) * ld + j] = cp[i];
+                }
+                if constexpr (PREC == PAIR) {
+                    // face coefficients dt a / h^2 as pairs, in the FP64 table's place
+                    float2 *cpair = reinterpret_cast<float2 *>(tab64);
+                    const double ih2 = 1.0 / (GI.h[i] * GI.h[i]);
+                    const double am = a.faces[(GI.off + j) * (2 * D) + 2 * i];
+                    const double ap = a.faces[(GI.off + j) * (2 * D) + 2 * i + 1];
+                    cpair[(2 * i) * ld + j] = split_pair(dt * am * ih2, 0);
+                    cpair[(2 * i + 1) * ld + j] = split_pair(dt * ap * ih2, 0);
                 }
                 if constexpr (PREC != PLAIN) {
                     tab32[(1 + 2 * i) * ld + j] = (float)cm[i];
@@ -885,8 +933,16 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         H64.diag = diag;
         HT.diag = (T)diag;
     }
+    PairTab<D> PT;
+    if constexpr (PREC == PAIR && OP != PIT_OP_HEAT) {
+        PT.mask = mask;
+        PT.c = reinterpret_cast<const float2 *>(tab64);
+        PT.ld = ld;
+#pragma unroll
+        for (int i = 0; i < D; ++i) PT.S[i] = GI.S[i];
+    }
     PairHeat<D> PH;
-    if constexpr (PREC == PAIR) {
+    if constexpr (PREC == PAIR && OP == PIT_OP_HEAT) {
         PH.mask = mask;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -1072,11 +1128,15 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             continue;
         } else if constexpr (PREC == PAIR) {
             // Refinement on FP32 pairs of the state scaled by 2^ks: b - A x
-            // from PairHeat, the correction equation solved in FP32 as in
+            // from PairHeat (PairTab), the correction equation solved in FP32 as in
             // MIXED, the correction added to the pairs.  The residual copies
             // are in the state's scale (its norm is kept in [2^-10, 2^10]), so
             // no per-step rescaling of them is needed.
             float *e = f32;
+            auto PR = [&](int j, float &xmb) -> float {
+                if constexpr (OP == PIT_OP_HEAT) return PH(xp, bp, j, xmb);
+                else return PT(xp, bp, j, xmb);
+            };
             if (a.guess) {
                 const long long sb0 = (long long)(step - 1);
                 const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
@@ -1117,7 +1177,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
                     float xmb;
-                    const float rf = PH(xp, bp, j, xmb);
+                    const float rf = PR(j, xmb);
                     rv[j] = rf;
                     accf[0] += rf * rf;
                 }
@@ -1154,8 +1214,12 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     e[j] = 0.0f;
                 }
                 int st, k;
-                if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
-                else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                if constexpr (OP == PIT_OP_HEAT) {
+                    if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
+                    else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                } else {
+                    k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
+                }
                 iters += k;
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
                 // x += e 2^kn on the pairs (the scaling is exact)
@@ -1168,7 +1232,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
                     float xmb;
-                    const float rf = PH(xp, bp, j, xmb);
+                    const float rf = PR(j, xmb);
                     rv[j] = rf;
                     accf[0] += rf * rf;
                     if (carry_ok) {
@@ -1413,7 +1477,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 PIT_STEPS_DECL(heat, fp64) PIT_STEPS_DECL(heat, mixed) PIT_STEPS_DECL(heat, fp32)
 PIT_STEPS_DECL(varheat, fp64) PIT_STEPS_DECL(varheat, mixed) PIT_STEPS_DECL(varheat, fp32)
 PIT_STEPS_DECL(ou, fp64) PIT_STEPS_DECL(ou, mixed) PIT_STEPS_DECL(ou, fp32)
-PIT_STEPS_DECL(heat, pair)
+PIT_STEPS_DECL(heat, pair) PIT_STEPS_DECL(varheat, pair)
 
 // Instantiates the attribute setter and launcher of one operator and form for
 // D = 1..6 (XGV: whether the form has the global-state variant).

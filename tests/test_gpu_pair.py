@@ -46,12 +46,15 @@ def opts(rtol=1e-12, ir_maxit=30):
 
 
 HEAT = {
-    # name: (d, n, L0, lo, hi, dt)
-    "heat1d": (1, 9, 1, [0.0], [1.0], 0.01),
-    "heat2d": (2, 5, 1, [0.0] * 2, [1.0] * 2, 0.1 / 64),
-    "heat3d": (3, 6, 1, [0.0] * 3, [1.0] * 3, 0.05 / 1024),
-    "heat3d_l0": (3, 7, 2, [0.0] * 3, [1.0] * 3, 0.05 / 256),
-    "heat6d": (6, 4, 1, [0.0] * 6, [1.0] * 6, 0.02 / 512),
+    # name: (d, n, L0, lo, hi, dt, operator)
+    "heat1d": (1, 9, 1, [0.0], [1.0], 0.01, W.OP_HEAT),
+    "heat2d": (2, 5, 1, [0.0] * 2, [1.0] * 2, 0.1 / 64, W.OP_HEAT),
+    "heat3d": (3, 6, 1, [0.0] * 3, [1.0] * 3, 0.05 / 1024, W.OP_HEAT),
+    "heat3d_l0": (3, 7, 2, [0.0] * 3, [1.0] * 3, 0.05 / 256, W.OP_HEAT),
+    "heat6d": (6, 4, 1, [0.0] * 6, [1.0] * 6, 0.02 / 512, W.OP_HEAT),
+    "varheat2d": (2, 6, 1, [0.0] * 2, [1.0] * 2, 0.1 / 256, W.OP_VARHEAT),
+    "varheat3d": (3, 5, 1, [0.0] * 3, [1.0] * 3, 0.1 / 2048, W.OP_VARHEAT),
+    "varheat4d": (4, 4, 1, [0.0] * 4, [1.0] * 4, 0.05 / 256, W.OP_VARHEAT),
 }
 
 
@@ -64,9 +67,9 @@ def per_grid(P, got, ref, nb, tol):
 
 @pytest.mark.parametrize("name", list(HEAT))
 def test_pair_phi_batch_matches_oracle(name):
-    d, n, L0, lo, hi, dt = HEAT[name]
-    P = B.Problem(d, n, L0, B.PIT_OP_HEAT, lo, hi)
-    O = oracle.Problem(d, n, L0, W.OP_HEAT, lo, hi)
+    d, n, L0, lo, hi, dt, op = HEAT[name]
+    P = B.Problem(d, n, L0, op, lo, hi)
+    O = oracle.Problem(d, n, L0, op, lo, hi)
     nb = 4
     u = W.random_vector(222, nb * P.n_total)
     f = W.random_vector(223, nb * P.n_total)
@@ -81,12 +84,13 @@ def test_pair_phi_batch_matches_oracle(name):
 
 
 @pytest.mark.parametrize("d, n, dt", [(2, 6, 0.1), (3, 6, 0.01), (3, 5, 0.2), (4, 5, 0.05)])
-def test_pair_stiff_anisotropic_steps_match_oracle(d, n, dt):
-    # large steps (dt / h^2 up to 400) on grids that use the line
-    # preconditioner: the differences of neighbours are formed exactly from
-    # the pairs, so the stiff stencil does not amplify the rounding
-    P = B.Problem(d, n, 1, B.PIT_OP_HEAT)
-    O = oracle.Problem(d, n, 1, W.OP_HEAT)
+@pytest.mark.parametrize("op", [W.OP_HEAT, W.OP_VARHEAT])
+def test_pair_stiff_anisotropic_steps_match_oracle(d, n, dt, op):
+    # large steps (dt / h^2 up to 100) on anisotropic grids (heat: with the
+    # line preconditioner): the differences of neighbours are formed exactly
+    # from the pairs, so the stiff stencil does not amplify the rounding
+    P = B.Problem(d, n, 1, op)
+    O = oracle.Problem(d, n, 1, op)
     nb = 2
     u = W.random_vector(616 + d, nb * P.n_total)
     out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
@@ -124,10 +128,11 @@ def test_pair_long_run_tracks_the_fp64_form():
 
 
 @pytest.mark.parametrize("scale", [1e-120, 1e-30, 1e30, 1e120])
-def test_pair_steps_scale_with_the_state(scale):
+@pytest.mark.parametrize("op", [W.OP_HEAT, W.OP_VARHEAT])
+def test_pair_steps_scale_with_the_state(scale, op):
     # Phi is linear; the pairs hold the state scaled by a power of two
-    P = B.Problem(3, 6, 1, B.PIT_OP_HEAT)
-    O = oracle.Problem(3, 6, 1, W.OP_HEAT)
+    P = B.Problem(3, 6, 1, op)
+    O = oracle.Problem(3, 6, 1, op)
     dt = 0.05 / 1024
     u0 = W.random_vector(313, P.n_total)
     ref = O.sequential(u0, dt, 6, rtol=1e-15)
@@ -158,6 +163,8 @@ MG = {
     "w2_f": (2, 5, 128, 8, 2, B.PIT_RELAX_F),
     "w2_3lev": (2, 4, 64, 4, 3, B.PIT_RELAX_FCF),
     "w5_f": (5, 3, 64, 4, 3, B.PIT_RELAX_F),
+    "w4_f": (4, 4, 128, 8, 2, B.PIT_RELAX_F),
+    "w4_fcf": (4, 4, 128, 8, 2, B.PIT_RELAX_FCF),
 }
 
 
@@ -165,8 +172,8 @@ MG = {
 def test_pair_mgrit_matches_oracle(name):
     k, n, N, m, lev, relax = MG[name]
     wl = W.workload(k)
-    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
-    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi)
+    P = B.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
     u0 = O.initial(wl.ic_kind, wl.ic_params)
     tol = 1e-10 * np.abs(u0).max()
     fine = B.solve_opts(PAIR, rtol=1e-13, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
@@ -238,7 +245,7 @@ def test_pair_large_grids_keep_their_pairs_in_global_memory():
 
 
 def test_pair_rejects_other_operators_and_reports_errors():
-    P = B.Problem(3, 5, 1, B.PIT_OP_VARHEAT)
+    P = B.Problem(4, 3, 1, B.PIT_OP_OU, [-6.0] * 4, [6.0] * 4)
     u = cuda(W.random_vector(8, P.n_total))
     with pytest.raises(B.PitError) as e:
         P.phi_batch(1e-3, u, torch.empty_like(u), opts())
