@@ -198,8 +198,10 @@ COARSE_RTOL_3LEVEL = 1e-6  # coarse solves of a three-level hierarchy
 
 
 def fine_prec_of(wl, B):
-    """Precision form of the fine solves: the refinement on FP32 pairs."""
-    return B.PIT_PREC_MIXED_PAIR
+    """Precision form of the fine solves: the pair refinement for the
+    symmetric operators (the ones it is implemented for), FP64 refinement for
+    the drift operator."""
+    return B.PIT_PREC_MIXED if wl.op == B.PIT_OP_OU else B.PIT_PREC_MIXED_PAIR
 
 
 def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_prec=None, init=True, fine_prec=None):
@@ -364,16 +366,14 @@ def run_pit(args, rank, world, local):
     # roofline of the dominant kernel: the relaxation launches (family 0: many
     # entries per grid), from the kernel's own work counters of one profiled
     # step with every grid in one lane, over those launches' event time.
-    #   pair form: bound by FP32 arithmetic issue, no FP64 work.  FP32
-    #     operations per node, counted from the kernel source: refinement
-    #     pass = correction added to the pairs (14) + residual check (heat
-    #     39 d + 17, variable coefficient 46 d + 17, drift 30 d + 32); Krylov
-    #     iteration = CG: stencil (heat 3 d + 1, variable coefficient 4 d + 1)
+    #   pair form (heat, variable coefficient): bound by FP32 arithmetic
+    #     issue, no FP64 work.  FP32 operations per node, counted from the
+    #     kernel source: refinement pass = correction added to the pairs (14)
+    #     + residual check (heat 39 d + 17, variable coefficient 46 d + 17);
+    #     CG iteration = stencil (heat 3 d + 1, variable coefficient 4 d + 1)
     #     + two dot products (4) + four vector updates (8) (the
     #     line-preconditioned iterations do more, so the count is a lower
-    #     bound); BiCGStab (drift): two stencils (2 (4 d + 1)) + five dot
-    #     products (10) + six vector updates (12) = 8 d + 24; peak = 152 SMs x
-    #     128 FP32 lanes x 2 (FMA) x SM clock.
+    #     bound); peak = 152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock.
     #   FP64-refinement form: bound by the FP64 pipe; FP64 flops per node and
     #     residual pass = stencil diag x + sum_i off_i (x_-i + x_+i) (3d + 1),
     #     b - A x (1) and the correction update (2) = 3d + 4, against GB300's
@@ -391,10 +391,8 @@ def run_pit(args, rank, world, local):
     if pair:
         if wl.op == B.PIT_OP_HEAT:
             flops_pass, flops_iter = 39 * d + 31, 3 * d + 13
-        elif wl.op == B.PIT_OP_VARHEAT:
-            flops_pass, flops_iter = 46 * d + 31, 4 * d + 13
         else:
-            flops_pass, flops_iter = 30 * d + 46, 8 * d + 24
+            flops_pass, flops_iter = 46 * d + 31, 4 * d + 13
         flops = prof.point_passes_f[0] * flops_pass + prof.point_iters_f[0] * flops_iter
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         kernel = f"steps_kernel<{opname},PAIR,{d}> (grid-resident multi-step BE, FP32 CG in a refinement on FP32 pairs)"

@@ -123,12 +123,10 @@ typedef struct {
  *                          states on grids with dt / h^2 in the hundreds near
  *                          1e-12, where FP64 reaches about 1e-13; choose rtol
  *                          above it.  Same options and stopping rule as
- *                          PIT_PREC_MIXED.  The symmetric operators form the
- *                          residual from neighbour differences (the variable
- *                          coefficient through its face coefficients dt a / h^2,
- *                          also held as pairs); the drift operator from the
- *                          products of its coefficients (pairs) with the state,
- *                          with a floor of about 2^-47 |x|.  Grids whose state does
+ *                          PIT_PREC_MIXED.  Heat and variable-coefficient
+ *                          operators (the latter through its face coefficients
+ *                          dt a / h^2, also held as pairs); the drift operator
+ *                          gives PIT_ERR_UNSUPPORTED.  Grids whose state does
  *                          not fit in shared memory keep their pairs in global
  *                          memory, as PIT_PREC_MIXED keeps its FP64 state.
  *                          Inputs and outputs stay FP64; values below 2^-102 of

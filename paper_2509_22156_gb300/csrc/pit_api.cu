@@ -271,6 +271,8 @@ size_t grid_smem_bytes(const pit_problem *P, int prec, int g)
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
+    if (prec == PAIR && P->desc.op == PIT_OP_OU)
+        return fail(PIT_ERR_UNSUPPORTED, "the pair precision form is implemented for the symmetric operators only");
     std::vector<int> order(P->G);
     for (int g = 0; g < P->G; ++g) order[g] = g;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P->info[a].n > P->info[b].n; });

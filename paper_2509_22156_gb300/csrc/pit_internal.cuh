@@ -97,7 +97,7 @@ struct StepArgs {
 // Precision forms of the multi-step kernel: PLAIN = FP64 Krylov, MIXED = FP32
 // Krylov in FP64 refinement, SINGLE = FP32 Krylov on a power-of-two-scaled
 // FP32 copy of the state (FP64 input and output), PAIR = FP32 Krylov in a
-// refinement whose state and residual are FP32 pairs.
+// refinement whose state and residual are FP32 pairs (symmetric operators).
 enum Prec { PLAIN = 0, MIXED = 1, SINGLE = 2, PAIR = 3 };
 constexpr int NPREC = 4;
 // Launch parts of one multi-step call: NBKT shared-memory buckets of the

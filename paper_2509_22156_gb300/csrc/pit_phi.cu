@@ -29,7 +29,7 @@ cudaError_t phi_kernels_init(size_t max_smem)
     cudaError_t (*inits[])(int) = {steps_init_heat_fp64,    steps_init_heat_mixed,    steps_init_heat_fp32,
                                    steps_init_varheat_fp64, steps_init_varheat_mixed, steps_init_varheat_fp32,
                                    steps_init_ou_fp64,      steps_init_ou_mixed,      steps_init_ou_fp32,
-                                   steps_init_heat_pair,    steps_init_varheat_pair,  steps_init_ou_pair};
+                                   steps_init_heat_pair,    steps_init_varheat_pair};
     for (auto f : inits)
         if (e == cudaSuccess) e = f(bytes);
     if (e == cudaSuccess) g_max_smem = max_smem;
@@ -43,12 +43,17 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
     if (blocks > 0x7fffffffLL || smem > g_max_smem || threads < 32 || threads > 512 || (threads & 31))
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)blocks), block(threads);
+    if (prec == PAIR) {
+        // symmetric operators only (the plan rejects the drift operator)
+        if (a.op.op == PIT_OP_HEAT) return steps_launch_heat_pair(a.op.d, a, grid, block, smem, s, xg);
+        if (a.op.op == PIT_OP_VARHEAT) return steps_launch_varheat_pair(a.op.d, a, grid, block, smem, s, xg);
+        return cudaErrorInvalidValue;
+    }
     switch (a.op.op) {
 #define PIT_BY_PREC(OPN)                                                                                          \
     switch (prec) {                                                                                               \
     case PLAIN: return steps_launch_##OPN##_fp64(a.op.d, a, grid, block, smem, s, xg);                            \
     case MIXED: return steps_launch_##OPN##_mixed(a.op.d, a, grid, block, smem, s, xg);                           \
-    case PAIR: return steps_launch_##OPN##_pair(a.op.d, a, grid, block, smem, s, xg);                             \
     case SINGLE: return steps_launch_##OPN##_fp32(a.op.d, a, grid, block, smem, s, xg);                           \
     default: return cudaErrorInvalidValue;                                                                        \
     }

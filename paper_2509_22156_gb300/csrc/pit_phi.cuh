@@ -360,52 +360,6 @@ struct PairTab {
     }
 };
 
-// (s, comp) -= a x for pairs a, x: the product of the hi parts with its FMA
-// error, the cross terms, and the subtraction from s by two_sum; the errors
-// and small terms go to comp.
-__device__ __forceinline__ void pair_sub_prod(float &s, float &comp, float2 a, float2 x)
-{
-    const float p = __fmul_rn(a.x, x.x);
-    const float ep = __fmaf_rn(a.x, x.x, -p);
-    float e;
-    two_sum(s, -p, s, e);
-    comp = comp + (e - (ep + (a.x * x.y + a.y * x.x)));
-}
-
-// b_j - (A x)_j for a general (2d+1)-point stencil on pairs, from the
-// operator's coefficients held as pairs (the drift operator, whose rows do
-// not sum to one and whose upwind terms are not differences):
-//     A x = c_0 x_j + sum_i c_{1+2i} x_{j-e_i} + c_{2+2i} x_{j+e_i},
-// table c[k ld + j] like TabSt, zero coefficients towards the boundary.  Every
-// product enters two_sum exactly; what is lost is about 2^-48 of the sum of
-// the terms' magnitudes, which here (diagonal near 1, small off-diagonal
-// coefficients) is about 2^-47 |x_j|.  Also yields x_j - b_j rounded to FP32.
-template <int D>
-struct PairGen {
-    const uint16_t *mask;
-    const float2 *c;
-    int ld;
-    int S[D];
-    __device__ __forceinline__ float operator()(const float2 *x, const float2 *bv, int j, float &xmb) const
-    {
-        const unsigned mk = mask[j];
-        const float2 xj = x[j], bj = bv[j];
-        float d0, e0;
-        two_sum(xj.x, -bj.x, d0, e0);
-        xmb = __fadd_rn(d0, __fadd_rn(e0, __fsub_rn(xj.y, bj.y)));
-        float s = bj.x, comp = bj.y;
-        pair_sub_prod(s, comp, c[j], xj);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const int jm = ((mk >> (2 * i)) & 1u) ? j - S[i] : j;
-            const int jp = ((mk >> (2 * i + 1)) & 1u) ? j + S[i] : j;
-            pair_sub_prod(s, comp, c[(1 + 2 * i) * ld + j], x[jm]);
-            pair_sub_prod(s, comp, c[(2 + 2 * i) * ld + j], x[jp]);
-        }
-        return __fadd_rn(s, comp);
-    }
-};
-
 __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0e300; }
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
@@ -869,6 +823,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
     static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE || PREC == PAIR, "unknown precision form");
+    static_assert(PREC != PAIR || OP != PIT_OP_OU, "the pair form is for the symmetric operators");
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -940,14 +895,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     tab64[(1 + 2 * i) * ld + j] = cm[i];
                     tab64[(2 + 2 * i) * ld + j] = cp[i];
                 }
-                if constexpr (PREC == PAIR && OP == PIT_OP_OU) {
-                    // the coefficients themselves as pairs, in the FP64 table's place
-                    float2 *cpair = reinterpret_cast<float2 *>(tab64);
-                    if (i == 0) cpair[j] = split_pair(diag, 0);
-                    cpair[(1 + 2 * i) * ld + j] = split_pair(cm[i], 0);
-                    cpair[(2 + 2 * i) * ld + j] = split_pair(cp[i], 0);
-                }
-                if constexpr (PREC == PAIR && OP == PIT_OP_VARHEAT) {
+                if constexpr (PREC == PAIR) {
                     // face coefficients dt a / h^2 as pairs, in the FP64 table's place
                     float2 *cpair = reinterpret_cast<float2 *>(tab64);
                     const double ih2 = 1.0 / (GI.h[i] * GI.h[i]);
@@ -986,13 +934,12 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         HT.diag = (T)diag;
     }
     PairTab<D> PT;
-    PairGen<D> PG;
     if constexpr (PREC == PAIR && OP != PIT_OP_HEAT) {
-        PT.mask = PG.mask = mask;
-        PT.c = PG.c = reinterpret_cast<const float2 *>(tab64);
-        PT.ld = PG.ld = ld;
+        PT.mask = mask;
+        PT.c = reinterpret_cast<const float2 *>(tab64);
+        PT.ld = ld;
 #pragma unroll
-        for (int i = 0; i < D; ++i) PT.S[i] = PG.S[i] = GI.S[i];
+        for (int i = 0; i < D; ++i) PT.S[i] = GI.S[i];
     }
     PairHeat<D> PH;
     if constexpr (PREC == PAIR && OP == PIT_OP_HEAT) {
@@ -1186,13 +1133,9 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             // are in the state's scale (its norm is kept in [2^-10, 2^10]), so
             // no per-step rescaling of them is needed.
             float *e = f32;
-            // the vector that carries the next step's initial residual (free
-            // after the Krylov solve: BiCGStab works in wv)
-            float *&cvr = (OP == PIT_OP_OU) ? tv : wv;
             auto PR = [&](int j, float &xmb) -> float {
                 if constexpr (OP == PIT_OP_HEAT) return PH(xp, bp, j, xmb);
-                else if constexpr (OP == PIT_OP_VARHEAT) return PT(xp, bp, j, xmb);
-                else return PG(xp, bp, j, xmb);
+                else return PT(xp, bp, j, xmb);
             };
             if (a.guess) {
                 const long long sb0 = (long long)(step - 1);
@@ -1208,7 +1151,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             double rn2, bb;
             if (have_r0 && bb_c >= 0x1p-20 && bb_c <= 0x1p20) {
                 // r0 = x_{s-1} - A x_{s-1}, from the last check of the previous step (in wv)
-                float *t_ = rv; rv = cvr; cvr = t_;
+                float *t_ = rv; rv = wv; wv = t_;
                 rn2 = rn0_c;
                 bb = bb_c;
             } else {
@@ -1251,7 +1194,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     if (rn2 != rn2) st_step = PIT_ERR_NONFINITE;
                     else if (carry_ok && pass == 0) {
                         // x unchanged: its residual is the next step's r0
-                        float *t_ = rv; rv = cvr; cvr = t_;
+                        float *t_ = rv; rv = wv; wv = t_;
                         rn0_c = rn2;
                         bb_c = bb;
                         carried = true;
@@ -1274,10 +1217,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 if constexpr (OP == PIT_OP_HEAT) {
                     if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
                     else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
-                } else if constexpr (OP == PIT_OP_VARHEAT) {
-                    k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
                 } else {
-                    k = bicgstab_core<float, float>(T32, n, e, rv, pv, sv, wv, tv, R32, stop32, a.maxit, st);
+                    k = cg_core<float, float>(T32, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
                 }
                 iters += k;
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
@@ -1297,7 +1238,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     if (carry_ok) {
                         const float cj = rf + xmb;
                         const float xf = xp[j].x;
-                        cvr[j] = cj;
+                        wv[j] = cj;
                         accf[1] += cj * cj;
                         accf[2] += xf * xf;
                     }
@@ -1536,7 +1477,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 PIT_STEPS_DECL(heat, fp64) PIT_STEPS_DECL(heat, mixed) PIT_STEPS_DECL(heat, fp32)
 PIT_STEPS_DECL(varheat, fp64) PIT_STEPS_DECL(varheat, mixed) PIT_STEPS_DECL(varheat, fp32)
 PIT_STEPS_DECL(ou, fp64) PIT_STEPS_DECL(ou, mixed) PIT_STEPS_DECL(ou, fp32)
-PIT_STEPS_DECL(heat, pair) PIT_STEPS_DECL(varheat, pair) PIT_STEPS_DECL(ou, pair)
+PIT_STEPS_DECL(heat, pair) PIT_STEPS_DECL(varheat, pair)
 
 // Instantiates the attribute setter and launcher of one operator and form for
 // D = 1..6 (XGV: whether the form has the global-state variant).
