@@ -163,34 +163,56 @@ __global__ void combine_kernel(const GridInfo *grids, const double *coef, const 
     const int g0 = (int)blockIdx.y * gchunk;
     const int g1 = min(G, g0 + gchunk);
     const int d = op.d;
-    double x[PIT_D];
-    for (int i = 0; i < d; ++i) x[i] = pts[(long long)k * d + i];
+    // position in units of the domain, once per point: the cell coordinate on
+    // a grid of level l is then xr 2^l, an exact scaling (no division per grid)
+    double xr[PIT_D];
+    for (int i = 0; i < d; ++i) {
+        // domain extent hi - lo = h 2^l of any grid (exact: h was (hi - lo) / 2^l)
+        const double ext = ldexp(grids[0].h[i], levels[i]);
+        xr[i] = (pts[(long long)k * d + i] - op.lo[i]) / ext;
+    }
+    const int dl = d / 2;  // corner weights: products over the first dl axes times the rest
     double acc = 0.0;
     for (int g = g0; g < g1; ++g) {
         const GridInfo &GI = grids[g];
         int cell[PIT_D];
         double t[PIT_D];
         for (int i = 0; i < d; ++i) {
-            const int M = 1 << levels[g * d + i];
-            const double s = (x[i] - op.lo[i]) / GI.h[i];
+            const int l = levels[g * d + i];
+            const int M = 1 << l;
+            const double s = ldexp(xr[i], l);
             int c = (int)floor(s);
             c = c < 0 ? 0 : (c > M - 1 ? M - 1 : c);
             cell[i] = c;
             t[i] = s - (double)c;
         }
+        double wlo[8], whi[8];
+        wlo[0] = 1.0;
+        for (int i = 0; i < dl; ++i)
+            for (int q = (1 << i) - 1; q >= 0; --q) {
+                wlo[2 * q + 1] = wlo[q] * t[i];
+                wlo[2 * q] = wlo[q] * (1.0 - t[i]);
+            }
+        whi[0] = 1.0;
+        for (int i = dl; i < d; ++i)
+            for (int q = (1 << (i - dl)) - 1; q >= 0; --q) {
+                whi[2 * q + 1] = whi[q] * t[i];
+                whi[2 * q] = whi[q] * (1.0 - t[i]);
+            }
         double val = 0.0;
         for (int corner = 0; corner < (1 << d); ++corner) {
-            double w = 1.0;
             long long idx = 0;
             bool inside = true;
+            int lo_bits = 0, hi_bits = 0;
             for (int i = 0; i < d; ++i) {
                 const int bit = (corner >> i) & 1;
                 const int node = cell[i] + bit;  // 0 and 2^l are boundary nodes
-                w *= bit ? t[i] : (1.0 - t[i]);
+                if (i < dl) lo_bits |= bit << (dl - 1 - i);
+                else hi_bits |= bit << (d - 1 - i);
                 if (node <= 0 || node > GI.N[i]) inside = false;
                 else idx += (long long)(node - 1) * GI.S[i];
             }
-            if (inside) val += w * u[GI.off + idx];
+            if (inside) val += (wlo[lo_bits] * whi[hi_bits]) * u[GI.off + idx];
         }
         acc += coef[g] * val;
     }
