@@ -26,6 +26,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -149,9 +150,17 @@ def measured_peaks():
 
 
 def phi_source_hash() -> str:
+    """Hash of the multi-step kernel's code (its header and the shared
+    declarations) with comments and blank lines removed, so that an edit of a
+    comment keeps a capture valid and any change of code invalidates it."""
     h = hashlib.sha256()
     for f in ("pit_phi.cuh", "pit_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2509_22156_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2509_22156_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code.strip():
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -33,6 +33,13 @@
 //          accumulated in FP32, and the squared norms that feed the stopping
 //          test and the tolerances are summed from the FP32 copies (relative
 //          accuracy about 1e-7, far below what a stopping test resolves).
+//   PAIR   the MIXED refinement with the state and right-hand side held as
+//          pairs of FP32 numbers (about 48 significant bits, scaled by a power
+//          of two) and b - A x formed from them by error-free FP32
+//          transformations (PairHeat, PairTab): no FP64 arithmetic per step
+//          (heat and variable-coefficient operators).
+//   SINGLE FP32 Krylov on an FP32 copy of the state scaled by a power of two,
+//          for loose tolerances (the coarse correction solves).
 // CG is the single-reduction (Chronopoulos-Gear) form: one fused block
 // reduction of (r,r) and (Ar,r) per iteration and two barriers.
 #pragma once
