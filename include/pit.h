@@ -117,12 +117,11 @@ typedef struct {
  *                          error-free FP32 transformations (two-sum, two-product
  *                          by FMA) with one compensation term, without FP64
  *                          arithmetic (which GB300 runs at 1/58 of the FP32
- *                          rate).  The residual's floor is about 2^-48 (|x| +
- *                          sum_i (dt / h_i^2) |2 x_j - x_{j-e_i} - x_{j+e_i}|):
- *                          about 1e-14 of ||b|| for smooth states, but for rough
- *                          states on grids with dt / h^2 in the hundreds near
- *                          1e-12, where FP64 reaches about 1e-13; choose rtol
- *                          above it.  Same options and stopping rule as
+ *                          rate).  The residual's floor is about 2^-48 (1 + 4
+ *                          sum_i dt / h_i^2) |x|, 32 times the FP64 residual's
+ *                          (2^-53 for 2^-48): about 1e-14 of ||b|| where
+ *                          dt / h^2 is of order one, near 1e-12 where it is in
+ *                          the hundreds; choose rtol above it.  Same options and stopping rule as
  *                          PIT_PREC_MIXED.  Heat and variable-coefficient
  *                          operators (the latter through its face coefficients
  *                          dt a / h^2, also held as pairs); the drift operator

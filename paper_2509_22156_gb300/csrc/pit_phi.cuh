@@ -293,9 +293,11 @@ __device__ __forceinline__ float2 pair_add(float2 x, float2 y)
 // The hi parts of b - x and of the neighbour differences are formed with
 // two_sum, c_i (a pair) times the difference with the FMA product error, and
 // the big terms are summed with two_sum; every rounding error, the lo parts
-// and the small cross products go to one FP32 compensation term.  What is
-// lost is second order (about 2^-48 of |x| + sum_i c_i |2 x_j - x_m - x_p|),
-// so the residual keeps FP64-like accuracy when b - A x cancels to 1e-11 of b.
+// and the small cross products go to one FP32 compensation term.  The lo
+// parts of the differences are combined in FP32, so the residual is lost
+// below about 2^-48 (|x_j| + sum_i c_i (2 |x_j| + |x_m| + |x_p|)) (the FP64
+// residual's bound with 2^-48 for 2^-53): far below the 1e-11 relative
+// residuals the refinement asks for unless dt / h^2 reaches the hundreds.
 // Also yields x_j - b_j rounded to FP32.
 template <int D>
 struct PairHeat {
