@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pit_internal.cuh"
@@ -1465,12 +1466,18 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
             return PIT_OK;
         };
         for (pit_lane &L : P->lanes) TRY(enqueue(L));
-        bool any = true;
-        while (any) {
-            any = false;
+        // the host serves whichever lane finished its cycle first (a blocking
+        // wait on the lanes in turn would leave a finished lane idle behind a
+        // slower one)
+        int n_busy = (int)P->lanes.size();
+        while (n_busy > 0) {
+            bool served = false;
             for (pit_lane &L : P->lanes) {
                 if (!L.busy) continue;
-                CU(cudaEventSynchronize(L.done));
+                const cudaError_t q = cudaEventQuery(L.done);
+                if (q == cudaErrorNotReady) continue;
+                CU(q);
+                served = true;
                 int na = 0;
                 const double rmax = mg_evaluate(L.h_res, G, Nc, L.grids.data(), (int)L.grids.size(), L.h_act,
                                                 o->tol, na);
@@ -1480,11 +1487,12 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
                 if (na > 0 && L.it < o->maxit && rmax == rmax) {
                     CU(cudaMemcpyAsync(L.d_act, L.h_act, sizeof(int) * G, cudaMemcpyHostToDevice, L.s));
                     TRY(enqueue(L));
-                    any = true;
                 } else {
                     L.busy = false;
+                    --n_busy;
                 }
             }
+            if (!served) std::this_thread::yield();
         }
         n_active = 0;
         for (pit_lane &L : P->lanes) {
