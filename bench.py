@@ -632,8 +632,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     wl = W.workload(args.workload)
-    O, grids = oracle_sample(wl, 6)
     cores = os.cpu_count() or 1
+    # one sampled grid per host core (at least six), solved in parallel
+    O, grids = oracle_sample(wl, max(6, cores))
     oracle.set_threads(min(cores, len(grids)))
     u0 = O.initial(wl.ic_kind, wl.ic_params)
     dof = sum(int(O.offsets[g + 1] - O.offsets[g]) for g in grids)
