@@ -143,3 +143,81 @@ def test_pair_heat_residual_floor():
                 worst = max(worst, float((err - abs(ex) / 2 ** 23) / scale))
     # the bound is not loose by orders of magnitude: the model reaches it
     assert 2 ** -52 < worst <= 4 / 2 ** 48
+
+
+def pair_tab_residual(x, b, j, nb, cf):
+    """The kernel's operation order for the variable-coefficient operator:
+    nb[k] = neighbour index or None for k = 2 i (towards -e_i) and 2 i + 1;
+    cf[k] = (hi, lo) of the face coefficient dt a / h_i^2."""
+    xj, bj = x[j], b[j]
+    s, comp = two_sum(bj[0], f32(-xj[0]))
+    comp = f32(comp + f32(bj[1] - xj[1]))
+    for k, n in enumerate(nb):
+        xn = x[n] if n is not None else (f32(0), f32(0))
+        dh, e1 = two_sum(xj[0], f32(-xn[0]))
+        dl = f32(e1 + f32(xj[1] - xn[1]))
+        ch, cl = cf[k]
+        pr = f32(ch * dh)
+        q = f32(fma(ch, dh, f32(-pr)) + fma(ch, dl, f32(cl * dh)))
+        s, e2 = two_sum(s, f32(-pr))
+        comp = f32(comp + f32(e2 - q))
+    return f32(s + comp)
+
+
+def test_pair_tab_residual_floor():
+    """Variable coefficient (face coefficients from a = 1 + A sin cos, dt /
+    h^2 up to 400), near the solution of the step and away from it: the same
+    bound as the heat form, 4 x 2^-48 (|x_j| + sum_faces c (|x_j| + |x_n|))
+    plus one FP32 rounding."""
+    rng = np.random.default_rng(4)
+    worst = 0.0
+    for trial in range(200):
+        d = 1 + trial % 2
+        n = 8
+        shape = (n,) * d
+        N = int(np.prod(shape))
+        grid = np.indices(shape).reshape(d, -1).T
+        strides = [int(np.prod(shape[i + 1:])) for i in range(d)]
+        cs = [10.0 ** rng.uniform(-2, 2.6) for _ in range(d)]
+        # per node and face: c = dt a(face) / h^2 with a smooth positive a
+        cval = np.empty((N, 2 * d))
+        for j in range(N):
+            for i in range(d):
+                for side in (0, 1):
+                    xf = (grid[j][i] + 1 + (side - 0.5)) / (n + 1)
+                    cval[j, 2 * i + side] = cs[i] * (1.0 + 0.5 * np.sin(2 * np.pi * xf))
+        nbs = []
+        for j in range(N):
+            nb = []
+            for i in range(d):
+                nb.append(j - strides[i] if grid[j][i] > 0 else None)
+                nb.append(j + strides[i] if grid[j][i] < n - 1 else None)
+            nbs.append(nb)
+        bv = rng.normal(size=N) if trial % 3 == 0 else np.prod(np.sin(np.pi * (grid + 1) / (n + 1)), axis=1)
+        if trial % 2 == 0:
+            A = np.eye(N)
+            for j in range(N):
+                for k, nn in enumerate(nbs[j]):
+                    A[j, j] += cval[j, k]
+                    if nn is not None:
+                        A[j, nn] -= cval[j, k]
+            xv = np.linalg.solve(A, bv)
+        else:
+            xv = bv * (1.0 + 1e-3 * rng.normal(size=N))
+        x = [split(v) for v in xv]
+        b = [split(v) for v in bv]
+        for j in range(N):
+            cf = [split(v) for v in cval[j]]
+            r = pair_tab_residual(x, b, j, nbs[j], cf)
+            xj = exact(x[j])
+            ex = exact(b[j]) - xj
+            scale = abs(xj)
+            for k, nn in enumerate(nbs[j]):
+                xn = exact(x[nn]) if nn is not None else Fraction(0)
+                ex -= exact(cf[k]) * (xj - xn)
+                scale += exact(cf[k]) * (abs(xj) + abs(xn))
+            err = abs(Fraction(float(r)) - ex)
+            bound = 4 * scale / 2 ** 48 + abs(ex) / 2 ** 23
+            assert err <= bound, (trial, j, float(err), float(bound))
+            worst = max(worst, float((err - abs(ex) / 2 ** 23) / scale))
+    assert worst <= 4 / 2 ** 48
