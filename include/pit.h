@@ -175,7 +175,7 @@ typedef struct {
     pit_solve_opts crs;   /* options of every coarse-level Phi solve */
     int relax;            /* pit_relax of the finest level           */
     int lanes;            /* concurrent grid groups (Alg. 3 runs MGRIT per grid): 0 = library
-                             default (6), 1 = all grids in lockstep; more than one lane is
+                             default (5), 1 = all grids in lockstep; more than one lane is
                              used with the correction form and the implicit coarse step only
                              (a learned propagator that was not accepted counts as implicit),
                              other forms run as one lane                                    */
