@@ -31,7 +31,9 @@
  *   or_combine                     interpolation property at sparse-grid nodes
  *   or_initial                     direct evaluation at node coordinates
  *   or_net_forward / backward      finite-difference gradient check; linear
- *                                  special cases
+ *                                  special cases; single-tap, s-channel,
+ *                                  coefficient-channel and hidden-channel
+ *                                  closed forms; an array restatement
  */
 #include <math.h>
 #include <stdlib.h>
