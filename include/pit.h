@@ -269,8 +269,9 @@ pit_status pit_train_coarse(pit_problem_t p, const pit_train_opts *opts, pit_tra
 
 /* Creates a problem on the current CUDA device: enumerates the component
  * grids (Eq. "combination_technique_solution"; l >= level0 componentwise,
- * |l|_1 = level_n + d - 1 - w, w = 0..d-1), uploads the grid table and
- * allocates workspaces lazily.  stream is a cudaStream_t (NULL = legacy
+ * |l|_1 = level_n + d - 1 - w, w = 0..d-1), uploads the grid table, makes the
+ * launch plan of every precision form the operator and grid sizes support,
+ * and allocates the solvers' workspaces lazily.  stream is a cudaStream_t (NULL = legacy
  * default stream).  Errors: PIT_ERR_INVALID_ARG (d outside 1..6, level0 < 1,
  * level_n < level0, hi <= lo, unknown op), PIT_ERR_CUDA (no device). */
 pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_problem_t *out);
@@ -353,6 +354,9 @@ typedef struct {
     long long point_iters_f[2];   /* point_iters of family 0 and of family 1     */
     long long point_passes_f[2];  /* point_passes of family 0 and of family 1    */
     long long point_steps_f[2];   /* point_steps of family 0 and of family 1     */
+    long long device_allocs;      /* device allocations (cudaMalloc) the library made
+                                     since pit_profile_enable, counted over every
+                                     problem of the process                       */
 } pit_profile;
 
 pit_status pit_profile_enable(pit_problem_t p, int on);
@@ -377,9 +381,20 @@ pit_status pit_profile_read(pit_problem_t p, pit_profile *out);
  *   - All calls on a device share the one array, and every call overwrites it
  *     entirely before reading it.  Calls whose work overlaps on the GPU (on
  *     different streams, or from several threads) race on it: order them.
- *   - Calls no cudaMalloc, cudaFree or allocating library routine.  The CTA
- *     size is the one the autotuner already chose for this problem, else 128.
- *   - stats as in pit_phi_batch (NULL skips the synchronisation). */
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine: the launch
+ *     plan comes from pit_problem_create, so the first call on a new problem
+ *     allocates nothing either (pit_profile_read's device_allocs counts the
+ *     library's allocations).  With profiling enabled (pit_profile_enable) the
+ *     timing events of the call may be created on first use.
+ *   - One launch covers every grid, with the shared memory of the largest and
+ *     the CTA size the autotuner chose for the first shared-memory bucket of
+ *     this problem and batch width (else 128 threads).
+ *   - PIT_ERR_UNSUPPORTED for problems with grids too large for the on-chip
+ *     solve (their solver state needs global scratch), and for any precision
+ *     form that pit_phi_batch rejects on this problem (such as the pair form
+ *     on the drift operator).
+ *   - stats as in pit_phi_batch (NULL skips the synchronisation); the step
+ *     counts in pit_profile_read like a pit_phi_batch call. */
 #define PIT_STATIC_SCRATCH_DOUBLES (1 << 20)
 pit_status pit_phi_batch_inplace_static(pit_problem_t p, double dt, int n_batch, double *u, const double *f,
                                         const pit_solve_opts *opts, pit_phi_stats *stats);

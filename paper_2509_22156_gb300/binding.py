@@ -75,7 +75,7 @@ class pit_profile(ctypes.Structure):
                 ("point_iters", ctypes.c_longlong), ("point_passes", ctypes.c_longlong),
                 ("point_steps", ctypes.c_longlong), ("kernels", ctypes.c_longlong * 4),
                 ("point_iters_f", ctypes.c_longlong * 2), ("point_passes_f", ctypes.c_longlong * 2),
-                ("point_steps_f", ctypes.c_longlong * 2)]
+                ("point_steps_f", ctypes.c_longlong * 2), ("device_allocs", ctypes.c_longlong)]
 
 
 class pit_train_opts(ctypes.Structure):
@@ -166,13 +166,6 @@ def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=
     crs = crs or fine
     return pit_train_opts(dt_fine, m, n_pairs, n_holdout, epochs, batch, lr, seed, ic_modes, ic_fmax, traj_len,
                           fine, crs, accept_ratio)
-
-
-def bf16_round(w) -> np.ndarray:
-    """Round float32 values to BF16 (nearest even), returned as float32."""
-    b = np.ascontiguousarray(w, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
-    return b.astype(np.uint32).view(np.float32)
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,

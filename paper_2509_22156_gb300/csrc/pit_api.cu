@@ -2,6 +2,7 @@
 // backward-Euler propagator, time-sequential stepping, the MGRIT driver and
 // the combination sum.  Method: Griebel, Schweitzer, Troska, arXiv 2509.22156.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -45,6 +46,20 @@ pit_status fail(pit_status st, const char *fmt, ...)
         if (s_ != PIT_OK) return s_;       \
     } while (0)
 
+// Every device allocation of the library goes through dev_malloc, which counts
+// it (process-wide; reported by pit_profile_read as device_allocs).
+std::atomic<long long> g_dev_allocs{0};
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc((void **)p, bytes);
+}
+
 // Device buffer that only grows.
 struct DBuf {
     void *p = nullptr;
@@ -55,7 +70,7 @@ struct DBuf {
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
-        cudaError_t e = cudaMalloc(&p, want);
+        cudaError_t e = dev_malloc(&p, want);
         if (e == cudaSuccess) bytes = want;
         return e;
     }
@@ -155,6 +170,7 @@ struct pit_problem {
     long long prof_items = 0, prof_point_iters = 0, prof_point_passes = 0, prof_point_steps = 0;
     long long prof_kernels[4] = {0, 0, 0, 0};  // kernel launches per profile family
     long long prof_fam_iters[2] = {0, 0}, prof_fam_passes[2] = {0, 0}, prof_fam_steps[2] = {0, 0};
+    long long prof_allocs0 = 0;  // process-wide device allocation count at pit_profile_enable
 };
 
 namespace {
@@ -317,7 +333,7 @@ pit_status plan(pit_problem *P, int prec)
         P->h_order_cls[prec][c] = cls[c];
         P->smem_cls[prec][c] = need[c];
         if (!cls[c].empty()) {
-            CU(cudaMalloc(&P->d_order_cls[prec][c], sizeof(int) * cls[c].size()));
+            CU(dev_malloc(&P->d_order_cls[prec][c], sizeof(int) * cls[c].size()));
             CU(cudaMemcpy(P->d_order_cls[prec][c], cls[c].data(), sizeof(int) * cls[c].size(), cudaMemcpyHostToDevice));
         }
     }
@@ -741,15 +757,15 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     CUB(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     CUB(phi_kernels_init(P->max_smem));
     CUB(net_kernels_init(P->max_smem));
-    CUB(cudaMalloc(&P->d_grids, sizeof(GridInfo) * P->G));
+    CUB(dev_malloc(&P->d_grids, sizeof(GridInfo) * P->G));
     CUB(cudaMemcpy(P->d_grids, P->info.data(), sizeof(GridInfo) * P->G, cudaMemcpyHostToDevice));
-    CUB(cudaMalloc(&P->d_coef, sizeof(double) * P->G));
+    CUB(dev_malloc(&P->d_coef, sizeof(double) * P->G));
     CUB(cudaMemcpy(P->d_coef, P->coef.data(), sizeof(double) * P->G, cudaMemcpyHostToDevice));
-    CUB(cudaMalloc(&P->d_levels, sizeof(int) * P->G * d));
+    CUB(dev_malloc(&P->d_levels, sizeof(int) * P->G * d));
     CUB(cudaMemcpy(P->d_levels, P->levels.data(), sizeof(int) * P->G * d, cudaMemcpyHostToDevice));
-    CUB(cudaMalloc(&P->d_hi, sizeof(double) * PIT_MAX_DIM));
+    CUB(dev_malloc(&P->d_hi, sizeof(double) * PIT_MAX_DIM));
     CUB(cudaMemcpy(P->d_hi, desc->hi, sizeof(double) * PIT_MAX_DIM, cudaMemcpyHostToDevice));
-    CUB(cudaMalloc(&P->d_stats, 2 * sizeof(DevStats)));
+    CUB(dev_malloc(&P->d_stats, 2 * sizeof(DevStats)));
     CUB(cudaMallocHost(&P->h_stats, 2 * sizeof(DevStats)));
     CUB(cudaMallocHost(&P->h_rmax, sizeof(double) * P->G));
     CUB(cudaMallocHost(&P->h_act, sizeof(int) * P->G));
@@ -758,15 +774,24 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
         for (int g = 0; g < P->G; ++g) order[g] = g;
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return P->info[a].n > P->info[b].n; });
-        CUB(cudaMalloc(&P->d_order, sizeof(int) * P->G));
+        CUB(dev_malloc(&P->d_order, sizeof(int) * P->G));
         CUB(cudaMemcpy(P->d_order, order.data(), sizeof(int) * P->G, cudaMemcpyHostToDevice));
     }
-    CUB(cudaMalloc(&P->d_masks, sizeof(uint16_t) * P->ntot));
+    CUB(dev_malloc(&P->d_masks, sizeof(uint16_t) * P->ntot));
     CUB(launch_masks(P->d_grids, P->G, d, P->d_masks, P->stream));
     if (desc->op == PIT_OP_VARHEAT) {
-        CUB(cudaMalloc(&P->d_faces, sizeof(double) * P->ntot * 2 * d));
+        CUB(dev_malloc(&P->d_faces, sizeof(double) * P->ntot * 2 * d));
         CUB(launch_faces(P->d_grids, P->G, P->op, P->d_faces, P->stream));
     }
+    // launch plans of every precision form the problem supports, so that no
+    // later call needs to allocate for one (pit_phi_batch_inplace_static
+    // relies on this); a form that plan() rejects stays unplanned and is
+    // rejected again, with its message, by the call that asks for it
+    for (int prec = 0; prec < NPREC; ++prec) {
+        const pit_status st = plan(P, prec);
+        if (st == PIT_ERR_CUDA || st == PIT_ERR_OOM) return bail(st);
+    }
+    g_err.clear();
     CUB(cudaStreamSynchronize(P->stream));
 #undef CUB
     *out = P;
@@ -1265,7 +1290,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
             CU(cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
-            CU(cudaMalloc(&L.d_act, sizeof(int) * P->G));
+            CU(dev_malloc(&L.d_act, sizeof(int) * P->G));
             CU(cudaMallocHost(&L.h_act, sizeof(int) * P->G));
         }
     }
@@ -1292,7 +1317,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
                     if (mine[g]) lst.push_back(g);
                 L.n_cls[prec][c] = (int)lst.size();
                 if (!lst.empty()) {
-                    CU(cudaMalloc(&L.d_order_cls[prec][c], sizeof(int) * lst.size()));
+                    CU(dev_malloc(&L.d_order_cls[prec][c], sizeof(int) * lst.size()));
                     CU(cudaMemcpy(L.d_order_cls[prec][c], lst.data(), sizeof(int) * lst.size(),
                                   cudaMemcpyHostToDevice));
                 }
@@ -1569,6 +1594,7 @@ extern "C" pit_status pit_profile_enable(pit_problem_t P, int on)
     if (!P) return fail(PIT_ERR_INVALID_ARG, "NULL problem");
     CU(cudaStreamSynchronize(P->stream));
     P->prof_on = on != 0;
+    P->prof_allocs0 = g_dev_allocs.load();
     P->ev_used = 0;
     P->prof_recs.clear();
     P->prof_items = P->prof_point_iters = P->prof_point_passes = P->prof_point_steps = 0;
@@ -1594,6 +1620,7 @@ extern "C" pit_status pit_profile_read(pit_problem_t P, pit_profile *out)
         out->point_passes_f[f] = P->prof_fam_passes[f];
         out->point_steps_f[f] = P->prof_fam_steps[f];
     }
+    out->device_allocs = g_dev_allocs.load() - P->prof_allocs0;
     out->phi_items = P->prof_items;
     out->point_iters = P->prof_point_iters;
     out->point_passes = P->prof_point_passes;
@@ -1647,12 +1674,18 @@ extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, i
         scratch = g_static_ptr[dev];
     }
     const int prec = prec_form(opts->prec);
-    TRY(plan(P, prec));
+    // the launch plan was made when the problem was created; planning here
+    // would allocate, so a form without a plan is refused
+    if (!P->planned[prec])
+        return fail(PIT_ERR_UNSUPPORTED, "precision form %d is not supported on this problem (operator or grid "
+                                         "sizes); pit_phi_batch gives the reason",
+                    opts->prec);
     if (P->n_cls[prec][1] > 0)
         return fail(PIT_ERR_UNSUPPORTED, "this problem has grids whose solver state needs global scratch; "
                                          "pit_phi_batch_inplace_static cannot serve it");
     const bool wide = n_batch >= 8;
-    const int threads = P->threads[prec][wide ? 1 : 0][0] ? P->threads[prec][wide ? 1 : 0][0] : 128;
+    const int family = wide ? 0 : 1;
+    const int threads = P->threads[prec][family == 0 ? 1 : 0][0] ? P->threads[prec][family == 0 ? 1 : 0][0] : 128;
     StepCall c;
     c.dt = dt;
     c.nb = n_batch;
@@ -1666,16 +1699,23 @@ extern "C" pit_status pit_phi_batch_inplace_static(pit_problem_t P, double dt, i
     StepArgs a = make_args(P, *opts, c, nullptr);
     a.order = P->d_order_cls[prec][0];
     a.n_order = P->n_cls[prec][0];
-    if (stats) CU(cudaMemsetAsync(P->d_stats, 0, sizeof(DevStats), P->stream));
-    else a.stats = nullptr;
-    CU(launch_steps(prec, a, threads, P->smem_need[prec], P->stream));
+    // counters as in pit_phi_batch: the family of the batch width, both reset
+    const bool want = stats || P->prof_on;
+    if (want) TRY(reset_stats(P));
+    a.stats = want ? P->d_stats + family : nullptr;
+    {
+        ProfScope ps(P, family);
+        CU(launch_steps(prec, a, threads, P->smem_need[prec], P->stream));
+        count_kernels(P, family);
+    }
     CU(cudaMemcpyAsync(u, scratch, sizeof(double) * count, cudaMemcpyDeviceToDevice, P->stream));
-    if (stats) {
-        CU(cudaMemcpyAsync(P->h_stats, P->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, P->stream));
-        CU(cudaStreamSynchronize(P->stream));
-        const DevStats s = *P->h_stats;
-        fill_phi_stats(s, stats);
-        TRY(status_of(s));
+    if (want) {
+        DevStats s;
+        TRY(read_stats(P, s));
+        if (stats) {
+            fill_phi_stats(s, stats);
+            TRY(status_of(s));
+        }
     }
     return PIT_OK;
 }
