@@ -71,6 +71,10 @@ def lib():
                                    vp, c_double, c_int, vp, vp, vp, vp, c_int, c_int]
             L.or_combine.argtypes = [vp, vp, c_int, vp, vp]
             L.or_interp.argtypes = [vp, c_int, vp, c_int, vp, vp]
+            L.or_hierarchize.restype = c_int
+            L.or_hierarchize.argtypes = [vp, vp, vp, c_int]
+            L.or_recombine.restype = c_int
+            L.or_recombine.argtypes = [vp, vp, vp]
             L.or_initial.restype = c_int
             L.or_initial.argtypes = [vp, c_int, vp, c_int, vp]
             L.or_net_param_count.restype = c_ll
@@ -226,6 +230,23 @@ class Problem:
         pts = _f64(pts).reshape(-1, self.d)
         out = np.empty(pts.shape[0])
         lib().or_interp(self._h, g, _p(ug), pts.shape[0], _p(pts), _p(out))
+        return out
+
+    def hierarchize(self, u, inverse=False) -> np.ndarray:
+        """Hierarchical surpluses of every grid's nodal values (inverse:
+        nodal values from surpluses), Sec. 2.2.2."""
+        u = _f64(u)
+        out = np.empty_like(u)
+        lib().or_hierarchize(self._h, _p(u), _p(out), 1 if inverse else 0)
+        return out
+
+    def recombine(self, u) -> np.ndarray:
+        """Q u of Eq. "overall_combination_operator": hierarchize, combine
+        the surpluses node by node over the grids that share the node, and
+        dehierarchize."""
+        u = _f64(u)
+        out = np.empty_like(u)
+        lib().or_recombine(self._h, _p(u), _p(out))
         return out
 
     def initial(self, kind: int, params) -> np.ndarray:

@@ -29,6 +29,11 @@
  *                                  ceil(Nc/2) cycles, F exactness after Nc
  *                                  cycles; one cycle with Phi^m
  *   or_combine                     interpolation property at sparse-grid nodes
+ *   or_hierarchize                 inverse pair; a hierarchical hat function
+ *                                  sampled on a grid has one unit surplus
+ *   or_recombine                   equals the combined solution (or_combine)
+ *                                  at every node of every grid; a projection
+ *                                  (Q Q = Q); fixes sparse-grid functions
  *   or_initial                     direct evaluation at node coordinates
  *   or_net_forward / backward      finite-difference gradient check; linear
  *                                  special cases; single-tap, s-channel,
@@ -901,6 +906,106 @@ int or_interp(void *vp, int g, const double *ug, int npts, const double *pts, do
 {
     or_problem *P = (or_problem *)vp;
     for (int k = 0; k < npts; ++k) out[k] = interp_grid(P, g, ug, pts + (long long)k * P->d);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Recombination (Sec. 2.2.2).  Hierarchical basis of one axis of a grid of
+ * level l: the interior node with 1-based index J (x = a + J h) has
+ * hierarchical level l - t, t the number of trailing zero bits of J, and
+ * hierarchical parents J - 2^t and J + 2^t (index 0 or 2^l lies on the
+ * boundary, value 0).  Hierarchization replaces every nodal value by its
+ * surplus over the linear interpolant of its two parents,
+ *   s_J = u_J - (u_{J - 2^t} + u_{J + 2^t}) / 2,
+ * finest level first (the parents still hold nodal values); the inverse adds
+ * the parents' mean back, coarsest level first.  In d dimensions the 1-D
+ * transform is applied along every axis in turn (H_l of Eq.
+ * "overall_combination_operator" is their tensor product).                 */
+static int trailing_zeros(long long J)
+{
+    int t = 0;
+    while (!(J & 1)) { J >>= 1; ++t; }
+    return t;
+}
+
+static void hier_axis(const geom *G, int i, int lev, double *v, int inverse)
+{
+    long long N = G->N[i], S = G->S[i];
+    for (long long j0 = 0; j0 < G->n; ++j0) {
+        if ((j0 / S) % N != 0) continue;            /* first node of a line along axis i */
+        for (int k = 0; k < lev; ++k) {
+            int t = inverse ? lev - 1 - k : k;
+            long long step = 1LL << t;
+            for (long long J = step; J <= N; J += 2 * step) {  /* odd multiples of 2^t */
+                double left = (J - step >= 1) ? v[j0 + (J - step - 1) * S] : 0.0;
+                double right = (J + step <= N) ? v[j0 + (J + step - 1) * S] : 0.0;
+                double mean = 0.5 * (left + right);
+                v[j0 + (J - 1) * S] += inverse ? mean : -mean;
+            }
+        }
+    }
+}
+
+/* out = H_l u (inverse = 0) or H_l^{-1} u (inverse = 1) on every grid. */
+int or_hierarchize(void *vp, const double *u, double *out, int inverse)
+{
+    or_problem *P = (or_problem *)vp;
+    memmove(out, u, sizeof(double) * P->off[P->G]);
+#pragma omp parallel for schedule(dynamic)
+    for (int g = 0; g < P->G; ++g) {
+        geom G = grid_geom(P, g);
+        const int *l = P->lev + (size_t)g * P->d;
+        for (int i = 0; i < P->d; ++i) hier_axis(&G, i, l[i], out + P->off[g], inverse);
+    }
+    return OR_OK;
+}
+
+/* out = Q u = H^{-1} Qbar H u (Eq. "overall_combination_operator"): the
+ * surplus of node i of grid l becomes the sum, over every grid m that has a
+ * node at the same coordinates (the set S(i, Omega_l)), of m's combination
+ * coefficient times m's surplus there (Eq. "recombination_operator").  The
+ * node with 1-based indices J on grid l sits at J_k / 2^{l_k} of the box
+ * along axis k; grid m has it where J_k 2^{m_k - l_k} is an integer.
+ * out may alias u.                                                         */
+int or_recombine(void *vp, const double *u, double *out)
+{
+    or_problem *P = (or_problem *)vp;
+    long long nt = P->off[P->G];
+    double *hat = malloc(sizeof(double) * nt);
+    double *sum = malloc(sizeof(double) * nt);
+    or_hierarchize(vp, u, hat, 0);
+#pragma omp parallel for schedule(dynamic)
+    for (int g = 0; g < P->G; ++g) {
+        geom G = grid_geom(P, g);
+        const int *l = P->lev + (size_t)g * P->d;
+        long long c[OR_MAXD];
+        for (long long j = 0; j < G.n; ++j) {
+            coords(&G, j, c);
+            double acc = 0.0;
+            for (int m = 0; m < P->G; ++m) {
+                geom Gm = grid_geom(P, m);
+                const int *lm = P->lev + (size_t)m * P->d;
+                long long idx = 0;
+                int found = 1;
+                for (int k = 0; k < P->d; ++k) {
+                    long long J = c[k] + 1, Jm;
+                    if (lm[k] >= l[k]) {
+                        Jm = J << (lm[k] - l[k]);
+                    } else {
+                        long long q = 1LL << (l[k] - lm[k]);
+                        if (J % q) { found = 0; break; }
+                        Jm = J / q;
+                    }
+                    idx += (Jm - 1) * Gm.S[k];
+                }
+                if (found) acc += P->coef[m] * hat[P->off[m] + idx];
+            }
+            sum[P->off[g] + j] = acc;
+        }
+    }
+    or_hierarchize(vp, sum, out, 1);
+    free(hat);
+    free(sum);
     return OR_OK;
 }
 
