@@ -182,6 +182,12 @@ typedef struct {
     int init;             /* initial guess: 0 = u0 at every time point; 1 = one sweep of the
                              level-1 coarse propagator from u0 over the C-points (the paper
                              leaves the initial guess open; the fixed point is the same)   */
+    int recomb;           /* recombination steps s of Alg. 3 (Sec. 2.2.1): 0 = none (one MGRIT
+                             solve over [t0, t1], combined afterwards by pit_combine); s >= 1:
+                             [t0, t1] is split at tau_k = t0 + k (t1 - t0) / s, and before each
+                             of the s intervals every grid's state is replaced by the projection
+                             of the combined solution onto its grid (pit_recombine); nsteps
+                             must then be a multiple of s m^(levels-1)                        */
 } pit_mgrit_opts;
 
 typedef struct {
@@ -330,6 +336,20 @@ pit_status pit_mgrit_solve(pit_problem_t p, const double *u0, const pit_mgrit_op
  * (row-major); out: host or device, n_pts doubles.  Points outside the box
  * are clamped to its boundary cell. */
 pit_status pit_combine(pit_problem_t p, const double *u, int n_pts, const double *pts, double *out);
+
+/* Recombination (Sec. 2.2.2, Eq. "overall_combination_operator"):
+ * out = Q u = H^{-1} Qbar H u.  Every grid's nodal values are hierarchized
+ * (surplus of each node over the linear interpolant of its two hierarchical
+ * parents, along every axis in turn), the surplus at every node becomes the
+ * sum over all grids that have a node at the same coordinates of their
+ * combination coefficient times their surplus there (Eq.
+ * "recombination_operator"), and the grids are dehierarchized.  The result on
+ * grid l is the nodal interpolant on Omega_l of the combined solution
+ * sum_m c_m I_m[u_m].  u, out: device, n_total doubles; out may alias u
+ * exactly.  The sparse grid's block plan is built, and its scratch (n_total
+ * plus the number of sparse-grid nodes doubles) allocated, on the first call.
+ * PIT_ERR_UNSUPPORTED when (largest level + 1)^d exceeds 2^24. */
+pit_status pit_recombine(pit_problem_t p, const double *u, double *out);
 
 /* Kernel timing of a problem: while enabled, every library call that launches
  * device work is bracketed by CUDA events recorded on the problem's stream

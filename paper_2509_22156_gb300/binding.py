@@ -35,7 +35,7 @@ PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
             "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",
             "pit_profile_read", "pit_phi_batch_inplace_static", "pit_net_set_params", "pit_net_get_params",
-            "pit_net_forward", "pit_net_loss_grad", "pit_train_coarse", "pit_last_error"]
+            "pit_net_forward", "pit_net_loss_grad", "pit_train_coarse", "pit_recombine", "pit_last_error"]
 NET_PARAMS = 3094
 STATIC_SCRATCH_DOUBLES = 1 << 20
 
@@ -60,7 +60,7 @@ class pit_mgrit_opts(ctypes.Structure):
     _fields_ = [("t0", ctypes.c_double), ("t1", ctypes.c_double), ("nsteps", ctypes.c_int), ("m", ctypes.c_int),
                 ("levels", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts),
-                ("relax", ctypes.c_int), ("lanes", ctypes.c_int), ("init", ctypes.c_int)]
+                ("relax", ctypes.c_int), ("lanes", ctypes.c_int), ("init", ctypes.c_int), ("recomb", ctypes.c_int)]
 
 
 class pit_mgrit_stats(ctypes.Structure):
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
         L.pit_net_forward.argtypes = [vp, cd, ci, vp, vp]
         L.pit_net_loss_grad.argtypes = [vp, cd, ci, vp, vp, P(cd), vp]
         L.pit_train_coarse.argtypes = [vp, P(pit_train_opts), P(pit_train_stats)]
+        L.pit_recombine.argtypes = [vp, vp, vp]
         L.pit_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name != "pit_last_error":
@@ -169,12 +170,12 @@ def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
-               crs=None, fas=False, relax=None, lanes=0, init=False) -> pit_mgrit_opts:
+               crs=None, fas=False, relax=None, lanes=0, init=False, recomb=0) -> pit_mgrit_opts:
     fine = fine or solve_opts()
     crs = crs or fine
     relax = PIT_RELAX_FCF if relax is None else relax
     return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes,
-                          1 if init else 0)
+                          1 if init else 0, recomb)
 
 
 class Problem:
@@ -292,6 +293,10 @@ class Problem:
         pr = pit_profile()
         _check(load().pit_profile_read(self._h, ctypes.byref(pr)), "pit_profile_read")
         return pr
+
+    def recombine(self, u, out):
+        _check(load().pit_recombine(self._h, _ptr(u), _ptr(out)), "pit_recombine")
+        return out
 
     def combine(self, u, pts, out):
         n_pts = (pts.size if isinstance(pts, np.ndarray) else pts.numel()) // self.d

@@ -171,6 +171,12 @@ struct pit_problem {
     long long prof_kernels[4] = {0, 0, 0, 0};  // kernel launches per profile family
     long long prof_fam_iters[2] = {0, 0}, prof_fam_passes[2] = {0, 0}, prof_fam_steps[2] = {0, 0};
     long long prof_allocs0 = 0;  // process-wide device allocation count at pit_profile_enable
+    // recombination (Sec. 2.2.2): sparse-grid block plan, built on first use
+    bool rc_ready = false;
+    RecombPlan rc{};
+    int *rc_lam = nullptr, *rc_list_off = nullptr, *rc_list = nullptr, *rc_lookup = nullptr;
+    long long *rc_off = nullptr;
+    DBuf rc_H, rc_S, rc_cur;
 };
 
 namespace {
@@ -830,6 +836,14 @@ pit_status pit_problem_destroy(pit_problem_t P)
         }
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
+    cudaFree(P->rc_lam);
+    cudaFree(P->rc_off);
+    cudaFree(P->rc_list_off);
+    cudaFree(P->rc_list);
+    cudaFree(P->rc_lookup);
+    P->rc_H.release();
+    P->rc_S.release();
+    P->rc_cur.release();
     cudaFree(P->d_grids);
     cudaFree(P->d_coef);
     cudaFree(P->d_levels);
@@ -989,6 +1003,106 @@ pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Recombination (Sec. 2.2.2, Eq. "overall_combination_operator"): the block
+// plan of the sparse grid's hierarchical increments, built once per problem.
+namespace {
+
+pit_status recomb_plan(pit_problem *P)
+{
+    if (P->rc_ready) return PIT_OK;
+    const int d = P->desc.d, G = P->G;
+    int Lmax = 1;
+    for (int l : P->levels) Lmax = l > Lmax ? l : Lmax;
+    const int R = Lmax + 1;
+    double cells = 1.0;
+    for (int i = 0; i < d; ++i) cells *= R;
+    if (cells > (double)(1 << 24))
+        return fail(PIT_ERR_UNSUPPORTED, "recombination: the increment table would need %.0f entries (levels up to %d "
+                                         "in %d dimensions)", cells, Lmax, d);
+    const int ncell = (int)cells;
+    auto code_of = [&](const int *lam) {
+        int c = 0;
+        for (int i = 0; i < d; ++i) c = c * R + lam[i];
+        return c;
+    };
+    // every increment lam <= l of every grid l (odometer over the box 1..l)
+    std::vector<char> used(ncell, 0);
+    auto for_box = [&](int g, auto &&fn) {
+        const int *l = &P->levels[(size_t)g * d];
+        int lam[PIT_MAX_DIM];
+        for (int i = 0; i < d; ++i) lam[i] = 1;
+        for (;;) {
+            fn(lam);
+            int i = d - 1;
+            while (i >= 0 && lam[i] == l[i]) lam[i--] = 1;
+            if (i < 0) break;
+            ++lam[i];
+        }
+    };
+    for (int g = 0; g < G; ++g) for_box(g, [&](const int *lam) { used[code_of(lam)] = 1; });
+    std::vector<int> lookup(ncell, -1), blk_lam;
+    std::vector<long long> blk_off(1, 0);
+    int n_blk = 0;
+    for (int c = 0; c < ncell; ++c) {
+        if (!used[c]) continue;
+        int lam[PIT_MAX_DIM], r = c, e = 0;
+        for (int i = d - 1; i >= 0; --i) {
+            lam[i] = r % R;
+            r /= R;
+            e += lam[i] - 1;
+        }
+        lookup[c] = n_blk++;
+        blk_lam.insert(blk_lam.end(), lam, lam + d);
+        blk_off.push_back(blk_off.back() + (1LL << e));
+    }
+    std::vector<std::vector<int>> lists(n_blk);
+    for (int g = 0; g < G; ++g) for_box(g, [&](const int *lam) { lists[lookup[code_of(lam)]].push_back(g); });
+    std::vector<int> list_off(1, 0), list;
+    for (auto &L : lists) {
+        list.insert(list.end(), L.begin(), L.end());
+        list_off.push_back((int)list.size());
+    }
+    auto up = [&](auto *&dst, const auto &v) -> cudaError_t {
+        cudaError_t e = dev_malloc(&dst, sizeof(v[0]) * v.size());
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice);
+    };
+    CU(up(P->rc_lam, blk_lam));
+    CU(up(P->rc_off, blk_off));
+    CU(up(P->rc_list_off, list_off));
+    CU(up(P->rc_list, list));
+    CU(up(P->rc_lookup, lookup));
+    CU(P->rc_H.ensure(sizeof(double) * P->ntot));
+    CU(P->rc_S.ensure(sizeof(double) * blk_off.back()));
+    P->rc = RecombPlan{n_blk, R, blk_off.back(), P->rc_lam, P->rc_off, P->rc_list_off, P->rc_list, P->rc_lookup};
+    P->rc_ready = true;
+    return PIT_OK;
+}
+
+// out = Q u on the problem's stream (out may alias u).
+pit_status recombine(pit_problem *P, const double *u, double *out)
+{
+    TRY(recomb_plan(P));
+    ProfScope ps(P, 3);
+    CU(launch_recombine(P->rc, P->desc.d, P->d_grids, P->d_coef, P->G, u, P->rc_H.d(), P->rc_S.d(), out, P->stream));
+    count_kernels(P, 3, 3);
+    return PIT_OK;
+}
+
+}  // namespace
+
+extern "C" pit_status pit_recombine(pit_problem_t P, const double *u, double *out)
+{
+    if (!P || !u || !out) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
+    if (!ptr_is_device(u) || !ptr_is_device(out)) return fail(PIT_ERR_INVALID_ARG, "u and out must be device memory");
+    const size_t bytes = sizeof(double) * P->ntot;
+    const char *a0 = (const char *)u, *b0 = (const char *)out;
+    if (a0 != b0 && a0 < b0 + bytes && b0 < a0 + bytes)
+        return fail(PIT_ERR_INVALID_ARG, "out overlaps u without being the same vector");
+    return recombine(P, u, out);
+}
 
 // ---------------------------------------------------------------------------
 // MGRIT driver (Sec. 3.3, Alg. 2 with FCF or F relaxation; Alg. 3 per grid).
@@ -1368,8 +1482,8 @@ pit_status lanes_prime(Mg &M, int Nc)
 
 }  // namespace
 
-extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const pit_mgrit_opts *o, double *uT,
-                                      pit_mgrit_stats *stats)
+namespace {
+pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o, double *uT, pit_mgrit_stats *stats)
 {
     auto t_start = std::chrono::steady_clock::now();
     if (!P || !u0 || !uT || !o) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
@@ -1558,6 +1672,65 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     if (stats) *stats = st;
     TRY(status_of(ds));
     if (n_active > 0) return fail(PIT_ERR_NOCONV, "%d grids did not meet tol within %d cycles", n_active, it);
+    return PIT_OK;
+}
+}  // namespace
+
+// CTMGRIT^loc (Alg. 3).  recomb = 0: one MGRIT solve over [t0, t1], the
+// combination left to pit_combine.  recomb = s >= 1: the interval is split at
+// the recombination steps tau_k = t0 + k (t1 - t0) / s; before each of the s
+// intervals every grid's state is replaced by the projection of the combined
+// solution onto its grid (Q of Eq. "overall_combination_operator"), then every
+// grid runs MGRIT on the interval independently.
+extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const pit_mgrit_opts *o, double *uT,
+                                      pit_mgrit_stats *stats)
+{
+    if (!P || !u0 || !uT || !o) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
+    if (o->recomb < 0) return fail(PIT_ERR_INVALID_ARG, "recomb must be >= 0");
+    if (o->recomb == 0) return mgrit_run(P, u0, o, uT, stats);
+    auto t_start = std::chrono::steady_clock::now();
+    const int s = o->recomb;
+    long long div = (long long)s * o->m * (o->levels == 3 ? o->m : 1);
+    if (o->m < 2 || o->nsteps < 1 || o->nsteps % div != 0)
+        return fail(PIT_ERR_INVALID_ARG, "nsteps must be a multiple of recomb x m^(levels-1)");
+    const long long nt = P->ntot;
+    const size_t vb = sizeof(double) * nt;
+    const double *src;
+    TRY(stage_in(P, P->w_in, u0, nt, &src));
+    CU(P->rc_cur.ensure(2 * vb));
+    double *cur = P->rc_cur.d(), *nxt = cur + nt;
+    pit_mgrit_opts oi = *o;
+    oi.recomb = 0;
+    oi.nsteps = o->nsteps / s;
+    pit_mgrit_stats tot;
+    memset(&tot, 0, sizeof(tot));
+    tot.n_converged = P->G;
+    pit_status worst = PIT_OK;
+    for (int k = 0; k < s; ++k) {
+        oi.t0 = o->t0 + (o->t1 - o->t0) * k / s;
+        oi.t1 = (k + 1 == s) ? o->t1 : o->t0 + (o->t1 - o->t0) * (k + 1) / s;
+        TRY(recombine(P, k == 0 ? src : cur, cur));
+        pit_mgrit_stats sk;
+        memset(&sk, 0, sizeof(sk));
+        const pit_status rs = mgrit_run(P, cur, &oi, nxt, &sk);
+        if (rs != PIT_OK && rs != PIT_ERR_NOCONV) return rs;
+        if (rs != PIT_OK) worst = rs;
+        std::swap(cur, nxt);
+        tot.max_cycles = sk.max_cycles > tot.max_cycles ? sk.max_cycles : tot.max_cycles;
+        tot.n_converged = sk.n_converged < tot.n_converged ? sk.n_converged : tot.n_converged;
+        for (int q = 0; q < PIT_MAX_HIST; ++q)
+            if (!(sk.res_hist[q] <= tot.res_hist[q])) tot.res_hist[q] = sk.res_hist[q];
+        tot.phi_items += sk.phi_items;
+        tot.krylov_iters += sk.krylov_iters;
+        tot.point_iters += sk.point_iters;
+        tot.learned_used |= sk.learned_used;
+        tot.fallback |= sk.fallback;
+    }
+    CU(cudaMemcpyAsync(uT, cur, vb, ptr_is_device(uT) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream));
+    CU(cudaStreamSynchronize(P->stream));
+    tot.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = tot;
+    if (worst != PIT_OK) return fail(worst, "a grid did not meet tol within maxit cycles on a recombination interval");
     return PIT_OK;
 }
 

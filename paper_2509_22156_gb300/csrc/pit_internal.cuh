@@ -179,4 +179,24 @@ cudaError_t launch_add_states(const GridInfo *grids, int G, long long ntot, int 
 cudaError_t launch_resid_max(int G, int nb, const double *resid, const int *active, double *rmax,
                              cudaStream_t s);
 
+// Recombination (Sec. 2.2.2): the sparse grid's hierarchical increments lam
+// (level multi-indices contained in some grid), block b holding the
+// 2^{|lam|_1 - d} surpluses of increment blk_lam[b*d .. b*d+d-1] at
+// [blk_off[b], blk_off[b+1]) in C order; list[list_off[b] .. list_off[b+1])
+// are the grids that contain lam, ascending; lookup[code(lam)] = b (-1: none),
+// code(lam) = ((lam_0 radix + lam_1) radix + ...) + lam_{d-1}.  Device pointers.
+struct RecombPlan {
+    int n_blk;
+    int radix;
+    long long n_sparse;
+    const int *blk_lam;
+    const long long *blk_off;
+    const int *list_off;
+    const int *list;
+    const int *lookup;
+};
+// out = Q u on every grid (out may alias u); H: n_total, S: n_sparse doubles of scratch.
+cudaError_t launch_recombine(const RecombPlan &R, int d, const GridInfo *grids, const double *coef, int G,
+                             const double *u, double *H, double *S, double *out, cudaStream_t s);
+
 }  // namespace pit
