@@ -65,10 +65,10 @@ def lib():
             L.or_dense_solve.restype = c_int
             L.or_dense_solve.argtypes = [vp, c_int, c_double, vp, vp]
             L.or_sequential.restype = c_int
-            L.or_sequential.argtypes = [vp, vp, c_double, c_int, c_double, c_int, vp, vp]
+            L.or_sequential.argtypes = [vp, vp, c_double, c_int, c_double, c_int, vp, vp, vp, vp]
             L.or_mgrit.restype = c_int
             L.or_mgrit.argtypes = [vp, vp, c_double, c_int, c_int, c_int, c_double, c_int, c_int,
-                                   vp, c_double, c_int, vp, vp, vp, vp, c_int, c_int]
+                                   vp, c_double, c_int, vp, vp, vp, vp, c_int, c_int, vp, vp]
             L.or_combine.argtypes = [vp, vp, c_int, vp, vp]
             L.or_interp.argtypes = [vp, c_int, vp, c_int, vp, vp]
             L.or_hierarchize.restype = c_int
@@ -186,19 +186,40 @@ class Problem:
         m[np.asarray(grids, dtype=np.int64)] = 1
         return m
 
-    def sequential(self, u0, dt, nsteps, rtol=1e-14, maxit=100000, grids=None) -> np.ndarray:
+    def _forcing(self, forcing, nsteps):
+        if forcing is None:
+            return None
+        f = _f64(forcing)
+        if f.size != nsteps * self.n_total:
+            raise ValueError("forcing must hold nsteps packed states")
+        return f
+
+    def _tmul(self, tmul):
+        if tmul is None:
+            return None
+        t = np.ascontiguousarray(tmul, dtype=np.int32)
+        if t.size != self.G or np.any(t < 1):
+            raise ValueError("tmul must hold one integer >= 1 per grid")
+        return t
+
+    def sequential(self, u0, dt, nsteps, rtol=1e-14, maxit=100000, grids=None, forcing=None,
+                   tmul=None) -> np.ndarray:
         """Sequential stepping; with `grids`, only those grids are computed
-        (the other entries of the result are zero)."""
+        (the other entries of the result are zero).  forcing: f_n of steps
+        n = 1..nsteps (nsteps packed states); tmul: per grid steps per step."""
         u0 = _f64(u0)
         out = np.zeros_like(u0)
         gm = self._gmask(grids)
-        st = lib().or_sequential(self._h, _p(u0), dt, nsteps, rtol, maxit, _p(out), _p(gm))
+        F = self._forcing(forcing, nsteps)
+        tm = self._tmul(tmul)
+        st = lib().or_sequential(self._h, _p(u0), dt, nsteps, rtol, maxit, _p(out), _p(gm), _p(F), _p(tm))
         if st != 0:
             raise RuntimeError(f"oracle sequential: {STATUS.get(st, st)}")
         return out
 
     def mgrit(self, u0, dt, nsteps, m, levels=2, tol=1e-10, maxit=100, coarse_kind=0,
-              theta=None, rtol=1e-14, krylov_maxit=100000, check=True, grids=None, relax="FCF", init=False):
+              theta=None, rtol=1e-14, krylov_maxit=100000, check=True, grids=None, relax="FCF", init=False,
+              forcing=None, tmul=None):
         """Returns (uT, cycles per grid, residual history G x maxit, status);
         with `grids`, only those grids are computed.  relax: "FCF" (Sec. 4.1)
         or "F" (F-relaxation on the finest level).  init: start from one sweep
@@ -211,9 +232,11 @@ class Problem:
         its = np.zeros(self.G, dtype=np.int32)
         hist = np.full((self.G, maxit), np.nan)
         th = _f64(theta) if theta is not None else None
+        F = self._forcing(forcing, nsteps)
+        tm = self._tmul(tmul)
         st = lib().or_mgrit(self._h, _p(u0), dt, nsteps, m, levels, tol, maxit, coarse_kind,
                             _p(th), rtol, krylov_maxit, _p(out), _p(its), _p(hist), _p(gm),
-                            1 if relax == "F" else 0, 1 if init else 0)
+                            1 if relax == "F" else 0, 1 if init else 0, _p(F), _p(tm))
         if check and st != 0:
             raise RuntimeError(f"oracle mgrit: {STATUS.get(st, st)}")
         return out, its, hist, st

@@ -447,23 +447,33 @@ int or_dense_solve(void *vp, int g, double dt, const double *b, double *x)
 }
 
 /* Time-sequential solution (Alg. 1 with s = 1): nsteps backward-Euler steps
- * on every grid, f = 0. */
+ * on every grid.  F (or NULL: f = 0) holds the forcing f_n of step n =
+ * 1..nsteps, packed like nsteps states (Eq. "parabolic_problem_time_
+ * propagation_LES": (I + dt L) u_n = u_{n-1} + dt f_n).  tmul (or NULL: all
+ * 1) gives every grid its own time partition (Sec. 2.2.1): grid g takes
+ * tmul[g] steps of dt / tmul[g] inside each step n, all with f_n. */
 int or_sequential(void *vp, const double *u0, double dt, int nsteps, double rtol, int maxit,
-                  double *uT, const unsigned char *gmask /* G or NULL: grids to compute */)
+                  double *uT, const unsigned char *gmask /* G or NULL: grids to compute */,
+                  const double *F, const int *tmul)
 {
     or_problem *P = (or_problem *)vp;
+    long long nt = P->off[P->G];
     int worst = OR_OK;
 #pragma omp parallel for schedule(dynamic)
     for (int g = 0; g < P->G; ++g) {
         if (gmask && !gmask[g]) continue;
         long long n = P->off[g + 1] - P->off[g];
+        int tm = tmul ? tmul[g] : 1;
         double *u = uT + P->off[g];
         memcpy(u, u0 + P->off[g], sizeof(double) * n);
         for (int s = 0; s < nsteps; ++s) {
-            int st = phi_grid(P, g, dt, u, NULL, u, rtol, maxit, NULL);
-            if (st != OR_OK) {
+            const double *f = F ? F + (long long)s * nt + P->off[g] : NULL;
+            for (int q = 0; q < tm; ++q) {
+                int st = phi_grid(P, g, dt / tm, u, f, u, rtol, maxit, NULL);
+                if (st != OR_OK) {
 #pragma omp critical
-                worst = st;
+                    worst = st;
+                }
             }
         }
     }
@@ -715,25 +725,36 @@ typedef struct {
     const double *theta;/* net parameters (coarse_kind 2) */
     int relax_f;        /* 1: F-relaxation on the finest level, 0: FCF */
     int status;
+    const double *F;    /* forcing of the common steps 1..N (grid's part), stride nt, or NULL */
+    long long nt;
+    int tm;             /* the grid's steps per common step (its own time partition) */
 } mg_ctx;
 
-/* v_out = Phi_level(v_in) (+ g if non-NULL). */
-static void mg_step(mg_ctx *C, int level, const double *v_in, const double *gk, double *v_out)
+/* Coarsening factor between `level` and level + 1: the finest level of a
+ * grid with its own time partition (tm steps per common step) has tm m
+ * steps per coarse interval; the coarser levels m. */
+static int mg_factor(const mg_ctx *C, int level) { return level == 0 ? C->m * C->tm : C->m; }
+
+/* v_out = Phi_level(v_in) (+ g if non-NULL); k = index (1-based) of the step
+ * on the finest level, which selects its forcing (the coarser levels carry no
+ * forcing: FAS cancels it, Alg. 2). */
+static void mg_step(mg_ctx *C, int level, int k, const double *v_in, const double *gk, double *v_out)
 {
     long long n = C->P->off[C->g + 1] - C->P->off[C->g];
-    double dtl = C->dt;
-    for (int q = 0; q < level; ++q) dtl *= C->m;
+    double dtl = C->dt / C->tm;
+    for (int q = 0; q < level; ++q) dtl *= mg_factor(C, q);
     int st = OR_OK;
     if (level == 1 && C->coarse_kind == 1) {
         memcpy(v_out, v_in, sizeof(double) * n);
-        for (int s = 0; s < C->m; ++s) {
-            int s2 = phi_grid(C->P, C->g, C->dt, v_out, NULL, v_out, C->rtol, C->maxit, NULL);
+        for (int s = 0; s < mg_factor(C, 0); ++s) {
+            int s2 = phi_grid(C->P, C->g, C->dt / C->tm, v_out, NULL, v_out, C->rtol, C->maxit, NULL);
             if (s2 != OR_OK) st = s2;
         }
     } else if (level == 1 && C->coarse_kind == 2) {
         net_forward_grid(C->P, C->g, dtl, C->theta, v_in, v_out, NULL, NULL);
     } else {
-        st = phi_grid(C->P, C->g, dtl, v_in, NULL, v_out, C->rtol, C->maxit, NULL);
+        const double *f = (level == 0 && C->F) ? C->F + (long long)((k - 1) / C->tm) * C->nt : NULL;
+        st = phi_grid(C->P, C->g, dtl, v_in, f, v_out, C->rtol, C->maxit, NULL);
     }
     if (st != OR_OK) C->status = st;
     if (gk)
@@ -748,20 +769,20 @@ static void mg_step(mg_ctx *C, int level, const double *v_in, const double *gk, 
 static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
 {
     long long n = C->P->off[C->g + 1] - C->P->off[C->g];
-    int m = C->m;
+    int m = mg_factor(C, level);
     int Nc = N / m;
 #define V(k) (v + (long long)(k) * n)
 #define GF(k) (g ? g + (long long)(k) * n : NULL)
     /* F-relaxation: inside every coarse interval j, propagate from the
      * C-point jm over the F-points jm+1 .. jm+m-1. */
     for (int j = 0; j < Nc; ++j)
-        for (int i = 1; i < m; ++i) mg_step(C, level, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
+        for (int i = 1; i < m; ++i) mg_step(C, level, j * m + i, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
     if (!(level == 0 && C->relax_f)) {
         /* C-relaxation: one step into every C-point. */
-        for (int j = 1; j <= Nc; ++j) mg_step(C, level, V(j * m - 1), GF(j * m), V(j * m));
+        for (int j = 1; j <= Nc; ++j) mg_step(C, level, j * m, V(j * m - 1), GF(j * m), V(j * m));
         /* F-relaxation again (FCF, Sec. 4.1). */
         for (int j = 0; j < Nc; ++j)
-            for (int i = 1; i < m; ++i) mg_step(C, level, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
+            for (int i = 1; i < m; ++i) mg_step(C, level, j * m + i, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
     }
     /* C-point residual r_j = Phi(v_{jm-1}) + g_{jm} - v_{jm}; utilde_j keeps
      * Phi(v_{jm-1}) + g_{jm}. */
@@ -769,7 +790,7 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
     double rmax = 0.0;
     for (int j = 1; j <= Nc; ++j) {
         double *u_j = ut + (long long)j * n;
-        mg_step(C, level, V(j * m - 1), GF(j * m), u_j);
+        mg_step(C, level, j * m, V(j * m - 1), GF(j * m), u_j);
         double rr = 0.0;
         for (long long t = 0; t < n; ++t) { double r = u_j[t] - V(j * m)[t]; rr += r * r; }
         double rn = sqrt(rr);
@@ -783,12 +804,12 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
     double *tmp = malloc(sizeof(double) * n);
     for (int j = 0; j <= Nc; ++j) memcpy(w + (long long)j * n, V(j * m), sizeof(double) * n);
     for (int j = 1; j <= Nc; ++j) {
-        mg_step(C, level + 1, V((j - 1) * m), NULL, tmp);
+        mg_step(C, level + 1, 0, V((j - 1) * m), NULL, tmp);
         for (long long t = 0; t < n; ++t) gc[(long long)j * n + t] = ut[(long long)j * n + t] - tmp[t];
     }
     if (level + 1 == C->nlev - 1) {
         for (int j = 1; j <= Nc; ++j)
-            mg_step(C, level + 1, w + (long long)(j - 1) * n, gc + (long long)j * n, w + (long long)j * n);
+            mg_step(C, level + 1, 0, w + (long long)(j - 1) * n, gc + (long long)j * n, w + (long long)j * n);
     } else {
         mg_cycle(C, level + 1, Nc, w, gc);
     }
@@ -812,35 +833,42 @@ int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev,
              int maxit, int coarse_kind, const double *theta, double rtol, int krylov_maxit,
              double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */,
              int relax_f /* 1: F-relaxation on the finest level instead of FCF */,
-             int init /* 1: initial C-points from one sweep of the level-1 propagator */)
+             int init /* 1: initial C-points from one sweep of the level-1 propagator */,
+             const double *F /* forcing f_n, n = 1..nsteps, packed like states, or NULL */,
+             const int *tmul /* per grid steps per common step (own time partition), or NULL */)
 {
     or_problem *P = (or_problem *)vp;
     if (m < 2 || nlev < 2) return OR_EINVAL;
     long long div = 1;
     for (int q = 0; q < nlev - 1; ++q) div *= m;
     if (nsteps % div != 0) return OR_EINVAL;
+    long long ntot = P->off[P->G];
     int worst = OR_OK;
 #pragma omp parallel for schedule(dynamic)
     for (int g = 0; g < P->G; ++g) {
         if (gmask && !gmask[g]) continue;
         long long n = P->off[g + 1] - P->off[g];
-        double *v = malloc(sizeof(double) * (size_t)(nsteps + 1) * n);
-        for (int k = 0; k <= nsteps; ++k) memcpy(v + (long long)k * n, u0 + P->off[g], sizeof(double) * n);
-        mg_ctx C = {P, g, dt, m, nlev, rtol, krylov_maxit, coarse_kind, theta, relax_f, OR_OK};
+        int tm = tmul ? tmul[g] : 1;
+        int Ng = nsteps * tm;   /* steps of the grid's own partition */
+        double *v = malloc(sizeof(double) * (size_t)(Ng + 1) * n);
+        for (int k = 0; k <= Ng; ++k) memcpy(v + (long long)k * n, u0 + P->off[g], sizeof(double) * n);
+        mg_ctx C = {P, g, dt, m, nlev, rtol, krylov_maxit, coarse_kind, theta, relax_f, OR_OK,
+                    F ? F + P->off[g] : NULL, ntot, tm};
+        int m0 = m * tm;
         if (init) {
             /* initial guess at the C-points: u_{jm} = Phi_c(u_{(j-1)m}); the
              * F-points follow from the first relaxation */
-            for (int j = 1; j <= nsteps / m; ++j)
-                mg_step(&C, 1, v + (long long)(j - 1) * m * n, NULL, v + (long long)j * m * n);
+            for (int j = 1; j <= Ng / m0; ++j)
+                mg_step(&C, 1, 0, v + (long long)(j - 1) * m0 * n, NULL, v + (long long)j * m0 * n);
         }
         int it = 0, conv = 0;
         while (it < maxit) {
-            double r = mg_cycle(&C, 0, nsteps, v, NULL);
+            double r = mg_cycle(&C, 0, Ng, v, NULL);
             if (res_hist) res_hist[(long long)g * maxit + it] = r;
             ++it;
             if (r <= tol) { conv = 1; break; }
         }
-        memcpy(uT + P->off[g], v + (long long)nsteps * n, sizeof(double) * n);
+        memcpy(uT + P->off[g], v + (long long)Ng * n, sizeof(double) * n);
         if (iters) iters[g] = it;
         int st = C.status != OR_OK ? C.status : (conv ? OR_OK : OR_ENOCONV);
         if (st != OR_OK) {
@@ -1010,11 +1038,49 @@ int or_recombine(void *vp, const double *u, double *out)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Manufactured solution of the heat experiment (Sec. 4.2, Eq. "heat_equation"):
+ *   u*(x, t) = rho e^{-t} S(x),  rho = sqrt(|x|^2 + t^2),
+ *   S(x) = prod_i sin(pi xi_i),  xi_i = (x_i - a_i) / (b_i - a_i),
+ * and the forcing f = d(u^*)/dt - Laplace u* that makes it the exact solution:
+ *   d(u^*)/dt = e^{-t} S (t / rho - rho),
+ *   Laplace u* = e^{-t} (S Laplace rho + 2 grad rho . grad S + rho Laplace S),
+ *   grad rho = x / rho,  Laplace rho = d / rho - |x|^2 / rho^3,
+ *   d S / d x_i = (pi / w_i) cos(pi xi_i) prod_{k != i} sin(pi xi_k),
+ *   Laplace S = -pi^2 sum_i S / w_i^2,  w_i = b_i - a_i.                   */
+static double manufactured(const or_problem *P, const double *x, double t, int forcing)
+{
+    int d = P->d;
+    double r2 = 0.0, S = 1.0;
+    for (int i = 0; i < d; ++i) {
+        r2 += x[i] * x[i];
+        S *= sin(M_PI * (x[i] - P->lo[i]) / (P->hi[i] - P->lo[i]));
+    }
+    double rho = sqrt(r2 + t * t);
+    double et = exp(-t);
+    if (!forcing) return rho * et * S;
+    double ut = et * S * (t / rho - rho);
+    double lap_rho = d / rho - r2 / (rho * rho * rho);
+    double grad = 0.0, lapS = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double w = P->hi[i] - P->lo[i];
+        double dS = (M_PI / w) * cos(M_PI * (x[i] - P->lo[i]) / w);
+        for (int k = 0; k < d; ++k)
+            if (k != i) dS *= sin(M_PI * (x[k] - P->lo[k]) / (P->hi[k] - P->lo[k]));
+        grad += (x[i] / rho) * dS;
+        lapS -= M_PI * M_PI * S / (w * w);
+    }
+    double lap = et * (S * lap_rho + 2.0 * grad + rho * lapS);
+    return ut - lap;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Initial values sampled at the interior nodes of every grid.
  * kind 0: sum of K product-sine modes, params = [K, (A_k, m_k1..m_kd)_k]:
  *         u0(x) = sum_k A_k prod_i sin(pi m_ki (x_i - a_i)/(b_i - a_i))
  * kind 1: product Gaussian, params = [mean_1..mean_d, std_1..std_d]:
- *         u0(x) = prod_i exp(-(x_i - mean_i)^2 / (2 std_i^2)) / (std_i sqrt(2 pi)) */
+ *         u0(x) = prod_i exp(-(x_i - mean_i)^2 / (2 std_i^2)) / (std_i sqrt(2 pi))
+ * kind 2: the manufactured solution u*(x, t) of the heat experiment, params = [t]
+ * kind 3: its forcing f(x, t) = d(u^*)/dt - Laplace u*, params = [t]          */
 int or_initial(void *vp, int kind, const double *params, int nparams, double *out)
 {
     or_problem *P = (or_problem *)vp;
@@ -1024,6 +1090,8 @@ int or_initial(void *vp, int kind, const double *params, int nparams, double *ou
         if (nparams < 1 + K * (d + 1)) return OR_EINVAL;
     } else if (kind == 1) {
         if (nparams < 2 * d) return OR_EINVAL;
+    } else if (kind == 2 || kind == 3) {
+        if (nparams < 1) return OR_EINVAL;
     } else {
         return OR_EINVAL;
     }
@@ -1044,12 +1112,14 @@ int or_initial(void *vp, int kind, const double *params, int nparams, double *ou
                         prod *= sin(M_PI * pk[1 + i] * (x[i] - P->lo[i]) / (P->hi[i] - P->lo[i]));
                     v += prod;
                 }
-            } else {
+            } else if (kind == 1) {
                 v = 1.0;
                 for (int i = 0; i < d; ++i) {
                     double z = (x[i] - params[i]) / params[d + i];
                     v *= exp(-0.5 * z * z) / (params[d + i] * sqrt(2.0 * M_PI));
                 }
+            } else {
+                v = manufactured(P, x, params[0], kind == 3);
             }
             out[P->off[g] + j] = v;
         }
