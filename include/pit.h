@@ -188,6 +188,15 @@ typedef struct {
                              of the s intervals every grid's state is replaced by the projection
                              of the combined solution onto its grid (pit_recombine); nsteps
                              must then be a multiple of s m^(levels-1)                        */
+    const double *forcing; /* device, nsteps packed states or NULL: f_n of the fine steps
+                             n = 1..nsteps in (I + dt L) u_n = u_{n-1} + dt f_n (Eq.
+                             "parabolic_problem_time_propagation_LES"); the coarse levels
+                             carry none (the FAS / correction coarse problem cancels it)     */
+    const int *tmul;      /* host, G ints in 1..4096, or NULL: each grid's own time partition
+                             (Sec. 2.2.1): grid g takes tmul[g] steps of dt / tmul[g] inside
+                             each fine step n, all with f_n; the coarse step dT = m dt is
+                             common.  Grids with different tmul run as separate lanes, which
+                             needs the correction form with the implicit coarse step        */
 } pit_mgrit_opts;
 
 typedef struct {
@@ -295,6 +304,11 @@ pit_status pit_problem_info(pit_problem_t p, int *n_grids, long long *n_total, i
  * kind 0: sum of K product-sine modes, params = [K, (A_k, m_k1..m_kd) for k < K]:
  *         u0(x) = sum_k A_k prod_i sin(pi m_ki (x_i - lo_i) / (hi_i - lo_i))
  * kind 1: product Gaussian, params = [mean_1..mean_d, std_1..std_d].
+ * kind 2: the manufactured solution of the heat experiment (Sec. 4.2, Eq.
+ *         "heat_equation"), params = [t]: u*(x, t) = sqrt(|x|^2 + t^2) e^{-t}
+ *         prod_i sin(pi (x_i - lo_i) / (hi_i - lo_i)).
+ * kind 3: its forcing for the heat operator, params = [t]:
+ *         f(x, t) = du*(x, t)/dt - Laplace u*(x, t).
  * params: host, n_params doubles.  u0: host or device, n_total doubles. */
 pit_status pit_sample_initial(pit_problem_t p, int kind, const double *params, int n_params, double *u0);
 
@@ -319,6 +333,15 @@ pit_status pit_phi_batch(pit_problem_t p, double dt, int n_batch, const double *
  * may alias.  Synchronises; stats may be NULL. */
 pit_status pit_sequential_solve(pit_problem_t p, const double *u0, double dt, int nsteps,
                                 const pit_solve_opts *opts, double *uT, pit_phi_stats *stats);
+
+/* Time-sequential stepping with forcing and per-grid time partitions (Alg. 1
+ * with s = 1; Sec. 2.2.1): grid g takes nsteps x tmul[g] steps of
+ * dt / tmul[g]; the steps inside fine step n use f_n.  forcing: device,
+ * nsteps packed states (f_n, n = 1..nsteps) or NULL; tmul: host, G ints in
+ * 1..4096 or NULL (all 1).  Otherwise as pit_sequential_solve. */
+pit_status pit_sequential_solve_forced(pit_problem_t p, const double *u0, double dt, int nsteps,
+                                       const double *forcing, const int *tmul, const pit_solve_opts *opts,
+                                       double *uT, pit_phi_stats *stats);
 
 /* CTMGRIT^loc with s = 1 (Alg. 3): independent MGRIT (Alg. 2, FCF, FAS) on
  * every grid from u0 over [t0, t1] with nsteps fine steps, returning the

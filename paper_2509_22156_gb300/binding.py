@@ -35,7 +35,8 @@ PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
             "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",
             "pit_profile_read", "pit_phi_batch_inplace_static", "pit_net_set_params", "pit_net_get_params",
-            "pit_net_forward", "pit_net_loss_grad", "pit_train_coarse", "pit_recombine", "pit_last_error"]
+            "pit_net_forward", "pit_net_loss_grad", "pit_train_coarse", "pit_recombine",
+            "pit_sequential_solve_forced", "pit_last_error"]
 NET_PARAMS = 3094
 STATIC_SCRATCH_DOUBLES = 1 << 20
 
@@ -60,7 +61,8 @@ class pit_mgrit_opts(ctypes.Structure):
     _fields_ = [("t0", ctypes.c_double), ("t1", ctypes.c_double), ("nsteps", ctypes.c_int), ("m", ctypes.c_int),
                 ("levels", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts),
-                ("relax", ctypes.c_int), ("lanes", ctypes.c_int), ("init", ctypes.c_int), ("recomb", ctypes.c_int)]
+                ("relax", ctypes.c_int), ("lanes", ctypes.c_int), ("init", ctypes.c_int), ("recomb", ctypes.c_int),
+                ("forcing", ctypes.c_void_p), ("tmul", ctypes.c_void_p)]
 
 
 class pit_mgrit_stats(ctypes.Structure):
@@ -126,6 +128,7 @@ def load(path: str = LIB_PATH):
         L.pit_net_loss_grad.argtypes = [vp, cd, ci, vp, vp, P(cd), vp]
         L.pit_train_coarse.argtypes = [vp, P(pit_train_opts), P(pit_train_stats)]
         L.pit_recombine.argtypes = [vp, vp, vp]
+        L.pit_sequential_solve_forced.argtypes = [vp, vp, cd, ci, vp, vp, P(pit_solve_opts), vp, P(pit_phi_stats)]
         L.pit_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name != "pit_last_error":
@@ -170,12 +173,27 @@ def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=
 
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
-               crs=None, fas=False, relax=None, lanes=0, init=False, recomb=0) -> pit_mgrit_opts:
+               crs=None, fas=False, relax=None, lanes=0, init=False, recomb=0, forcing=None,
+               tmul=None) -> pit_mgrit_opts:
+    """forcing: device tensor of nsteps packed states (kept alive by the
+    returned struct's _keep); tmul: per-grid steps per fine step (host)."""
     fine = fine or solve_opts()
     crs = crs or fine
     relax = PIT_RELAX_FCF if relax is None else relax
-    return pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes,
-                          1 if init else 0, recomb)
+    keep = []
+    fptr = None
+    if forcing is not None:
+        fptr = _ptr(forcing).value
+        keep.append(forcing)
+    tptr = None
+    if tmul is not None:
+        t = np.ascontiguousarray(tmul, dtype=np.int32)
+        keep.append(t)
+        tptr = t.ctypes.data
+    o = pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes,
+                       1 if init else 0, recomb, fptr, tptr)
+    o._keep = keep
+    return o
 
 
 class Problem:
@@ -249,6 +267,15 @@ class Problem:
         st = pit_phi_stats()
         _check(load().pit_sequential_solve(self._h, _ptr(u0), dt, nsteps, ctypes.byref(opts or solve_opts()),
                                            _ptr(uT), ctypes.byref(st)), "pit_sequential_solve")
+        return st
+
+    def sequential_solve_forced(self, u0, dt, nsteps, uT, opts=None, forcing=None, tmul=None):
+        st = pit_phi_stats()
+        t = np.ascontiguousarray(tmul, dtype=np.int32) if tmul is not None else None
+        _check(load().pit_sequential_solve_forced(self._h, _ptr(u0), dt, nsteps, _ptr(forcing),
+                                                  ctypes.c_void_p(t.ctypes.data) if t is not None else None,
+                                                  ctypes.byref(opts or solve_opts()), _ptr(uT), ctypes.byref(st)),
+               "pit_sequential_solve_forced")
         return st
 
     def mgrit_solve(self, u0, opts, uT, check=True):

@@ -107,6 +107,7 @@ struct pit_lane {
     // per-solve state
     int it = 0, n_active = 0;
     bool busy = false;
+    int tm = 1;  // steps per common step of the lane's grids (their own time partition)
 };
 
 struct pit_problem {
@@ -151,6 +152,7 @@ struct pit_problem {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf w_xg;                       // FP64 state of class-1 items
     std::vector<pit_lane> lanes;     // MGRIT lanes (built on first use)
+    std::vector<int> lane_assign;    // grid -> lane when given explicitly; empty: balanced
     // workspaces
     DBuf w_in, w_out, w_pts, w_u, w_prm;
     DBuf w_part;  // partial sums of the chunked combination sum
@@ -356,7 +358,8 @@ struct StepCall {
     const double *in;
     long long is;
     const double *f = nullptr;
-    long long fs = 0;
+    long long fs = 0, fst = 0;
+    int fdiv = 1;
     const double *g = nullptr;
     long long gs = 0, gst = 0;
     double *out_steps = nullptr;
@@ -395,6 +398,8 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.in_stride = c.is;
     a.f = c.f;
     a.f_stride = c.fs;
+    a.f_step = c.fst;
+    a.f_div = c.fdiv;
     a.g = c.g;
     a.g_stride = c.gs;
     a.g_step = c.gst;
@@ -475,6 +480,8 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     t.is = c.is;
     t.f = c.f;
     t.fs = c.fs;
+    t.fst = c.fst;
+    t.fdiv = c.fdiv;
     t.g = c.g;
     t.gs = c.gs;
     t.gst = c.gst;
@@ -888,6 +895,8 @@ pit_status pit_sample_initial(pit_problem_t P, int kind, const double *params, i
         if (n_params < 2 * d) return fail(PIT_ERR_INVALID_ARG, "need 2d parameters");
         for (int i = 0; i < d; ++i)
             if (!(params[d + i] > 0.0)) return fail(PIT_ERR_INVALID_ARG, "std must be positive");
+    } else if (kind == 2 || kind == 3) {
+        if (n_params < 1 || !std::isfinite(params[0])) return fail(PIT_ERR_INVALID_ARG, "need the time t");
     } else {
         return fail(PIT_ERR_INVALID_ARG, "unknown initial-value kind %d", kind);
     }
@@ -963,12 +972,31 @@ pit_status pit_phi_batch(pit_problem_t P, double dt, int n_batch, const double *
     return PIT_OK;
 }
 
-pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, int nsteps,
-                                const pit_solve_opts *opts, double *uT, pit_phi_stats *stats)
+pit_status pit_sequential_solve_forced(pit_problem_t P, const double *u0, double dt, int nsteps, const double *forcing,
+                                       const int *tmul, const pit_solve_opts *opts, double *uT, pit_phi_stats *stats)
 {
     if (!P || !u0 || !uT || nsteps < 0) return fail(PIT_ERR_INVALID_ARG, "bad argument");
     if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(PIT_ERR_INVALID_ARG, "dt must be finite and >= 0");
     TRY(check_solve_opts(opts));
+    if (forcing && !ptr_is_device(forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
+    // grids grouped by their own time partition (steps per common step)
+    std::vector<int> tm_vals, group(P->G, 0);
+    if (tmul) {
+        for (int g = 0; g < P->G; ++g) {
+            const int t = tmul[g];
+            if (t < 1 || t > 4096) return fail(PIT_ERR_INVALID_ARG, "tmul[%d] = %d outside 1..4096", g, t);
+            auto pos = std::find(tm_vals.begin(), tm_vals.end(), t);
+            if (pos == tm_vals.end()) {
+                tm_vals.push_back(t);
+                group[g] = (int)tm_vals.size() - 1;
+            } else {
+                group[g] = (int)(pos - tm_vals.begin());
+            }
+        }
+    } else {
+        tm_vals.push_back(1);
+    }
+    const int n_groups = (int)tm_vals.size();
     const size_t bytes = sizeof(double) * P->ntot;
     const double *src;
     TRY(stage_in(P, P->w_in, u0, P->ntot, &src));
@@ -982,16 +1010,36 @@ pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, in
     if (nsteps == 0) {
         CU(cudaMemcpyAsync(target, src, bytes, cudaMemcpyDeviceToDevice, P->stream));
     } else {
-        // every grid is one CTA that takes all nsteps steps on chip
-        StepCall c;
-        c.dt = dt;
-        c.nb = 1;
-        c.nsteps = nsteps;
-        c.in = src;
-        c.is = P->ntot;
-        c.out_last = target;
-        c.ols = P->ntot;
-        TRY(run_steps(P, *opts, c, nullptr));
+        int *masks = nullptr;
+        if (n_groups > 1) {
+            // one activity mask per group, uploaded once
+            CU(P->m_act.ensure(sizeof(int) * (size_t)P->G * n_groups));
+            std::vector<int> h((size_t)P->G * n_groups, 0);
+            for (int g = 0; g < P->G; ++g) h[(size_t)group[g] * P->G + g] = 1;
+            masks = (int *)P->m_act.p;
+            CU(cudaMemcpyAsync(masks, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, P->stream));
+            CU(cudaStreamSynchronize(P->stream));  // h is freed on return
+        }
+        for (int q = 0; q < n_groups; ++q) {
+            // every grid is one CTA that takes all its steps on chip; grid g
+            // takes tm steps of dt / tm per common step, each with the common
+            // step's forcing
+            const int tm = tm_vals[q];
+            StepCall c;
+            c.dt = dt / tm;
+            c.nb = 1;
+            c.nsteps = nsteps * tm;
+            c.in = src;
+            c.is = P->ntot;
+            if (forcing) {
+                c.f = forcing;
+                c.fst = P->ntot;
+                c.fdiv = tm;
+            }
+            c.out_last = target;
+            c.ols = P->ntot;
+            TRY(run_steps(P, *opts, c, masks ? masks + (size_t)q * P->G : nullptr));
+        }
     }
     if (target != uT)
         CU(cudaMemcpyAsync(uT, target, bytes, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream));
@@ -1000,6 +1048,12 @@ pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, in
     if (stats) fill_phi_stats(s, stats);
     TRY(status_of(s));
     return PIT_OK;
+}
+
+pit_status pit_sequential_solve(pit_problem_t P, const double *u0, double dt, int nsteps,
+                                const pit_solve_opts *opts, double *uT, pit_phi_stats *stats)
+{
+    return pit_sequential_solve_forced(P, u0, dt, nsteps, nullptr, nullptr, opts, uT, stats);
 }
 
 }  // extern "C"
@@ -1134,14 +1188,20 @@ struct Mg {
     bool learned;    // level-1 coarse propagator is the network
     pit_lane *L;     // lane of the cycle; nullptr: every grid on the problem's stream
     cudaStream_t s;  // stream of the cycle
+    // finest level of the cycle's grids (their own time partition, Sec. 2.2.1):
+    // tm steps of dtf = dt / tm per common step, mf = m tm per coarse interval;
+    // forcing F of the common steps (NULL: none); the coarse levels keep dT = m dt
+    double dtf = 0.0;
+    int mf = 0, tm = 1;
+    const double *F = nullptr;
 };
 
 // Coarse propagator of level 1: backward Euler with m dt, or m fine steps.
 void coarse_call(Mg &M, StepCall &c, int level)
 {
     if (level == 1 && M.o->coarse == PIT_COARSE_EXACT) {
-        c.dt = M.dt;
-        c.nsteps *= M.o->m;
+        c.dt = M.dtf;
+        c.nsteps *= M.mf;
     } else {
         double dtl = M.dt;
         for (int q = 0; q < level; ++q) dtl *= M.o->m;
@@ -1240,9 +1300,15 @@ pit_status mg_cycle(Mg &M, int Nc, bool corr, double *h_res)
     const bool relax_f = o->relax == PIT_RELAX_F;
     double *Rx = relax_f ? U : R;
     StepCall fc;  // FC relaxation
-    fc.dt = M.dt;
+    fc.dt = M.dtf;
     fc.nb = Nc;
-    fc.nsteps = m;
+    fc.nsteps = M.mf;
+    if (M.F) {  // forcing of common step j m + (s - 1) / tm for step s of interval j
+        fc.f = M.F;
+        fc.fs = (long long)m * nt;
+        fc.fst = nt;
+        fc.fdiv = M.tm;
+    }
     fc.in = U;
     fc.is = nt;
     fc.out_last = R + nt;
@@ -1367,9 +1433,14 @@ double mg_evaluate(const double *h_res, int G, int Nc, const int *grids, int n_g
 // K lanes over the grids, balanced by nodes (largest grid first to the lane
 // with the fewest nodes); each lane keeps the class lists of both precision
 // forms in the problem's decreasing-size order.
-pit_status lanes_prepare(pit_problem *P, int K, int Nc)
+pit_status lanes_prepare(pit_problem *P, int K, int Nc, const std::vector<int> *lane_of_in = nullptr,
+                         const std::vector<int> *lane_tm = nullptr)
 {
-    if ((int)P->lanes.size() != K) {
+    // lanes balanced by nodes, or the given assignment (grids with their own
+    // time partition: one lane per partition)
+    std::vector<int> want;
+    if (lane_of_in) want = *lane_of_in;
+    if ((int)P->lanes.size() != K || want != P->lane_assign) {
         for (pit_lane &L : P->lanes) {
             cudaStreamSynchronize(L.s);
             for (auto sq : L.sides) cudaStreamSynchronize(sq);
@@ -1385,17 +1456,20 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
             cudaEventDestroy(L.done);
         }
         P->lanes.assign(K, pit_lane());
+        P->lane_assign = want;
         std::vector<int> order(P->G);
         for (int g = 0; g < P->G; ++g) order[g] = g;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P->info[a].n > P->info[b].n; });
         std::vector<long long> load(K, 0);
-        std::vector<int> lane_of(P->G, 0);
         for (int g : order) {
             int best = 0;
-            for (int k = 1; k < K; ++k)
-                if (load[k] < load[best]) best = k;
+            if (lane_of_in) {
+                best = (*lane_of_in)[g];
+            } else {
+                for (int k = 1; k < K; ++k)
+                    if (load[k] < load[best]) best = k;
+            }
             load[best] += P->info[g].n;
-            lane_of[g] = best;
             P->lanes[best].grids.push_back(g);
         }
         for (pit_lane &L : P->lanes) {
@@ -1439,6 +1513,7 @@ pit_status lanes_prepare(pit_problem *P, int K, int Nc)
             L.planned[prec] = true;
         }
     }
+    for (int k = 0; k < K; ++k) P->lanes[k].tm = lane_tm ? (*lane_tm)[k] : 1;
     for (pit_lane &L : P->lanes) {
         const size_t want = (size_t)P->G * Nc;
         if (L.h_res_cap < want) {
@@ -1506,6 +1581,7 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     if (o->init != 0 && o->init != 1) return fail(PIT_ERR_INVALID_ARG, "init must be 0 or 1");
+    if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
     const int G = P->G, m = o->m, Nc = o->nsteps / m;
     const long long nt = P->ntot;
     const size_t vb = sizeof(double) * nt;
@@ -1538,6 +1614,31 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
 
     Mg M{P, o, (o->t1 - o->t0) / o->nsteps, nt, act, o->coarse == PIT_COARSE_LEARNED && P->net_accepted, nullptr,
          P->stream};
+    M.dtf = M.dt;
+    M.mf = m;
+    M.F = o->forcing;
+    // per-grid time partitions: grids with the same number of steps per common
+    // step form one lane; a single partition for all grids needs no lanes
+    std::vector<int> tm_vals, lane_of;
+    if (o->tmul) {
+        lane_of.assign(G, 0);
+        for (int g = 0; g < G; ++g) {
+            const int t = o->tmul[g];
+            if (t < 1 || t > 4096) return fail(PIT_ERR_INVALID_ARG, "tmul[%d] = %d outside 1..4096", g, t);
+            auto pos = std::find(tm_vals.begin(), tm_vals.end(), t);
+            if (pos == tm_vals.end()) {
+                tm_vals.push_back(t);
+                lane_of[g] = (int)tm_vals.size() - 1;
+            } else {
+                lane_of[g] = (int)(pos - tm_vals.begin());
+            }
+        }
+        if (tm_vals.size() == 1) {
+            M.tm = tm_vals[0];
+            M.dtf = M.dt / M.tm;
+            M.mf = m * M.tm;
+        }
+    }
     pit_mgrit_stats st;
     memset(&st, 0, sizeof(st));
     st.learned_used = M.learned ? 1 : 0;
@@ -1581,10 +1682,17 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     int K = o->lanes == 0 ? 5 : o->lanes;
     if (!corr_form()) K = 1;
     if (K > G) K = G;
+    const bool by_tm = tm_vals.size() > 1;
+    if (by_tm) {
+        if (!corr_form())
+            return fail(PIT_ERR_UNSUPPORTED, "per-grid time partitions need the correction form with the implicit "
+                                             "coarse step (fas = 0)");
+        K = (int)tm_vals.size();
+    }
     int it = 0, n_active = G;
     if (K > 1) {
         TRY(lanes_prime(M, Nc));
-        TRY(lanes_prepare(P, K, Nc));
+        TRY(lanes_prepare(P, K, Nc, by_tm ? &lane_of : nullptr, by_tm ? &tm_vals : nullptr));
         CU(cudaEventRecord(P->ev_fork, P->stream));
         for (pit_lane &L : P->lanes) {
             CU(cudaStreamWaitEvent(L.s, P->ev_fork, 0));
@@ -1600,6 +1708,9 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
             ML.active = L.d_act;
             ML.L = &L;
             ML.s = L.s;
+            ML.tm = L.tm;
+            ML.dtf = M.dt / L.tm;
+            ML.mf = m * L.tm;
             TRY(mg_cycle(ML, Nc, true, L.h_res));
             CU(cudaEventRecord(L.done, L.s));
             return PIT_OK;
@@ -1707,6 +1818,7 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
     tot.n_converged = P->G;
     pit_status worst = PIT_OK;
     for (int k = 0; k < s; ++k) {
+        if (o->forcing) oi.forcing = o->forcing + (long long)k * oi.nsteps * nt;
         oi.t0 = o->t0 + (o->t1 - o->t0) * k / s;
         oi.t1 = (k + 1 == s) ? o->t1 : o->t0 + (o->t1 - o->t0) * (k + 1) / s;
         TRY(recombine(P, k == 0 ? src : cur, cur));

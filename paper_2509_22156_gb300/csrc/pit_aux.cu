@@ -82,11 +82,39 @@ __global__ void initial_kernel(const GridInfo *grids, OpParams op, const double 
                 for (int i = 0; i < d; ++i) prod *= sin(M_PI * pk[1 + i] * (x[i] - op.lo[i]) / (hi[i] - op.lo[i]));
                 v += prod;
             }
-        } else {
+        } else if (kind == 1) {
             v = 1.0;
             for (int i = 0; i < d; ++i) {
                 const double z = (x[i] - prm[i]) / prm[d + i];
                 v *= exp(-0.5 * z * z) / (prm[d + i] * sqrt(2.0 * M_PI));
+            }
+        } else {
+            // heat experiment (Sec. 4.2): u*(x,t) = rho e^{-t} S(x), rho = sqrt(|x|^2 + t^2),
+            // S = prod_i sin(pi xi_i), xi_i = (x_i - a_i) / w_i; kind 3 gives
+            // f = du*/dt - Laplace u* = e^{-t} [S (t/rho - rho) - S (d/rho - |x|^2/rho^3)
+            //     - 2 sum_i (x_i/rho) dS/dx_i + rho pi^2 S sum_i 1/w_i^2]
+            const double t = prm[0];
+            double r2 = 0.0, S = 1.0, sn[PIT_D], cs[PIT_D], w[PIT_D];
+            for (int i = 0; i < d; ++i) {
+                w[i] = hi[i] - op.lo[i];
+                sincospi((x[i] - op.lo[i]) / w[i], &sn[i], &cs[i]);
+                S *= sn[i];
+                r2 += x[i] * x[i];
+            }
+            const double rho = sqrt(r2 + t * t), et = exp(-t);
+            if (kind == 2) {
+                v = rho * et * S;
+            } else {
+                double grad = 0.0, iw2 = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    double dS = M_PI / w[i] * cs[i];
+                    for (int k = 0; k < d; ++k)
+                        if (k != i) dS *= sn[k];
+                    grad += x[i] / rho * dS;
+                    iw2 += 1.0 / (w[i] * w[i]);
+                }
+                v = et * (S * (t / rho - rho) - S * (d / rho - r2 / (rho * rho * rho)) - 2.0 * grad +
+                          rho * M_PI * M_PI * S * iw2);
             }
         }
         u[GI.off + j] = v;

@@ -46,6 +46,8 @@ struct DevStats {
 // Arguments of one multi-step backward-Euler launch.  Item k = item0 +
 // blockIdx.x is grid order[k / n_batch] of batch entry b = k % n_batch.  Entry b starts
 // from in + b*in_stride (+ grid offset) and takes nsteps steps of size dt;
+// the forcing of step s (1-based) is f + b*f_stride + ((s-1)/f_div)*f_step
+// (f may be NULL: no forcing);
 // after step s (1-based) x <- x + g_s with g_s = g + b*g_stride + (s-1)*g_step
 // (g may be NULL); states after steps 1..nsteps-1 are written to out_steps +
 // b*os_stride + (s-1)*os_step when out_steps is non-NULL; the final state x is
@@ -68,7 +70,8 @@ struct StepArgs {
     int nsteps;
     double dt;
     const double *in;        long long in_stride;
-    const double *f;         long long f_stride;
+    const double *f;         long long f_stride, f_step;
+    int f_div;
     const double *g;         long long g_stride, g_step;
     double *out_steps;       long long os_stride, os_step;
     double *out_last;        long long ol_stride;

@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
 
     const double *in = a.in + (long long)b * a.in_stride + GI.off;
-    const double *f = a.f ? a.f + (long long)b * a.f_stride + GI.off : nullptr;
+    const double *f0 = a.f ? a.f + (long long)b * a.f_stride + GI.off : nullptr;
     const uint16_t *gmask = a.masks + GI.off;
 
     Reducer<double> R64{red64, 0};
@@ -996,7 +996,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     };
 
     int status = PIT_OK, iters = 0, passes = 0;
-    const bool carry_ok = (f == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
+    const bool carry_ok = (f0 == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
     // MIXED: carried initial residual of the next step (see the file comment).
     // FP32 copies of FP64 vectors are scaled by a power of two 2^k chosen from
     // ||b|| (exact, folded into the conversion), so they stay inside the normal
@@ -1011,6 +1011,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                    : f32 + (size_t)NKV * ld;
 
     for (int step = 1; step <= a.nsteps; ++step) {
+        // forcing of this step: f_div consecutive steps share one forcing vector
+        const double *f = f0 ? f0 + (long long)((step - 1) / a.f_div) * a.f_step : nullptr;
         __syncthreads();  // state complete
         if constexpr (PREC == PLAIN) {
             double *r = v64, *q1 = v64 + vs, *q2 = v64 + 2 * vs, *q3 = v64 + 3 * vs, *q4 = v64 + 4 * vs;
