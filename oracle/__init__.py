@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OP_HEAT, OP_VARHEAT, OP_OU = 0, 1, 2
+OP_HEAT, OP_VARHEAT, OP_OU, OP_LSDE = 0, 1, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 4: "no convergence", 5: "breakdown"}
 
 
@@ -56,6 +56,8 @@ def lib():
             L.or_create.restype = vp
             L.or_create.argtypes = [c_int, c_int, c_int, c_int, vp, vp, c_double, c_double, c_double]
             L.or_destroy.argtypes = [vp]
+            L.or_set_sde.restype = c_int
+            L.or_set_sde.argtypes = [vp, vp, vp]
             L.or_info.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_set_threads.argtypes = [c_int]
             L.or_max_threads.restype = c_int
@@ -127,7 +129,8 @@ def max_threads() -> int:
 class Problem:
     """One combination-technique problem on the CPU (FP64)."""
 
-    def __init__(self, d, n, L0=1, op=OP_HEAT, lo=None, hi=None, theta=1.0, sigma=1.0, vamp=0.5):
+    def __init__(self, d, n, L0=1, op=OP_HEAT, lo=None, hi=None, theta=1.0, sigma=1.0, vamp=0.5,
+                 drift=None, diffusion=None):
         self.d, self.n, self.L0, self.op = d, n, L0, op
         self.lo = _f64(lo if lo is not None else [0.0] * d)
         self.hi = _f64(hi if hi is not None else [1.0] * d)
@@ -135,6 +138,11 @@ class Problem:
         self._h = lib().or_create(d, n, L0, op, _p(self.lo), _p(self.hi), theta, sigma, vamp)
         if not self._h:
             raise ValueError("invalid problem description")
+        if op == OP_LSDE:
+            # linear SDE dX = A X dt + sigma dW, H = 2 sigma D sigma^T (Sec. 4.4)
+            self.drift = _f64(drift).reshape(d, d)
+            self.diffusion = _f64(diffusion).reshape(d, d)
+            lib().or_set_sde(self._h, _p(self.drift), _p(self.diffusion))
         G = ctypes.c_int()
         nt = ctypes.c_longlong()
         lib().or_info(self._h, ctypes.byref(G), ctypes.byref(nt), None, None, None)

@@ -49,13 +49,15 @@
 
 #define OR_MAXD 6
 
-enum { OR_HEAT = 0, OR_VARHEAT = 1, OR_OU = 2 };
+enum { OR_HEAT = 0, OR_VARHEAT = 1, OR_OU = 2, OR_LSDE = 3 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOCONV = 4, OR_EBREAK = 5 };
 
 typedef struct {
     int d, n, L0, op;
     double lo[OR_MAXD], hi[OR_MAXD];
     double theta, sigma, vamp;       /* OU drift/diffusion; var-coef amplitude */
+    double sde_A[OR_MAXD * OR_MAXD]; /* linear SDE dX = A X dt + sigma dW: drift matrix */
+    double sde_H[OR_MAXD * OR_MAXD]; /* H = 2 sigma D sigma^T (row major)              */
     int G;
     int *lev;                        /* G*d level multi-indices               */
     long long *off;                  /* G+1 packed offsets                    */
@@ -131,7 +133,7 @@ long long or_grid_points(int d, const int *l)
 void *or_create(int d, int n, int L0, int op, const double *lo, const double *hi,
                 double theta, double sigma, double vamp)
 {
-    if (d < 1 || d > OR_MAXD || L0 < 1 || n < L0 || op < 0 || op > 2) return NULL;
+    if (d < 1 || d > OR_MAXD || L0 < 1 || n < L0 || op < 0 || op > 3) return NULL;
     or_problem *P = (or_problem *)calloc(1, sizeof(or_problem));
     P->d = d; P->n = n; P->L0 = L0; P->op = op;
     for (int i = 0; i < d; ++i) { P->lo[i] = lo[i]; P->hi[i] = hi[i]; }
@@ -149,6 +151,16 @@ void *or_create(int d, int n, int L0, int op, const double *lo, const double *hi
     }
     free(layer);
     return P;
+}
+
+/* Drift matrix A and diffusion matrix H (row major, d x d) of the linear SDE
+ * operator (op 3). */
+int or_set_sde(void *vp, const double *A, const double *H)
+{
+    or_problem *P = (or_problem *)vp;
+    memcpy(P->sde_A, A, sizeof(double) * P->d * P->d);
+    memcpy(P->sde_H, H, sizeof(double) * P->d * P->d);
+    return OR_OK;
 }
 
 void or_destroy(void *vp)
@@ -239,7 +251,15 @@ static double varcoef(const or_problem *P, const double *x)
  *   with diagonal drift): (L p)_j = sum_i (F_{j+1/2} - F_{j-1/2}) / h_i
  *               + (sigma^2/2)(2 p_j - p_{j-e_i} - p_{j+e_i}) / h_i^2,
  *               donor-cell flux F_{j+1/2} = v+ p_j + v- p_{j+e_i},
- *               face velocity v = -theta x_{j+1/2}.                        */
+ *               face velocity v = -theta x_{j+1/2}.
+ *   linear SDE (Eq. "sde_fokker_planck", dX = A X dt + sigma dW, H = 2 sigma
+ *   D sigma^T): L p = sum_i d_i((A x)_i p) - (1/2) sum_ij H_ij d_i d_j p:
+ *               drift as the donor-cell flux above with face velocity
+ *               v = (A x)_i at the face x_{j+1/2 e_i}; diagonal diffusion
+ *               (H_ii / 2)(2 p_j - p_{j-e_i} - p_{j+e_i}) / h_i^2; for i < k
+ *               the mixed term -((H_ik + H_ki) / 2) (p_{++} - p_{+-} - p_{-+}
+ *               + p_{--}) / (4 h_i h_k) over the four diagonal neighbours
+ *               j +- e_i +- e_k (zero outside the grid).                   */
 static void apply_grid(const or_problem *P, int g, double dt, const double *p, double *q)
 {
     geom G = grid_geom(P, g);
@@ -263,12 +283,33 @@ static void apply_grid(const or_problem *P, int g, double dt, const double *p, d
                 xf[i] = x[i] - 0.5 * h;
                 double am = varcoef(P, xf);
                 Lp += (ap * (p[j] - pp) + am * (p[j] - pm)) / (h * h);
-            } else {
+            } else if (P->op == OR_OU) {
                 double vp = -P->theta * (x[i] + 0.5 * h);
                 double vm = -P->theta * (x[i] - 0.5 * h);
                 double Fp = fmax(vp, 0.0) * p[j] + fmin(vp, 0.0) * pp;
                 double Fm = fmax(vm, 0.0) * pm + fmin(vm, 0.0) * p[j];
                 Lp += (Fp - Fm) / h + 0.5 * P->sigma * P->sigma * (2.0 * p[j] - pm - pp) / (h * h);
+            } else {
+                /* face velocities (A x)_i at x -+ h/2 e_i */
+                double ax = 0.0;
+                for (int k = 0; k < G.d; ++k) ax += P->sde_A[i * G.d + k] * x[k];
+                double vp = ax + 0.5 * h * P->sde_A[i * G.d + i];
+                double vm = ax - 0.5 * h * P->sde_A[i * G.d + i];
+                double Fp = fmax(vp, 0.0) * p[j] + fmin(vp, 0.0) * pp;
+                double Fm = fmax(vm, 0.0) * pm + fmin(vm, 0.0) * p[j];
+                Lp += (Fp - Fm) / h + 0.5 * P->sde_H[i * G.d + i] * (2.0 * p[j] - pm - pp) / (h * h);
+                for (int k = i + 1; k < G.d; ++k) {
+                    double hik = 0.5 * (P->sde_H[i * G.d + k] + P->sde_H[k * G.d + i]);
+                    if (hik == 0.0) continue;
+                    double corner[4];  /* (+,+) (+,-) (-,+) (-,-) in (i, k) */
+                    for (int q2 = 0; q2 < 4; ++q2) {
+                        int si = (q2 < 2) ? 1 : -1, sk = (q2 % 2 == 0) ? 1 : -1;
+                        long long ci = c[i] + si, ck = c[k] + sk;
+                        corner[q2] = (ci >= 0 && ci < G.N[i] && ck >= 0 && ck < G.N[k])
+                                         ? p[j + si * G.S[i] + sk * G.S[k]] : 0.0;
+                    }
+                    Lp -= hik * (corner[0] - corner[1] - corner[2] + corner[3]) / (4.0 * h * G.h[k]);
+                }
             }
         }
         q[j] = p[j] + dt * Lp;
@@ -378,8 +419,8 @@ static int phi_grid(const or_problem *P, int g, double dt, const double *u_prev,
     double *b = malloc(sizeof(double) * n);
     for (long long j = 0; j < n; ++j) b[j] = u_prev[j] + (f ? dt * f[j] : 0.0);
     if (u_next != u_prev) memcpy(u_next, u_prev, sizeof(double) * n);
-    int st = (P->op == OR_OU) ? bicgstab_grid(P, g, dt, b, u_next, rtol, maxit, iters)
-                              : cg_grid(P, g, dt, b, u_next, rtol, maxit, iters);
+    int st = (P->op == OR_OU || P->op == OR_LSDE) ? bicgstab_grid(P, g, dt, b, u_next, rtol, maxit, iters)
+                                                   : cg_grid(P, g, dt, b, u_next, rtol, maxit, iters);
     free(b);
     return st;
 }
@@ -1080,7 +1121,11 @@ static double manufactured(const or_problem *P, const double *x, double t, int f
  * kind 1: product Gaussian, params = [mean_1..mean_d, std_1..std_d]:
  *         u0(x) = prod_i exp(-(x_i - mean_i)^2 / (2 std_i^2)) / (std_i sqrt(2 pi))
  * kind 2: the manufactured solution u*(x, t) of the heat experiment, params = [t]
- * kind 3: its forcing f(x, t) = d(u^*)/dt - Laplace u*, params = [t]          */
+ * kind 3: its forcing f(x, t) = d(u^*)/dt - Laplace u*, params = [t]
+ * kind 4: normal density with mean M and covariance C (the law of the
+ *         linear SDE, Eq. "sde_analytical_solution"), params = [M (d), C (d x d,
+ *         row major)]: (2 pi)^{-d/2} det(C)^{-1/2} exp(-(x - M)^T C^{-1} (x - M) / 2),
+ *         evaluated with the Cholesky factor C = R R^T                           */
 int or_initial(void *vp, int kind, const double *params, int nparams, double *out)
 {
     or_problem *P = (or_problem *)vp;
@@ -1092,8 +1137,27 @@ int or_initial(void *vp, int kind, const double *params, int nparams, double *ou
         if (nparams < 2 * d) return OR_EINVAL;
     } else if (kind == 2 || kind == 3) {
         if (nparams < 1) return OR_EINVAL;
+    } else if (kind == 4) {
+        if (nparams < d + d * d) return OR_EINVAL;
     } else {
         return OR_EINVAL;
+    }
+    double R[OR_MAXD * OR_MAXD] = {0.0}, logdet = 0.0;
+    if (kind == 4) {
+        const double *C = params + d;
+        for (int i = 0; i < d; ++i) {
+            for (int k = 0; k <= i; ++k) {
+                double v = C[i * d + k];
+                for (int q = 0; q < k; ++q) v -= R[i * d + q] * R[k * d + q];
+                if (i == k) {
+                    if (!(v > 0.0)) return OR_EINVAL;
+                    R[i * d + i] = sqrt(v);
+                    logdet += log(R[i * d + i]);
+                } else {
+                    R[i * d + k] = v / R[k * d + k];
+                }
+            }
+        }
     }
     for (int g = 0; g < P->G; ++g) {
         geom G = grid_geom(P, g);
@@ -1118,6 +1182,15 @@ int or_initial(void *vp, int kind, const double *params, int nparams, double *ou
                     double z = (x[i] - params[i]) / params[d + i];
                     v *= exp(-0.5 * z * z) / (params[d + i] * sqrt(2.0 * M_PI));
                 }
+            } else if (kind == 4) {
+                double z[OR_MAXD], q = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    double r = x[i] - params[i];
+                    for (int k = 0; k < i; ++k) r -= R[i * d + k] * z[k];
+                    z[i] = r / R[i * d + i];
+                    q += z[i] * z[i];
+                }
+                v = exp(-0.5 * q - logdet - 0.5 * d * log(2.0 * M_PI));
             } else {
                 v = manufactured(P, x, params[0], kind == 3);
             }
