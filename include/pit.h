@@ -63,9 +63,16 @@ typedef enum {
     PIT_OP_HEAT = 0,    /* L = -Laplace (Sec. 4.2, Eq. "heat_equation"), (2d+1)-point stencil */
     PIT_OP_VARHEAT = 1, /* L = -div(a grad), a = 1 + A sin(2 pi x1) cos(2 pi x2) sin(2 pi x3)...
                            evaluated at face midpoints; symmetric, CG                        */
-    PIT_OP_OU = 2       /* Fokker-Planck operator of dX = -theta X dt + sigma dW
+    PIT_OP_OU = 2,      /* Fokker-Planck operator of dX = -theta X dt + sigma dW
                            (Sec. 4.4, Eq. "sde_fokker_planck" with diagonal drift):
                            donor-cell upwind drift + central diffusion; BiCGStab            */
+    PIT_OP_LSDE = 3     /* Fokker-Planck operator of the linear SDE dX = A X dt + sigma dW
+                           (Sec. 4.4, Eqs. "sde", "sde_fokker_planck"), A = drift (d x d),
+                           H = 2 sigma D sigma^T = diffusion (d x d):
+                           L p = sum_i d_i((A x)_i p) - (1/2) sum_ij H_ij d_i d_j p, donor-cell
+                           drift with face velocity (A x)_i, central diagonal diffusion, and
+                           for i != k the four-point mixed stencil
+                           (p_{++} - p_{+-} - p_{-+} + p_{--}) / (4 h_i h_k); BiCGStab      */
 } pit_op;
 
 typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2, PIT_PREC_MIXED_PAIR = 3 } pit_prec;
@@ -81,8 +88,9 @@ typedef enum {
 
 /* Problem: d-dimensional box [lo, hi], zero Dirichlet values, combination
  * level level_n (the paper's L) with minimum level level0 (the paper's L0,
- * Sec. 2.1.1), operator op with parameters theta, sigma (OU) and vamp
- * (variable-coefficient amplitude A). */
+ * Sec. 2.1.1), operator op with parameters theta, sigma (OU), vamp
+ * (variable-coefficient amplitude A), and drift, diffusion (linear SDE: the
+ * d x d matrices A and H, row major, first d*d entries used). */
 typedef struct {
     int d;
     int level_n;
@@ -93,6 +101,8 @@ typedef struct {
     double theta;
     double sigma;
     double vamp;
+    double drift[PIT_MAX_DIM * PIT_MAX_DIM];
+    double diffusion[PIT_MAX_DIM * PIT_MAX_DIM];
 } pit_problem_desc;
 
 /* Options of one batched backward-Euler solve.
@@ -309,6 +319,9 @@ pit_status pit_problem_info(pit_problem_t p, int *n_grids, long long *n_total, i
  *         prod_i sin(pi (x_i - lo_i) / (hi_i - lo_i)).
  * kind 3: its forcing for the heat operator, params = [t]:
  *         f(x, t) = du*(x, t)/dt - Laplace u*(x, t).
+ * kind 4: normal density with mean M and covariance C (the law of the linear
+ *         SDE, Eq. "sde_analytical_solution"), params = [M (d), C (d x d, row
+ *         major, symmetric positive definite)].
  * params: host, n_params doubles.  u0: host or device, n_total doubles. */
 pit_status pit_sample_initial(pit_problem_t p, int kind, const double *params, int n_params, double *u0);
 

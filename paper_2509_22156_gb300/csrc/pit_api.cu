@@ -296,7 +296,7 @@ size_t grid_smem_bytes(const pit_problem *P, int prec, int g)
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
-    if (prec == PAIR && P->desc.op == PIT_OP_OU)
+    if (prec == PAIR && (P->desc.op == PIT_OP_OU || P->desc.op == PIT_OP_LSDE))
         return fail(PIT_ERR_UNSUPPORTED, "the pair precision form is implemented for the symmetric operators only");
     std::vector<int> order(P->G);
     for (int g = 0; g < P->G; ++g) order[g] = g;
@@ -692,7 +692,11 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     if (d < 1 || d > PIT_MAX_DIM) return fail(PIT_ERR_INVALID_ARG, "d = %d outside 1..%d", d, PIT_MAX_DIM);
     if (desc->level0 < 1 || desc->level_n < desc->level0 || desc->level_n > 30)
         return fail(PIT_ERR_INVALID_ARG, "levels must satisfy 1 <= level0 <= level_n <= 30");
-    if (desc->op < PIT_OP_HEAT || desc->op > PIT_OP_OU) return fail(PIT_ERR_INVALID_ARG, "unknown operator %d", desc->op);
+    if (desc->op < PIT_OP_HEAT || desc->op > PIT_OP_LSDE) return fail(PIT_ERR_INVALID_ARG, "unknown operator %d", desc->op);
+    if (desc->op == PIT_OP_LSDE)
+        for (int k = 0; k < d * d; ++k)
+            if (!std::isfinite(desc->drift[k]) || !std::isfinite(desc->diffusion[k]))
+                return fail(PIT_ERR_INVALID_ARG, "drift and diffusion matrices must be finite");
     for (int i = 0; i < d; ++i)
         if (!(desc->hi[i] > desc->lo[i])) return fail(PIT_ERR_INVALID_ARG, "empty box on axis %d", i);
     int ndev = 0;
@@ -753,6 +757,11 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     P->op.theta = desc->theta;
     P->op.sigma = desc->sigma;
     P->op.vamp = desc->vamp;
+    if (desc->op == PIT_OP_LSDE)
+        for (int k = 0; k < d * d; ++k) {
+            P->op.A[k] = desc->drift[k];
+            P->op.H[k] = desc->diffusion[k];
+        }
 
     auto bail = [&](pit_status st) {
         pit_problem_destroy(P);
@@ -897,11 +906,37 @@ pit_status pit_sample_initial(pit_problem_t P, int kind, const double *params, i
             if (!(params[d + i] > 0.0)) return fail(PIT_ERR_INVALID_ARG, "std must be positive");
     } else if (kind == 2 || kind == 3) {
         if (n_params < 1 || !std::isfinite(params[0])) return fail(PIT_ERR_INVALID_ARG, "need the time t");
+    } else if (kind == 4) {
+        if (n_params < d + d * d) return fail(PIT_ERR_INVALID_ARG, "need d + d*d parameters");
     } else {
         return fail(PIT_ERR_INVALID_ARG, "unknown initial-value kind %d", kind);
     }
+    std::vector<double> prm(params, params + n_params);
+    if (kind == 4) {
+        // the kernel takes the mean, the Cholesky factor R of the covariance
+        // (C = R R^T, lower, row major) and log det R
+        const double *C = params + d;
+        std::vector<double> R((size_t)d * d, 0.0);
+        double logdet = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int k = 0; k <= i; ++k) {
+                double v = C[i * d + k];
+                for (int q = 0; q < k; ++q) v -= R[i * d + q] * R[k * d + q];
+                if (i == k) {
+                    if (!(v > 0.0)) return fail(PIT_ERR_INVALID_ARG, "the covariance is not positive definite");
+                    R[i * d + i] = sqrt(v);
+                    logdet += log(R[i * d + i]);
+                } else {
+                    R[i * d + k] = v / R[k * d + k];
+                }
+            }
+        prm.assign(params, params + d);
+        prm.insert(prm.end(), R.begin(), R.end());
+        prm.push_back(logdet);
+        n_params = (int)prm.size();
+    }
     CU(P->w_prm.ensure(sizeof(double) * n_params));
-    CU(cudaMemcpyAsync(P->w_prm.p, params, sizeof(double) * n_params, cudaMemcpyHostToDevice, P->stream));
+    CU(cudaMemcpyAsync(P->w_prm.p, prm.data(), sizeof(double) * n_params, cudaMemcpyHostToDevice, P->stream));
     const bool dev = ptr_is_device(u0);
     double *target = u0;
     if (!dev) {

@@ -38,10 +38,20 @@ __global__ void apply_kernel(const GridInfo *grids, int G, long long ntot, doubl
                 const double am = faces[(GI.off + j) * (2 * d) + 2 * i];
                 const double ap = faces[(GI.off + j) * (2 * d) + 2 * i + 1];
                 dd = (am + ap) * ih2; dm = -am * ih2; dp = -ap * ih2;
-            } else {
+            } else if (op.op == PIT_OP_OU) {
                 const double x = op.lo[i] + (double)(c + 1) * h;
                 const double vp = -op.theta * (x + 0.5 * h), vm = -op.theta * (x - 0.5 * h);
                 const double s2 = 0.5 * op.sigma * op.sigma * ih2;
+                dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
+                dm = -fmax(vm, 0.0) / h - s2;
+                dp = fmin(vp, 0.0) / h - s2;
+            } else {
+                // linear SDE: face velocities (A x)_i at x -+ h/2 e_i, diagonal diffusion
+                double ax = 0.0;
+                for (int k = 0; k < d; ++k)
+                    ax += op.A[i * d + k] * (op.lo[k] + (double)(axis_coord(GI, j, k) + 1) * GI.h[k]);
+                const double vp = ax + 0.5 * h * op.A[i * d + i], vm = ax - 0.5 * h * op.A[i * d + i];
+                const double s2 = 0.5 * op.H[i * d + i] * ih2;
                 dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
                 dm = -fmax(vm, 0.0) / h - s2;
                 dp = fmin(vp, 0.0) / h - s2;
@@ -49,6 +59,22 @@ __global__ void apply_kernel(const GridInfo *grids, int G, long long ntot, doubl
             diag += dt * dd;
             if (c > 0) s += dt * dm * pg[j - GI.S[i]];
             if (c < GI.N[i] - 1) s += dt * dp * pg[j + GI.S[i]];
+        }
+        if (op.op == PIT_OP_LSDE) {
+            // mixed derivatives: -(H_ik + H_ki)/2 (p_{++} - p_{+-} - p_{-+} + p_{--}) / (4 h_i h_k)
+            for (int i = 0; i < d; ++i) {
+                const int ci = axis_coord(GI, j, i);
+                for (int k = i + 1; k < d; ++k) {
+                    const int ck = axis_coord(GI, j, k);
+                    const double w = -dt * 0.5 * (op.H[i * d + k] + op.H[k * d + i]) / (4.0 * GI.h[i] * GI.h[k]);
+                    double c4 = 0.0;
+                    if (ci < GI.N[i] - 1 && ck < GI.N[k] - 1) c4 += pg[j + GI.S[i] + GI.S[k]];
+                    if (ci < GI.N[i] - 1 && ck > 0) c4 -= pg[j + GI.S[i] - GI.S[k]];
+                    if (ci > 0 && ck < GI.N[k] - 1) c4 -= pg[j - GI.S[i] + GI.S[k]];
+                    if (ci > 0 && ck > 0) c4 += pg[j - GI.S[i] - GI.S[k]];
+                    s += w * c4;
+                }
+            }
         }
         qg[j] = diag * pg[j] + s;
     }
@@ -82,6 +108,17 @@ __global__ void initial_kernel(const GridInfo *grids, OpParams op, const double 
                 for (int i = 0; i < d; ++i) prod *= sin(M_PI * pk[1 + i] * (x[i] - op.lo[i]) / (hi[i] - op.lo[i]));
                 v += prod;
             }
+        } else if (kind == 4) {
+            // normal density with the covariance's Cholesky factor R (prm[d..]) and
+            // log det R (prm[d + d*d]), prepared on the host
+            double z[PIT_D], q = 0.0;
+            for (int i = 0; i < d; ++i) {
+                double r = x[i] - prm[i];
+                for (int k = 0; k < i; ++k) r -= prm[d + i * d + k] * z[k];
+                z[i] = r / prm[d + i * d + i];
+                q += z[i] * z[i];
+            }
+            v = exp(-0.5 * q - prm[d + d * d] - 0.5 * d * log(2.0 * M_PI));
         } else if (kind == 1) {
             v = 1.0;
             for (int i = 0; i < d; ++i) {

@@ -28,6 +28,8 @@ struct OpParams {
     int d;
     double lo[PIT_D];
     double theta, sigma, vamp;
+    double A[PIT_D * PIT_D];  // linear SDE: drift matrix (row major, d x d)
+    double H[PIT_D * PIT_D];  // linear SDE: H = 2 sigma D sigma^T (row major, d x d)
 };
 
 // Global counters filled by the backward-Euler kernels (one atomic per item).

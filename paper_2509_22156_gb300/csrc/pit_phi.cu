@@ -29,6 +29,7 @@ cudaError_t phi_kernels_init(size_t max_smem)
     cudaError_t (*inits[])(int) = {steps_init_heat_fp64,    steps_init_heat_mixed,    steps_init_heat_fp32,
                                    steps_init_varheat_fp64, steps_init_varheat_mixed, steps_init_varheat_fp32,
                                    steps_init_ou_fp64,      steps_init_ou_mixed,      steps_init_ou_fp32,
+                                   steps_init_lsde_fp64,    steps_init_lsde_mixed,    steps_init_lsde_fp32,
                                    steps_init_heat_pair,    steps_init_varheat_pair};
     for (auto f : inits)
         if (e == cudaSuccess) e = f(bytes);
@@ -60,6 +61,7 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
     case PIT_OP_HEAT: PIT_BY_PREC(heat)
     case PIT_OP_VARHEAT: PIT_BY_PREC(varheat)
     case PIT_OP_OU: PIT_BY_PREC(ou)
+    case PIT_OP_LSDE: PIT_BY_PREC(lsde)
 #undef PIT_BY_PREC
     default: return cudaErrorInvalidValue;
     }

@@ -59,6 +59,10 @@ namespace pit {
 //   varheat L p = sum_i [a_+ (p_j - p_+) + a_- (p_j - p_-)] / h_i^2
 //   OU      L p = sum_i (F_+ - F_-) / h_i + (sigma^2/2)(2 p_j - p_- - p_+) / h_i^2,
 //           F_+ = max(v_+,0) p_j + min(v_+,0) p_+,  v_+ = -theta (x_i + h_i/2).
+//   LSDE    the same donor-cell flux with the face velocity (A x)_i of the
+//           linear SDE dX = A X dt + sigma dW (Sec. 4.4) and diffusion
+//           (H_ii/2)(2 p_j - p_- - p_+) / h_i^2; its mixed-derivative terms
+//           (i != k) are constant per grid and applied by TabSt<.., true>.
 template <int D>
 __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, const double *faces, int j,
                                         double dt, double &diag, double *cm, double *cp)
@@ -76,11 +80,22 @@ __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, c
             const double am = faces[(G.off + j) * (2 * D) + 2 * i];
             const double ap = faces[(G.off + j) * (2 * D) + 2 * i + 1];
             dd = (am + ap) * ih2; dm = -am * ih2; dp = -ap * ih2;
-        } else {
+        } else if (op.op == PIT_OP_OU) {
             const double x = op.lo[i] + (double)(c + 1) * h;
             const double vp = -op.theta * (x + 0.5 * h);
             const double vm = -op.theta * (x - 0.5 * h);
             const double s2 = 0.5 * op.sigma * op.sigma * ih2;
+            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
+            dm = -fmax(vm, 0.0) / h - s2;
+            dp = fmin(vp, 0.0) / h - s2;
+        } else {
+            // face velocities (A x)_i at x -+ h/2 e_i
+            double ax = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) ax += op.A[i * D + k] * (op.lo[k] + (double)((j / G.S[k]) % G.N[k] + 1) * G.h[k]);
+            const double vp = ax + 0.5 * h * op.A[i * D + i];
+            const double vm = ax - 0.5 * h * op.A[i * D + i];
+            const double s2 = 0.5 * op.H[i * D + i] * ih2;
             dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
             dm = -fmax(vm, 0.0) / h - s2;
             dp = fmin(vp, 0.0) / h - s2;
@@ -115,13 +130,18 @@ struct HeatSt {
 
 // Variable-coefficient stencil from a per-node table in shared memory
 // (structure of arrays: tab[k*ld + j], k = 0 diagonal, 1+2i minus, 2+2i plus;
-// zero coefficients towards the boundary).
-template <typename T, int D>
+// zero coefficients towards the boundary).  CROSS adds the mixed-derivative
+// terms of the linear-SDE operator, constant per grid: for every axis pair
+// i < k, cr[q] (p_{++} - p_{+-} - p_{-+} + p_{--}) over the four diagonal
+// neighbours j +- e_i +- e_k, a corner outside the grid reading zero.
+template <typename T, int D, bool CROSS = false>
 struct TabSt {
+    static constexpr int NP = D * (D - 1) / 2;
     const uint16_t *mask;
     const T *tab;
     int ld;
     int S[D];
+    T cr[NP > 0 ? NP : 1];
     __device__ __forceinline__ T operator()(const T *p, int j) const
     {
         const unsigned mk = mask[j];
@@ -131,6 +151,23 @@ struct TabSt {
             const int jm = ((mk >> (2 * i)) & 1u) ? j - S[i] : j;
             const int jp = ((mk >> (2 * i + 1)) & 1u) ? j + S[i] : j;
             s += tab[(1 + 2 * i) * ld + j] * p[jm] + tab[(2 + 2 * i) * ld + j] * p[jp];
+        }
+        if constexpr (CROSS && NP > 0) {
+            int q = 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const bool im = (mk >> (2 * i)) & 1u, ip = (mk >> (2 * i + 1)) & 1u;
+#pragma unroll
+                for (int k = i + 1; k < D; ++k, ++q) {
+                    const bool km = (mk >> (2 * k)) & 1u, kp = (mk >> (2 * k + 1)) & 1u;
+                    T c = T(0);
+                    if (ip && kp) c += p[j + S[i] + S[k]];
+                    if (ip && km) c -= p[j + S[i] - S[k]];
+                    if (im && kp) c -= p[j - S[i] + S[k]];
+                    if (im && km) c += p[j - S[i] - S[k]];
+                    s += cr[q] * c;
+                }
+            }
         }
         return s;
     }
@@ -796,7 +833,7 @@ __host__ __device__ inline bool line_pc_form(int op, int prec, bool xg)
 }
 __host__ __device__ inline int krylov_vecs(int op, int prec, bool xg = false)
 {
-    if (op == PIT_OP_OU) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e or x)
+    if (op == PIT_OP_OU || op == PIT_OP_LSDE) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e or x)
     if (line_pc_form(op, prec, xg)) return 6;           // r p s w u (+ e or x): u for the line preconditioner
     return prec == PLAIN ? 4 : 5;                        // r p s w (+ e or x)
 }
@@ -832,7 +869,9 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
     static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE || PREC == PAIR, "unknown precision form");
-    static_assert(PREC != PAIR || OP != PIT_OP_OU, "the pair form is for the symmetric operators");
+    static_assert(PREC != PAIR || (OP != PIT_OP_OU && OP != PIT_OP_LSDE), "the pair form is for the symmetric operators");
+    constexpr bool DRIFT = (OP == PIT_OP_OU || OP == PIT_OP_LSDE);  // non-symmetric: BiCGStab
+    constexpr bool CROSS = (OP == PIT_OP_LSDE);                      // mixed-derivative terms
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
     const int b = item % a.n_batch;
@@ -845,8 +884,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     const int ld = (n + 3) & ~3;
     const double dt = a.dt;
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
-    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (OP == PIT_OP_OU ? 5 : 4) : 2) + K;
-    constexpr int NKV = (OP == PIT_OP_OU) ? (PREC == PLAIN ? 5 : 6)
+    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (DRIFT ? 5 : 4) : 2) + K;
+    constexpr int NKV = DRIFT ? (PREC == PLAIN ? 5 : 6)
                                           : (PREC == PLAIN ? 4 : (OP == PIT_OP_HEAT && !XG ? 6 : 5));
     constexpr int NDV = (PREC == MIXED && !XG) ? 1 : 0;  // dv in shared memory
     constexpr int NF32 = (PREC != PLAIN) ? NKV + NDV + K : 0;
@@ -923,12 +962,23 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     // stencils in FP64 and in the working precision
     HeatSt<double, D> H64;
     HeatSt<T, D> HT;
-    TabSt<double, D> T64;
-    TabSt<float, D> T32;
+    TabSt<double, D, CROSS> T64;
+    TabSt<float, D, CROSS> T32;
     H64.mask = HT.mask = T64.mask = T32.mask = mask;
     T64.tab = tab64;
     T32.tab = tab32;
     T64.ld = T32.ld = ld;
+    if constexpr (CROSS) {
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = i + 1; k < D; ++k, ++q) {
+                const double c = -dt * 0.5 * (a.op.H[i * D + k] + a.op.H[k * D + i]) / (4.0 * GI.h[i] * GI.h[k]);
+                T64.cr[q] = c;
+                T32.cr[q] = (float)c;
+            }
+    }
     {
         double diag = 1.0;
 #pragma unroll
@@ -1041,7 +1091,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             ++passes;
             const double stop2 = a.rtol * a.rtol * bb[0];
             int st, k;
-            if constexpr (OP == PIT_OP_OU) k = bicgstab_core<double, double>(T64, n, x, r, q1, q2, q3, q4, R64, stop2, a.maxit, st);
+            if constexpr (DRIFT) k = bicgstab_core<double, double>(T64, n, x, r, q1, q2, q3, q4, R64, stop2, a.maxit, st);
             else if constexpr (OP == PIT_OP_HEAT) k = cg_core<double, double>(H64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
             else k = cg_core<double, double>(T64, n, x, r, q1, q2, q3, R64, stop2, a.maxit, st);
             iters += k;
@@ -1094,7 +1144,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             const float rt = (float)a.rtol;
             const float stop2 = rt * rt * bb[0];
             int st, k;
-            if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, xs, r, q1, q2, q3, q4, R32, stop2, a.maxit, st);
+            if constexpr (DRIFT) k = bicgstab_core<float, float>(T32, n, xs, r, q1, q2, q3, q4, R32, stop2, a.maxit, st);
             else if constexpr (OP == PIT_OP_HEAT) {
                 if (use_pc) k = pcg_core<float, float>(HT, LM, n, xs, r, q4, q1, q2, q3, R32, stop2, a.maxit, st);
                 else k = cg_core<float, float>(HT, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
@@ -1318,7 +1368,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             if (have_r0) {
                 // r0 = x_{s-1} - A x_{s-1}, computed by the last check of the
                 // previous step into wv (OU: tv)
-                if constexpr (OP == PIT_OP_OU) { float *t_ = rv; rv = tv; tv = t_; }
+                if constexpr (DRIFT) { float *t_ = rv; rv = tv; tv = t_; }
                 else { float *t_ = rv; rv = wv; wv = t_; }
                 rn2 = rn0_c;
                 bb = bb_c;
@@ -1352,7 +1402,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     if (rn2 != rn2) st_step = PIT_ERR_NONFINITE;
                     else if (carry_ok && pass == 0) {
                         // x unchanged: its residual is the next step's r0
-                        if constexpr (OP == PIT_OP_OU) { float *t_ = rv; rv = tv; tv = t_; }
+                        if constexpr (DRIFT) { float *t_ = rv; rv = tv; tv = t_; }
                         else { float *t_ = rv; rv = wv; wv = t_; }
                         rn0_c = rn2;
                         bb_c = bb;
@@ -1376,7 +1426,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     e[j] = 0.0f;
                 }
                 int st, k;
-                if constexpr (OP == PIT_OP_OU) k = bicgstab_core<float, float>(T32, n, e, rv, pv, sv, wv, tv, R32, stop32, a.maxit, st);
+                if constexpr (DRIFT) k = bicgstab_core<float, float>(T32, n, e, rv, pv, sv, wv, tv, R32, stop32, a.maxit, st);
                 else if constexpr (OP == PIT_OP_HEAT) {
                     if (use_pc) k = pcg_core<float, float>(HT, LM, n, e, rv, f32 + 5 * ld, pv, sv, wv, R32, stop32, a.maxit, st);
                     else k = cg_core<float, float>(HT, n, e, rv, pv, sv, wv, R32, stop32, a.maxit, st);
@@ -1401,7 +1451,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 // step's r0 = x - A x = r + (x - b) work on the FP32 copies
                 // (their squared norms accumulated in FP32), as does ||x||^2,
                 // the next right-hand side's norm
-                float *cv = (OP == PIT_OP_OU) ? tv : wv;
+                float *cv = DRIFT ? tv : wv;
                 float accf[3] = {0.0f, 0.0f, 0.0f};
                 // (unrolled: independent nodes keep several FP64 stencil
                 // chains in flight, the FP64 latency is long on GB300)
@@ -1488,6 +1538,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 PIT_STEPS_DECL(heat, fp64) PIT_STEPS_DECL(heat, mixed) PIT_STEPS_DECL(heat, fp32)
 PIT_STEPS_DECL(varheat, fp64) PIT_STEPS_DECL(varheat, mixed) PIT_STEPS_DECL(varheat, fp32)
 PIT_STEPS_DECL(ou, fp64) PIT_STEPS_DECL(ou, mixed) PIT_STEPS_DECL(ou, fp32)
+PIT_STEPS_DECL(lsde, fp64) PIT_STEPS_DECL(lsde, mixed) PIT_STEPS_DECL(lsde, fp32)
 PIT_STEPS_DECL(heat, pair) PIT_STEPS_DECL(varheat, pair)
 
 // Instantiates the attribute setter and launcher of one operator and form for
