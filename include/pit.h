@@ -207,6 +207,15 @@ typedef struct {
                              each fine step n, all with f_n; the coarse step dT = m dt is
                              common.  Grids with different tmul run as separate lanes, which
                              needs the correction form with the implicit coarse step        */
+    int global_every;     /* 0: MGRIT on every subproblem independently (CTMGRIT^loc, Alg. 3).
+                             r >= 1: global MGRIT (Sec. 3.4: MGRIT on the whole combination
+                             problem): the propagator of r fine steps is Phi^r o Q, Q the
+                             recombination (pit_recombine), so all grids are coupled every r
+                             steps and iterate together until the largest C-point residual
+                             of all grids meets tol; its fixed point is Alg. 1 with a
+                             recombination step every r fine steps.  r must divide m; two
+                             levels, F-relaxation, implicit coarse step Phi_c o Q in the
+                             correction form, no tmul or recomb                              */
 } pit_mgrit_opts;
 
 typedef struct {

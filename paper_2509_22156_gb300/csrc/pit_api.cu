@@ -1163,19 +1163,20 @@ pit_status recomb_plan(pit_problem *P)
     CU(up(P->rc_list_off, list_off));
     CU(up(P->rc_list, list));
     CU(up(P->rc_lookup, lookup));
-    CU(P->rc_H.ensure(sizeof(double) * P->ntot));
-    CU(P->rc_S.ensure(sizeof(double) * blk_off.back()));
     P->rc = RecombPlan{n_blk, R, blk_off.back(), P->rc_lam, P->rc_off, P->rc_list_off, P->rc_list, P->rc_lookup};
     P->rc_ready = true;
     return PIT_OK;
 }
 
-// out = Q u on the problem's stream (out may alias u).
-pit_status recombine(pit_problem *P, const double *u, double *out)
+// out_b = Q u_b for nb consecutive states on the problem's stream (out may alias u).
+pit_status recombine(pit_problem *P, const double *u, double *out, int nb = 1)
 {
     TRY(recomb_plan(P));
+    CU(P->rc_H.ensure(sizeof(double) * P->ntot * (size_t)nb));
+    CU(P->rc_S.ensure(sizeof(double) * P->rc.n_sparse * (size_t)nb));
     ProfScope ps(P, 3);
-    CU(launch_recombine(P->rc, P->desc.d, P->d_grids, P->d_coef, P->G, u, P->rc_H.d(), P->rc_S.d(), out, P->stream));
+    CU(launch_recombine(P->rc, P->desc.d, P->d_grids, P->d_coef, P->G, P->ntot, nb, u, P->rc_H.d(), P->rc_S.d(), out,
+                        P->stream));
     count_kernels(P, 3, 3);
     return PIT_OK;
 }
@@ -1822,6 +1823,140 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
 }
 }  // namespace
 
+// Global MGRIT (Sec. 3.4: MGRIT applied to the whole combination-technique
+// problem instead of each subproblem): the propagator of one block of r fine
+// steps is Psi = Phi^r o Q, the recombination Q (Eq. "overall_combination_
+// operator") followed by r backward-Euler steps on every grid, so that the
+// grids are coupled every r steps and iterate together.  Two levels, F-
+// relaxation, coarse problem for the correction with Psi_c = Phi_c o Q, one
+// stopping rule over all grids (the largest C-point residual).  Its fixed
+// point is the time-sequential combination method (Alg. 1) with a
+// recombination step every r fine steps.
+namespace {
+pit_status mgrit_global(pit_problem_t P, const double *u0, const pit_mgrit_opts *o, double *uT,
+                        pit_mgrit_stats *stats)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    const int r = o->global_every, m = o->m;
+    if (o->levels != 2 || o->relax != PIT_RELAX_F || o->fas || o->coarse != PIT_COARSE_IMPLICIT || o->tmul ||
+        o->recomb)
+        return fail(PIT_ERR_UNSUPPORTED, "global MGRIT runs two levels, F-relaxation, the implicit coarse step in the "
+                                         "correction form, without per-grid partitions or recombination intervals");
+    if (r < 1 || m % r != 0) return fail(PIT_ERR_INVALID_ARG, "global_every must divide m");
+    if (o->nsteps % m != 0) return fail(PIT_ERR_INVALID_ARG, "nsteps must be a multiple of m");
+    const int G = P->G, Nc = o->nsteps / m;
+    const long long nt = P->ntot;
+    const size_t vb = sizeof(double) * nt;
+    const double dt = (o->t1 - o->t0) / o->nsteps;
+    CU(P->m_U.ensure(vb * (Nc + 1)));
+    CU(P->m_R.ensure(vb * (size_t)Nc * 2));  // relaxation work states (ping-pong)
+    CU(P->m_GC.ensure(vb * Nc));
+    CU(P->m_E.ensure(vb * (Nc + 1)));
+    CU(P->m_res.ensure(sizeof(double) * G * Nc));
+    CU(P->m_Z.ensure(vb));
+    double *U = P->m_U.d(), *W0 = P->m_R.d(), *W1 = W0 + (long long)Nc * nt, *GC = P->m_GC.d(), *E = P->m_E.d();
+    double *res = P->m_res.d(), *Z = P->m_Z.d();
+    P->h_res.resize((size_t)G * Nc);
+    const double *src;
+    TRY(stage_in(P, P->w_in, u0, nt, &src));
+    TRY(reset_stats(P));
+    // initial guess: u_0 at every C-point, or one sweep of Psi_c
+    for (int j = 0; j <= Nc; ++j)
+        CU(cudaMemcpyAsync(U + (long long)j * nt, src, vb, cudaMemcpyDeviceToDevice, P->stream));
+    auto coarse_step = [&](const double *in, const double *g, double *out) -> pit_status {
+        TRY(recombine(P, in, Z));
+        StepCall c;
+        c.dt = dt * m;
+        c.nb = 1;
+        c.nsteps = 1;
+        c.in = Z;
+        c.is = nt;
+        c.g = g;
+        c.out_last = out;
+        c.ols = nt;
+        return run_steps(P, o->crs, c, nullptr);
+    };
+    if (o->init)
+        for (int j = 0; j < Nc; ++j) TRY(coarse_step(U + (long long)j * nt, nullptr, U + (long long)(j + 1) * nt));
+    CU(cudaMemsetAsync(E, 0, vb, P->stream));  // e_0 = 0
+    pit_mgrit_stats st;
+    memset(&st, 0, sizeof(st));
+    int it = 0;
+    bool conv = false;
+    while (it < o->maxit) {
+        // F-relaxation with Psi: per block, recombine all intervals' states,
+        // then r fine steps; the last block writes r_{j+1} = Psi^{m/r}(u_j) - u_{j+1}
+        const int nblk = m / r;
+        const double *in = U;
+        for (int q = 0; q < nblk; ++q) {
+            double *w = (q % 2 == 0) ? W0 : W1;
+            TRY(recombine(P, in, w, Nc));
+            StepCall c;
+            c.dt = dt;
+            c.nb = Nc;
+            c.nsteps = r;
+            c.in = w;
+            c.is = nt;
+            if (o->forcing) {
+                c.f = o->forcing + (long long)q * r * nt;
+                c.fs = (long long)m * nt;
+                c.fst = nt;
+            }
+            if (q + 1 < nblk) {
+                double *wo = (q % 2 == 0) ? W1 : W0;
+                c.out_last = wo;
+                c.ols = nt;
+                TRY(run_steps(P, o->fine, c, nullptr));
+                // the next block recombines the block's outputs in place
+                in = wo;
+                // (recombine reads wo into its own scratch, then writes w of the next block)
+            } else {
+                c.out_last = GC;
+                c.ols = nt;
+                c.h = U + nt;
+                c.hs = nt;
+                c.hscale = -1.0;
+                c.cmp = U + nt;
+                c.cs = nt;
+                c.norms = res;
+                TRY(run_steps(P, o->fine, c, nullptr));
+            }
+        }
+        CU(cudaMemcpyAsync(P->h_res.data(), res, sizeof(double) * G * Nc, cudaMemcpyDeviceToHost, P->stream));
+        // coarse correction: e_{j+1} = Phi_c(Q e_j) + r_{j+1}; u_{j+1} += e_{j+1}
+        for (int j = 0; j < Nc; ++j)
+            TRY(coarse_step(E + (long long)j * nt, GC + (long long)j * nt, E + (long long)(j + 1) * nt));
+        CU(launch_add_states(P->d_grids, G, nt, Nc, U + nt, E + nt, U + nt, nullptr, P->stream));
+        count_kernels(P, 3);
+        CU(cudaStreamSynchronize(P->stream));
+        double rmax = 0.0;
+        for (double v : P->h_res)
+            if (!(v <= rmax)) rmax = v;
+        if (it < PIT_MAX_HIST) st.res_hist[it] = rmax;
+        ++it;
+        if (!(rmax == rmax)) break;
+        if (rmax <= o->tol) {
+            conv = true;
+            break;
+        }
+    }
+    CU(cudaMemcpyAsync(uT, U + (long long)Nc * nt, vb, ptr_is_device(uT) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       P->stream));
+    DevStats ds;
+    TRY(read_stats(P, ds));
+    st.max_cycles = it;
+    st.n_converged = conv ? G : 0;
+    st.phi_items = (long long)ds.items;
+    st.krylov_iters = (long long)ds.sum_iters;
+    st.point_iters = (long long)ds.point_iters;
+    st.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = st;
+    TRY(status_of(ds));
+    if (!conv) return fail(PIT_ERR_NOCONV, "global MGRIT did not meet tol within %d cycles", it);
+    return PIT_OK;
+}
+}  // namespace
+
 // CTMGRIT^loc (Alg. 3).  recomb = 0: one MGRIT solve over [t0, t1], the
 // combination left to pit_combine.  recomb = s >= 1: the interval is split at
 // the recombination steps tau_k = t0 + k (t1 - t0) / s; before each of the s
@@ -1833,6 +1968,15 @@ extern "C" pit_status pit_mgrit_solve(pit_problem_t P, const double *u0, const p
 {
     if (!P || !u0 || !uT || !o) return fail(PIT_ERR_INVALID_ARG, "NULL argument");
     if (o->recomb < 0) return fail(PIT_ERR_INVALID_ARG, "recomb must be >= 0");
+    if (o->global_every < 0) return fail(PIT_ERR_INVALID_ARG, "global_every must be >= 0");
+    if (o->global_every > 0) {
+        TRY(check_solve_opts(&o->fine));
+        TRY(check_solve_opts(&o->crs));
+        if (o->m < 2 || o->nsteps < 1 || o->maxit < 1 || !(o->tol >= 0.0) || !(o->t1 > o->t0))
+            return fail(PIT_ERR_INVALID_ARG, "need m >= 2, nsteps >= 1, maxit >= 1, tol >= 0, t1 > t0");
+        if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
+        return mgrit_global(P, u0, o, uT, stats);
+    }
     if (o->recomb == 0) return mgrit_run(P, u0, o, uT, stats);
     auto t_start = std::chrono::steady_clock::now();
     const int s = o->recomb;

@@ -200,8 +200,10 @@ struct RecombPlan {
     const int *list;
     const int *lookup;
 };
-// out = Q u on every grid (out may alias u); H: n_total, S: n_sparse doubles of scratch.
+// out_b = Q u_b on every grid for nb consecutive states b (stride ntot; out
+// may alias u); H: nb x n_total, S: nb x n_sparse doubles of scratch.
 cudaError_t launch_recombine(const RecombPlan &R, int d, const GridInfo *grids, const double *coef, int G,
-                             const double *u, double *H, double *S, double *out, cudaStream_t s);
+                             long long ntot, int nb, const double *u, double *H, double *S, double *out,
+                             cudaStream_t s);
 
 }  // namespace pit

@@ -42,11 +42,14 @@ __device__ void hier_level(double *v, const GridInfo &G, int ax, int t, double s
 }
 
 template <int D>
-__global__ void hier_kernel(const GridInfo *grids, const double *coef, const double *u, double *H)
+__global__ void hier_kernel(const GridInfo *grids, const double *coef, int n_grids, long long ntot, const double *u,
+                            double *H)
 {
-    const GridInfo G = grids[blockIdx.x];
-    const double *src = u + G.off;
-    double *v = H + G.off;
+    const int g = blockIdx.x % n_grids;
+    const long long b = blockIdx.x / n_grids;  // state of the batch
+    const GridInfo G = grids[g];
+    const double *src = u + b * ntot + G.off;
+    double *v = H + b * ntot + G.off;
     for (int j = threadIdx.x; j < G.n; j += blockDim.x) v[j] = src[j];
     __syncthreads();
 #pragma unroll
@@ -57,15 +60,18 @@ __global__ void hier_kernel(const GridInfo *grids, const double *coef, const dou
             __syncthreads();
         }
     }
-    const double c = coef[blockIdx.x];
+    const double c = coef[g];
     for (int j = threadIdx.x; j < G.n; j += blockDim.x) v[j] *= c;
 }
 
 template <int D>
-__global__ void gather_kernel(RecombPlan R, const GridInfo *grids, const double *H, double *S)
+__global__ void gather_kernel(RecombPlan R, const GridInfo *grids, long long ntot, int nb, const double *Hb, double *Sb)
 {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= R.n_sparse) return;
+    const long long qb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qb >= R.n_sparse * nb) return;
+    const long long bst = qb / R.n_sparse, q = qb - bst * R.n_sparse;  // state of the batch, sparse node
+    const double *H = Hb + bst * ntot;
+    double *S = Sb + bst * R.n_sparse;
     // block of the node: last b with blk_off[b] <= q
     int lo = 0, hi = R.n_blk - 1;
     while (lo < hi) {
@@ -99,10 +105,14 @@ __global__ void gather_kernel(RecombPlan R, const GridInfo *grids, const double 
 }
 
 template <int D>
-__global__ void dehier_kernel(RecombPlan R, const GridInfo *grids, const double *S, double *out)
+__global__ void dehier_kernel(RecombPlan R, const GridInfo *grids, int n_grids, long long ntot, const double *Sb,
+                              double *out)
 {
-    const GridInfo G = grids[blockIdx.x];
-    double *v = out + G.off;
+    const int g = blockIdx.x % n_grids;
+    const long long bst = blockIdx.x / n_grids;
+    const GridInfo G = grids[g];
+    const double *S = Sb + bst * R.n_sparse;
+    double *v = out + bst * ntot + G.off;
     for (int j = threadIdx.x; j < G.n; j += blockDim.x) {
         int code = 0;
         long long pos = 0;
@@ -129,28 +139,31 @@ __global__ void dehier_kernel(RecombPlan R, const GridInfo *grids, const double 
 }
 
 template <int D>
-cudaError_t launch_recombine_d(const RecombPlan &R, const GridInfo *grids, const double *coef, int G, const double *u,
-                               double *H, double *S, double *out, cudaStream_t s)
+cudaError_t launch_recombine_d(const RecombPlan &R, const GridInfo *grids, const double *coef, int G, long long ntot,
+                               int nb, const double *u, double *H, double *S, double *out, cudaStream_t s)
 {
-    hier_kernel<D><<<G, 256, 0, s>>>(grids, coef, u, H);
-    const long long nb = (R.n_sparse + 255) / 256;
-    gather_kernel<D><<<(unsigned)nb, 256, 0, s>>>(R, grids, H, S);
-    dehier_kernel<D><<<G, 256, 0, s>>>(R, grids, S, out);
+    const long long cta = (long long)G * nb, nodes = R.n_sparse * nb;
+    if (cta > 0x7fffffffLL || (nodes + 255) / 256 > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    hier_kernel<D><<<(unsigned)cta, 256, 0, s>>>(grids, coef, G, ntot, u, H);
+    gather_kernel<D><<<(unsigned)((nodes + 255) / 256), 256, 0, s>>>(R, grids, ntot, nb, H, S);
+    dehier_kernel<D><<<(unsigned)cta, 256, 0, s>>>(R, grids, G, ntot, S, out);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_recombine(const RecombPlan &R, int d, const GridInfo *grids, const double *coef, int G,
-                             const double *u, double *H, double *S, double *out, cudaStream_t s)
+                             long long ntot, int nb, const double *u, double *H, double *S, double *out,
+                             cudaStream_t s)
 {
+    if (nb <= 0) return cudaSuccess;
     switch (d) {
-    case 1: return launch_recombine_d<1>(R, grids, coef, G, u, H, S, out, s);
-    case 2: return launch_recombine_d<2>(R, grids, coef, G, u, H, S, out, s);
-    case 3: return launch_recombine_d<3>(R, grids, coef, G, u, H, S, out, s);
-    case 4: return launch_recombine_d<4>(R, grids, coef, G, u, H, S, out, s);
-    case 5: return launch_recombine_d<5>(R, grids, coef, G, u, H, S, out, s);
-    case 6: return launch_recombine_d<6>(R, grids, coef, G, u, H, S, out, s);
+    case 1: return launch_recombine_d<1>(R, grids, coef, G, ntot, nb, u, H, S, out, s);
+    case 2: return launch_recombine_d<2>(R, grids, coef, G, ntot, nb, u, H, S, out, s);
+    case 3: return launch_recombine_d<3>(R, grids, coef, G, ntot, nb, u, H, S, out, s);
+    case 4: return launch_recombine_d<4>(R, grids, coef, G, ntot, nb, u, H, S, out, s);
+    case 5: return launch_recombine_d<5>(R, grids, coef, G, ntot, nb, u, H, S, out, s);
+    case 6: return launch_recombine_d<6>(R, grids, coef, G, ntot, nb, u, H, S, out, s);
     default: return cudaErrorInvalidValue;
     }
 }

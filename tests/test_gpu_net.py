@@ -190,3 +190,48 @@ def test_acceptance_ratio_of_the_holdout_judge():
     opts = B.mgrit_opts(wl.t0, wl.t1, 64, 4, 2, tol=1e-9, maxit=40, coarse=B.PIT_COARSE_LEARNED, fine=mixed, crs=mixed)
     stm = P.mgrit_solve(u0, opts, uT)
     assert stm.learned_used == 0
+
+
+def test_learned_versus_implicit_coarse_propagator_on_varheat3d_n8(capsys):
+    """What the trained network gains or loses on the variable-coefficient
+    workload at full size (d = 3, level 8, 85 grids, 2048 steps, m = 32):
+    MGRIT (FAS form, one lane, F-relaxation, initial coarse sweep) with the
+    trained network forced in as the coarse propagator, against the same
+    MGRIT with the implicit coarse step; the cycles and times are printed.
+    Both must reach the fine solution (the oracle's sequential one, 1e-6 per
+    grid on a sample of grids); with the network the runtime judge may switch
+    back to the implicit step, which the statistics report."""
+    import time
+    wl = W.workload(4)
+    P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    O = oracle.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
+    mixed = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-11, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+    topts = B.train_opts(wl.dt, wl.m, n_pairs=4096, n_holdout=256, epochs=10, batch=64, lr=1e-3, seed=0,
+                         traj_len=8, fine=mixed, crs=mixed, accept_ratio=1.0)
+    tst = P.train_coarse(topts)
+    P.net_set_params(P.net_get_params())  # use the trained network whatever the hold-out judge said
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    u0d = cuda(u0)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    crs = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-6, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+    res = {}
+    grids = list(range(0, P.G, 9))
+    seq = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14, grids=grids)
+    for name, coarse in (("learned", B.PIT_COARSE_LEARNED), ("implicit", B.PIT_COARSE_IMPLICIT)):
+        opts = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, 2, tol=1e-10, maxit=64, coarse=coarse, fine=mixed,
+                            crs=crs, fas=True, relax=B.PIT_RELAX_F, lanes=1, init=True)
+        P.mgrit_solve(u0d, opts, uT)  # first call: launch-shape tuning
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = P.mgrit_solve(u0d, opts, uT)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        got = host(uT)
+        err = max(rel(got[O.grid_slice(g)], seq[O.grid_slice(g)]) for g in grids)
+        res[name] = dict(cycles=st.max_cycles, ms=round(ms, 1), learned_used=st.learned_used, fell_back=st.fallback,
+                         max_grid_err=err)
+        assert err < 1e-6, (name, err)
+    with capsys.disabled():
+        print(f"\nvarheat3d_n8 coarse propagator: hold-out error learned {tst.holdout_err_learned:.4f} vs "
+              f"implicit {tst.holdout_err_implicit:.4f}; MGRIT {res}")
+    assert res["learned"]["learned_used"] == 1

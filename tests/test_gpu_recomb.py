@@ -124,3 +124,40 @@ def test_recombination_changes_the_anisotropic_solution_and_rejects_bad_step_cou
         P.mgrit_solve(u0d, B.mgrit_opts(0.0, 0.1, N, m, 2, tol=1e-12, fine=fine, recomb=32), b)
     assert e.value.status == B.PIT_ERR_INVALID_ARG
     P.close()
+
+
+@pytest.mark.parametrize("prec,tolerance", [(B.PIT_PREC_FP64, 1e-10), (B.PIT_PREC_MIXED, 1e-9)])
+@pytest.mark.parametrize("r", [2, 8])
+def test_global_mgrit_matches_combination_method_recombined_every_r_steps(prec, tolerance, r):
+    """Global MGRIT (Sec. 3.4): the propagator of r fine steps is Phi^r o Q,
+    so every grid is recombined every r steps inside MGRIT; the fixed point
+    is Alg. 1 with a recombination step every r fine steps (computed by the
+    oracle step by step), here with the heat experiment's forcing."""
+    d, n, N, m, T = 3, 5, 64, 8, 0.1
+    dt = T / N
+    P = B.Problem(d, n, 1, B.PIT_OP_HEAT)
+    O = oracle.Problem(d, n, 1, W.OP_HEAT)
+    F = torch.empty(N * P.n_total, dtype=torch.float64, device="cuda")
+    for k in range(N):
+        P.sample_initial(3, [(k + 1) * dt], F[k * P.n_total:(k + 1) * P.n_total])
+    Fo = np.concatenate([O.initial(3, [(k + 1) * dt]) for k in range(N)])
+    u0 = O.initial(2, [0.0])
+    ref = u0.copy()
+    for k in range(N // r):
+        ref = O.recombine(ref)
+        ref = O.sequential(ref, dt, r, rtol=1e-15, forcing=Fo[k * r * O.n_total:(k + 1) * r * O.n_total])
+    fine = B.solve_opts(prec, rtol=1e-13, maxit=5000, inner_rtol=1e-5, ir_maxit=40)
+    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=5000)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    opts = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-13 * np.abs(ref).max(), maxit=64, fine=fine, crs=crs,
+                        relax=B.PIT_RELAX_F, init=True, forcing=F, global_every=r)
+    st = P.mgrit_solve(torch.from_numpy(u0).cuda(), opts, uT)
+    assert st.n_converged == P.G and st.max_cycles >= 2
+    assert rel(uT.cpu().numpy(), ref) < tolerance
+    # r must divide m
+    with pytest.raises(B.PitError) as e:
+        P.mgrit_solve(torch.from_numpy(u0).cuda(),
+                      B.mgrit_opts(0.0, T, N, m, 2, tol=1e-10, fine=fine, crs=crs, relax=B.PIT_RELAX_F,
+                                   global_every=3), uT)
+    assert e.value.status == B.PIT_ERR_INVALID_ARG
+    P.close()
