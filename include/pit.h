@@ -216,6 +216,16 @@ typedef struct {
                              recombination step every r fine steps.  r must divide m; two
                              levels, F-relaxation, implicit coarse step Phi_c o Q in the
                              correction form, no tmul or recomb                              */
+    int residual;         /* 1: residual mode (the XBraid option of Sec. 4.4.1): the fine
+                             steps of the F-relaxation are the fine solves as configured, for
+                             instance a fixed small number of Krylov iterations (fine.rtol 0,
+                             fine.maxit k; hitting the caps is then not a failure), the C-point
+                             residual is the space-time residual of the backward-Euler
+                             equation rho_j = u_{jm-1} + dt f_{jm} - (I + dt L) u_{jm}, the
+                             coarse problem (I + dT L) e_j = e_{j-1} + rho_j, and MGRIT stops
+                             when every ||rho_j||_2 <= tol.  With exact fine solves its fixed
+                             point is the sequential solution.  Two levels, F-relaxation,
+                             implicit coarse step, correction form, no tmul                  */
 } pit_mgrit_opts;
 
 typedef struct {

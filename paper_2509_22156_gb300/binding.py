@@ -63,7 +63,7 @@ class pit_mgrit_opts(ctypes.Structure):
                 ("levels", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("coarse", ctypes.c_int), ("fas", ctypes.c_int), ("fine", pit_solve_opts), ("crs", pit_solve_opts),
                 ("relax", ctypes.c_int), ("lanes", ctypes.c_int), ("init", ctypes.c_int), ("recomb", ctypes.c_int),
-                ("forcing", ctypes.c_void_p), ("tmul", ctypes.c_void_p), ("global_every", ctypes.c_int)]
+                ("forcing", ctypes.c_void_p), ("tmul", ctypes.c_void_p), ("global_every", ctypes.c_int), ("residual", ctypes.c_int)]
 
 
 class pit_mgrit_stats(ctypes.Structure):
@@ -175,7 +175,7 @@ def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=
 
 def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARSE_IMPLICIT, fine=None,
                crs=None, fas=False, relax=None, lanes=0, init=False, recomb=0, forcing=None,
-               tmul=None, global_every=0) -> pit_mgrit_opts:
+               tmul=None, global_every=0, residual=False) -> pit_mgrit_opts:
     """forcing: device tensor of nsteps packed states (kept alive by the
     returned struct's _keep); tmul: per-grid steps per fine step (host)."""
     fine = fine or solve_opts()
@@ -192,7 +192,7 @@ def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARS
         keep.append(t)
         tptr = t.ctypes.data
     o = pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes,
-                       1 if init else 0, recomb, fptr, tptr, global_every)
+                       1 if init else 0, recomb, fptr, tptr, global_every, 1 if residual else 0)
     o._keep = keep
     return o
 

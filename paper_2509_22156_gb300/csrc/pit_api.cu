@@ -377,6 +377,7 @@ struct StepCall {
     double *norms = nullptr;
     const double *guess = nullptr;
     long long gus = 0, gust = 0;
+    int inexact = 0;  // fixed-iteration solves (residual mode): the iteration caps are not failures
 };
 
 StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
@@ -428,6 +429,7 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.maxit = o.maxit;
     a.inner_rtol = (float)o.inner_rtol;
     a.ir_maxit = o.ir_maxit;
+    a.inexact = c.inexact;
     a.stats = P->d_stats;
     return a;
 }
@@ -1335,6 +1337,49 @@ pit_status mg_cycle(Mg &M, int Nc, bool corr, double *h_res)
     // are U itself, and the correction updates U in place
     const bool relax_f = o->relax == PIT_RELAX_F;
     double *Rx = relax_f ? U : R;
+    if (o->residual) {
+        // residual mode: the m - 1 F-points of every interval by the fine
+        // solves as configured (a fixed number of iterations: inexact), then
+        // the space-time residual of the backward-Euler equation at the
+        // C-point, rho_{j+1} = u_{(j+1)m-1} + dt f_{(j+1)m} - A u_{(j+1)m};
+        // the coarse problem A_c e_{j+1} = e_j + rho_{j+1} (e_0 = 0) is solved
+        // by the sweep with forcing rho / dT, and u_{j+1} += e_{j+1}
+        StepCall fr;
+        fr.dt = M.dtf;
+        fr.nb = Nc;
+        fr.nsteps = m - 1;
+        fr.in = U;
+        fr.is = nt;
+        if (M.F) {
+            fr.f = M.F;
+            fr.fs = (long long)m * nt;
+            fr.fst = nt;
+        }
+        fr.out_last = R + nt;
+        fr.ols = nt;
+        fr.inexact = 1;
+        TRY(run_steps(P, o->fine, fr, M.active, M.L));
+        const double dT = M.dt * m;
+        CU(launch_st_resid(P->d_grids, G, nt, Nc, M.dtf, R + nt, nt, M.F ? M.F + (long long)(m - 1) * nt : nullptr,
+                           (long long)m * nt, U + nt, nt, 1.0 / dT, GC, nt, res, M.active, P->d_faces, P->op, M.s));
+        count_kernels(P, 3);
+        CU(cudaMemcpyAsync(h_res, res, sizeof(double) * G * Nc, cudaMemcpyDeviceToHost, M.s));
+        StepCall sw;
+        sw.nb = 1;
+        sw.nsteps = Nc;
+        sw.in = P->m_Z.d();
+        sw.is = nt;
+        sw.f = GC;
+        sw.fst = nt;
+        sw.hstep = U + nt;  // u_{j+1} + e_{j+1}, read and written by the same thread
+        sw.hsst = nt;
+        sw.out_steps = U + nt;
+        sw.osst = nt;
+        sw.out_last = U + (long long)Nc * nt;
+        sw.ols = nt;
+        TRY(run_coarse(M, sw, 1));
+        return PIT_OK;
+    }
     StepCall fc;  // FC relaxation
     fc.dt = M.dtf;
     fc.nb = Nc;
@@ -1618,6 +1663,11 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     if (o->init != 0 && o->init != 1) return fail(PIT_ERR_INVALID_ARG, "init must be 0 or 1");
     if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
+    if (o->residual != 0 && o->residual != 1) return fail(PIT_ERR_INVALID_ARG, "residual must be 0 or 1");
+    if (o->residual && (o->levels != 2 || o->relax != PIT_RELAX_F || o->fas || o->coarse != PIT_COARSE_IMPLICIT ||
+                        o->tmul))
+        return fail(PIT_ERR_UNSUPPORTED, "residual mode runs two levels, F-relaxation and the implicit coarse step in "
+                                         "the correction form, without per-grid partitions");
     const int G = P->G, m = o->m, Nc = o->nsteps / m;
     const long long nt = P->ntot;
     const size_t vb = sizeof(double) * nt;

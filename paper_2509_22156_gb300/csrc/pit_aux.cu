@@ -16,8 +16,65 @@ __device__ double varcoef(const OpParams &op, const double *x)
     return 1.0 + op.vamp * prod;
 }
 
-// q = (I + dt L) p, one CTA per (batch entry, grid), FP64 with coefficients
-// evaluated per node (the reference application of the operator).
+// (I + dt L) p at node j of grid GI, FP64 with coefficients evaluated per
+// node (the reference application of the operator).
+__device__ double apply_node(const GridInfo &GI, int j, const double *pg, double dt, const double *faces,
+                             const OpParams &op)
+{
+    const int d = op.d;
+    double s = 0.0, diag = 1.0;
+    for (int i = 0; i < d; ++i) {
+        const int c = axis_coord(GI, j, i);
+        const double h = GI.h[i], ih2 = 1.0 / (h * h);
+        double dd, dm, dp;
+        if (op.op == PIT_OP_HEAT) {
+            dd = 2.0 * ih2; dm = -ih2; dp = -ih2;
+        } else if (op.op == PIT_OP_VARHEAT) {
+            const double am = faces[(GI.off + j) * (2 * d) + 2 * i];
+            const double ap = faces[(GI.off + j) * (2 * d) + 2 * i + 1];
+            dd = (am + ap) * ih2; dm = -am * ih2; dp = -ap * ih2;
+        } else if (op.op == PIT_OP_OU) {
+            const double x = op.lo[i] + (double)(c + 1) * h;
+            const double vp = -op.theta * (x + 0.5 * h), vm = -op.theta * (x - 0.5 * h);
+            const double s2 = 0.5 * op.sigma * op.sigma * ih2;
+            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
+            dm = -fmax(vm, 0.0) / h - s2;
+            dp = fmin(vp, 0.0) / h - s2;
+        } else {
+            // linear SDE: face velocities (A x)_i at x -+ h/2 e_i, diagonal diffusion
+            double ax = 0.0;
+            for (int k = 0; k < d; ++k)
+                ax += op.A[i * d + k] * (op.lo[k] + (double)(axis_coord(GI, j, k) + 1) * GI.h[k]);
+            const double vp = ax + 0.5 * h * op.A[i * d + i], vm = ax - 0.5 * h * op.A[i * d + i];
+            const double s2 = 0.5 * op.H[i * d + i] * ih2;
+            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
+            dm = -fmax(vm, 0.0) / h - s2;
+            dp = fmin(vp, 0.0) / h - s2;
+        }
+        diag += dt * dd;
+        if (c > 0) s += dt * dm * pg[j - GI.S[i]];
+        if (c < GI.N[i] - 1) s += dt * dp * pg[j + GI.S[i]];
+    }
+    if (op.op == PIT_OP_LSDE) {
+        // mixed derivatives: -(H_ik + H_ki)/2 (p_{++} - p_{+-} - p_{-+} + p_{--}) / (4 h_i h_k)
+        for (int i = 0; i < d; ++i) {
+            const int ci = axis_coord(GI, j, i);
+            for (int k = i + 1; k < d; ++k) {
+                const int ck = axis_coord(GI, j, k);
+                const double w = -dt * 0.5 * (op.H[i * d + k] + op.H[k * d + i]) / (4.0 * GI.h[i] * GI.h[k]);
+                double c4 = 0.0;
+                if (ci < GI.N[i] - 1 && ck < GI.N[k] - 1) c4 += pg[j + GI.S[i] + GI.S[k]];
+                if (ci < GI.N[i] - 1 && ck > 0) c4 -= pg[j + GI.S[i] - GI.S[k]];
+                if (ci > 0 && ck < GI.N[k] - 1) c4 -= pg[j - GI.S[i] + GI.S[k]];
+                if (ci > 0 && ck > 0) c4 += pg[j - GI.S[i] - GI.S[k]];
+                s += w * c4;
+            }
+        }
+    }
+    return diag * pg[j] + s;
+}
+
+// q = (I + dt L) p, one CTA per (batch entry, grid).
 __global__ void apply_kernel(const GridInfo *grids, int G, long long ntot, double dt, const double *p, double *q,
                              const double *faces, OpParams op)
 {
@@ -25,59 +82,51 @@ __global__ void apply_kernel(const GridInfo *grids, int G, long long ntot, doubl
     const GridInfo GI = grids[g];
     const double *pg = p + (long long)b * ntot + GI.off;
     double *qg = q + (long long)b * ntot + GI.off;
-    const int d = op.d;
+    for (int j = threadIdx.x; j < GI.n; j += blockDim.x) qg[j] = apply_node(GI, j, pg, dt, faces, op);
+}
+
+// Space-time residual of the backward-Euler equation at a C-point (the
+// residual mode of MGRIT): rho_b = x_b + dt f_b - (I + dt L) u_b, written as
+// scale * rho_b, with ||rho_b||_2 per grid in norms[b * G + g]; active grids
+// only (others untouched).  One CTA of 256 threads per (batch entry, grid).
+__global__ void st_resid_kernel(const GridInfo *grids, int G, long long ntot, double dt, const double *x,
+                                long long xs, const double *f, long long fs, const double *u, long long us,
+                                double scale, double *out, long long os, double *norms, const int *active,
+                                const double *faces, OpParams op)
+{
+    const int g = blockIdx.x % G, b = blockIdx.x / G;
+    if (active && !active[g]) return;
+    const GridInfo GI = grids[g];
+    const double *xg = x + b * xs + GI.off, *ug = u + b * us + GI.off;
+    const double *fg = f ? f + b * fs + GI.off : nullptr;
+    double *og = out + b * os + GI.off;
+    double acc = 0.0;
     for (int j = threadIdx.x; j < GI.n; j += blockDim.x) {
-        double s = 0.0, diag = 1.0;
-        for (int i = 0; i < d; ++i) {
-            const int c = axis_coord(GI, j, i);
-            const double h = GI.h[i], ih2 = 1.0 / (h * h);
-            double dd, dm, dp;
-            if (op.op == PIT_OP_HEAT) {
-                dd = 2.0 * ih2; dm = -ih2; dp = -ih2;
-            } else if (op.op == PIT_OP_VARHEAT) {
-                const double am = faces[(GI.off + j) * (2 * d) + 2 * i];
-                const double ap = faces[(GI.off + j) * (2 * d) + 2 * i + 1];
-                dd = (am + ap) * ih2; dm = -am * ih2; dp = -ap * ih2;
-            } else if (op.op == PIT_OP_OU) {
-                const double x = op.lo[i] + (double)(c + 1) * h;
-                const double vp = -op.theta * (x + 0.5 * h), vm = -op.theta * (x - 0.5 * h);
-                const double s2 = 0.5 * op.sigma * op.sigma * ih2;
-                dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
-                dm = -fmax(vm, 0.0) / h - s2;
-                dp = fmin(vp, 0.0) / h - s2;
-            } else {
-                // linear SDE: face velocities (A x)_i at x -+ h/2 e_i, diagonal diffusion
-                double ax = 0.0;
-                for (int k = 0; k < d; ++k)
-                    ax += op.A[i * d + k] * (op.lo[k] + (double)(axis_coord(GI, j, k) + 1) * GI.h[k]);
-                const double vp = ax + 0.5 * h * op.A[i * d + i], vm = ax - 0.5 * h * op.A[i * d + i];
-                const double s2 = 0.5 * op.H[i * d + i] * ih2;
-                dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
-                dm = -fmax(vm, 0.0) / h - s2;
-                dp = fmin(vp, 0.0) / h - s2;
-            }
-            diag += dt * dd;
-            if (c > 0) s += dt * dm * pg[j - GI.S[i]];
-            if (c < GI.N[i] - 1) s += dt * dp * pg[j + GI.S[i]];
-        }
-        if (op.op == PIT_OP_LSDE) {
-            // mixed derivatives: -(H_ik + H_ki)/2 (p_{++} - p_{+-} - p_{-+} + p_{--}) / (4 h_i h_k)
-            for (int i = 0; i < d; ++i) {
-                const int ci = axis_coord(GI, j, i);
-                for (int k = i + 1; k < d; ++k) {
-                    const int ck = axis_coord(GI, j, k);
-                    const double w = -dt * 0.5 * (op.H[i * d + k] + op.H[k * d + i]) / (4.0 * GI.h[i] * GI.h[k]);
-                    double c4 = 0.0;
-                    if (ci < GI.N[i] - 1 && ck < GI.N[k] - 1) c4 += pg[j + GI.S[i] + GI.S[k]];
-                    if (ci < GI.N[i] - 1 && ck > 0) c4 -= pg[j + GI.S[i] - GI.S[k]];
-                    if (ci > 0 && ck < GI.N[k] - 1) c4 -= pg[j - GI.S[i] + GI.S[k]];
-                    if (ci > 0 && ck > 0) c4 += pg[j - GI.S[i] - GI.S[k]];
-                    s += w * c4;
-                }
-            }
-        }
-        qg[j] = diag * pg[j] + s;
+        const double r = xg[j] + (fg ? dt * fg[j] : 0.0) - apply_node(GI, j, ug, dt, faces, op);
+        og[j] = scale * r;
+        acc += r * r;
     }
+    __shared__ double part[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        norms[(long long)b * G + g] = sqrt(t);
+    }
+}
+
+cudaError_t launch_st_resid(const GridInfo *grids, int G, long long ntot, int nb, double dt, const double *x,
+                            long long xs, const double *f, long long fs, const double *u, long long us, double scale,
+                            double *out, long long os, double *norms, const int *active, const double *faces,
+                            OpParams op, cudaStream_t s)
+{
+    const long long blocks = (long long)G * nb;
+    if (blocks == 0) return cudaSuccess;
+    st_resid_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, G, ntot, dt, x, xs, f, fs, u, us, scale, out, os, norms,
+                                                      active, faces, op);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const GridInfo *grids, int G, long long ntot, int n_batch, double dt, const double *p,

@@ -96,6 +96,7 @@ struct StepArgs {
     int maxit;
     float inner_rtol;
     int ir_maxit;
+    int inexact;             // 1: a solve stopped by its iteration caps is not a failure
     DevStats *stats;
 };
 
@@ -163,6 +164,13 @@ cudaError_t launch_masks(const GridInfo *grids, int G, int d, uint16_t *masks, c
 
 cudaError_t launch_apply(const GridInfo *grids, int G, long long ntot, int n_batch, double dt,
                          const double *p, double *q, const double *faces, OpParams op, cudaStream_t s);
+// Space-time residual rho_b = x_b + dt f_b - (I + dt L) u_b at nb C-points
+// (strides xs, fs, us, os in doubles; f may be NULL), written as scale * rho_b;
+// ||rho_b||_2 per grid in norms[b * G + g]; active grids only.
+cudaError_t launch_st_resid(const GridInfo *grids, int G, long long ntot, int nb, double dt, const double *x,
+                            long long xs, const double *f, long long fs, const double *u, long long us, double scale,
+                            double *out, long long os, double *norms, const int *active, const double *faces,
+                            OpParams op, cudaStream_t s);
 cudaError_t launch_initial(const GridInfo *grids, int G, OpParams op, const double *hi, int kind,
                            const double *params_dev, int n_params, double *u, cudaStream_t s);
 cudaError_t launch_faces(const GridInfo *grids, int G, OpParams op, double *faces, cudaStream_t s);

@@ -1514,6 +1514,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             }
         }
     }
+    if (a.inexact && status == PIT_ERR_NOCONV) status = PIT_OK;  // fixed-iteration (inexact) solves
     if (tid == 0 && a.stats) {
         atomicAdd(&a.stats->sum_iters, (unsigned long long)iters);
         atomicAdd(&a.stats->items, (unsigned long long)a.nsteps);

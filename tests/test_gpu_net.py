@@ -213,7 +213,9 @@ def test_learned_versus_implicit_coarse_propagator_on_varheat3d_n8(capsys):
     u0 = O.initial(wl.ic_kind, wl.ic_params)
     u0d = cuda(u0)
     uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
-    crs = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-6, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+    # (the FAS form solves the coarse problem for the state, not the
+    # correction: its coarse tolerance must lie below the MGRIT tolerance)
+    crs = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-12, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
     res = {}
     grids = list(range(0, P.G, 9))
     seq = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14, grids=grids)
