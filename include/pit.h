@@ -140,12 +140,26 @@ typedef struct {
  *                          memory, as PIT_PREC_MIXED keeps its FP64 state.
  *                          Inputs and outputs stay FP64; values below 2^-102 of
  *                          the state's norm lose their low part. */
+/* Preconditioner of the Krylov solves (the paper preconditions its CG and
+ * BiCGStab by domain decomposition, Sec. 2.1.2 and Sec. 4.1; on one GPU the
+ * grid-resident solver offers these):
+ *   DEFAULT  heat operator: the line preconditioner (tridiagonal along the
+ *            finest axis, in the FP32 Krylov forms on anisotropic grids at
+ *            stiff steps); other operators: none.
+ *   NONE     no preconditioner.
+ *   JACOBI   diagonal (Jacobi) preconditioning of the FP32 correction solves
+ *            of the refinement forms (PIT_PREC_MIXED, PIT_PREC_MIXED_PAIR) for
+ *            the variable-coefficient and drift (OU) operators, applied as
+ *            the symmetric scaling D^{-1/2} A D^{-1/2}; elsewhere as NONE. */
+typedef enum { PIT_PRECOND_DEFAULT = 0, PIT_PRECOND_NONE = 1, PIT_PRECOND_JACOBI = 2 } pit_precond;
+
 typedef struct {
     int prec;
     double rtol;
     int maxit;
     double inner_rtol;
     int ir_maxit;
+    int precond;          /* pit_precond */
 } pit_solve_opts;
 
 typedef struct {

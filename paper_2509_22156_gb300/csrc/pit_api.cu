@@ -274,6 +274,8 @@ pit_status check_solve_opts(const pit_solve_opts *o)
         o->prec != PIT_PREC_MIXED_PAIR)
         return fail(PIT_ERR_INVALID_ARG, "unknown precision %d", o->prec);
     if (!(o->rtol >= 0.0) || o->maxit < 1) return fail(PIT_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
+    if (o->precond < PIT_PRECOND_DEFAULT || o->precond > PIT_PRECOND_JACOBI)
+        return fail(PIT_ERR_INVALID_ARG, "unknown preconditioner %d", o->precond);
     if ((o->prec == PIT_PREC_MIXED || o->prec == PIT_PREC_MIXED_PAIR) &&
         (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->ir_maxit < 1))
         return fail(PIT_ERR_INVALID_ARG, "mixed precision needs 0 < inner_rtol < 1 and ir_maxit >= 1");
@@ -430,6 +432,7 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.inner_rtol = (float)o.inner_rtol;
     a.ir_maxit = o.ir_maxit;
     a.inexact = c.inexact;
+    a.precond = o.precond;
     a.stats = P->d_stats;
     return a;
 }
@@ -589,7 +592,7 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
 pit_status run_net(pit_problem *P, const StepCall &c, const int *active)
 {
     if (c.nb <= 0 || c.nsteps <= 0) return PIT_OK;
-    pit_solve_opts dummy{PIT_PREC_FP64, 0.0, 1, 0.5, 1};
+    pit_solve_opts dummy{PIT_PREC_FP64, 0.0, 1, 0.5, 1, PIT_PRECOND_DEFAULT};
     StepArgs a = make_args(P, dummy, c, active);
     int nmax = 0;
     for (const GridInfo &I : P->info) nmax = I.n > nmax ? I.n : nmax;

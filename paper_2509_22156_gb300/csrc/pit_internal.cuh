@@ -97,6 +97,7 @@ struct StepArgs {
     float inner_rtol;
     int ir_maxit;
     int inexact;             // 1: a solve stopped by its iteration caps is not a failure
+    int precond;             // pit_precond of the Krylov solves
     DevStats *stats;
 };
 

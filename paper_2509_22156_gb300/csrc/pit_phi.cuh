@@ -142,10 +142,11 @@ struct TabSt {
     int ld;
     int S[D];
     T cr[NP > 0 ? NP : 1];
+    bool unit = false;  // Jacobi-scaled table: unit diagonal, the diagonal slot holds D^{-1/2}
     __device__ __forceinline__ T operator()(const T *p, int j) const
     {
         const unsigned mk = mask[j];
-        T s = tab[j] * p[j];
+        T s = unit ? p[j] : tab[j] * p[j];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             const int jm = ((mk >> (2 * i)) & 1u) ? j - S[i] : j;
@@ -992,6 +993,30 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         H64.diag = diag;
         HT.diag = (T)diag;
     }
+    // Jacobi preconditioning of the FP32 correction solves (table operators
+    // without mixed-derivative terms, refinement forms): the FP32 system is
+    // scaled symmetrically, D^{-1/2} A D^{-1/2} y = D^{-1/2} r, e = D^{-1/2} y,
+    // D = diag(A): its off-diagonal entries become a_jk / sqrt(d_j d_k) and
+    // its diagonal one, whose slot then keeps D^{-1/2} (T32.unit)
+    bool jac = false;
+    if constexpr ((PREC == MIXED || PREC == PAIR) && (OP == PIT_OP_VARHEAT || OP == PIT_OP_OU)) {
+        if (a.precond == PIT_PRECOND_JACOBI) {
+            jac = true;
+            __syncthreads();  // table complete
+            for (int j = tid; j < n; j += nt) {
+                const unsigned mk = mask[j];
+                const float dj = tab32[j];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    if ((mk >> (2 * i)) & 1u) tab32[(1 + 2 * i) * ld + j] *= rsqrtf(dj * tab32[j - GI.S[i]]);
+                    if ((mk >> (2 * i + 1)) & 1u) tab32[(2 + 2 * i) * ld + j] *= rsqrtf(dj * tab32[j + GI.S[i]]);
+                }
+            }
+            __syncthreads();  // every off-diagonal scaled with the old diagonals
+            for (int j = tid; j < n; j += nt) tab32[j] = rsqrtf(tab32[j]);
+            T32.unit = true;
+        }
+    }
     PairTab<D> PT;
     if constexpr (PREC == PAIR && OP != PIT_OP_HEAT) {
         PT.mask = mask;
@@ -1031,7 +1056,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             if (i != ax && GI.h[i] < h2) h2 = GI.h[i];
         const double ha = GI.h[ax];
         const int Na = GI.N[ax];
-        use_pc = Na >= 3 && 2.0 * ha <= h2 * (1.0 + 1e-12) && 4.0 * dt / (ha * ha) >= 2.0;
+        use_pc = a.precond != PIT_PRECOND_NONE && Na >= 3 && 2.0 * ha <= h2 * (1.0 + 1e-12) &&
+                 4.0 * dt / (ha * ha) >= 2.0;
         if (use_pc) {
             float *lf = reinterpret_cast<float *>(mask + ld);
             LM.layout(Na, GI.S[ax], n, nt);
@@ -1271,7 +1297,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 const float tgt = want > a.inner_rtol ? want : (float)a.inner_rtol;
                 const float stop32 = tgt * tgt * R2n;
                 for (int j = tid; j < n; j += nt) {
-                    rv[j] *= inv;
+                    rv[j] *= jac ? inv * tab32[j] : inv;
                     e[j] = 0.0f;
                 }
                 int st, k;
@@ -1283,10 +1309,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 }
                 iters += k;
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
-                // x += e 2^kn on the pairs (the scaling is exact)
+                // x += e 2^kn on the pairs (the scaling is exact; Jacobi: e = D^{-1/2} y)
                 const float csf = __uint_as_float((unsigned)(127 + kn) << 23);
 #pragma unroll 4
-                for (int j = tid; j < n; j += nt) xp[j] = pair_add(xp[j], e[j] * csf);
+                for (int j = tid; j < n; j += nt) xp[j] = pair_add(xp[j], (jac ? e[j] * tab32[j] : e[j]) * csf);
                 __syncthreads();  // x complete
                 // check: r = b - A x; the next step's r0 = x - A x = r + (x - b)
                 float accf[3] = {0.0f, 0.0f, 0.0f};
@@ -1422,7 +1448,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 const float tgt = want > a.inner_rtol ? want : (float)a.inner_rtol;
                 const float stop32 = tgt * tgt * R2n;
                 for (int j = tid; j < n; j += nt) {
-                    rv[j] *= inv;
+                    rv[j] *= jac ? inv * tab32[j] : inv;
                     e[j] = 0.0f;
                 }
                 int st, k;
@@ -1442,7 +1468,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 const float csf = __uint_as_float((unsigned)(127 + kd) << 23);
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
-                    const float ej = e[j];
+                    const float ej = jac ? e[j] * tab32[j] : e[j];  // Jacobi: e = D^{-1/2} y
                     x[j] = fma(to_f64(ej, 0), cs, x[j]);
                     if (carry_ok) dv[j] = fmaf(ej, csf, dv[j]);
                 }
