@@ -579,6 +579,9 @@ def run_pit(args, rank, world, local):
                 roofline["relax_node_steps"] / max(1, args.steps) / dofsteps)
         result["forms"] = forms
 
+    if not args.no_forms and rank == 0:
+        result["extras"] = extras(P, wl, B, W, u0, stream)
+
     if not args.no_cpu and rank == 0 and world == 1:
         result["cpu_baseline"], result["accuracy"] = cpu_baseline(wl, k, uT_h, out_h_chosen, pts_h, chosen,
                                                                   form_outs)
@@ -593,6 +596,112 @@ def run_pit(args, rank, world, local):
 
 
 # ---------------------------------------------------------------------------
+def extras(P, wl, B, W, u0, stream):
+    """The scope's further rows on the same GPU, each bounded to a few seconds:
+    (1) the recombination Q of Sec. 2.2.2 on the headline problem's state,
+    with its streaming bytes per application; (2) the heat experiment of
+    Sec. 4.2 (manufactured u*, forcing, s = 4 recombination steps, MGRIT per
+    grid) on the heat3d_n9 grid set, error against u*(T); (3) the
+    two-dimensional linear oscillator of Sec. 4.4.1 (Table 3's tuned problem:
+    level 14, L0 = 6, T = 1, 3200 steps) with the general linear-SDE operator,
+    error against the closed-form normal law on the diagonal."""
+    import torch
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts), r
+
+    # (1) recombination: hierarchize (read u, write H), gather (read H, write
+    # S), dehierarchize (read S, write u): 8 B each, per node and sparse node
+    q = torch.empty_like(u0)
+    ms, _ = timed(lambda: P.recombine(u0, q))
+    nodes = P.n_total
+    out["recombination"] = {"workload": wl.name, "ms": ms, "nodes": nodes,
+                            "algorithmic_bytes": "32 B per node (u, H, out) + 16 B per sparse-grid node, "
+                                                 "sparse nodes counted as nodes (upper bound)",
+                            "gbs_lower_bound": 32.0 * nodes / (ms / 1e3) / 1e9}
+    # (2) heat experiment
+    try:
+        Ph = B.Problem(3, 9, 1, B.PIT_OP_HEAT, stream=stream.cuda_stream)
+        T, N, m, s_rec = 1.0, 1024, 16, 4
+        dt = T / N
+        F = torch.empty(N * Ph.n_total, dtype=torch.float64, device=u0.device)
+        for n in range(N):
+            Ph.sample_initial(3, [(n + 1) * dt], F[n * Ph.n_total:(n + 1) * Ph.n_total])
+        uh = torch.empty(Ph.n_total, dtype=torch.float64, device=u0.device)
+        Ph.sample_initial(2, [0.0], uh)
+        uT = torch.empty_like(uh)
+        fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-11, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+        crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=4000)
+        o = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-8, maxit=64, fine=fine, crs=crs, relax=B.PIT_RELAX_F, init=True,
+                         recomb=s_rec, forcing=F)
+        ms, st = timed(lambda: Ph.mgrit_solve(uh, o, uT))
+        pts = W.eval_points(3, [0.0] * 3, [1.0] * 3, n_uniform=8192, n_diag=65)
+        vals = np.empty(pts.shape[0])
+        Ph.combine(uT, pts, vals)
+        ustar = np.sqrt(np.sum(pts * pts, axis=1) + T * T) * np.exp(-T) * np.prod(np.sin(np.pi * pts), axis=1)
+        out["heat_experiment"] = {"grids": Ph.G, "n_total": Ph.n_total, "nsteps": N, "t": [0.0, T], "m": m,
+                                  "recombination_steps": s_rec, "ms": ms, "cycles": st.max_cycles,
+                                  "value": Ph.n_total * N / (ms / 1e3), "unit": UNIT,
+                                  "rel_l2_error_vs_u_star": float(np.linalg.norm(vals - ustar) / np.linalg.norm(ustar))}
+        Ph.close()
+    except B.PitError as err:
+        out["heat_experiment"] = {"unavailable": str(err)}
+    # (3) linear oscillator of Sec. 4.4.1
+    try:
+        A = np.array([[0.0, 1.0], [-1.0, -0.1]])
+        H = np.array([[0.0, 0.0], [0.0, 0.2]])  # 2 sigma D sigma^T, sigma = (0, 1)^T, D = 0.1
+        Po = B.Problem(2, 14, 6, B.PIT_OP_LSDE, [-10.0] * 2, [10.0] * 2, drift=A, diffusion=H,
+                       stream=stream.cuda_stream)
+        T, N, m = 1.0, 3200, 16
+        M0, C0 = np.array([5.0, 5.0]), np.diag([1.0 / 9.0] * 2)
+        uo = torch.empty(Po.n_total, dtype=torch.float64, device=u0.device)
+        Po.sample_initial(4, np.concatenate([M0, C0.ravel()]), uo)
+        uT = torch.empty_like(uo)
+        fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-10, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
+        crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=4000)
+        o = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-8, maxit=64, fine=fine, crs=crs, relax=B.PIT_RELAX_F, init=True)
+        ms, st = timed(lambda: Po.mgrit_solve(uo, o, uT))
+        seq_ms, _ = timed(lambda: Po.sequential_solve(uo, T / N, N, uT, fine))
+        # closed-form law: mean e^{AT} M0, covariance e^{AT} C0 e^{A^T T} + int_0^T e^{As} H e^{A^T s} ds
+        import scipy.linalg as sl
+        import scipy.integrate as si
+        E = sl.expm(A * T)
+        Q = si.quad_vec(lambda t: (sl.expm(A * t) @ H @ sl.expm(A * t).T).ravel(), 0.0, T)[0].reshape(2, 2)
+        Mt, Ct = E @ M0, E @ C0 @ E.T + Q
+        x = np.linspace(-10.0, 10.0, 401)[1:-1]
+        diag_pts = np.stack([x, x], axis=1)
+        vals = np.empty(diag_pts.shape[0])
+        Po.mgrit_solve(uo, o, uT)
+        Po.combine(uT, diag_pts, vals)
+        z = diag_pts - Mt
+        Ci = np.linalg.inv(Ct)
+        exact = np.exp(-0.5 * np.einsum("ni,ij,nj->n", z, Ci, z)) / (2 * np.pi * np.sqrt(np.linalg.det(Ct)))
+        out["linear_oscillator"] = {
+            "problem": "Sec. 4.4.1 tuned case: d = 2, level 14, L0 = 6, [-10, 10]^2, T = 1, 3200 steps, "
+                       "A = [[0, 1], [-1, -0.1]], H = diag(0, 0.2), normal initial law mean (5, 5), cov I/9",
+            "grids": Po.G, "n_total": Po.n_total, "m": m, "ms": ms, "cycles": st.max_cycles,
+            "value": Po.n_total * N / (ms / 1e3), "unit": UNIT, "sequential_ms": seq_ms,
+            "max_abs_error_on_diagonal": float(np.abs(vals - exact).max()),
+            "max_density_on_diagonal": float(exact.max()),
+            "paper_context": "Table 3: tuned CTMGRIT^loc 107 s (1760 cores), CT 162 s (176 cores), "
+                             "error on the diagonal 0.0028 / 0.008 (Yuma cluster, residual mode tol 1e-4)"}
+        Po.close()
+    except B.PitError as err:
+        out["linear_oscillator"] = {"unavailable": str(err)}
+    return out
+
+
 def seeded_grids(G, count, seed=7):
     """A seeded random subset of `count` grids (sorted)."""
     from paper_2509_22156_gb300 import workloads as W
