@@ -545,7 +545,7 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     }
     // (a lane's workspaces and CTA sizes are prepared before its first launch)
     if (v[NBKT].n > 0 && !L)
-        CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op)));
+        CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op, P->desc.d)));
     if (!L)
         for (int q = 0; q < NPART; ++q) TRY(tune(P, prec, wide, q, o, c, active));
     cudaStream_t st[NPART];
@@ -1633,7 +1633,7 @@ pit_status lanes_prime(Mg &M, int Nc)
         c.nsteps = reps[r].nsteps;
         c.in = P->m_U.d();  // u0 at every C-point
         c.is = nt;
-        if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op)));
+        if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op, P->desc.d)));
         for (int part = 0; part < NPART; ++part) TRY(tune(P, prec, c.nb >= 8, part, *reps[r].so, c, M.active));
     }
     return PIT_OK;

@@ -87,7 +87,9 @@ struct StepArgs {
     double *xg;              // state in global memory (grids too large for shared memory):
     double *bg;              //   x and b (MIXED) of entry b at xg/bg + b*n_total + grid offset, the
                              //   FP32 step increment (MIXED) at slab 2;
-                             //   PLAIN: Krylov vector k at xg + ((1+k) n_batch + b) n_total + offset
+                             //   PLAIN: Krylov vector k at xg + ((1+k) n_batch + b) n_total + offset,
+                             //   then (table operators) the item's 2d+1 coefficient rows of n values
+                             //   at xg + (1+NKV) n_batch n_total + (b n_total + offset)(2d+1)
     long long n_total;
     const int *active;       // per grid, NULL = all active
     const double *faces;     // variable coefficient at the 2d faces of every node, or NULL
@@ -157,7 +159,7 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
 // (x, b and the FP32 step increment for MIXED; x and the Krylov vectors for
 // PLAIN).
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n);
-int xg_slabs(int prec, int op);
+int xg_slabs(int prec, int op, int d);
 // Raise the dynamic shared-memory limit of every backward-Euler kernel.
 cudaError_t phi_kernels_init(size_t max_smem);
 // Neighbour masks of every node (bit 2i: interior neighbour at -e_i, 2i+1: at +e_i).

@@ -14,11 +14,18 @@ size_t phi_smem_bytes(int prec, int op, int d, int n, int na)
 
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n)
 {
+    // the FP64 form keeps its coefficient table in global memory as well
     const size_t ld = (size_t)((n + 3) & ~3);
-    return (size_t)n_tab(op, d) * ld * 8 + (size_t)n_f32(op, prec, d, true) * ld * 4 + ld * 2 + 16;
+    return (size_t)(prec == PLAIN ? 0 : n_tab(op, d)) * ld * 8 + (size_t)n_f32(op, prec, d, true) * ld * 4 + ld * 2 +
+           16;
 }
 
-int xg_slabs(int prec, int op) { return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) : 3; }  // PAIR uses two
+int xg_slabs(int prec, int op, int d)
+{
+    // PLAIN: x, the Krylov vectors and the coefficient table; MIXED: x, b and
+    // the step increment; PAIR uses two
+    return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) + n_tab(op, d) : 3;
+}
 
 static size_t g_max_smem = 0;
 

@@ -885,7 +885,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     const int ld = (n + 3) & ~3;
     const double dt = a.dt;
     constexpr int K = (OP == PIT_OP_HEAT) ? 0 : 2 * D + 1;
-    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (DRIFT ? 5 : 4) : 2) + K;
+    // the FP64 global-state variant keeps the coefficient table in global
+    // memory too (grids of any size); the others keep it on chip
+    constexpr bool GTAB = XG && PREC == PLAIN && K > 0;
+    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (DRIFT ? 5 : 4) : 2) + (GTAB ? 0 : K);
     constexpr int NKV = DRIFT ? (PREC == PLAIN ? 5 : 6)
                                           : (PREC == PLAIN ? 4 : (OP == PIT_OP_HEAT && !XG ? 6 : 5));
     constexpr int NDV = (PREC == MIXED && !XG) ? 1 : 0;  // dv in shared memory
@@ -900,7 +903,13 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     // global-state variant, in per-vector slabs of n_batch x n_total after x
     double *v64 = XG ? a.xg + ((long long)a.n_batch + b) * a.n_total + GI.off : s64 + ld;
     const long long vs = XG ? (long long)a.n_batch * a.n_total : (long long)ld;
-    double *tab64 = PREC == SINGLE ? nullptr : s64 + (size_t)(NF64 - K) * ld;
+    // GTAB: the item's table is K x n contiguous doubles in the slab after the
+    // Krylov vectors, at (b n_total + grid offset) K
+    double *tab64 = PREC == SINGLE ? nullptr
+                    : GTAB ? a.xg + (long long)(1 + NKV) * a.n_batch * a.n_total +
+                                 ((long long)b * a.n_total + GI.off) * K
+                           : s64 + (size_t)(NF64 - (GTAB ? 0 : K)) * ld;
+    const int tld = GTAB ? n : ld;  // stride between the table's entries
     float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
     float *tab32 = f32 + (size_t)(NKV + NDV) * ld;
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
@@ -941,8 +950,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 #pragma unroll
             for (int i = 0; i < D; ++i) {
                 if constexpr (PREC != SINGLE && PREC != PAIR) {
-                    tab64[(1 + 2 * i) * ld + j] = cm[i];
-                    tab64[(2 + 2 * i) * ld + j] = cp[i];
+                    tab64[(1 + 2 * i) * tld + j] = cm[i];
+                    tab64[(2 + 2 * i) * tld + j] = cp[i];
                 }
                 if constexpr (PREC == PAIR) {
                     // face coefficients dt a / h^2 as pairs, in the FP64 table's place
@@ -968,7 +977,8 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     H64.mask = HT.mask = T64.mask = T32.mask = mask;
     T64.tab = tab64;
     T32.tab = tab32;
-    T64.ld = T32.ld = ld;
+    T64.ld = tld;
+    T32.ld = ld;
     if constexpr (CROSS) {
         int q = 0;
 #pragma unroll

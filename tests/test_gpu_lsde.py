@@ -119,3 +119,32 @@ def test_pair_form_is_refused_for_the_drift_operator():
         P.phi_batch(0.01, x, torch.empty_like(x), B.solve_opts(B.PIT_PREC_MIXED_PAIR, inner_rtol=1e-4))
     assert e.value.status == B.PIT_ERR_UNSUPPORTED
     P.close()
+
+
+def test_large_grids_in_the_fp64_global_state_class_match_oracle():
+    """Grids too large for the on-chip solve (here up to 8,001 nodes, the
+    oscillator at level 12, L0 = 5) run the FP64 form's global-state variant,
+    which keeps x, the Krylov vectors and the coefficient table in global
+    memory; steps and MGRIT against the oracle."""
+    d, n, L0, w = 2, 12, 5, 10.0
+    P = B.Problem(d, n, L0, B.PIT_OP_LSDE, [-w] * d, [w] * d, drift=OSC_A, diffusion=OSC_H)
+    O = oracle.Problem(d, n, L0, oracle.OP_LSDE, [-w] * d, [w] * d, drift=OSC_A, diffusion=OSC_H)
+    assert max(O.offsets[g + 1] - O.offsets[g] for g in range(O.G)) == 8001
+    nb, dt = 2, 0.01
+    u = W.random_vector(51, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    st = P.phi_batch(dt, torch.from_numpy(u).cuda(), out, B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=20000))
+    assert st.n_failed == 0
+    assert rel(out.cpu().numpy(), O.phi(dt, u, rtol=1e-15)) < 1e-10
+    # MGRIT in FP64 on the oscillator's normal initial law
+    N, m, T = 64, 8, 0.5
+    u0 = O.initial(4, np.concatenate([[5.0, 5.0], np.diag([1 / 9.0, 1 / 9.0]).ravel()]))
+    ref = O.sequential(u0, T / N, N, rtol=1e-15)
+    fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=20000)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    opts = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-12 * np.abs(ref).max(), maxit=64, fine=fine, crs=fine,
+                        relax=B.PIT_RELAX_F, init=True)
+    st = P.mgrit_solve(torch.from_numpy(u0).cuda(), opts, uT)
+    assert st.n_converged == P.G
+    assert rel(uT.cpu().numpy(), ref) < 1e-10
+    P.close()
