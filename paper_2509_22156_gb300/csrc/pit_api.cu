@@ -543,6 +543,11 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
         v[q] = part_view(P, L, prec, q);
         if (v[q].n > 0) ++n_parts;
     }
+    // the FP64 global-state variant of the table operators indexes its table
+    // rows with a 32-bit stride of n_batch x n_total
+    if (v[NBKT].n > 0 && prec == PLAIN && P->desc.op != PIT_OP_HEAT && (long long)c.nb * P->ntot >= (1LL << 31))
+        return fail(PIT_ERR_UNSUPPORTED, "batch of %d states of %lld nodes too large for the FP64 global-state "
+                                         "solver of this operator", c.nb, P->ntot);
     // (a lane's workspaces and CTA sizes are prepared before its first launch)
     if (v[NBKT].n > 0 && !L)
         CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op, P->desc.d)));

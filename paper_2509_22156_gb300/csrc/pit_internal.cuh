@@ -88,8 +88,8 @@ struct StepArgs {
     double *bg;              //   x and b (MIXED) of entry b at xg/bg + b*n_total + grid offset, the
                              //   FP32 step increment (MIXED) at slab 2;
                              //   PLAIN: Krylov vector k at xg + ((1+k) n_batch + b) n_total + offset,
-                             //   then (table operators) the item's 2d+1 coefficient rows of n values
-                             //   at xg + (1+NKV) n_batch n_total + (b n_total + offset)(2d+1)
+                             //   then (table operators) coefficient row k of the item at
+                             //   xg + ((1+NKV+k) n_batch + b) n_total + offset
     long long n_total;
     const int *active;       // per grid, NULL = all active
     const double *faces;     // variable coefficient at the 2d faces of every node, or NULL

@@ -903,13 +903,15 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     // global-state variant, in per-vector slabs of n_batch x n_total after x
     double *v64 = XG ? a.xg + ((long long)a.n_batch + b) * a.n_total + GI.off : s64 + ld;
     const long long vs = XG ? (long long)a.n_batch * a.n_total : (long long)ld;
-    // GTAB: the item's table is K x n contiguous doubles in the slab after the
-    // Krylov vectors, at (b n_total + grid offset) K
+    // GTAB: table entry k of the item in slab (1 + NKV + k) n_batch + b after
+    // the Krylov vectors, at the grid's offset (every array of the global
+    // workspace is partitioned by grid, so launches of different lanes and
+    // batch widths that run concurrently on disjoint grids never overlap)
     double *tab64 = PREC == SINGLE ? nullptr
-                    : GTAB ? a.xg + (long long)(1 + NKV) * a.n_batch * a.n_total +
-                                 ((long long)b * a.n_total + GI.off) * K
+                    : GTAB ? a.xg + ((long long)(1 + NKV) * a.n_batch + b) * a.n_total + GI.off
                            : s64 + (size_t)(NF64 - (GTAB ? 0 : K)) * ld;
-    const int tld = GTAB ? n : ld;  // stride between the table's entries
+    // stride between the table's entries (the host keeps n_batch n_total below 2^31 here)
+    const int tld = GTAB ? (int)((long long)a.n_batch * a.n_total) : ld;
     float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
     float *tab32 = f32 + (size_t)(NKV + NDV) * ld;
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
