@@ -609,12 +609,11 @@ def extras(P, wl, B, W, u0, stream):
     with its streaming bytes per application; (2) the heat experiment of
     Sec. 4.2 (manufactured u*, forcing, s = 4 recombination steps, MGRIT per
     grid) on the heat3d_n9 grid set, error against u*(T); (3) the
-    two-dimensional linear oscillator of Sec. 4.4.1 (Table 3's tuned problem,
-    T = 1, 3200 steps) with the general linear-SDE operator at level 10,
-    L0 = 3 instead of the paper's 14 and 6 (the table-driven drift operators
-    keep per-node coefficient tables on chip, which limits their grids to
-    about 2,000 nodes; the paper's grids hold up to 32,193), error against the
-    closed-form normal law on the diagonal."""
+    two-dimensional linear oscillator of Sec. 4.4.1 (Table 3's tuned problem:
+    level 14, L0 = 6, T = 1, 3200 steps) with the general linear-SDE operator
+    in the FP64 form (its grids of up to 32,385 nodes run in the global-state
+    class), sequential stepping and MGRIT, error against the closed-form
+    normal law on the diagonal."""
     import torch
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -671,18 +670,18 @@ def extras(P, wl, B, W, u0, stream):
     try:
         A = np.array([[0.0, 1.0], [-1.0, -0.1]])
         H = np.array([[0.0, 0.0], [0.0, 0.2]])  # 2 sigma D sigma^T, sigma = (0, 1)^T, D = 0.1
-        Po = B.Problem(2, 10, 3, B.PIT_OP_LSDE, [-10.0] * 2, [10.0] * 2, drift=A, diffusion=H,
+        Po = B.Problem(2, 14, 6, B.PIT_OP_LSDE, [-10.0] * 2, [10.0] * 2, drift=A, diffusion=H,
                        stream=stream.cuda_stream)
         T, N, m = 1.0, 3200, 16
         M0, C0 = np.array([5.0, 5.0]), np.diag([1.0 / 9.0] * 2)
         uo = torch.empty(Po.n_total, dtype=torch.float64, device=u0.device)
         Po.sample_initial(4, np.concatenate([M0, C0.ravel()]), uo)
         uT = torch.empty_like(uo)
-        fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-10, maxit=4000, inner_rtol=1e-5, ir_maxit=12)
-        crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=4000)
+        fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-10, maxit=20000)
+        crs = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-2, maxit=20000)
         o = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-8, maxit=64, fine=fine, crs=crs, relax=B.PIT_RELAX_F, init=True)
-        ms, st = timed(lambda: Po.mgrit_solve(uo, o, uT))
-        seq_ms, _ = timed(lambda: Po.sequential_solve(uo, T / N, N, uT, fine))
+        ms, st = timed(lambda: Po.mgrit_solve(uo, o, uT), reps=1)
+        seq_ms, _ = timed(lambda: Po.sequential_solve(uo, T / N, N, uT, fine), reps=1)
         # closed-form law: mean e^{AT} M0, covariance e^{AT} C0 e^{A^T T} + int_0^T e^{As} H e^{A^T s} ds
         import scipy.linalg as sl
         import scipy.integrate as si
@@ -698,9 +697,9 @@ def extras(P, wl, B, W, u0, stream):
         Ci = np.linalg.inv(Ct)
         exact = np.exp(-0.5 * np.einsum("ni,ij,nj->n", z, Ci, z)) / (2 * np.pi * np.sqrt(np.linalg.det(Ct)))
         out["linear_oscillator"] = {
-            "problem": "Sec. 4.4.1 tuned case at level 10, L0 = 3 (the paper: 14, 6): d = 2, [-10, 10]^2, T = 1, "
-                       "3200 steps, A = [[0, 1], [-1, -0.1]], H = diag(0, 0.2), normal initial law mean (5, 5), "
-                       "cov I/9",
+            "problem": "Sec. 4.4.1 tuned case: d = 2, level 14, L0 = 6, [-10, 10]^2, T = 1, 3200 steps, "
+                       "A = [[0, 1], [-1, -0.1]], H = diag(0, 0.2), normal initial law mean (5, 5), cov I/9; "
+                       "FP64 BiCGStab to 1e-10, MGRIT m = 16, tolerance 1e-8",
             "grids": Po.G, "n_total": Po.n_total, "m": m, "ms": ms, "cycles": st.max_cycles,
             "value": Po.n_total * N / (ms / 1e3), "unit": UNIT, "sequential_ms": seq_ms,
             "max_abs_error_on_diagonal": float(np.abs(vals - exact).max()),
