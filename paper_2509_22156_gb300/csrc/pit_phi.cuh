@@ -126,6 +126,20 @@ struct HeatSt {
         }
         return s;
     }
+    // b_j - (A p)_j as one chain of fused multiply-adds (one instruction fewer
+    // than the product followed by a subtraction)
+    __device__ __forceinline__ T resid(T bj, const T *p, int j) const
+    {
+        const unsigned mk = mask[j];
+        T s = fma(-diag, p[j], bj);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T pm = ((mk >> (2 * i)) & 1u) ? p[j - S[i]] : T(0);
+            const T pp = ((mk >> (2 * i + 1)) & 1u) ? p[j + S[i]] : T(0);
+            s = fma(-off[i], pm + pp, s);
+        }
+        return s;
+    }
 };
 
 // Variable-coefficient stencil from a per-node table in shared memory
@@ -153,23 +167,42 @@ struct TabSt {
             const int jp = ((mk >> (2 * i + 1)) & 1u) ? j + S[i] : j;
             s += tab[(1 + 2 * i) * ld + j] * p[jm] + tab[(2 + 2 * i) * ld + j] * p[jp];
         }
-        if constexpr (CROSS && NP > 0) {
-            int q = 0;
+        if constexpr (CROSS && NP > 0) s += cross(p, j, mk);
+        return s;
+    }
+    __device__ __forceinline__ T cross(const T *p, int j, unsigned mk) const
+    {
+        T s = T(0);
+        int q = 0;
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                const bool im = (mk >> (2 * i)) & 1u, ip = (mk >> (2 * i + 1)) & 1u;
+        for (int i = 0; i < D; ++i) {
+            const bool im = (mk >> (2 * i)) & 1u, ip = (mk >> (2 * i + 1)) & 1u;
 #pragma unroll
-                for (int k = i + 1; k < D; ++k, ++q) {
-                    const bool km = (mk >> (2 * k)) & 1u, kp = (mk >> (2 * k + 1)) & 1u;
-                    T c = T(0);
-                    if (ip && kp) c += p[j + S[i] + S[k]];
-                    if (ip && km) c -= p[j + S[i] - S[k]];
-                    if (im && kp) c -= p[j - S[i] + S[k]];
-                    if (im && km) c += p[j - S[i] - S[k]];
-                    s += cr[q] * c;
-                }
+            for (int k = i + 1; k < D; ++k, ++q) {
+                const bool km = (mk >> (2 * k)) & 1u, kp = (mk >> (2 * k + 1)) & 1u;
+                T c = T(0);
+                if (ip && kp) c += p[j + S[i] + S[k]];
+                if (ip && km) c -= p[j + S[i] - S[k]];
+                if (im && kp) c -= p[j - S[i] + S[k]];
+                if (im && km) c += p[j - S[i] - S[k]];
+                s += cr[q] * c;
             }
         }
+        return s;
+    }
+    // b_j - (A p)_j as one chain of fused multiply-adds (unscaled table)
+    __device__ __forceinline__ T resid(T bj, const T *p, int j) const
+    {
+        const unsigned mk = mask[j];
+        T s = fma(-tab[j], p[j], bj);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int jm = ((mk >> (2 * i)) & 1u) ? j - S[i] : j;
+            const int jp = ((mk >> (2 * i + 1)) & 1u) ? j + S[i] : j;
+            s = fma(-tab[(1 + 2 * i) * ld + j], p[jm], s);
+            s = fma(-tab[(2 + 2 * i) * ld + j], p[jp], s);
+        }
+        if constexpr (CROSS && NP > 0) s -= cross(p, j, mk);
         return s;
     }
 };
@@ -1082,6 +1115,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         if constexpr (OP == PIT_OP_HEAT) return H64(v, j);
         else return T64(v, j);
     };
+    auto RES64 = [&](double bj, const double *v, int j) -> double {  // b_j - (A v)_j
+        if constexpr (OP == PIT_OP_HEAT) return H64.resid(bj, v, j);
+        else return T64.resid(bj, v, j);
+    };
 
     int status = PIT_OK, iters = 0, passes = 0;
     const bool carry_ok = (f0 == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
@@ -1121,7 +1158,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             } else {
                 for (int j = tid; j < n; j += nt) {
                     const double bj = f ? x[j] + dt * f[j] : x[j];
-                    r[j] = bj - A64(x, j);
+                    r[j] = RES64(bj, x, j);
                     bb[0] += bj * bj;
                 }
             }
@@ -1420,7 +1457,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 float accf[1] = {0.0f};
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
-                    const float rf = to_f32(bvec[j] - A64(x, j), kr);
+                    const float rf = to_f32(RES64(bvec[j], x, j), kr);
                     rv[j] = rf;
                     accf[0] += rf * rf;
                 }
@@ -1496,7 +1533,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
                     const double xj = x[j];
-                    const float rf = to_f32(bvec[j] - A64(x, j), ks);
+                    const float rf = to_f32(RES64(bvec[j], x, j), ks);
                     rv[j] = rf;
                     accf[0] += rf * rf;
                     if (carry_ok) {
