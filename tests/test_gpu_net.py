@@ -158,7 +158,7 @@ def test_training_reduces_loss_and_is_judged():
     assert st.loss_last_epoch < st.loss_first_epoch
     assert st.holdout_err_learned > 0 and st.holdout_err_implicit > 0
     assert st.accepted == (1 if st.holdout_err_learned <= st.holdout_err_implicit else 0)
-    # whatever the judge said, MGRIT with the coarse choice reaches the fine solution
+    # whatever the hold-out judge said, MGRIT with the coarse choice reaches the fine solution
     O = oracle.Problem(wl.d, n, wl.L0, wl.op, wl.lo, wl.hi, vamp=wl.vamp)
     u0 = O.initial(wl.ic_kind, wl.ic_params)
     tol = 1e-10 * np.abs(u0).max()
