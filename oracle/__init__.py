@@ -57,7 +57,7 @@ def lib():
             L.or_create.argtypes = [c_int, c_int, c_int, c_int, vp, vp, c_double, c_double, c_double]
             L.or_destroy.argtypes = [vp]
             L.or_set_sde.restype = c_int
-            L.or_set_sde.argtypes = [vp, vp, vp]
+            L.or_set_sde.argtypes = [vp, vp, vp, c_int]
             L.or_info.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_set_threads.argtypes = [c_int]
             L.or_max_threads.restype = c_int
@@ -130,7 +130,7 @@ class Problem:
     """One combination-technique problem on the CPU (FP64)."""
 
     def __init__(self, d, n, L0=1, op=OP_HEAT, lo=None, hi=None, theta=1.0, sigma=1.0, vamp=0.5,
-                 drift=None, diffusion=None):
+                 drift=None, diffusion=None, central=False):
         self.d, self.n, self.L0, self.op = d, n, L0, op
         self.lo = _f64(lo if lo is not None else [0.0] * d)
         self.hi = _f64(hi if hi is not None else [1.0] * d)
@@ -139,10 +139,13 @@ class Problem:
         if not self._h:
             raise ValueError("invalid problem description")
         if op == OP_LSDE:
-            # linear SDE dX = A X dt + sigma dW, H = 2 sigma D sigma^T (Sec. 4.4)
+            # linear SDE dX = A X dt + sigma dW, H = 2 sigma D sigma^T (Sec. 4.4);
+            # drift flux donor cell (first order) or central (second order)
             self.drift = _f64(drift).reshape(d, d)
             self.diffusion = _f64(diffusion).reshape(d, d)
-            lib().or_set_sde(self._h, _p(self.drift), _p(self.diffusion))
+            self.central = bool(central)
+            if lib().or_set_sde(self._h, _p(self.drift), _p(self.diffusion), int(self.central)) != 0:
+                raise ValueError("invalid linear-SDE parameters")
         G = ctypes.c_int()
         nt = ctypes.c_longlong()
         lib().or_info(self._h, ctypes.byref(G), ctypes.byref(nt), None, None, None)

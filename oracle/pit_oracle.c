@@ -23,6 +23,12 @@
  *                                  discrete mass balance, M-matrix sign pattern
  *   or_apply (var. coeff. heat)    consistency order 2 vs analytic operator,
  *                                  symmetry, reduction to heat at amplitude 0
+ *   or_apply (linear SDE)          reduction to OU for diagonal drift; order 1
+ *                                  (donor cell) and order 2 (central) vs the
+ *                                  analytic operator on a full-covariance
+ *                                  normal density; mass balance; central
+ *                                  drift: symmetric part diagonal (trace A);
+ *                                  closed-form normal law approached
  *   or_cg / or_bicgstab            dense direct solve (numpy) on tiny grids
  *   or_phi / or_sequential         heat closed form per mode; OU Gaussian trend
  *   or_mgrit                       converged = sequential; FCF exactness after
@@ -58,6 +64,7 @@ typedef struct {
     double theta, sigma, vamp;       /* OU drift/diffusion; var-coef amplitude */
     double sde_A[OR_MAXD * OR_MAXD]; /* linear SDE dX = A X dt + sigma dW: drift matrix */
     double sde_H[OR_MAXD * OR_MAXD]; /* H = 2 sigma D sigma^T (row major)              */
+    int sde_central;                 /* drift flux: 0 donor cell, 1 central average   */
     int G;
     int *lev;                        /* G*d level multi-indices               */
     long long *off;                  /* G+1 packed offsets                    */
@@ -154,12 +161,15 @@ void *or_create(int d, int n, int L0, int op, const double *lo, const double *hi
 }
 
 /* Drift matrix A and diffusion matrix H (row major, d x d) of the linear SDE
- * operator (op 3). */
-int or_set_sde(void *vp, const double *A, const double *H)
+ * operator (op 3), and its drift flux: central = 0 donor cell (first order),
+ * 1 the central average of the two neighbours (second order). */
+int or_set_sde(void *vp, const double *A, const double *H, int central)
 {
     or_problem *P = (or_problem *)vp;
+    if (central != 0 && central != 1) return OR_EINVAL;
     memcpy(P->sde_A, A, sizeof(double) * P->d * P->d);
     memcpy(P->sde_H, H, sizeof(double) * P->d * P->d);
+    P->sde_central = central;
     return OR_OK;
 }
 
@@ -255,7 +265,8 @@ static double varcoef(const or_problem *P, const double *x)
  *   linear SDE (Eq. "sde_fokker_planck", dX = A X dt + sigma dW, H = 2 sigma
  *   D sigma^T): L p = sum_i d_i((A x)_i p) - (1/2) sum_ij H_ij d_i d_j p:
  *               drift as the donor-cell flux above with face velocity
- *               v = (A x)_i at the face x_{j+1/2 e_i}; diagonal diffusion
+ *               v = (A x)_i at the face x_{j+1/2 e_i}, or (central) the
+ *               flux F_{j+1/2} = v (p_j + p_{j+e_i}) / 2; diagonal diffusion
  *               (H_ii / 2)(2 p_j - p_{j-e_i} - p_{j+e_i}) / h_i^2; for i < k
  *               the mixed term -((H_ik + H_ki) / 2) (p_{++} - p_{+-} - p_{-+}
  *               + p_{--}) / (4 h_i h_k) over the four diagonal neighbours
@@ -295,8 +306,14 @@ static void apply_grid(const or_problem *P, int g, double dt, const double *p, d
                 for (int k = 0; k < G.d; ++k) ax += P->sde_A[i * G.d + k] * x[k];
                 double vp = ax + 0.5 * h * P->sde_A[i * G.d + i];
                 double vm = ax - 0.5 * h * P->sde_A[i * G.d + i];
-                double Fp = fmax(vp, 0.0) * p[j] + fmin(vp, 0.0) * pp;
-                double Fm = fmax(vm, 0.0) * pm + fmin(vm, 0.0) * p[j];
+                double Fp, Fm;
+                if (P->sde_central) {
+                    Fp = vp * 0.5 * (p[j] + pp);
+                    Fm = vm * 0.5 * (pm + p[j]);
+                } else {
+                    Fp = fmax(vp, 0.0) * p[j] + fmin(vp, 0.0) * pp;
+                    Fm = fmax(vm, 0.0) * pm + fmin(vm, 0.0) * p[j];
+                }
                 Lp += (Fp - Fm) / h + 0.5 * P->sde_H[i * G.d + i] * (2.0 * p[j] - pm - pp) / (h * h);
                 for (int k = i + 1; k < G.d; ++k) {
                     double hik = 0.5 * (P->sde_H[i * G.d + k] + P->sde_H[k * G.d + i]);

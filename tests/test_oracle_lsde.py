@@ -8,6 +8,10 @@ with a full drift matrix A and H = 2 sigma D sigma^T, so that
     analytic operator, written out in numpy from the density's derivatives
     (d_i p = -p g_i, d_i d_j p = p (g_i g_j - Cinv_ij), g = Cinv (x - M)),
     at first order in h (donor-cell drift);
+  - with the central drift flux (the paper's second-order finite differences)
+    the same comparison converges at second order, and the symmetric part of
+    the drift operator is trace(A) times the identity (the face fluxes are
+    skew, only the divergence of the velocity field, trace A, is left);
   - the flux form and the four-point mixed stencil conserve mass away from
     the boundary;
   - a normal initial density evolves towards the closed-form normal law of
@@ -95,12 +99,56 @@ def test_operator_is_first_order_consistent_on_a_full_covariance_gaussian():
     assert errs[2] < 0.2, errs
 
 
-def test_mass_is_conserved_away_from_the_boundary():
+def test_central_drift_is_second_order_consistent_on_a_full_covariance_gaussian():
+    M, C = np.array([0.4, -0.2]), np.array([[0.5, 0.2], [0.2, 0.4]])
+    errs = []
+    for lev in (5, 6, 7):
+        O = oracle.Problem(2, 2 * lev - 1, lev, oracle.OP_LSDE, lo=[-4.0] * 2, hi=[4.0] * 2, drift=A2,
+                           diffusion=H2, central=True)
+        g = [k for k in range(O.G) if tuple(O.levels[k]) == (lev, lev)][0]
+        p = O.initial(4, gauss_params(M, C))
+        Lp = (O.apply(1.0, p) - p)[O.grid_slice(g)]
+        ref = analytic_L(node_coords(O, g), M, C, A2, H2)
+        errs.append(np.abs(Lp - ref).max() / np.abs(ref).max())
+    # measured 0.060, 0.016, 0.0040: second order
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+    assert errs[2] < 0.005, errs
+
+
+@pytest.mark.parametrize("central", [False, True])
+def test_symmetric_part_of_the_central_drift_is_the_trace(central):
+    # (I + dt L) assembled column by column on every grid of a small problem,
+    # drift only: M + M^T - 2 I = dt (L + L^T) = dt trace(A) I for the central
+    # flux; the donor-cell flux adds numerical diffusion, which this detects
+    A = np.array([[-0.4, 1.0], [-1.0, -0.3]])
+    dt = 0.1
+    O = oracle.Problem(2, 4, 1, oracle.OP_LSDE, lo=[-3.0] * 2, hi=[3.0] * 2, drift=A, diffusion=np.zeros((2, 2)),
+                       central=central)
+    worst = 0.0
+    for g in range(O.G):
+        sl = O.grid_slice(g)
+        n = sl.stop - sl.start
+        Mx = np.zeros((n, n))
+        for k in range(n):
+            e = np.zeros(O.n_total)
+            e[sl.start + k] = 1.0
+            Mx[:, k] = O.apply(dt, e)[sl]
+        S = (Mx + Mx.T - 2.0 * np.eye(n)) / dt
+        worst = max(worst, float(np.abs(S - np.trace(A) * np.eye(n)).max()))
+    if central:
+        assert worst < 1e-13
+    else:
+        assert worst > 1.0
+
+
+@pytest.mark.parametrize("central", [False, True])
+def test_mass_is_conserved_away_from_the_boundary(central):
     M, C = np.array([0.3, 0.1, -0.2]), np.array([[0.4, 0.1, 0.0], [0.1, 0.5, 0.1], [0.0, 0.1, 0.3]])
     A3 = np.array([[-0.5, 0.3, 0.0], [-0.2, -0.4, 0.6], [0.1, -0.6, -0.3]])
     H3 = np.array([[0.4, 0.1, 0.0], [0.1, 0.3, 0.05], [0.0, 0.05, 0.2]])
     # a box wide enough that the density is negligible at the boundary nodes
-    O = oracle.Problem(3, 8, 3, oracle.OP_LSDE, lo=[-9.0] * 3, hi=[9.0] * 3, drift=A3, diffusion=H3)
+    O = oracle.Problem(3, 8, 3, oracle.OP_LSDE, lo=[-9.0] * 3, hi=[9.0] * 3, drift=A3, diffusion=H3,
+                       central=central)
     p = O.initial(4, gauss_params(M, C))
     q = O.apply(0.01, p)
     for g in range(O.G):
@@ -121,14 +169,21 @@ def test_backward_euler_approaches_the_closed_form_law():
     Mt, Ct = law(T, M, C, A2, H2)
     pts = W.eval_points(2, [-3.0, -3.0], [4.0, 4.0], n_uniform=3000, n_diag=0)
     ref = gauss(pts, Mt, Ct)
-    errs = []
-    for n, N in ((6, 16), (7, 64), (8, 256)):
-        O = oracle.Problem(2, n, 3, oracle.OP_LSDE, lo=[-6.0] * 2, hi=[6.0] * 2, drift=A2, diffusion=H2)
-        u = O.sequential(O.initial(4, gauss_params(M, C)), T / N, N, rtol=1e-13)
-        errs.append(np.linalg.norm(O.combine(u, pts) - ref) / np.linalg.norm(ref))
-    # measured 0.50, 0.31, 0.19: the donor-cell drift and backward Euler are
+    errs = {}
+    for central in (False, True):
+        errs[central] = []
+        for n, N in ((6, 16), (7, 64), (8, 256)):
+            O = oracle.Problem(2, n, 3, oracle.OP_LSDE, lo=[-6.0] * 2, hi=[6.0] * 2, drift=A2, diffusion=H2,
+                               central=central)
+            u = O.sequential(O.initial(4, gauss_params(M, C)), T / N, N, rtol=1e-13)
+            errs[central].append(np.linalg.norm(O.combine(u, pts) - ref) / np.linalg.norm(ref))
+    up, ce = errs[False], errs[True]
+    # donor cell, measured 0.50, 0.31, 0.19: its drift and backward Euler are
     # first order, the combination second order
-    assert errs[0] / errs[1] > 1.4 and errs[1] / errs[2] > 1.4 and errs[2] < 0.25, errs
+    assert up[0] / up[1] > 1.4 and up[1] / up[2] > 1.4 and up[2] < 0.25, up
+    # central, measured 0.36, 0.17, 0.078: below the donor cell at every level
+    assert ce[0] / ce[1] > 1.8 and ce[1] / ce[2] > 1.8 and ce[2] < 0.1, ce
+    assert all(c < u for c, u in zip(ce, up)), errs
 
 
 def test_bicgstab_matches_a_dense_solve():
