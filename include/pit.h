@@ -69,11 +69,23 @@ typedef enum {
     PIT_OP_LSDE = 3     /* Fokker-Planck operator of the linear SDE dX = A X dt + sigma dW
                            (Sec. 4.4, Eqs. "sde", "sde_fokker_planck"), A = drift (d x d),
                            H = 2 sigma D sigma^T = diffusion (d x d):
-                           L p = sum_i d_i((A x)_i p) - (1/2) sum_ij H_ij d_i d_j p, donor-cell
-                           drift with face velocity (A x)_i, central diagonal diffusion, and
-                           for i != k the four-point mixed stencil
+                           L p = sum_i d_i((A x)_i p) - (1/2) sum_ij H_ij d_i d_j p, drift
+                           flux with face velocity (A x)_i (donor cell or central, see
+                           pit_drift_scheme), central diagonal diffusion, and for i != k the
+                           four-point mixed stencil
                            (p_{++} - p_{+-} - p_{-+} + p_{--}) / (4 h_i h_k); BiCGStab      */
 } pit_op;
+
+/* Drift flux of the linear-SDE operator at the face x_{j+1/2 e_i} with face
+ * velocity v = (A x)_i there:
+ *   PIT_DRIFT_UPWIND   donor cell, F = max(v,0) p_j + min(v,0) p_{j+e_i}
+ *                      (first order; monotone)
+ *   PIT_DRIFT_CENTRAL  F = v (p_j + p_{j+e_i}) / 2 (second order, the paper's
+ *                      "second order finite difference" of Sec. 4.4.1; the
+ *                      drift part of L is then skew up to its diagonal
+ *                      trace(A) / 2 per axis sum)
+ * The OU operator always uses the donor cell. */
+typedef enum { PIT_DRIFT_UPWIND = 0, PIT_DRIFT_CENTRAL = 1 } pit_drift_scheme;
 
 typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2, PIT_PREC_MIXED_PAIR = 3 } pit_prec;
 
@@ -90,7 +102,9 @@ typedef enum {
  * level level_n (the paper's L) with minimum level level0 (the paper's L0,
  * Sec. 2.1.1), operator op with parameters theta, sigma (OU), vamp
  * (variable-coefficient amplitude A), and drift, diffusion (linear SDE: the
- * d x d matrices A and H, row major, first d*d entries used). */
+ * d x d matrices A and H, row major, first d*d entries used) with the drift
+ * flux drift_scheme (pit_drift_scheme; must be PIT_DRIFT_UPWIND for the other
+ * operators, else PIT_ERR_INVALID_ARG). */
 typedef struct {
     int d;
     int level_n;
@@ -103,6 +117,7 @@ typedef struct {
     double vamp;
     double drift[PIT_MAX_DIM * PIT_MAX_DIM];
     double diffusion[PIT_MAX_DIM * PIT_MAX_DIM];
+    int drift_scheme;
 } pit_problem_desc;
 
 /* Options of one batched backward-Euler solve.

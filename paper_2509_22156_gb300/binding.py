@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "PIT_OK", 1: "PIT_ERR_INVALID_ARG", 2: "PIT_ERR_CUDA", 3: "PI
                 4: "PIT_ERR_NOCONV", 5: "PIT_ERR_BREAKDOWN", 6: "PIT_ERR_NONFINITE", 7: "PIT_ERR_TIMEOUT",
                 8: "PIT_ERR_UNSUPPORTED"}
 PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU, PIT_OP_LSDE = 0, 1, 2, 3
+PIT_DRIFT_UPWIND, PIT_DRIFT_CENTRAL = 0, 1
 PIT_PREC_FP64, PIT_PREC_MIXED, PIT_PREC_FP32, PIT_PREC_MIXED_PAIR = 0, 1, 2, 3
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
 PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
@@ -45,7 +46,8 @@ class pit_problem_desc(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("level_n", ctypes.c_int), ("level0", ctypes.c_int), ("op", ctypes.c_int),
                 ("lo", ctypes.c_double * MAX_DIM), ("hi", ctypes.c_double * MAX_DIM),
                 ("theta", ctypes.c_double), ("sigma", ctypes.c_double), ("vamp", ctypes.c_double),
-                ("drift", ctypes.c_double * (MAX_DIM * MAX_DIM)), ("diffusion", ctypes.c_double * (MAX_DIM * MAX_DIM))]
+                ("drift", ctypes.c_double * (MAX_DIM * MAX_DIM)), ("diffusion", ctypes.c_double * (MAX_DIM * MAX_DIM)),
+                ("drift_scheme", ctypes.c_int)]
 
 
 class pit_solve_opts(ctypes.Structure):
@@ -205,7 +207,7 @@ class Problem:
     """A combination-technique problem on the current CUDA device."""
 
     def __init__(self, d, n, L0=1, op=PIT_OP_HEAT, lo=None, hi=None, theta=1.0, sigma=1.0, vamp=0.5, stream=None,
-                 drift=None, diffusion=None):
+                 drift=None, diffusion=None, drift_scheme=0):
         L = load()
         desc = pit_problem_desc()
         desc.d, desc.level_n, desc.level0, desc.op = d, n, L0, op
@@ -219,6 +221,7 @@ class Problem:
             hm = np.ascontiguousarray(diffusion, dtype=np.float64).ravel()
             for k in range(d * d):
                 desc.drift[k], desc.diffusion[k] = a[k], hm[k]
+        desc.drift_scheme = drift_scheme
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream) if stream is not None else None
         _check(L.pit_problem_create(ctypes.byref(desc), s, ctypes.byref(h)), "pit_problem_create")

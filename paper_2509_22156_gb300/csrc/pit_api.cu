@@ -707,6 +707,10 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
         for (int k = 0; k < d * d; ++k)
             if (!std::isfinite(desc->drift[k]) || !std::isfinite(desc->diffusion[k]))
                 return fail(PIT_ERR_INVALID_ARG, "drift and diffusion matrices must be finite");
+    if (desc->drift_scheme != PIT_DRIFT_UPWIND && desc->drift_scheme != PIT_DRIFT_CENTRAL)
+        return fail(PIT_ERR_INVALID_ARG, "unknown drift scheme %d", desc->drift_scheme);
+    if (desc->drift_scheme != PIT_DRIFT_UPWIND && desc->op != PIT_OP_LSDE)
+        return fail(PIT_ERR_INVALID_ARG, "the central drift flux is offered for the linear-SDE operator only");
     for (int i = 0; i < d; ++i)
         if (!(desc->hi[i] > desc->lo[i])) return fail(PIT_ERR_INVALID_ARG, "empty box on axis %d", i);
     int ndev = 0;
@@ -772,6 +776,7 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
             P->op.A[k] = desc->drift[k];
             P->op.H[k] = desc->diffusion[k];
         }
+    P->op.central = desc->drift_scheme == PIT_DRIFT_CENTRAL ? 1 : 0;
 
     auto bail = [&](pit_status st) {
         pit_problem_destroy(P);

@@ -37,9 +37,10 @@ __device__ double apply_node(const GridInfo &GI, int j, const double *pg, double
             const double x = op.lo[i] + (double)(c + 1) * h;
             const double vp = -op.theta * (x + 0.5 * h), vm = -op.theta * (x - 0.5 * h);
             const double s2 = 0.5 * op.sigma * op.sigma * ih2;
-            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
-            dm = -fmax(vm, 0.0) / h - s2;
-            dp = fmin(vp, 0.0) / h - s2;
+            drift_coef(vp, vm, h, false, dd, dm, dp);
+            dd += 2.0 * s2;
+            dm -= s2;
+            dp -= s2;
         } else {
             // linear SDE: face velocities (A x)_i at x -+ h/2 e_i, diagonal diffusion
             double ax = 0.0;
@@ -47,9 +48,10 @@ __device__ double apply_node(const GridInfo &GI, int j, const double *pg, double
                 ax += op.A[i * d + k] * (op.lo[k] + (double)(axis_coord(GI, j, k) + 1) * GI.h[k]);
             const double vp = ax + 0.5 * h * op.A[i * d + i], vm = ax - 0.5 * h * op.A[i * d + i];
             const double s2 = 0.5 * op.H[i * d + i] * ih2;
-            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
-            dm = -fmax(vm, 0.0) / h - s2;
-            dp = fmin(vp, 0.0) / h - s2;
+            drift_coef(vp, vm, h, op.central != 0, dd, dm, dp);
+            dd += 2.0 * s2;
+            dm -= s2;
+            dp -= s2;
         }
         diag += dt * dd;
         if (c > 0) s += dt * dm * pg[j - GI.S[i]];

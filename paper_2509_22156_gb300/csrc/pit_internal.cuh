@@ -30,7 +30,26 @@ struct OpParams {
     double theta, sigma, vamp;
     double A[PIT_D * PIT_D];  // linear SDE: drift matrix (row major, d x d)
     double H[PIT_D * PIT_D];  // linear SDE: H = 2 sigma D sigma^T (row major, d x d)
+    int central;              // linear SDE: central drift flux (else donor cell)
 };
+
+// Drift part of one axis of the flux-form operator (F_+ - F_-) / h at node j,
+// face velocities vp at x + h/2 e_i and vm at x - h/2 e_i: coefficients of
+// p_j, p_{j-e_i}, p_{j+e_i}.  Donor cell: F_+ = max(vp,0) p_j + min(vp,0)
+// p_{j+e_i}; central: F_+ = vp (p_j + p_{j+e_i}) / 2.
+__host__ __device__ __forceinline__ void drift_coef(double vp, double vm, double h, bool central, double &dd,
+                                                    double &dm, double &dp)
+{
+    if (central) {
+        dd = 0.5 * (vp - vm) / h;
+        dm = -0.5 * vm / h;
+        dp = 0.5 * vp / h;
+    } else {
+        dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h;
+        dm = -fmax(vm, 0.0) / h;
+        dp = fmin(vp, 0.0) / h;
+    }
+}
 
 // Global counters filled by the backward-Euler kernels (one atomic per item).
 struct DevStats {

@@ -59,7 +59,7 @@ namespace pit {
 //   varheat L p = sum_i [a_+ (p_j - p_+) + a_- (p_j - p_-)] / h_i^2
 //   OU      L p = sum_i (F_+ - F_-) / h_i + (sigma^2/2)(2 p_j - p_- - p_+) / h_i^2,
 //           F_+ = max(v_+,0) p_j + min(v_+,0) p_+,  v_+ = -theta (x_i + h_i/2).
-//   LSDE    the same donor-cell flux with the face velocity (A x)_i of the
+//   LSDE    the donor-cell (or central) flux with the face velocity (A x)_i of the
 //           linear SDE dX = A X dt + sigma dW (Sec. 4.4) and diffusion
 //           (H_ii/2)(2 p_j - p_- - p_+) / h_i^2; its mixed-derivative terms
 //           (i != k) are constant per grid and applied by TabSt<.., true>.
@@ -85,9 +85,10 @@ __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, c
             const double vp = -op.theta * (x + 0.5 * h);
             const double vm = -op.theta * (x - 0.5 * h);
             const double s2 = 0.5 * op.sigma * op.sigma * ih2;
-            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
-            dm = -fmax(vm, 0.0) / h - s2;
-            dp = fmin(vp, 0.0) / h - s2;
+            drift_coef(vp, vm, h, false, dd, dm, dp);
+            dd += 2.0 * s2;
+            dm -= s2;
+            dp -= s2;
         } else {
             // face velocities (A x)_i at x -+ h/2 e_i
             double ax = 0.0;
@@ -96,9 +97,10 @@ __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, c
             const double vp = ax + 0.5 * h * op.A[i * D + i];
             const double vm = ax - 0.5 * h * op.A[i * D + i];
             const double s2 = 0.5 * op.H[i * D + i] * ih2;
-            dd = (fmax(vp, 0.0) - fmin(vm, 0.0)) / h + 2.0 * s2;
-            dm = -fmax(vm, 0.0) / h - s2;
-            dp = fmin(vp, 0.0) / h - s2;
+            drift_coef(vp, vm, h, op.central != 0, dd, dm, dp);
+            dd += 2.0 * s2;
+            dm -= s2;
+            dp -= s2;
         }
         diag += dt * dd;
         cm[i] = (c > 0) ? dt * dm : 0.0;
@@ -772,12 +774,21 @@ __device__ int pcg_core(const ST &A, const PC &M, int n, TX *X, T *r, T *u, T *p
 }
 
 // BiCGStab (van der Vorst 1992) on A e = r0: r holds r0 on entry; rh, p, v
-// are initialised here; s shares r's storage.
+// are initialised here; s shares r's storage.  A (near-)breakdown (the shadow
+// residual rh almost orthogonal to r, (rh, A p) = 0, omega = 0, or a step
+// coefficient beyond 1e30) restarts the method from the current iterate with
+// rh = r, provided an iteration has completed since the last restart (so the
+// solve still ends within maxit iterations); a second breakdown without
+// progress is reported.  Strongly non-normal systems (the central drift flux
+// at large dt |v| / h) lose the shadow residual's orthogonality every few
+// tens of iterations and need this.
 template <typename T, typename TX, class ST>
 __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v, T *t, Reducer<T> &R, T stop2,
                              int maxit, int &status)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
+    // cosine below which (rh, r) counts as a breakdown
+    const T near0 = sizeof(T) == 8 ? T(1e-12) : T(1e-6);
     T rr[1] = {T(0)};
 #pragma unroll 4
     for (int j = tid; j < n; j += nt) {
@@ -788,9 +799,23 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         rr[0] += rj * rj;
     }
     R.template sum<1>(rr);
-    T rho = T(1), alpha = T(1), omega = T(1), rrv = rr[0];
-    int k = 0;
+    T rho = T(1), alpha = T(1), omega = T(1), rrv = rr[0], rhh = rr[0];
+    int k = 0, k_restart = -1;
     status = PIT_OK;
+    // restart from the current residual (every thread reads and writes only
+    // its own nodes here; the next use of p behind a barrier is A(p, j))
+    auto restart = [&]() -> bool {
+        if (k == k_restart) return false;
+        k_restart = k;
+        for (int j = tid; j < n; j += nt) {
+            rh[j] = r[j];
+            p[j] = T(0);
+            v[j] = T(0);
+        }
+        rho = alpha = omega = T(1);
+        rhh = rrv;
+        return true;
+    };
     for (;;) {
         if (!(rrv > stop2)) {
             if (rrv != rrv) status = PIT_ERR_NONFINITE;
@@ -801,12 +826,19 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) rho_n[0] += rh[j] * r[j];
         R.template sum<1>(rho_n);
-        if (rho_n[0] == T(0) || omega == T(0) || rho_n[0] != rho_n[0]) {
-            status = (rho_n[0] != rho_n[0]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+        if (rho_n[0] != rho_n[0]) { status = PIT_ERR_NONFINITE; break; }
+        if (!(fabs(rho_n[0]) > near0 * sqrt(rrv) * sqrt(rhh))) {
+            if (restart()) continue;
+            status = PIT_ERR_BREAKDOWN;
             break;
         }
         const T beta = (rho_n[0] / rho) * (alpha / omega);
-        if (!(fabs(beta) < (T)1e30)) { status = (beta != beta) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        if (beta != beta) { status = PIT_ERR_NONFINITE; break; }
+        if (!(fabs(beta) < (T)1e30)) {
+            if (restart()) continue;
+            status = PIT_ERR_BREAKDOWN;
+            break;
+        }
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) p[j] = r[j] + beta * (p[j] - omega * v[j]);
         __syncthreads();
@@ -818,12 +850,13 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
             rhv[0] += rh[j] * vj;
         }
         R.template sum<1>(rhv);
-        if (rhv[0] == T(0) || rhv[0] != rhv[0]) {
-            status = (rhv[0] != rhv[0]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN;
+        if (rhv[0] != rhv[0]) { status = PIT_ERR_NONFINITE; break; }
+        alpha = rho_n[0] / rhv[0];
+        if (!(fabs(alpha) < (T)1e30)) {
+            if (restart()) continue;
+            status = PIT_ERR_BREAKDOWN;
             break;
         }
-        alpha = rho_n[0] / rhv[0];
-        if (!(fabs(alpha) < (T)1e30)) { status = (alpha != alpha) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) r[j] = r[j] - alpha * v[j];  // s
         __syncthreads();
@@ -837,7 +870,8 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         }
         R.template sum<2>(tt);
         omega = (tt[0] > T(0)) ? tt[1] / tt[0] : T(0);
-        if (!(fabs(omega) < (T)1e30)) { status = (omega != omega) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        if (omega != omega) { status = PIT_ERR_NONFINITE; break; }
+        if (!(fabs(omega) < (T)1e30)) omega = T(0);  // take the BiCG half step only
         T rn[1] = {T(0)};
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) {
@@ -850,7 +884,12 @@ __device__ int bicgstab_core(const ST &A, int n, TX *X, T *r, T *rh, T *p, T *v,
         rho = rho_n[0];
         rrv = rn[0];
         ++k;
-        if (omega == T(0) && rrv > stop2) { status = PIT_ERR_BREAKDOWN; break; }
+        if (omega == T(0) && rrv > stop2) {
+            if (rrv != rrv) { status = PIT_ERR_NONFINITE; break; }
+            if (restart()) continue;
+            status = PIT_ERR_BREAKDOWN;
+            break;
+        }
     }
     return k;
 }

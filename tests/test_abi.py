@@ -73,3 +73,12 @@ def test_invalid_descriptions_rejected_before_any_device_use(lib):
     desc.lo[0], desc.hi[0], desc.lo[1], desc.hi[1] = 0.0, 1.0, 1.0, 1.0  # empty box on axis 1
     h = ctypes.c_void_p()
     assert lib.pit_problem_create(ctypes.byref(desc), None, ctypes.byref(h)) == B.PIT_ERR_INVALID_ARG
+    # drift schemes: unknown value, and the central flux on an operator without it
+    for op, scheme in ((B.PIT_OP_LSDE, 2), (B.PIT_OP_LSDE, -1), (B.PIT_OP_HEAT, B.PIT_DRIFT_CENTRAL),
+                       (B.PIT_OP_OU, B.PIT_DRIFT_CENTRAL)):
+        desc = B.pit_problem_desc()
+        desc.d, desc.level_n, desc.level0, desc.op = 2, 5, 1, op
+        for i in range(2):
+            desc.lo[i], desc.hi[i] = -1.0, 1.0
+        desc.drift_scheme = scheme
+        assert lib.pit_problem_create(ctypes.byref(desc), None, ctypes.byref(h)) == B.PIT_ERR_INVALID_ARG, (op, scheme)

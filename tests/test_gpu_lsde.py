@@ -1,7 +1,8 @@
 """GPU parity of the linear-SDE Fokker-Planck operator (Sec. 4.4, Eqs. "sde",
 "sde_fokker_planck"): full drift matrix A, H = 2 sigma D sigma^T with
 off-diagonal entries (mixed-derivative stencil), BiCGStab inside every
-backward-Euler step, against the oracle.
+backward-Euler step, against the oracle; every case with the donor-cell and
+with the central (second-order) drift flux.
 
 Tolerances (relative L2): stencil and initial density 1e-13 (same formulas,
 different rounding order); backward-Euler batches and MGRIT 1e-10 in FP64,
@@ -43,12 +44,16 @@ H4 = 0.3 * np.eye(4) + 0.08 * (np.ones((4, 4)) - np.eye(4))
 CASES = {"osc2d": (2, 6, 2, OSC_A, OSC_H, 10.0), "sde3d": (3, 5, 1, A3, H3, 5.0), "sde4d": (4, 5, 1, A4, H4, 5.0)}
 
 
-def pair(name):
+def pair(name, central=False):
     d, n, L0, A, H, w = CASES[name]
     lo, hi = [-w] * d, [w] * d
-    P = B.Problem(d, n, L0, B.PIT_OP_LSDE, lo, hi, drift=A, diffusion=H)
-    O = oracle.Problem(d, n, L0, oracle.OP_LSDE, lo, hi, drift=A, diffusion=H)
+    P = B.Problem(d, n, L0, B.PIT_OP_LSDE, lo, hi, drift=A, diffusion=H,
+                  drift_scheme=B.PIT_DRIFT_CENTRAL if central else B.PIT_DRIFT_UPWIND)
+    O = oracle.Problem(d, n, L0, oracle.OP_LSDE, lo, hi, drift=A, diffusion=H, central=central)
     return P, O
+
+
+SCHEMES = pytest.mark.parametrize("central", [False, True], ids=["upwind", "central"])
 
 
 def gauss_params(d):
@@ -57,9 +62,10 @@ def gauss_params(d):
     return np.concatenate([M, C.ravel()])
 
 
+@SCHEMES
 @pytest.mark.parametrize("name", list(CASES))
-def test_stencil_and_initial_density_match_oracle(name):
-    P, O = pair(name)
+def test_stencil_and_initial_density_match_oracle(name, central):
+    P, O = pair(name, central)
     nb = 2
     p = W.random_vector(31, nb * P.n_total)
     q = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
@@ -74,8 +80,9 @@ def test_stencil_and_initial_density_match_oracle(name):
 
 @pytest.mark.parametrize("prec,tol", [(B.PIT_PREC_FP64, 1e-10), (B.PIT_PREC_MIXED, 1e-9), (B.PIT_PREC_FP32, 1e-4)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_phi_batch_matches_oracle(name, prec, tol):
-    P, O = pair(name)
+@SCHEMES
+def test_phi_batch_matches_oracle(name, prec, tol, central):
+    P, O = pair(name, central)
     nb, dt = 3, 0.02
     u = W.random_vector(41, nb * P.n_total)
     out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
@@ -94,8 +101,9 @@ def test_phi_batch_matches_oracle(name, prec, tol):
 
 @pytest.mark.parametrize("prec,tol", [(B.PIT_PREC_FP64, 1e-10), (B.PIT_PREC_MIXED, 1e-9)])
 @pytest.mark.parametrize("name", ["osc2d", "sde3d"])
-def test_mgrit_matches_oracle_sequential(name, prec, tol):
-    P, O = pair(name)
+@SCHEMES
+def test_mgrit_matches_oracle_sequential(name, prec, tol, central):
+    P, O = pair(name, central)
     N, m, T = 64, 8, 0.5
     dt = T / N
     u0 = O.initial(4, gauss_params(P.d))
@@ -121,14 +129,16 @@ def test_pair_form_is_refused_for_the_drift_operator():
     P.close()
 
 
-def test_large_grids_in_the_fp64_global_state_class_match_oracle():
+@SCHEMES
+def test_large_grids_in_the_fp64_global_state_class_match_oracle(central):
     """Grids too large for the on-chip solve (here up to 8,001 nodes, the
     oscillator at level 12, L0 = 5) run the FP64 form's global-state variant,
     which keeps x, the Krylov vectors and the coefficient table in global
     memory; steps and MGRIT against the oracle."""
     d, n, L0, w = 2, 12, 5, 10.0
-    P = B.Problem(d, n, L0, B.PIT_OP_LSDE, [-w] * d, [w] * d, drift=OSC_A, diffusion=OSC_H)
-    O = oracle.Problem(d, n, L0, oracle.OP_LSDE, [-w] * d, [w] * d, drift=OSC_A, diffusion=OSC_H)
+    P = B.Problem(d, n, L0, B.PIT_OP_LSDE, [-w] * d, [w] * d, drift=OSC_A, diffusion=OSC_H,
+                  drift_scheme=B.PIT_DRIFT_CENTRAL if central else B.PIT_DRIFT_UPWIND)
+    O = oracle.Problem(d, n, L0, oracle.OP_LSDE, [-w] * d, [w] * d, drift=OSC_A, diffusion=OSC_H, central=central)
     assert max(O.offsets[g + 1] - O.offsets[g] for g in range(O.G)) == 8001
     nb, dt = 2, 0.01
     u = W.random_vector(51, nb * P.n_total)
