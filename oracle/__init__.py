@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OP_HEAT, OP_VARHEAT, OP_OU, OP_LSDE = 0, 1, 2, 3
+OP_HEAT, OP_VARHEAT, OP_OU, OP_LSDE, OP_CME = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "invalid argument", 4: "no convergence", 5: "breakdown"}
 
 
@@ -58,6 +58,8 @@ def lib():
             L.or_destroy.argtypes = [vp]
             L.or_set_sde.restype = c_int
             L.or_set_sde.argtypes = [vp, vp, vp, c_int]
+            L.or_set_cme.restype = c_int
+            L.or_set_cme.argtypes = [vp, vp, vp, vp, vp, c_int]
             L.or_info.argtypes = [vp, vp, vp, vp, vp, vp]
             L.or_set_threads.argtypes = [c_int]
             L.or_max_threads.restype = c_int
@@ -130,7 +132,7 @@ class Problem:
     """One combination-technique problem on the CPU (FP64)."""
 
     def __init__(self, d, n, L0=1, op=OP_HEAT, lo=None, hi=None, theta=1.0, sigma=1.0, vamp=0.5,
-                 drift=None, diffusion=None, central=False):
+                 drift=None, diffusion=None, central=False, cme=None):
         self.d, self.n, self.L0, self.op = d, n, L0, op
         self.lo = _f64(lo if lo is not None else [0.0] * d)
         self.hi = _f64(hi if hi is not None else [1.0] * d)
@@ -146,6 +148,14 @@ class Problem:
             self.central = bool(central)
             if lib().or_set_sde(self._h, _p(self.drift), _p(self.diffusion), int(self.central)) != 0:
                 raise ValueError("invalid linear-SDE parameters")
+        if op == OP_CME:
+            # toggle-switch chemical master equation (Sec. 4.3): cme = (p, s, b,
+            # g), one entry per species each: production p / (s + y^b), y the
+            # other species' total, degradation g x_i
+            self.cme = [_f64(np.broadcast_to(np.asarray(c, dtype=float), (d,))) for c in cme]
+            self.central = bool(central)
+            if lib().or_set_cme(self._h, *[_p(c) for c in self.cme], int(self.central)) != 0:
+                raise ValueError("invalid CME parameters")
         G = ctypes.c_int()
         nt = ctypes.c_longlong()
         lib().or_info(self._h, ctypes.byref(G), ctypes.byref(nt), None, None, None)

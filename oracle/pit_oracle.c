@@ -23,6 +23,10 @@
  *                                  discrete mass balance, M-matrix sign pattern
  *   or_apply (var. coeff. heat)    consistency order 2 vs analytic operator,
  *                                  symmetry, reduction to heat at amplitude 0
+ *   or_apply (CME, toggle switch)  order 2 (central) / 1 (donor cell) vs the
+ *                                  analytic Fokker-Planck operator (sympy);
+ *                                  mass balance; the immigration-death special
+ *                                  case follows its closed-form mean
  *   or_apply (linear SDE)          reduction to OU for diagonal drift; order 1
  *                                  (donor cell) and order 2 (central) vs the
  *                                  analytic operator on a full-covariance
@@ -55,7 +59,7 @@
 
 #define OR_MAXD 6
 
-enum { OR_HEAT = 0, OR_VARHEAT = 1, OR_OU = 2, OR_LSDE = 3 };
+enum { OR_HEAT = 0, OR_VARHEAT = 1, OR_OU = 2, OR_LSDE = 3, OR_CME = 4 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOCONV = 4, OR_EBREAK = 5 };
 
 typedef struct {
@@ -65,6 +69,10 @@ typedef struct {
     double sde_A[OR_MAXD * OR_MAXD]; /* linear SDE dX = A X dt + sigma dW: drift matrix */
     double sde_H[OR_MAXD * OR_MAXD]; /* H = 2 sigma D sigma^T (row major)              */
     int sde_central;                 /* drift flux: 0 donor cell, 1 central average   */
+    /* chemical master equation, toggle-switch network (Sec. 4.3): species i
+     * is produced at rate cme_p[i] / (cme_s[i] + (sum_{k != i} x_k)^cme_b[i])
+     * and degraded at rate cme_g[i] x_i                                     */
+    double cme_p[OR_MAXD], cme_s[OR_MAXD], cme_b[OR_MAXD], cme_g[OR_MAXD];
     int G;
     int *lev;                        /* G*d level multi-indices               */
     long long *off;                  /* G+1 packed offsets                    */
@@ -140,7 +148,7 @@ long long or_grid_points(int d, const int *l)
 void *or_create(int d, int n, int L0, int op, const double *lo, const double *hi,
                 double theta, double sigma, double vamp)
 {
-    if (d < 1 || d > OR_MAXD || L0 < 1 || n < L0 || op < 0 || op > 3) return NULL;
+    if (d < 1 || d > OR_MAXD || L0 < 1 || n < L0 || op < 0 || op > 4) return NULL;
     or_problem *P = (or_problem *)calloc(1, sizeof(or_problem));
     P->d = d; P->n = n; P->L0 = L0; P->op = op;
     for (int i = 0; i < d; ++i) { P->lo[i] = lo[i]; P->hi[i] = hi[i]; }
@@ -169,6 +177,21 @@ int or_set_sde(void *vp, const double *A, const double *H, int central)
     if (central != 0 && central != 1) return OR_EINVAL;
     memcpy(P->sde_A, A, sizeof(double) * P->d * P->d);
     memcpy(P->sde_H, H, sizeof(double) * P->d * P->d);
+    P->sde_central = central;
+    return OR_OK;
+}
+
+/* Reaction rates of the toggle-switch chemical master equation operator
+ * (op 4, Sec. 4.3) per species: production p[i] / (s[i] + y^b[i]) with y
+ * the sum of the other species' counts, degradation g[i] x_i; drift flux as
+ * for the linear SDE (central = 1: central average). */
+int or_set_cme(void *vp, const double *p, const double *s, const double *b, const double *g, int central)
+{
+    or_problem *P = (or_problem *)vp;
+    if (central != 0 && central != 1) return OR_EINVAL;
+    for (int i = 0; i < P->d; ++i) {
+        P->cme_p[i] = p[i]; P->cme_s[i] = s[i]; P->cme_b[i] = b[i]; P->cme_g[i] = g[i];
+    }
     P->sde_central = central;
     return OR_OK;
 }
@@ -270,7 +293,24 @@ static double varcoef(const or_problem *P, const double *x)
  *               (H_ii / 2)(2 p_j - p_{j-e_i} - p_{j+e_i}) / h_i^2; for i < k
  *               the mixed term -((H_ik + H_ki) / 2) (p_{++} - p_{+-} - p_{-+}
  *               + p_{--}) / (4 h_i h_k) over the four diagonal neighbours
- *               j +- e_i +- e_k (zero outside the grid).                   */
+ *               j +- e_i +- e_k (zero outside the grid).
+ *   chemical master equation, Fokker-Planck form (Sec. 4.3, Eq. "cme_fp"),
+ *   toggle-switch network: species i has a production reaction (nu = +e_i,
+ *   propensity a_i(x)) and a degradation reaction (nu = -e_i, b_i(x) =
+ *   g_i x_i), so u_t = sum_i [-d_i((a_i - b_i) u) + (1/2) d_i^2((a_i + b_i) u)]
+ *   and L u = sum_i d_i(v_i u) - (1/2) d_i^2(D_i u), v_i = a_i - b_i,
+ *   D_i = a_i + b_i: drift as the linear SDE's flux with the face velocity
+ *   v_i(x_{j+1/2 e_i}), diffusion the second difference of D_i u,
+ *   -(D_i(x_{j+e_i}) p_{j+e_i} - 2 D_i(x_j) p_j + D_i(x_{j-e_i}) p_{j-e_i})
+ *   / (2 h_i^2).                                                            */
+static double cme_production(const or_problem *P, int i, const double *x)
+{
+    double y = 0.0;
+    for (int k = 0; k < P->d; ++k)
+        if (k != i) y += x[k];
+    return P->cme_p[i] / (P->cme_s[i] + pow(y, P->cme_b[i]));
+}
+
 static void apply_grid(const or_problem *P, int g, double dt, const double *p, double *q)
 {
     geom G = grid_geom(P, g);
@@ -300,6 +340,20 @@ static void apply_grid(const or_problem *P, int g, double dt, const double *p, d
                 double Fp = fmax(vp, 0.0) * p[j] + fmin(vp, 0.0) * pp;
                 double Fm = fmax(vm, 0.0) * pm + fmin(vm, 0.0) * p[j];
                 Lp += (Fp - Fm) / h + 0.5 * P->sigma * P->sigma * (2.0 * p[j] - pm - pp) / (h * h);
+            } else if (P->op == OR_CME) {
+                /* a_i does not depend on x_i; b_i = g_i x_i does */
+                double a = cme_production(P, i, x), gi = P->cme_g[i];
+                double vp = a - gi * (x[i] + 0.5 * h), vm = a - gi * (x[i] - 0.5 * h);
+                double Fp, Fm;
+                if (P->sde_central) {
+                    Fp = vp * 0.5 * (p[j] + pp);
+                    Fm = vm * 0.5 * (pm + p[j]);
+                } else {
+                    Fp = fmax(vp, 0.0) * p[j] + fmin(vp, 0.0) * pp;
+                    Fm = fmax(vm, 0.0) * pm + fmin(vm, 0.0) * p[j];
+                }
+                double Dm = a + gi * (x[i] - h), D0 = a + gi * x[i], Dp = a + gi * (x[i] + h);
+                Lp += (Fp - Fm) / h - 0.5 * (Dp * pp - 2.0 * D0 * p[j] + Dm * pm) / (h * h);
             } else {
                 /* face velocities (A x)_i at x -+ h/2 e_i */
                 double ax = 0.0;
@@ -436,7 +490,7 @@ static int phi_grid(const or_problem *P, int g, double dt, const double *u_prev,
     double *b = malloc(sizeof(double) * n);
     for (long long j = 0; j < n; ++j) b[j] = u_prev[j] + (f ? dt * f[j] : 0.0);
     if (u_next != u_prev) memcpy(u_next, u_prev, sizeof(double) * n);
-    int st = (P->op == OR_OU || P->op == OR_LSDE) ? bicgstab_grid(P, g, dt, b, u_next, rtol, maxit, iters)
+    int st = (P->op == OR_OU || P->op == OR_LSDE || P->op == OR_CME) ? bicgstab_grid(P, g, dt, b, u_next, rtol, maxit, iters)
                                                    : cg_grid(P, g, dt, b, u_next, rtol, maxit, iters);
     free(b);
     return st;
