@@ -66,7 +66,7 @@ typedef enum {
     PIT_OP_OU = 2,      /* Fokker-Planck operator of dX = -theta X dt + sigma dW
                            (Sec. 4.4, Eq. "sde_fokker_planck" with diagonal drift):
                            donor-cell upwind drift + central diffusion; BiCGStab            */
-    PIT_OP_LSDE = 3     /* Fokker-Planck operator of the linear SDE dX = A X dt + sigma dW
+    PIT_OP_LSDE = 3,    /* Fokker-Planck operator of the linear SDE dX = A X dt + sigma dW
                            (Sec. 4.4, Eqs. "sde", "sde_fokker_planck"), A = drift (d x d),
                            H = 2 sigma D sigma^T = diffusion (d x d):
                            L p = sum_i d_i((A x)_i p) - (1/2) sum_ij H_ij d_i d_j p, drift
@@ -74,6 +74,15 @@ typedef enum {
                            pit_drift_scheme), central diagonal diffusion, and for i != k the
                            four-point mixed stencil
                            (p_{++} - p_{+-} - p_{-+} + p_{--}) / (4 h_i h_k); BiCGStab      */
+    PIT_OP_CME = 4      /* Fokker-Planck form of the chemical master equation (Sec. 4.3,
+                           Eq. "cme_fp") of the toggle-switch networks (Tables
+                           "toggle_switch_2d", "toggle_switch_3d"): species i is produced at
+                           a_i = cme_prod[i] / (cme_sat[i] + y_i^cme_exp[i]), y_i the sum of
+                           the other species' counts, and degraded at b_i = cme_deg[i] x_i:
+                           L u = sum_i d_i((a_i - b_i) u) - (1/2) d_i^2((a_i + b_i) u), drift
+                           flux as for PIT_OP_LSDE (pit_drift_scheme) with the face velocity
+                           a_i - b_i, diffusion the second difference of (a_i + b_i) u;
+                           the box must lie in x >= 0; BiCGStab                              */
 } pit_op;
 
 /* Drift flux of the linear-SDE operator at the face x_{j+1/2 e_i} with face
@@ -84,7 +93,7 @@ typedef enum {
  *                      "second order finite difference" of Sec. 4.4.1; the
  *                      drift part of L is then skew up to its diagonal
  *                      trace(A) / 2 per axis sum)
- * The OU operator always uses the donor cell. */
+ * for PIT_OP_LSDE and PIT_OP_CME; the OU operator always uses the donor cell. */
 typedef enum { PIT_DRIFT_UPWIND = 0, PIT_DRIFT_CENTRAL = 1 } pit_drift_scheme;
 
 typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2, PIT_PREC_MIXED_PAIR = 3 } pit_prec;
@@ -102,9 +111,12 @@ typedef enum {
  * level level_n (the paper's L) with minimum level level0 (the paper's L0,
  * Sec. 2.1.1), operator op with parameters theta, sigma (OU), vamp
  * (variable-coefficient amplitude A), and drift, diffusion (linear SDE: the
- * d x d matrices A and H, row major, first d*d entries used) with the drift
- * flux drift_scheme (pit_drift_scheme; must be PIT_DRIFT_UPWIND for the other
- * operators, else PIT_ERR_INVALID_ARG). */
+ * d x d matrices A and H, row major, first d*d entries used), the reaction
+ * rates cme_prod, cme_sat, cme_exp, cme_deg of the toggle-switch chemical
+ * master equation (one entry per species; finite, cme_prod and cme_deg >= 0,
+ * cme_sat > 0, and lo >= 0 on every axis, else PIT_ERR_INVALID_ARG), and the
+ * drift flux drift_scheme (pit_drift_scheme; must be PIT_DRIFT_UPWIND for the
+ * heat, variable-coefficient and OU operators, else PIT_ERR_INVALID_ARG). */
 typedef struct {
     int d;
     int level_n;
@@ -118,6 +130,10 @@ typedef struct {
     double drift[PIT_MAX_DIM * PIT_MAX_DIM];
     double diffusion[PIT_MAX_DIM * PIT_MAX_DIM];
     int drift_scheme;
+    double cme_prod[PIT_MAX_DIM];
+    double cme_sat[PIT_MAX_DIM];
+    double cme_exp[PIT_MAX_DIM];
+    double cme_deg[PIT_MAX_DIM];
 } pit_problem_desc;
 
 /* Options of one batched backward-Euler solve.

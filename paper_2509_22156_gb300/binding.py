@@ -27,7 +27,7 @@ PIT_ERR_NOCONV, PIT_ERR_BREAKDOWN, PIT_ERR_NONFINITE, PIT_ERR_TIMEOUT, PIT_ERR_U
 STATUS_NAMES = {0: "PIT_OK", 1: "PIT_ERR_INVALID_ARG", 2: "PIT_ERR_CUDA", 3: "PIT_ERR_OOM",
                 4: "PIT_ERR_NOCONV", 5: "PIT_ERR_BREAKDOWN", 6: "PIT_ERR_NONFINITE", 7: "PIT_ERR_TIMEOUT",
                 8: "PIT_ERR_UNSUPPORTED"}
-PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU, PIT_OP_LSDE = 0, 1, 2, 3
+PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU, PIT_OP_LSDE, PIT_OP_CME = 0, 1, 2, 3, 4
 PIT_DRIFT_UPWIND, PIT_DRIFT_CENTRAL = 0, 1
 PIT_PREC_FP64, PIT_PREC_MIXED, PIT_PREC_FP32, PIT_PREC_MIXED_PAIR = 0, 1, 2, 3
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED = 0, 1, 2
@@ -47,7 +47,9 @@ class pit_problem_desc(ctypes.Structure):
                 ("lo", ctypes.c_double * MAX_DIM), ("hi", ctypes.c_double * MAX_DIM),
                 ("theta", ctypes.c_double), ("sigma", ctypes.c_double), ("vamp", ctypes.c_double),
                 ("drift", ctypes.c_double * (MAX_DIM * MAX_DIM)), ("diffusion", ctypes.c_double * (MAX_DIM * MAX_DIM)),
-                ("drift_scheme", ctypes.c_int)]
+                ("drift_scheme", ctypes.c_int),
+                ("cme_prod", ctypes.c_double * MAX_DIM), ("cme_sat", ctypes.c_double * MAX_DIM),
+                ("cme_exp", ctypes.c_double * MAX_DIM), ("cme_deg", ctypes.c_double * MAX_DIM)]
 
 
 class pit_solve_opts(ctypes.Structure):
@@ -207,7 +209,9 @@ class Problem:
     """A combination-technique problem on the current CUDA device."""
 
     def __init__(self, d, n, L0=1, op=PIT_OP_HEAT, lo=None, hi=None, theta=1.0, sigma=1.0, vamp=0.5, stream=None,
-                 drift=None, diffusion=None, drift_scheme=0):
+                 drift=None, diffusion=None, drift_scheme=0, cme=None):
+        """cme: (production, saturation, exponent, degradation) rates of the
+        toggle-switch CME operator, scalars or one entry per species."""
         L = load()
         desc = pit_problem_desc()
         desc.d, desc.level_n, desc.level0, desc.op = d, n, L0, op
@@ -222,6 +226,10 @@ class Problem:
             for k in range(d * d):
                 desc.drift[k], desc.diffusion[k] = a[k], hm[k]
         desc.drift_scheme = drift_scheme
+        if cme is not None:
+            rates = [np.broadcast_to(np.asarray(c, dtype=np.float64), (d,)) for c in cme]
+            for i in range(d):
+                desc.cme_prod[i], desc.cme_sat[i], desc.cme_exp[i], desc.cme_deg[i] = (float(r[i]) for r in rates)
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream) if stream is not None else None
         _check(L.pit_problem_create(ctypes.byref(desc), s, ctypes.byref(h)), "pit_problem_create")

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpit.so")
 SOURCES = ["pit_phi_heat_pair.cu", "pit_phi_varheat_pair.cu"] + \
-    [f"pit_phi_{op}_{p}.cu" for op in ("heat", "varheat", "ou", "lsde") for p in ("mixed", "fp64", "fp32")] + \
+    [f"pit_phi_{op}_{p}.cu" for op in ("heat", "varheat", "ou", "lsde", "cme") for p in ("mixed", "fp64", "fp32")] + \
     [f"pit_net_d{d}.cu" for d in range(1, 7)] + ["pit_phi.cu", "pit_net.cu", "pit_aux.cu", "pit_recomb.cu", "pit_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

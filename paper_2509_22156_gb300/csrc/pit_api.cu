@@ -298,7 +298,7 @@ size_t grid_smem_bytes(const pit_problem *P, int prec, int g)
 pit_status plan(pit_problem *P, int prec)
 {
     if (P->planned[prec]) return PIT_OK;
-    if (prec == PAIR && (P->desc.op == PIT_OP_OU || P->desc.op == PIT_OP_LSDE))
+    if (prec == PAIR && (P->desc.op == PIT_OP_OU || P->desc.op == PIT_OP_LSDE || P->desc.op == PIT_OP_CME))
         return fail(PIT_ERR_UNSUPPORTED, "the pair precision form is implemented for the symmetric operators only");
     std::vector<int> order(P->G);
     for (int g = 0; g < P->G; ++g) order[g] = g;
@@ -702,15 +702,26 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
     if (d < 1 || d > PIT_MAX_DIM) return fail(PIT_ERR_INVALID_ARG, "d = %d outside 1..%d", d, PIT_MAX_DIM);
     if (desc->level0 < 1 || desc->level_n < desc->level0 || desc->level_n > 30)
         return fail(PIT_ERR_INVALID_ARG, "levels must satisfy 1 <= level0 <= level_n <= 30");
-    if (desc->op < PIT_OP_HEAT || desc->op > PIT_OP_LSDE) return fail(PIT_ERR_INVALID_ARG, "unknown operator %d", desc->op);
+    if (desc->op < PIT_OP_HEAT || desc->op > PIT_OP_CME) return fail(PIT_ERR_INVALID_ARG, "unknown operator %d", desc->op);
     if (desc->op == PIT_OP_LSDE)
         for (int k = 0; k < d * d; ++k)
             if (!std::isfinite(desc->drift[k]) || !std::isfinite(desc->diffusion[k]))
                 return fail(PIT_ERR_INVALID_ARG, "drift and diffusion matrices must be finite");
     if (desc->drift_scheme != PIT_DRIFT_UPWIND && desc->drift_scheme != PIT_DRIFT_CENTRAL)
         return fail(PIT_ERR_INVALID_ARG, "unknown drift scheme %d", desc->drift_scheme);
-    if (desc->drift_scheme != PIT_DRIFT_UPWIND && desc->op != PIT_OP_LSDE)
-        return fail(PIT_ERR_INVALID_ARG, "the central drift flux is offered for the linear-SDE operator only");
+    if (desc->drift_scheme != PIT_DRIFT_UPWIND && desc->op != PIT_OP_LSDE && desc->op != PIT_OP_CME)
+        return fail(PIT_ERR_INVALID_ARG, "the central drift flux is offered for the linear-SDE and CME operators only");
+    if (desc->op == PIT_OP_CME)
+        for (int i = 0; i < d; ++i) {
+            if (!std::isfinite(desc->cme_prod[i]) || !std::isfinite(desc->cme_sat[i]) ||
+                !std::isfinite(desc->cme_exp[i]) || !std::isfinite(desc->cme_deg[i]))
+                return fail(PIT_ERR_INVALID_ARG, "CME rates of species %d must be finite", i);
+            if (desc->cme_prod[i] < 0.0 || desc->cme_deg[i] < 0.0 || !(desc->cme_sat[i] > 0.0))
+                return fail(PIT_ERR_INVALID_ARG, "CME rates of species %d: production and degradation >= 0, "
+                            "saturation > 0", i);
+            if (!(desc->lo[i] >= 0.0))
+                return fail(PIT_ERR_INVALID_ARG, "the CME box must lie in x >= 0 (axis %d)", i);
+        }
     for (int i = 0; i < d; ++i)
         if (!(desc->hi[i] > desc->lo[i])) return fail(PIT_ERR_INVALID_ARG, "empty box on axis %d", i);
     int ndev = 0;
@@ -777,6 +788,13 @@ pit_status pit_problem_create(const pit_problem_desc *desc, void *stream, pit_pr
             P->op.H[k] = desc->diffusion[k];
         }
     P->op.central = desc->drift_scheme == PIT_DRIFT_CENTRAL ? 1 : 0;
+    if (desc->op == PIT_OP_CME)
+        for (int i = 0; i < d; ++i) {
+            P->op.cp[i] = desc->cme_prod[i];
+            P->op.cs[i] = desc->cme_sat[i];
+            P->op.cb[i] = desc->cme_exp[i];
+            P->op.cg[i] = desc->cme_deg[i];
+        }
 
     auto bail = [&](pit_status st) {
         pit_problem_destroy(P);

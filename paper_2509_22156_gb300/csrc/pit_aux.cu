@@ -41,6 +41,10 @@ __device__ double apply_node(const GridInfo &GI, int j, const double *pg, double
             dd += 2.0 * s2;
             dm -= s2;
             dp -= s2;
+        } else if (op.op == PIT_OP_CME) {
+            double xc[PIT_D];
+            for (int k = 0; k < d; ++k) xc[k] = op.lo[k] + (double)(axis_coord(GI, j, k) + 1) * GI.h[k];
+            cme_coef(cme_production(op, i, xc, d), op.cg[i], xc[i], h, op.central != 0, dd, dm, dp);
         } else {
             // linear SDE: face velocities (A x)_i at x -+ h/2 e_i, diagonal diffusion
             double ax = 0.0;

@@ -30,7 +30,10 @@ struct OpParams {
     double theta, sigma, vamp;
     double A[PIT_D * PIT_D];  // linear SDE: drift matrix (row major, d x d)
     double H[PIT_D * PIT_D];  // linear SDE: H = 2 sigma D sigma^T (row major, d x d)
-    int central;              // linear SDE: central drift flux (else donor cell)
+    int central;              // linear SDE, CME: central drift flux (else donor cell)
+    // CME toggle network: production cp / (cs + y^cb), y the other species'
+    // total, degradation cg x_i (per species)
+    double cp[PIT_D], cs[PIT_D], cb[PIT_D], cg[PIT_D];
 };
 
 // Drift part of one axis of the flux-form operator (F_+ - F_-) / h at node j,
@@ -49,6 +52,30 @@ __host__ __device__ __forceinline__ void drift_coef(double vp, double vm, double
         dm = -fmax(vm, 0.0) / h;
         dp = fmin(vp, 0.0) / h;
     }
+}
+
+// Production propensity of species i of the CME toggle network at x.
+template <typename X>
+__host__ __device__ __forceinline__ double cme_production(const OpParams &op, int i, const X &x, int d)
+{
+    double y = 0.0;
+    for (int k = 0; k < d; ++k)
+        if (k != i) y += x[k];
+    return op.cp[i] / (op.cs[i] + pow(y, op.cb[i]));
+}
+
+// Coefficients of axis i of the CME operator at a node with coordinate xi on
+// that axis and production a (which does not depend on x_i): drift flux with
+// face velocities a - g (xi +- h/2), diffusion -(D_+ p_+ - 2 D_0 p_j + D_- p_-)
+// / (2 h^2) with D = a + g x.
+__host__ __device__ __forceinline__ void cme_coef(double a, double g, double xi, double h, bool central,
+                                                  double &dd, double &dm, double &dp)
+{
+    drift_coef(a - g * (xi + 0.5 * h), a - g * (xi - 0.5 * h), h, central, dd, dm, dp);
+    const double ih2 = 0.5 / (h * h);
+    dd += 2.0 * (a + g * xi) * ih2;
+    dm -= (a + g * (xi - h)) * ih2;
+    dp -= (a + g * (xi + h)) * ih2;
 }
 
 // Global counters filled by the backward-Euler kernels (one atomic per item).

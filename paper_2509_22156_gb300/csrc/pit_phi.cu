@@ -37,6 +37,7 @@ cudaError_t phi_kernels_init(size_t max_smem)
                                    steps_init_varheat_fp64, steps_init_varheat_mixed, steps_init_varheat_fp32,
                                    steps_init_ou_fp64,      steps_init_ou_mixed,      steps_init_ou_fp32,
                                    steps_init_lsde_fp64,    steps_init_lsde_mixed,    steps_init_lsde_fp32,
+                                   steps_init_cme_fp64,     steps_init_cme_mixed,     steps_init_cme_fp32,
                                    steps_init_heat_pair,    steps_init_varheat_pair};
     for (auto f : inits)
         if (e == cudaSuccess) e = f(bytes);
@@ -69,6 +70,7 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
     case PIT_OP_VARHEAT: PIT_BY_PREC(varheat)
     case PIT_OP_OU: PIT_BY_PREC(ou)
     case PIT_OP_LSDE: PIT_BY_PREC(lsde)
+    case PIT_OP_CME: PIT_BY_PREC(cme)
 #undef PIT_BY_PREC
     default: return cudaErrorInvalidValue;
     }

@@ -63,6 +63,9 @@ namespace pit {
 //           linear SDE dX = A X dt + sigma dW (Sec. 4.4) and diffusion
 //           (H_ii/2)(2 p_j - p_- - p_+) / h_i^2; its mixed-derivative terms
 //           (i != k) are constant per grid and applied by TabSt<.., true>.
+//   CME     toggle-switch chemical master equation (Sec. 4.3): the same
+//           flux with face velocity a_i - g_i x_i (production a_i, degradation
+//           g_i x_i) and the second difference of (a_i + g_i x_i) p / 2.
 template <int D>
 __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, const double *faces, int j,
                                         double dt, double &diag, double *cm, double *cp)
@@ -89,6 +92,11 @@ __device__ __forceinline__ void op_coef(const OpParams &op, const GridInfo &G, c
             dd += 2.0 * s2;
             dm -= s2;
             dp -= s2;
+        } else if (op.op == PIT_OP_CME) {
+            double xc[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) xc[k] = op.lo[k] + (double)((j / G.S[k]) % G.N[k] + 1) * G.h[k];
+            cme_coef(cme_production(op, i, xc, D), op.cg[i], xc[i], h, op.central != 0, dd, dm, dp);
         } else {
             // face velocities (A x)_i at x -+ h/2 e_i
             double ax = 0.0;
@@ -906,7 +914,7 @@ __host__ __device__ inline bool line_pc_form(int op, int prec, bool xg)
 }
 __host__ __device__ inline int krylov_vecs(int op, int prec, bool xg = false)
 {
-    if (op == PIT_OP_OU || op == PIT_OP_LSDE) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e or x)
+    if (op == PIT_OP_OU || op == PIT_OP_LSDE || op == PIT_OP_CME) return prec == PLAIN ? 5 : 6;  // r rh p v t (+ e or x)
     if (line_pc_form(op, prec, xg)) return 6;           // r p s w u (+ e or x): u for the line preconditioner
     return prec == PLAIN ? 4 : 5;                        // r p s w (+ e or x)
 }
@@ -942,8 +950,9 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     static_assert(!XG || PREC != SINGLE, "no global-state variant of the FP32 form");
     static_assert(PREC == PLAIN || PREC == MIXED || PREC == SINGLE || PREC == PAIR, "unknown precision form");
-    static_assert(PREC != PAIR || (OP != PIT_OP_OU && OP != PIT_OP_LSDE), "the pair form is for the symmetric operators");
-    constexpr bool DRIFT = (OP == PIT_OP_OU || OP == PIT_OP_LSDE);  // non-symmetric: BiCGStab
+    static_assert(PREC != PAIR || (OP != PIT_OP_OU && OP != PIT_OP_LSDE && OP != PIT_OP_CME),
+                  "the pair form is for the symmetric operators");
+    constexpr bool DRIFT = (OP == PIT_OP_OU || OP == PIT_OP_LSDE || OP == PIT_OP_CME);  // non-symmetric: BiCGStab
     constexpr bool CROSS = (OP == PIT_OP_LSDE);                      // mixed-derivative terms
     const int item = a.item0 + (int)blockIdx.x;
     const int g = a.order[item / a.n_batch];
@@ -1654,6 +1663,7 @@ PIT_STEPS_DECL(heat, fp64) PIT_STEPS_DECL(heat, mixed) PIT_STEPS_DECL(heat, fp32
 PIT_STEPS_DECL(varheat, fp64) PIT_STEPS_DECL(varheat, mixed) PIT_STEPS_DECL(varheat, fp32)
 PIT_STEPS_DECL(ou, fp64) PIT_STEPS_DECL(ou, mixed) PIT_STEPS_DECL(ou, fp32)
 PIT_STEPS_DECL(lsde, fp64) PIT_STEPS_DECL(lsde, mixed) PIT_STEPS_DECL(lsde, fp32)
+PIT_STEPS_DECL(cme, fp64) PIT_STEPS_DECL(cme, mixed) PIT_STEPS_DECL(cme, fp32)
 PIT_STEPS_DECL(heat, pair) PIT_STEPS_DECL(varheat, pair)
 
 // Instantiates the attribute setter and launcher of one operator and form for

@@ -82,3 +82,13 @@ def test_invalid_descriptions_rejected_before_any_device_use(lib):
             desc.lo[i], desc.hi[i] = -1.0, 1.0
         desc.drift_scheme = scheme
         assert lib.pit_problem_create(ctypes.byref(desc), None, ctypes.byref(h)) == B.PIT_ERR_INVALID_ARG, (op, scheme)
+    # CME rates: finite, production and degradation >= 0, saturation > 0, box in x >= 0
+    good = (3.0, 110.0, 2.0, 0.01)
+    for rates, lo in (((3.0, 0.0, 2.0, 0.01), 0.0), ((-3.0, 110.0, 2.0, 0.01), 0.0),
+                      ((3.0, 110.0, 2.0, -0.01), 0.0), ((3.0, 110.0, float("inf"), 0.01), 0.0), (good, -1.0)):
+        desc = B.pit_problem_desc()
+        desc.d, desc.level_n, desc.level0, desc.op = 2, 5, 1, B.PIT_OP_CME
+        for i in range(2):
+            desc.lo[i], desc.hi[i] = lo, 60.0
+            desc.cme_prod[i], desc.cme_sat[i], desc.cme_exp[i], desc.cme_deg[i] = rates
+        assert lib.pit_problem_create(ctypes.byref(desc), None, ctypes.byref(h)) == B.PIT_ERR_INVALID_ARG, rates

@@ -1,0 +1,156 @@
+"""GPU parity of the chemical-master-equation Fokker-Planck operator of the
+toggle-switch networks (Sec. 4.3, Eq. "cme_fp", Tables "toggle_switch_2d" and
+"toggle_switch_3d") against the oracle: the stencil, the initial density,
+backward-Euler batches (BiCGStab) in every precision form and MGRIT, with the
+donor-cell and with the central drift flux.
+
+Tolerances (relative L2): stencil and initial density 1e-13 (same formulas,
+different rounding order); backward-Euler batches and MGRIT 1e-10 in FP64,
+1e-9 with FP32 Krylov in FP64 refinement (both sides solve to 1e-13 or
+tighter); the FP32 form 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_22156_gb300 import binding as B
+from paper_2509_22156_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_22156_gb300 import build
+    build.build()
+    B.load()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# the paper's rates on a smaller box (production 3 / (110 + y^2), degradation
+# 0.01 x; the paper: 3e3 / (1.1e4 + y^2), 1e-3 x on [0, 399]^2)
+RATES = (3.0, 110.0, 2.0, 0.01)
+# (d, n, L0, box edge)
+CASES = {"toggle2d": (2, 7, 2, 60.0), "toggle3d": (3, 6, 1, 60.0)}
+SCHEMES = pytest.mark.parametrize("central", [False, True], ids=["upwind", "central"])
+
+
+def pair(name, central=False, rates=RATES):
+    d, n, L0, w = CASES[name]
+    lo, hi = [0.0] * d, [w] * d
+    P = B.Problem(d, n, L0, B.PIT_OP_CME, lo, hi, cme=rates,
+                  drift_scheme=B.PIT_DRIFT_CENTRAL if central else B.PIT_DRIFT_UPWIND)
+    O = oracle.Problem(d, n, L0, oracle.OP_CME, lo, hi, cme=rates, central=central)
+    return P, O
+
+
+def gauss_params(d):
+    M = np.linspace(20.0, 26.0, d)
+    C = 16.0 * np.eye(d) + 2.0 * (np.ones((d, d)) - np.eye(d))
+    return np.concatenate([M, C.ravel()])
+
+
+@SCHEMES
+@pytest.mark.parametrize("name", list(CASES))
+def test_stencil_and_initial_density_match_oracle(name, central):
+    P, O = pair(name, central)
+    nb = 2
+    p = W.random_vector(33, nb * P.n_total)
+    q = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    P.apply(0.7, torch.from_numpy(p).cuda(), q)
+    assert rel(q.cpu().numpy(), O.apply(0.7, p)) < 1e-13
+    u = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    prm = gauss_params(P.d)
+    P.sample_initial(4, prm, u)
+    assert rel(u.cpu().numpy(), O.initial(4, prm)) < 1e-13
+    P.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(B.PIT_PREC_FP64, 1e-10), (B.PIT_PREC_MIXED, 1e-9), (B.PIT_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("name", list(CASES))
+@SCHEMES
+def test_phi_batch_matches_oracle(name, prec, tol, central):
+    P, O = pair(name, central)
+    nb, dt = 3, 2.0
+    u = W.random_vector(43, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    opts = B.solve_opts(prec, rtol=1e-13 if prec != B.PIT_PREC_FP32 else 1e-6, maxit=20000, inner_rtol=1e-4,
+                        ir_maxit=30)
+    st = P.phi_batch(dt, torch.from_numpy(u).cuda(), out, opts)
+    assert st.n_failed == 0
+    ref = O.phi(dt, u, rtol=1e-15)
+    got = out.cpu().numpy()
+    for b in range(nb):
+        for g in range(P.G):
+            sl = slice(b * P.n_total + P.offsets[g], b * P.n_total + P.offsets[g + 1])
+            assert rel(got[sl], ref[sl]) < tol, (b, g)
+    P.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(B.PIT_PREC_FP64, 1e-10), (B.PIT_PREC_MIXED, 1e-9)])
+@pytest.mark.parametrize("name", list(CASES))
+@SCHEMES
+def test_mgrit_matches_oracle_sequential(name, prec, tol, central):
+    P, O = pair(name, central)
+    N, m, T = 64, 8, 64.0
+    dt = T / N
+    u0 = O.initial(4, gauss_params(P.d))
+    ref = O.sequential(u0, dt, N, rtol=1e-15)
+    fine = B.solve_opts(prec, rtol=1e-13, maxit=20000, inner_rtol=1e-5, ir_maxit=40)
+    crs = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=20000)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    for relax, fas in ((B.PIT_RELAX_F, False), (B.PIT_RELAX_FCF, True)):
+        opts = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-13 * np.abs(ref).max(), maxit=64, fine=fine, crs=crs,
+                            relax=relax, init=True, fas=fas)
+        st = P.mgrit_solve(torch.from_numpy(u0).cuda(), opts, uT)
+        assert st.n_converged == P.G
+        assert rel(uT.cpu().numpy(), ref) < tol, (relax, fas)
+    P.close()
+
+
+def test_pair_form_is_refused_and_rates_are_validated():
+    P, _ = pair("toggle2d")
+    x = torch.zeros(P.n_total, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.PitError) as e:
+        P.phi_batch(0.5, x, torch.empty_like(x), B.solve_opts(B.PIT_PREC_MIXED_PAIR, inner_rtol=1e-4))
+    assert e.value.status == B.PIT_ERR_UNSUPPORTED
+    P.close()
+    for rates, lo in (((3.0, 0.0, 2.0, 0.01), 0.0), ((-1.0, 110.0, 2.0, 0.01), 0.0),
+                      ((3.0, 110.0, 2.0, -0.01), 0.0), ((3.0, 110.0, float("nan"), 0.01), 0.0),
+                      (RATES, -1.0)):
+        with pytest.raises(B.PitError) as e:
+            B.Problem(2, 5, 1, B.PIT_OP_CME, [lo] * 2, [60.0] * 2, cme=rates)
+        assert e.value.status == B.PIT_ERR_INVALID_ARG, (rates, lo)
+
+
+@SCHEMES
+def test_large_grids_in_the_fp64_global_state_class_match_oracle(central):
+    """Grids too large for the on-chip solve (up to 8,001 nodes, level 12,
+    L0 = 5) run the FP64 form's global-state variant; steps and MGRIT."""
+    d, n, L0, w = 2, 12, 5, 120.0
+    P = B.Problem(d, n, L0, B.PIT_OP_CME, [0.0] * d, [w] * d, cme=RATES,
+                  drift_scheme=B.PIT_DRIFT_CENTRAL if central else B.PIT_DRIFT_UPWIND)
+    O = oracle.Problem(d, n, L0, oracle.OP_CME, [0.0] * d, [w] * d, cme=RATES, central=central)
+    assert max(O.offsets[g + 1] - O.offsets[g] for g in range(O.G)) == 8001
+    nb, dt = 2, 1.0
+    u = W.random_vector(53, nb * P.n_total)
+    out = torch.empty(nb * P.n_total, dtype=torch.float64, device="cuda")
+    st = P.phi_batch(dt, torch.from_numpy(u).cuda(), out, B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=20000))
+    assert st.n_failed == 0
+    assert rel(out.cpu().numpy(), O.phi(dt, u, rtol=1e-15)) < 1e-10
+    N, m, T = 64, 8, 64.0
+    u0 = O.initial(4, np.concatenate([[40.0, 45.0], np.diag([30.0, 30.0]).ravel()]))
+    ref = O.sequential(u0, T / N, N, rtol=1e-15)
+    fine = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-13, maxit=20000)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    opts = B.mgrit_opts(0.0, T, N, m, 2, tol=1e-12 * np.abs(ref).max(), maxit=64, fine=fine, crs=fine,
+                        relax=B.PIT_RELAX_F, init=True)
+    st = P.mgrit_solve(torch.from_numpy(u0).cuda(), opts, uT)
+    assert st.n_converged == P.G
+    assert rel(uT.cpu().numpy(), ref) < 1e-10
+    P.close()
