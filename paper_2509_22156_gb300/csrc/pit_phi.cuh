@@ -40,8 +40,10 @@
 //          (heat and variable-coefficient operators).
 //   SINGLE FP32 Krylov on an FP32 copy of the state scaled by a power of two,
 //          for loose tolerances (the coarse correction solves).
-// CG is the single-reduction (Chronopoulos-Gear) form: one fused block
-// reduction of (r,r) and (Ar,r) per iteration and two barriers.
+// CG uses the Chronopoulos-Gear recurrences: the update pass sums (r,r) of
+// the new residual, whose reduction (one barrier) decides convergence before
+// the stencil pass forms A r and (Ar,r) (a second reduction): the last,
+// converged iteration of every solve skips its stencil pass.
 #pragma once
 
 #include <type_traits>
@@ -454,9 +456,10 @@ __device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v < 1.0
 __device__ __forceinline__ bool finite_pos(float v) { return v > 0.0f && v < 1.0e37f; }
 
 // ----------------------------------------------------------------------------
-// Single-reduction CG (Chronopoulos & Gear 1989) on A e = r0: r holds r0 on
-// entry (own nodes written by the caller), the iterate is accumulated into X
-// (FP64 state or FP32 correction).  Stops when (r,r) <= stop2.
+// CG with the Chronopoulos & Gear (1989) recurrences on A e = r0: r holds r0
+// on entry (own nodes written by the caller), the iterate is accumulated into
+// X (FP64 state or FP32 correction).  Stops when (r,r) <= stop2, tested on
+// the sum of the update pass before the stencil pass of the next iteration.
 template <typename T, typename TX, class ST>
 __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reducer<T> &R, T stop2, int maxit,
                        int &status)
@@ -488,6 +491,9 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
     int k = 0;
     for (;;) {
         if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+        // (r, r) of the new residual is summed in the update pass and tested
+        // before the stencil: the converged last iteration skips A r
+        T rr[1] = {T(0)};
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T pj = first ? r[j] : r[j] + beta * p[j];
@@ -495,30 +501,30 @@ __device__ int cg_core(const ST &A, int n, TX *X, T *r, T *p, T *s, T *w, Reduce
             p[j] = pj;
             s[j] = sj;
             X[j] += (TX)(alpha * pj);
-            r[j] -= alpha * sj;
+            const T rj = r[j] - alpha * sj;
+            r[j] = rj;
+            rr[0] += rj * rj;
         }
         first = false;
         ++k;
-        __syncthreads();
-        T u[2] = {T(0), T(0)};
+        R.template sum<1>(rr);  // also: r complete
+        if (!(rr[0] > stop2)) {
+            if (rr[0] != rr[0]) status = PIT_ERR_NONFINITE;
+            break;
+        }
+        T wr[1] = {T(0)};
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T wj = A(r, j);
             w[j] = wj;
-            const T rj = r[j];
-            u[0] += rj * rj;
-            u[1] += wj * rj;
+            wr[0] += wj * r[j];
         }
-        R.template sum<2>(u);
-        if (!(u[0] > stop2)) {
-            if (u[0] != u[0]) status = PIT_ERR_NONFINITE;
-            break;
-        }
-        beta = u[0] / gam;
-        const T den = u[1] - beta * u[0] / alpha;
+        R.template sum<1>(wr);
+        beta = rr[0] / gam;
+        const T den = wr[0] - beta * rr[0] / alpha;
         if (!finite_pos(den)) { status = (den != den) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
-        alpha = u[0] / den;
-        gam = u[0];
+        alpha = rr[0] / den;
+        gam = rr[0];
     }
     return k;
 }
@@ -705,10 +711,11 @@ struct LineM {
     }
 };
 
-// Preconditioned single-reduction CG (the Chronopoulos-Gear recurrences with
-// u = M^{-1} r): one fused reduction of (r,r), (r,u), (Au,u) per iteration
-// and three barriers.  Stops when (r,r) <= stop2 (unpreconditioned norm, the
-// same test as cg_core).
+// Preconditioned CG (the Chronopoulos-Gear recurrences with u = M^{-1} r):
+// per iteration the update pass sums (r,r) (reduction, convergence test),
+// then M, then the stencil pass sums (r,u) and (Au,u) (second reduction); a
+// converged iteration skips M and the stencil.  Stops when (r,r) <= stop2
+// (unpreconditioned norm, the same test as cg_core).
 template <typename T, typename TX, class ST, class PC>
 __device__ int pcg_core(const ST &A, const PC &M, int n, TX *X, T *r, T *u, T *p, T *s, T *w, Reducer<T> &R,
                         T stop2, int maxit, int &status)
@@ -742,6 +749,9 @@ __device__ int pcg_core(const ST &A, const PC &M, int n, TX *X, T *r, T *u, T *p
     int k = 0;
     for (;;) {
         if (k >= maxit) { status = PIT_ERR_NOCONV; break; }
+        // (r, r) of the new residual is summed in the update pass and tested
+        // before the preconditioner: the converged last iteration skips M and A
+        T rr[1] = {T(0)};
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T pj = first ? u[j] : u[j] + beta * p[j];
@@ -749,34 +759,35 @@ __device__ int pcg_core(const ST &A, const PC &M, int n, TX *X, T *r, T *u, T *p
             p[j] = pj;
             s[j] = sj;
             X[j] += (TX)(alpha * pj);
-            r[j] -= alpha * sj;
+            const T rj = r[j] - alpha * sj;
+            r[j] = rj;
+            rr[0] += rj * rj;
         }
         first = false;
         ++k;
-        __syncthreads();  // r complete
+        R.template sum<1>(rr);  // also: r complete
+        if (!(rr[0] > stop2)) {
+            if (rr[0] != rr[0]) status = PIT_ERR_NONFINITE;
+            break;
+        }
         M(r, u);
         __syncthreads();  // u complete
-        T q[3] = {T(0), T(0), T(0)};
+        T q[2] = {T(0), T(0)};
 #pragma unroll 4
         for (int j = tid; j < n; j += nt) {
             const T wj = A(u, j);
             w[j] = wj;
-            const T rj = r[j], uj = u[j];
-            q[0] += rj * rj;
-            q[1] += rj * uj;
-            q[2] += wj * uj;
+            const T uj = u[j];
+            q[0] += r[j] * uj;
+            q[1] += wj * uj;
         }
-        R.template sum<3>(q);
-        if (!(q[0] > stop2)) {
-            if (q[0] != q[0]) status = PIT_ERR_NONFINITE;
-            break;
-        }
-        if (!finite_pos(q[1])) { status = (q[1] != q[1]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
-        beta = q[1] / gam;
-        const T den = q[2] - beta * q[1] / alpha;
+        R.template sum<2>(q);
+        if (!finite_pos(q[0])) { status = (q[0] != q[0]) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
+        beta = q[0] / gam;
+        const T den = q[1] - beta * q[0] / alpha;
         if (!finite_pos(den)) { status = (den != den) ? PIT_ERR_NONFINITE : PIT_ERR_BREAKDOWN; break; }
-        alpha = q[1] / den;
-        gam = q[1];
+        alpha = q[0] / den;
+        gam = q[0];
     }
     return k;
 }
@@ -1139,24 +1150,32 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     bool use_pc = false;
     LineM<float> LM{};
     if constexpr (OP == PIT_OP_HEAT && PREC != PLAIN && !XG) {
-        int ax = 0;
+        // (every per-axis value is read with a compile-time index, so that
+        // the grid description and the stencil stay in registers)
+        int ax = 0, Na = 0, Sa = 0;
+        double ha = 1e300;
+        float offa = 0.0f;
 #pragma unroll
-        for (int i = 1; i < D; ++i)
-            if (GI.h[i] < GI.h[ax]) ax = i;
+        for (int i = 0; i < D; ++i)
+            if (GI.h[i] < ha) {
+                ax = i;
+                ha = GI.h[i];
+                Na = GI.N[i];
+                Sa = GI.S[i];
+                offa = HT.off[i];
+            }
         double h2 = 1e300;
 #pragma unroll
         for (int i = 0; i < D; ++i)
             if (i != ax && GI.h[i] < h2) h2 = GI.h[i];
-        const double ha = GI.h[ax];
-        const int Na = GI.N[ax];
         use_pc = a.precond != PIT_PRECOND_NONE && Na >= 3 && 2.0 * ha <= h2 * (1.0 + 1e-12) &&
                  4.0 * dt / (ha * ha) >= 2.0;
         if (use_pc) {
             float *lf = reinterpret_cast<float *>(mask + ld);
-            LM.layout(Na, GI.S[ax], n, nt);
+            LM.layout(Na, Sa, n, nt);
             LM.f = lf;
-            LM.off = HT.off[ax];
-            if (tid == 0) LM.setup(lf, HT.off[ax], HT.diag);
+            LM.off = offa;
+            if (tid == 0) LM.setup(lf, offa, HT.diag);
         }
     }
     auto A64 = [&](const double *v, int j) -> double {
