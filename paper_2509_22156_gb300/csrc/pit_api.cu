@@ -475,12 +475,15 @@ pit_status tune(pit_problem *P, int prec, bool wide, int cls, const pit_solve_op
     const int cand[4] = {64, 128, 256, 512};
     CU(P->w_tune.ensure(sizeof(double) * P->ntot * c.nb));
     // the trial keeps the call's inputs (a correction sweep starts from zero
-    // and is driven by its forcing) and writes only scratch; narrow batches
-    // (sequential sweeps, latency bound) are timed over several steps
+    // and is driven by its forcing) and writes only scratch; it runs several
+    // steps, so that the refinement forms' carried residual (every step but
+    // the first) weighs as in the real launch: wide batches (relaxation
+    // intervals) 4, narrow ones (sequential sweeps, latency bound) 8
     StepCall t;
     t.dt = c.dt;
     t.nb = c.nb;
-    t.nsteps = wide ? 1 : (c.nsteps < 8 ? c.nsteps : 8);
+    const int trial = wide ? 4 : 8;
+    t.nsteps = c.nsteps < trial ? c.nsteps : trial;
     t.in = c.in;
     t.is = c.is;
     t.f = c.f;
