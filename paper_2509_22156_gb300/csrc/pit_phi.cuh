@@ -1582,11 +1582,29 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 const double cs = pow2d(kn - kr);
                 const int kd = min(max(kn - kr + ks, -120), 120);
                 const float csf = __uint_as_float((unsigned)(127 + kd) << 23);
-#pragma unroll 4
-                for (int j = tid; j < n; j += nt) {
-                    const float ej = jac ? e[j] * tab32[j] : e[j];  // Jacobi: e = D^{-1/2} y
-                    x[j] = fma(to_f64(ej, 0), cs, x[j]);
-                    if (carry_ok) dv[j] = fmaf(ej, csf, dv[j]);
+                // (four nodes per thread are loaded before any is stored: x and
+                // dv may live in global memory, where the compiler cannot
+                // reorder loads across the possibly aliasing stores)
+                for (int j0 = tid; j0 < n; j0 += 4 * nt) {
+                    double xv[4];
+                    float ev[4], dw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = j0 + q * nt;
+                        if (j < n) {
+                            ev[q] = jac ? e[j] * tab32[j] : e[j];  // Jacobi: e = D^{-1/2} y
+                            xv[q] = x[j];
+                            dw[q] = carry_ok ? dv[j] : 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = j0 + q * nt;
+                        if (j < n) {
+                            x[j] = fma(to_f64(ev[q], 0), cs, xv[q]);
+                            if (carry_ok) dv[j] = fmaf(ev[q], csf, dw[q]);
+                        }
+                    }
                 }
                 __syncthreads();  // x complete
                 // FP64 check: r = b - A x; the stopping test and the next
