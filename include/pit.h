@@ -184,6 +184,22 @@ typedef struct {
  *            the symmetric scaling D^{-1/2} A D^{-1/2}; elsewhere as NONE. */
 typedef enum { PIT_PRECOND_DEFAULT = 0, PIT_PRECOND_NONE = 1, PIT_PRECOND_JACOBI = 2 } pit_precond;
 
+/* Initial guess of each backward-Euler step's solve in the refinement form
+ * PIT_PREC_MIXED (the paper fixes none; it changes how many refinement passes
+ * a step takes, not the stopping rule or the fixed point):
+ *   DEFAULT      EXTRAPOLATE.
+ *   PREVIOUS     the previous state x_{s-1}.
+ *   EXTRAPOLATE  from the third step of a call on, when a step has no forcing
+ *                and no caller guess: the linear extrapolation
+ *                2 x_{s-1} - x_{s-2}.  Its initial residual is formed without
+ *                a stencil pass from the FP64 residuals of the two previous
+ *                steps (A (x_{s-1} - x_{s-2}) = A x_{s-1} - A x_{s-2}, each
+ *                known from its step's check), so for smooth solutions a step
+ *                starts near (dt lambda)^2 |x| instead of dt lambda |x| and
+ *                often needs one FP32 correction instead of two.
+ * Other precision forms ignore it. */
+typedef enum { PIT_GUESS_DEFAULT = 0, PIT_GUESS_PREVIOUS = 1, PIT_GUESS_EXTRAPOLATE = 2 } pit_guess;
+
 typedef struct {
     int prec;
     double rtol;
@@ -191,6 +207,7 @@ typedef struct {
     double inner_rtol;
     int ir_maxit;
     int precond;          /* pit_precond */
+    int guess;            /* pit_guess */
 } pit_solve_opts;
 
 typedef struct {

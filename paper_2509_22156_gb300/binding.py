@@ -54,7 +54,8 @@ class pit_problem_desc(ctypes.Structure):
 
 class pit_solve_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double), ("ir_maxit", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("ir_maxit", ctypes.c_int), ("precond", ctypes.c_int),
+                ("guess", ctypes.c_int)]
 
 
 class pit_phi_stats(ctypes.Structure):
@@ -166,11 +167,12 @@ def _ptr(x):
 
 
 PIT_PRECOND_DEFAULT, PIT_PRECOND_NONE, PIT_PRECOND_JACOBI = 0, 1, 2
+PIT_GUESS_DEFAULT, PIT_GUESS_PREVIOUS, PIT_GUESS_EXTRAPOLATE = 0, 1, 2
 
 
 def solve_opts(prec=PIT_PREC_FP64, rtol=1e-10, maxit=10000, inner_rtol=1e-4, ir_maxit=12,
-               precond=PIT_PRECOND_DEFAULT) -> pit_solve_opts:
-    return pit_solve_opts(prec, rtol, maxit, inner_rtol, ir_maxit, precond)
+               precond=PIT_PRECOND_DEFAULT, guess=PIT_GUESS_DEFAULT) -> pit_solve_opts:
+    return pit_solve_opts(prec, rtol, maxit, inner_rtol, ir_maxit, precond, guess)
 
 
 def train_opts(dt_fine, m, n_pairs=4096, n_holdout=256, epochs=20, batch=64, lr=1e-3, seed=0, ic_modes=8,

@@ -276,6 +276,8 @@ pit_status check_solve_opts(const pit_solve_opts *o)
     if (!(o->rtol >= 0.0) || o->maxit < 1) return fail(PIT_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
     if (o->precond < PIT_PRECOND_DEFAULT || o->precond > PIT_PRECOND_JACOBI)
         return fail(PIT_ERR_INVALID_ARG, "unknown preconditioner %d", o->precond);
+    if (o->guess < PIT_GUESS_DEFAULT || o->guess > PIT_GUESS_EXTRAPOLATE)
+        return fail(PIT_ERR_INVALID_ARG, "unknown initial guess %d", o->guess);
     if ((o->prec == PIT_PREC_MIXED || o->prec == PIT_PREC_MIXED_PAIR) &&
         (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || o->ir_maxit < 1))
         return fail(PIT_ERR_INVALID_ARG, "mixed precision needs 0 < inner_rtol < 1 and ir_maxit >= 1");
@@ -433,6 +435,7 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.ir_maxit = o.ir_maxit;
     a.inexact = c.inexact;
     a.precond = o.precond;
+    a.predict = o.guess != PIT_GUESS_PREVIOUS;
     a.stats = P->d_stats;
     return a;
 }

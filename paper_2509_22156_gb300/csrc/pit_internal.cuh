@@ -132,7 +132,7 @@ struct StepArgs {
     const double *guess;     long long guess_stride, guess_step;
     double *xg;              // state in global memory (grids too large for shared memory):
     double *bg;              //   x and b (MIXED) of entry b at xg/bg + b*n_total + grid offset, the
-                             //   FP32 step increment (MIXED) at slab 2;
+                             //   carried x - A x (MIXED, FP64) at slab 2;
                              //   PLAIN: Krylov vector k at xg + ((1+k) n_batch + b) n_total + offset,
                              //   then (table operators) coefficient row k of the item at
                              //   xg + ((1+NKV+k) n_batch + b) n_total + offset
@@ -146,6 +146,7 @@ struct StepArgs {
     int ir_maxit;
     int inexact;             // 1: a solve stopped by its iteration caps is not a failure
     int precond;             // pit_precond of the Krylov solves
+    int predict;             // MIXED without forcing: extrapolated initial guess 2 x_s - x_{s-1}
     DevStats *stats;
 };
 
@@ -202,7 +203,7 @@ size_t phi_smem_bytes(int prec, int op, int d, int n, int na);
 cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, cudaStream_t s, bool xg = false);
 // Shared memory per item of the global-state variant (PLAIN or MIXED), and
 // the number of n_batch x n_total FP64 slabs of global workspace it uses
-// (x, b and the FP32 step increment for MIXED; x and the Krylov vectors for
+// (x, b and the carried x - A x for MIXED; x and the Krylov vectors for
 // PLAIN).
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n);
 int xg_slabs(int prec, int op, int d);

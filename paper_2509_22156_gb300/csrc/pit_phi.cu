@@ -23,7 +23,7 @@ size_t phi_smem_bytes_xg(int prec, int op, int d, int n)
 int xg_slabs(int prec, int op, int d)
 {
     // PLAIN: x, the Krylov vectors and the coefficient table; MIXED: x, b and
-    // the step increment; PAIR uses two
+    // the carried x - A x; PAIR uses two
     return prec == PLAIN ? 1 + krylov_vecs(op, PLAIN) + n_tab(op, d) : 3;
 }
 

@@ -24,15 +24,20 @@
 //          GB300 FP64 arithmetic (and the hardware FP64<->FP32 conversion)
 //          runs at 1/58 of the FP32 rate, so the FP64 stencil passes bound the
 //          kernel and are kept lean: when a step has no forcing, the FP64 pass
-//          that verifies step s also yields x_s - A x_s, which is exactly the
-//          initial residual of step s+1 (b = x_s, x_0 = x_s), so each step
-//          costs one FP64 stencil pass per correction.  The FP64 pipe does
-//          only what needs FP64 (the stencil on the FP64 state and b - A x):
-//          conversions run on the integer pipes with an exact power-of-two
-//          scale, the carried residual is r + (x - b) with the step increment
-//          accumulated in FP32, and the squared norms that feed the stopping
-//          test and the tolerances are summed from the FP32 copies (relative
-//          accuracy about 1e-7, far below what a stopping test resolves).
+//          that verifies step s gives r_s = b_s - A x_s, hence
+//          c_s = x_s - A x_s = r_s + (x_s - x_{s-1}), the initial residual of
+//          step s+1 for the guess x_s, without a stencil pass; and with
+//          c_{s-1} kept in FP64 the residual of the extrapolated guess
+//          2 x_s - x_{s-1} is c_s - c_{s-1} + r_s, also without one (the
+//          extrapolation starts a smooth solution's step about (dt lambda)^2
+//          instead of dt lambda from its solution, so one FP32 correction
+//          mostly suffices).  Each step then costs one FP64 stencil pass per
+//          correction.  The FP64 pipe does only what needs FP64 (the stencil on
+//          the FP64 state, b - A x, the carried residuals): conversions run on
+//          the integer pipes with an exact power-of-two scale, and the squared
+//          norms that feed the stopping test and the tolerances are summed from
+//          the FP32 copies (relative accuracy about 1e-7, far below what a
+//          stopping test resolves).
 //   PAIR   the MIXED refinement with the state and right-hand side held as
 //          pairs of FP32 numbers (about 48 significant bits, scaled by a power
 //          of two) and b - A x formed from them by error-free FP32
@@ -304,6 +309,22 @@ __device__ __forceinline__ float to_f32(double v, int k)
     const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
     const unsigned bits = sign | ((unsigned)min(ex, 255) << 23) | mant;
     return __uint_as_float(ex > 0 ? bits : sign);
+}
+// to_f32_rn: the same with the mantissa rounded to nearest (ties away from
+//   zero): for residuals that a single correction solves for, where
+//   truncation's bias toward zero would leave the same sign of error in
+//   every step.
+__device__ __forceinline__ float to_f32_rn(double v, int k)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const int ex = (int)((hi >> 20) & 0x7ffu) - (1023 - 127) + k;
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned mag = ((unsigned)min(ex, 255) << 23) | mant;
+    // first dropped bit: add one unit in the last place of the magnitude (a
+    // carry out of the mantissa moves into the exponent, up to infinity)
+    const unsigned rmag = ex < 255 ? mag + ((lo >> 28) & 1u) : mag;
+    return __uint_as_float(ex > 0 ? (sign | rmag) : sign);
 }
 __device__ __forceinline__ double to_f64(float f, int k)
 {
@@ -937,17 +958,17 @@ __host__ __device__ inline int line_pc_bytes(int op, int prec, bool xg, int na)
 }
 
 __host__ __device__ inline int n_tab(int op, int d) { return op == PIT_OP_HEAT ? 0 : 2 * d + 1; }
+// (MIXED keeps a third FP64 array, the carried x - A x of the last step;
+// its global-state variant keeps it in global memory with x and b)
 __host__ __device__ inline int n_f64(int op, int prec, int d)
 {
     if (prec == SINGLE) return 0;
-    return (prec == PLAIN ? 1 + krylov_vecs(op, prec) : 2) + n_tab(op, d);
+    return (prec == PLAIN ? 1 + krylov_vecs(op, prec) : prec == MIXED ? 3 : 2) + n_tab(op, d);
 }
-// (MIXED keeps one more FP32 array in shared memory, the step increment dv;
-// its global-state variant keeps dv in global memory instead)
 __host__ __device__ inline int n_f32(int op, int prec, int d, bool xg = false)
 {
     if (prec == PLAIN) return 0;
-    return krylov_vecs(op, prec, xg) + (prec == MIXED && !xg ? 1 : 0) + n_tab(op, d);
+    return krylov_vecs(op, prec, xg) + n_tab(op, d);
 }
 
 template <int OP, int PREC, int D, bool XG = false>
@@ -980,11 +1001,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     // the FP64 global-state variant keeps the coefficient table in global
     // memory too (grids of any size); the others keep it on chip
     constexpr bool GTAB = XG && PREC == PLAIN && K > 0;
-    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (DRIFT ? 5 : 4) : 2) + (GTAB ? 0 : K);
+    constexpr int NF64 = PREC == SINGLE ? 0 : (XG ? 0 : PREC == PLAIN ? 1 + (DRIFT ? 5 : 4) : PREC == MIXED ? 3 : 2) + (GTAB ? 0 : K);
     constexpr int NKV = DRIFT ? (PREC == PLAIN ? 5 : 6)
                                           : (PREC == PLAIN ? 4 : (OP == PIT_OP_HEAT && !XG ? 6 : 5));
-    constexpr int NDV = (PREC == MIXED && !XG) ? 1 : 0;  // dv in shared memory
-    constexpr int NF32 = (PREC != PLAIN) ? NKV + NDV + K : 0;
+    constexpr int NF32 = (PREC != PLAIN) ? NKV + K : 0;
 
     double *s64 = reinterpret_cast<double *>(smem);
     double *x = XG ? a.xg + (long long)b * a.n_total + GI.off : s64;
@@ -1005,7 +1025,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     // stride between the table's entries (the host keeps n_batch n_total below 2^31 here)
     const int tld = GTAB ? (int)((long long)a.n_batch * a.n_total) : ld;
     float *f32 = reinterpret_cast<float *>(s64 + (size_t)NF64 * ld);
-    float *tab32 = f32 + (size_t)(NKV + NDV) * ld;
+    float *tab32 = f32 + (size_t)NKV * ld;
     uint16_t *mask = reinterpret_cast<uint16_t *>(f32 + (size_t)NF32 * ld);
 
     const double *in = a.in + (long long)b * a.in_stride + GI.off;
@@ -1197,10 +1217,12 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     double rn0_c = 0.0, bb_c = 0.0;
     int kr_c = 0;
     float *rv = f32 + ld, *pv = f32 + 2 * ld, *sv = f32 + 3 * ld, *wv = f32 + 4 * ld, *tv = f32 + 5 * ld;
-    // MIXED: increment x - b of the current step, scaled by 2^ks, accumulated
-    // in FP32 from the corrections (the carried residual is r + dv)
-    float *dv = XG ? reinterpret_cast<float *>(a.xg + ((long long)2 * a.n_batch + b) * a.n_total + GI.off)
-                   : f32 + (size_t)NKV * ld;
+    // MIXED: c = x_s - A x_s of the last completed step, in FP64 (the next
+    // step's initial residual for the guess x_s, and with the one before it
+    // the residual of the extrapolated guess); have_c: c holds c_{s-1} at the
+    // start of step s + 1
+    double *cvec = XG ? a.xg + ((long long)2 * a.n_batch + b) * a.n_total + GI.off : s64 + 2 * ld;
+    bool have_c = false;
 
     for (int step = 1; step <= a.nsteps; ++step) {
         // forcing of this step: f_div consecutive steps share one forcing vector
@@ -1493,64 +1515,87 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             continue;
         } else {
             float *e = f32;
-            // right-hand side b = x_{s-1} + dt f; optional initial guess
-            if (a.guess) {
-                const long long sb0 = (long long)(step - 1);
-                const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
-                const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
-                for (int j = tid; j < n; j += nt) {
-                    bvec[j] = f ? x[j] + dt * f[j] : x[j];
-                    x[j] = gf ? gu[j] - gf[j] : gu[j];
-                }
-            } else {
-                for (int j = tid; j < n; j += nt) bvec[j] = f ? x[j] + dt * f[j] : x[j];
-            }
             double rn2, bb;
             int kr;  // the stored FP32 residual rv holds r 2^kr
             if (have_r0) {
-                // r0 = x_{s-1} - A x_{s-1}, computed by the last check of the
-                // previous step into wv (OU: tv)
-                if constexpr (DRIFT) { float *t_ = rv; rv = tv; tv = t_; }
-                else { float *t_ = rv; rv = wv; wv = t_; }
-                rn2 = rn0_c;
-                bb = bb_c;
-                kr = kr_c;
+                // Step s + 1 without forcing: b = x_s, and rv holds r_s 2^kr_c,
+                // r_s = x_{s-1} - A x_s, the FP64 residual of the last check of
+                // step s.  With d = x_s - x_{s-1} (FP64), c_s = x_s - A x_s =
+                // r_s + d.  Guess x_s: r0 = c_s.  Extrapolated guess
+                // 2 x_s - x_{s-1} = x_s + d: A d = A x_s - A x_{s-1} =
+                // (x_{s-1} - r_s) - (x_{s-1} - c_{s-1}), so
+                // r0 = x_s - A x_s - A d = c_s - c_{s-1} + r_s, exact up to
+                // rounding without a stencil pass (the residual of the guess is
+                // about (dt lambda)^2 |x| for a smooth mode of decay rate lambda,
+                // against dt lambda |x| for the guess x_s).
+                const int kq = kr_c;
+                const bool pred = a.predict && have_c;
+                float acc[2] = {0.0f, 0.0f};
+#pragma unroll 4
+                for (int j = tid; j < n; j += nt) {
+                    const double xs = x[j], bo = bvec[j];
+                    const float rs = rv[j];
+                    const double d = xs - bo;
+                    const double cn = to_f64(rs, -kq) + d;
+                    float r0;
+                    if (pred) {
+                        r0 = to_f32_rn(cn - cvec[j], kq) + rs;
+                        x[j] = xs + d;
+                    } else {
+                        r0 = to_f32_rn(cn, kq);
+                    }
+                    cvec[j] = cn;
+                    bvec[j] = xs;
+                    rv[j] = r0;
+                    const float xf = to_f32(xs, kq);
+                    acc[0] += r0 * r0;
+                    acc[1] += xf * xf;
+                }
+                R32.template sum<2>(acc);  // also: x, b and rv complete
+                rn2 = to_f64(acc[0], -2 * kq);
+                bb = to_f64(acc[1], -2 * kq);
+                kr = kq;
+                have_c = true;
             } else {
+                // right-hand side b = x_{s-1} + dt f; optional initial guess
+                if (a.guess) {
+                    const long long sb0 = (long long)(step - 1);
+                    const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
+                    const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
+                    for (int j = tid; j < n; j += nt) {
+                        bvec[j] = f ? x[j] + dt * f[j] : x[j];
+                        x[j] = gf ? gu[j] - gf[j] : gu[j];
+                    }
+                } else {
+                    for (int j = tid; j < n; j += nt) bvec[j] = f ? x[j] + dt * f[j] : x[j];
+                }
                 double acc[1] = {0.0};
                 for (int j = tid; j < n; j += nt) acc[0] += bvec[j] * bvec[j];
                 R64.template sum<1>(acc);  // also: bvec and x complete
                 bb = acc[0];
                 kr = scale_exp(bb);
                 float accf[1] = {0.0f};
+                // without forcing x = b here, so r0 is c_{s-1} = x_{s-1} - A x_{s-1}
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
-                    const float rf = to_f32(RES64(bvec[j], x, j), kr);
+                    const double r = RES64(bvec[j], x, j);
+                    const float rf = to_f32_rn(r, kr);
+                    if (carry_ok) cvec[j] = r;
                     rv[j] = rf;
                     accf[0] += rf * rf;
                 }
                 R32.template sum<1>(accf);
                 ++passes;
                 rn2 = to_f64(accf[0], -2 * kr);
+                have_c = carry_ok;
             }
             have_r0 = false;
             const double stop2 = a.rtol * a.rtol * bb;
             const int ks = scale_exp(bb);  // FP32 copies of this step: value 2^ks, ||b|| 2^ks in [1, 2)
-            if (carry_ok)
-                for (int j = tid; j < n; j += nt) dv[j] = 0.0f;  // x = b at the start of the step
             int st_step = PIT_OK;
-            bool carried = false;
             for (int pass = 0;; ++pass) {
                 if (!(rn2 > stop2)) {
                     if (rn2 != rn2) st_step = PIT_ERR_NONFINITE;
-                    else if (carry_ok && pass == 0) {
-                        // x unchanged: its residual is the next step's r0
-                        if constexpr (DRIFT) { float *t_ = rv; rv = tv; tv = t_; }
-                        else { float *t_ = rv; rv = wv; wv = t_; }
-                        rn0_c = rn2;
-                        bb_c = bb;
-                        kr_c = kr;
-                        carried = true;
-                    }
                     break;
                 }
                 if (pass >= a.ir_maxit) { st_step = PIT_ERR_NOCONV; break; }
@@ -1578,70 +1623,51 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 if (st == PIT_ERR_NONFINITE) { st_step = st; break; }
                 // a stalled or broken-down inner solve still gives a usable
                 // correction; the FP64 residual decides.  x += e 2^(kn - kr)
-                // (FP64), dv += e 2^(kn - kr + ks) (FP32, exact scaling)
+                // (FP64, exact scaling)
                 const double cs = pow2d(kn - kr);
-                const int kd = min(max(kn - kr + ks, -120), 120);
-                const float csf = __uint_as_float((unsigned)(127 + kd) << 23);
-                // (four nodes per thread are loaded before any is stored: x and
-                // dv may live in global memory, where the compiler cannot
-                // reorder loads across the possibly aliasing stores)
+                // (four nodes per thread are loaded before any is stored: x may
+                // live in global memory, where the compiler cannot reorder
+                // loads across the possibly aliasing stores)
                 for (int j0 = tid; j0 < n; j0 += 4 * nt) {
                     double xv[4];
-                    float ev[4], dw[4];
+                    float ev[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int j = j0 + q * nt;
                         if (j < n) {
                             ev[q] = jac ? e[j] * tab32[j] : e[j];  // Jacobi: e = D^{-1/2} y
                             xv[q] = x[j];
-                            dw[q] = carry_ok ? dv[j] : 0.0f;
                         }
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int j = j0 + q * nt;
-                        if (j < n) {
-                            x[j] = fma(to_f64(ev[q], 0), cs, xv[q]);
-                            if (carry_ok) dv[j] = fmaf(ev[q], csf, dw[q]);
-                        }
+                        if (j < n) x[j] = fma(to_f64(ev[q], 0), cs, xv[q]);
                     }
                 }
                 __syncthreads();  // x complete
-                // FP64 check: r = b - A x; the stopping test and the next
-                // step's r0 = x - A x = r + (x - b) work on the FP32 copies
-                // (their squared norms accumulated in FP32), as does ||x||^2,
-                // the next right-hand side's norm
-                float *cv = DRIFT ? tv : wv;
-                float accf[3] = {0.0f, 0.0f, 0.0f};
+                // FP64 check: r = b - A x; the stopping test works on the FP32
+                // copy (its squared norm accumulated in FP32), which the next
+                // step also reads for its carried initial residual
+                float accf[1] = {0.0f};
                 // (unrolled: independent nodes keep several FP64 stencil
                 // chains in flight, the FP64 latency is long on GB300)
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
-                    const double xj = x[j];
-                    const float rf = to_f32(RES64(bvec[j], x, j), ks);
+                    const float rf = to_f32_rn(RES64(bvec[j], x, j), ks);
                     rv[j] = rf;
                     accf[0] += rf * rf;
-                    if (carry_ok) {
-                        const float cj = rf + dv[j];
-                        const float xf = to_f32(xj, ks);
-                        cv[j] = cj;
-                        accf[1] += cj * cj;
-                        accf[2] += xf * xf;
-                    }
                 }
-                R32.template sum<3>(accf);
+                R32.template sum<1>(accf);
                 ++passes;
                 rn2 = to_f64(accf[0], -2 * ks);
                 kr = ks;
-                if (carry_ok) {
-                    rn0_c = to_f64(accf[1], -2 * ks);
-                    bb_c = to_f64(accf[2], -2 * ks);
-                    kr_c = ks;
-                    carried = true;
-                }
             }
             if (st_step > status) status = st_step;
-            have_r0 = carried && st_step == PIT_OK && step < a.nsteps;
+            // rv holds the FP64 residual of the final x (from its check, or
+            // the unchanged initial residual when pass 0 met the tolerance)
+            have_r0 = carry_ok && st_step == PIT_OK && step < a.nsteps;
+            kr_c = kr;
         }
         // forcing of this step and the stored outputs (own nodes only)
         const long long sb = (long long)(step - 1);
