@@ -73,6 +73,8 @@ def lib():
             L.or_mgrit.restype = c_int
             L.or_mgrit.argtypes = [vp, vp, c_double, c_int, c_int, c_int, c_double, c_int, c_int,
                                    vp, c_double, c_int, vp, vp, vp, vp, c_int, c_int, vp, vp]
+            L.or_coarse_step.restype = c_int
+            L.or_coarse_step.argtypes = [vp, c_double, c_int, c_int, c_int, c_double, vp, vp]
             L.or_combine.argtypes = [vp, vp, c_int, vp, vp]
             L.or_interp.argtypes = [vp, c_int, vp, c_int, vp, vp]
             L.or_hierarchize.restype = c_int
@@ -261,6 +263,17 @@ class Problem:
         if check and st != 0:
             raise RuntimeError(f"oracle mgrit: {STATUS.get(st, st)}")
         return out, its, hist, st
+
+    def coarse_step(self, u, dt, m, level=1, coarse_kind=0, rtol=1e-14) -> np.ndarray:
+        """One step of the MGRIT hierarchy's level-`level` propagator (fine
+        step dt, coarsening m) on every grid: coarse_kind 0 backward Euler with
+        dt m^level, 3 the two-stage SDIRK step of that size."""
+        u = _f64(u)
+        out = np.empty_like(u)
+        st = lib().or_coarse_step(self._h, dt, m, level, coarse_kind, rtol, _p(u), _p(out))
+        if st != 0:
+            raise RuntimeError(f"oracle coarse_step: {STATUS.get(st, st)}")
+        return out
 
     def combine(self, u, pts) -> np.ndarray:
         u = _f64(u)

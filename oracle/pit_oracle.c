@@ -833,7 +833,8 @@ typedef struct {
     int nlev;           /* number of levels (>= 2) */
     double rtol;        /* Krylov tolerance */
     int maxit;
-    int coarse_kind;    /* 0 implicit BE, 1 m exact fine steps, 2 learned net */
+    int coarse_kind;    /* 0 implicit BE, 1 m exact fine steps, 2 learned net,
+                           3 two-stage SDIRK (every coarse level) */
     const double *theta;/* net parameters (coarse_kind 2) */
     int relax_f;        /* 1: F-relaxation on the finest level, 0: FCF */
     int status;
@@ -864,6 +865,24 @@ static void mg_step(mg_ctx *C, int level, int k, const double *v_in, const doubl
         }
     } else if (level == 1 && C->coarse_kind == 2) {
         net_forward_grid(C->P, C->g, dtl, C->theta, v_in, v_out, NULL, NULL);
+    } else if (level >= 1 && C->coarse_kind == 3) {
+        /* Two-stage singly diagonally implicit Runge-Kutta step of order 2,
+         * stiffly accurate and L-stable (Alexander's scheme, gamma =
+         * 1 - 1/sqrt 2): for u' = -L u the stages solve
+         *   (I + gamma dT L) U1 = u_n,
+         *   (I + gamma dT L) U2 = u_n - (1 - gamma) dT L U1
+         *                       = (1 - beta) u_n + beta U1,  beta = (1 - gamma) / gamma,
+         * (dT L U1 = (u_n - U1) / gamma) and u_{n+1} = U2; stability function
+         * (1 + (1 - 2 gamma) z) / (1 - gamma z)^2.  A coarse propagator of
+         * higher order than the fine backward Euler, closer to Phi^m for the
+         * smooth modes; the fixed point of MGRIT stays the fine solution. */
+        const double gam = 1.0 - 1.0 / sqrt(2.0), beta = (1.0 - gam) / gam;
+        double *u1 = malloc(sizeof(double) * n), *b2 = malloc(sizeof(double) * n);
+        st = phi_grid(C->P, C->g, gam * dtl, v_in, NULL, u1, C->rtol, C->maxit, NULL);
+        for (long long j = 0; j < n; ++j) b2[j] = (1.0 - beta) * v_in[j] + beta * u1[j];
+        int s2 = phi_grid(C->P, C->g, gam * dtl, b2, NULL, v_out, C->rtol, C->maxit, NULL);
+        if (s2 != OR_OK) st = s2;
+        free(u1); free(b2);
     } else {
         const double *f = (level == 0 && C->F) ? C->F + (long long)((k - 1) / C->tm) * C->nt : NULL;
         st = phi_grid(C->P, C->g, dtl, v_in, f, v_out, C->rtol, C->maxit, NULL);
@@ -871,6 +890,23 @@ static void mg_step(mg_ctx *C, int level, int k, const double *v_in, const doubl
     if (st != OR_OK) C->status = st;
     if (gk)
         for (long long j = 0; j < n; ++j) v_out[j] += gk[j];
+}
+
+/* One step of the level-`level` propagator of the MGRIT hierarchy (fine step
+ * dt, coarsening m, coarse kind 0 or 3) on every grid: out = Phi_level(in).
+ * Exposed to pin the coarse propagators against their closed forms.      */
+int or_coarse_step(void *vp, double dt, int m, int level, int coarse_kind, double rtol, const double *in,
+                   double *out)
+{
+    or_problem *P = (or_problem *)vp;
+    if (level < 0 || m < 1 || (coarse_kind != 0 && coarse_kind != 3)) return OR_EINVAL;
+    int worst = OR_OK;
+    for (int g = 0; g < P->G; ++g) {
+        mg_ctx C = {P, g, dt, m, level + 1, rtol, 100000, coarse_kind, NULL, 0, OR_OK, NULL, P->off[P->G], 1};
+        mg_step(&C, level, 1, in + P->off[g], NULL, out + P->off[g]);
+        if (C.status != OR_OK) worst = C.status;
+    }
+    return worst;
 }
 
 /* One two-level FAS cycle on level `level` (Alg. 2 with FCF relaxation),
