@@ -101,10 +101,29 @@ typedef enum { PIT_PREC_FP64 = 0, PIT_PREC_MIXED = 1, PIT_PREC_FP32 = 2, PIT_PRE
 typedef enum {
     PIT_COARSE_IMPLICIT = 0, /* Phi_coarse = backward Euler with dT = m dt (Sec. 3.3.1)  */
     PIT_COARSE_EXACT = 1,    /* Phi_coarse = m fine steps (exact coarse correction)        */
-    PIT_COARSE_LEARNED = 2   /* learned network (not in the paper; see pit_train_coarse); the
+    PIT_COARSE_LEARNED = 2,  /* learned network (not in the paper; see pit_train_coarse); the
                                 implicit step replaces it when it was not accepted, and for
                                 the remaining cycles when a cycle's residual fails to drop
                                 below 0.9 times the previous one or is not finite          */
+    PIT_COARSE_SDIRK2 = 3,   /* not in the paper: every coarse level steps with the two-stage
+                                L-stable SDIRK scheme of order 2 (gamma = 1 - 1/sqrt 2):
+                                (I + gamma dT L) U1 = u_n, (I + gamma dT L) U2 = -sqrt 2 u_n
+                                + (1 + sqrt 2) U1, u_{n+1} = U2.  Two solves per coarse step,
+                                closer to m fine backward-Euler steps than one with dT for
+                                the smooth modes, so MGRIT needs fewer cycles; its fixed
+                                point is still the fine solution.  The coarse solves must be
+                                PIT_PREC_MIXED or PIT_PREC_FP32 (PIT_ERR_UNSUPPORTED
+                                otherwise); not with the residual mode or global MGRIT    */
+    PIT_COARSE_EXTRAP = 4    /* not in the paper: every coarse level steps with the
+                                extrapolated backward Euler 2 BE(dT/2)^2 - BE(dT) (three
+                                solves per coarse step, second order, A-stable).  Its
+                                error against m fine backward-Euler steps is small over the
+                                whole decaying spectrum (smooth modes to second order, stiff
+                                ones damped like 1/(lambda dT)), so MGRIT needs fewer
+                                cycles; its fixed point is still the fine solution.  Heat
+                                operator with PIT_PREC_MIXED coarse solves
+                                (PIT_ERR_UNSUPPORTED otherwise); not with the residual mode
+                                or global MGRIT                                           */
 } pit_coarse;
 
 /* Problem: d-dimensional box [lo, hi], zero Dirichlet values, combination

@@ -382,6 +382,8 @@ struct StepCall {
     const double *guess = nullptr;
     long long gus = 0, gust = 0;
     int inexact = 0;  // fixed-iteration solves (residual mode): the iteration caps are not failures
+    int sdirk = 0;    // two-stage SDIRK steps with stage step dt (coarse propagator PIT_COARSE_SDIRK2)
+    int ext = 0;      // extrapolated backward-Euler steps with half step dt (PIT_COARSE_EXTRAP)
 };
 
 StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, const int *active)
@@ -436,6 +438,8 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.inexact = c.inexact;
     a.precond = o.precond;
     a.predict = o.guess != PIT_GUESS_PREVIOUS;
+    a.sdirk = c.sdirk;
+    a.ext = c.ext;
     a.stats = P->d_stats;
     return a;
 }
@@ -1271,7 +1275,11 @@ struct Mg {
     const double *F = nullptr;
 };
 
-// Coarse propagator of level 1: backward Euler with m dt, or m fine steps.
+// Coarse propagator of level 1: backward Euler with m dt, or m fine steps;
+// of every coarse level with PIT_COARSE_SDIRK2: two-stage SDIRK steps of
+// dT = m^level dt (the kernel takes the stage step gamma dT); with
+// PIT_COARSE_EXTRAP: extrapolated backward-Euler steps of dT (the kernel
+// takes the half step dT / 2).
 void coarse_call(Mg &M, StepCall &c, int level)
 {
     if (level == 1 && M.o->coarse == PIT_COARSE_EXACT) {
@@ -1281,6 +1289,13 @@ void coarse_call(Mg &M, StepCall &c, int level)
         double dtl = M.dt;
         for (int q = 0; q < level; ++q) dtl *= M.o->m;
         c.dt = dtl;
+        if (M.o->coarse == PIT_COARSE_SDIRK2) {
+            c.dt = (1.0 - 1.0 / std::sqrt(2.0)) * dtl;
+            c.sdirk = 1;
+        } else if (M.o->coarse == PIT_COARSE_EXTRAP) {
+            c.dt = 0.5 * dtl;
+            c.ext = 1;
+        }
     }
 }
 
@@ -1685,8 +1700,15 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     if (o->m < 2 || o->levels < 2 || o->levels > 3 || o->nsteps < 1 || o->maxit < 1 || !(o->tol >= 0.0) ||
         !(o->t1 > o->t0))
         return fail(PIT_ERR_INVALID_ARG, "need m >= 2, levels in {2,3}, nsteps >= 1, maxit >= 1, tol >= 0, t1 > t0");
-    if (o->coarse != PIT_COARSE_IMPLICIT && o->coarse != PIT_COARSE_EXACT && o->coarse != PIT_COARSE_LEARNED)
+    if (o->coarse != PIT_COARSE_IMPLICIT && o->coarse != PIT_COARSE_EXACT && o->coarse != PIT_COARSE_LEARNED &&
+        o->coarse != PIT_COARSE_SDIRK2 && o->coarse != PIT_COARSE_EXTRAP)
         return fail(PIT_ERR_INVALID_ARG, "unknown coarse propagator %d", o->coarse);
+    if (o->coarse == PIT_COARSE_EXTRAP && (o->crs.prec != PIT_PREC_MIXED || P->desc.op != PIT_OP_HEAT))
+        return fail(PIT_ERR_UNSUPPORTED, "the extrapolated coarse propagator is built for the heat operator with "
+                                         "PIT_PREC_MIXED coarse solves");
+    if (o->coarse == PIT_COARSE_SDIRK2 && o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32)
+        return fail(PIT_ERR_UNSUPPORTED, "the SDIRK coarse propagator needs PIT_PREC_MIXED or PIT_PREC_FP32 coarse "
+                                         "solves");
     if (o->coarse == PIT_COARSE_LEARNED && !P->have_net)
         return fail(PIT_ERR_INVALID_ARG, "the learned coarse propagator has no parameters (pit_train_coarse or "
                                          "pit_net_set_params)");

@@ -147,6 +147,8 @@ struct StepArgs {
     int inexact;             // 1: a solve stopped by its iteration caps is not a failure
     int precond;             // pit_precond of the Krylov solves
     int predict;             // MIXED without forcing: extrapolated initial guess 2 x_s - x_{s-1}
+    int sdirk;               // MIXED or SINGLE: every step is a two-stage SDIRK step, dt its stage step
+    int ext;                 // MIXED heat: every step is an extrapolated backward-Euler step, dt its half step
     DevStats *stats;
 };
 

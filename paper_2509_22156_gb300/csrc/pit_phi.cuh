@@ -1208,7 +1208,19 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     };
 
     int status = PIT_OK, iters = 0, passes = 0;
-    const bool carry_ok = (f0 == nullptr) && (a.g == nullptr) && (a.guess == nullptr);
+    const bool carry_ok = (f0 == nullptr) && (a.g == nullptr) && (a.guess == nullptr) && !a.sdirk && !a.ext;
+    // Two-stage SDIRK steps (a.sdirk, coarse propagators; dt is the stage
+    // step gamma dT, gamma = 1 - 1/sqrt 2): stage 1 solves (I + dt L) U1 = u_n,
+    // stage 2 (I + dt L) U2 = (1 - beta) u_n + beta U1 with beta =
+    // (1 - gamma) / gamma = 1 + sqrt 2, and u_{n+1} = U2 (L-stable, second
+    // order; see the MGRIT options of the interface)
+    // Extrapolated backward-Euler steps (a.ext, coarse propagators, MIXED
+    // heat; dt is the half step dT/2): U1 and U2 by two half steps from u_n,
+    // U3 by one full step (I + 2 dt L) U3 = u_n, u_{n+1} = 2 U2 - U3; u_n and
+    // then U2 wait in the carried-residual array, which these steps leave
+    // unused.
+    const int nstage = a.sdirk ? 2 : a.ext ? 3 : 1;
+    constexpr double SD_BETA = 2.4142135623730950488, SD_ALPHA = -1.4142135623730950488;
     // MIXED: carried initial residual of the next step (see the file comment).
     // FP32 copies of FP64 vectors are scaled by a power of two 2^k chosen from
     // ||b|| (exact, folded into the conversion), so they stay inside the normal
@@ -1265,8 +1277,23 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             float *xs = f32, *r = f32 + ld, *q1 = f32 + 2 * ld, *q2 = f32 + 3 * ld, *q3 = f32 + 4 * ld,
                   *q4 = f32 + 5 * ld;
             const float dtf = (float)dt;
+          for (int stage = 0; stage < nstage; ++stage) {
             float bb[1] = {0.0f};
-            if (a.guess) {
+            if (stage == 1) {
+                // second stage: b = (1 - beta) u_n + beta U1 with u_n = A U1
+                // (the first stage's equation, met to its tolerance), so
+                // b = beta U1 - sqrt 2 A U1 from U1 (in xs) alone, and
+                // r = b - A U1 = beta (U1 - A U1)
+                for (int j = tid; j < n; j += nt) {
+                    float Ax;
+                    if constexpr (OP == PIT_OP_HEAT) Ax = HT(xs, j);
+                    else Ax = T32(xs, j);
+                    const float xj = xs[j];
+                    const float bj = (float)SD_BETA * xj + (float)SD_ALPHA * Ax;
+                    r[j] = (float)SD_BETA * (xj - Ax);
+                    bb[0] += bj * bj;
+                }
+            } else if (a.guess) {
                 const long long sb0 = (long long)(step - 1);
                 const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
                 const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
@@ -1316,9 +1343,10 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             else k = cg_core<float, float>(T32, n, xs, r, q1, q2, q3, R32, stop2, a.maxit, st);
             iters += k;
             if (st > status) status = st;
+            __syncthreads();  // xs complete
+          }
             // forcing of this step and the stored outputs (FP64, own nodes only)
             const long long sb = (long long)(step - 1);
-            __syncthreads();  // xs complete
             if (a.g) {
                 const double *gs = a.g + (long long)b * a.g_stride + sb * a.g_step + GI.off;
                 for (int j = tid; j < n; j += nt) xs[j] += to_f32(gs[j], ks);
@@ -1515,6 +1543,26 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             continue;
         } else {
             float *e = f32;
+            const bool use_pc0 = use_pc;
+            const double diag64h = H64.diag;
+            const T diagTh = HT.diag;
+#pragma unroll 1
+          for (int stage = 0; stage < nstage; ++stage) {
+            if constexpr (OP == PIT_OP_HEAT) {
+                if (a.ext && stage == 2) {
+                    // the full step: I + 2 dt L (off-diagonal entries doubled
+                    // exactly, diagonal 2 diag - 1), without the line
+                    // preconditioner, whose factors are those of the half step
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        H64.off[i] *= 2.0;
+                        HT.off[i] *= (T)2;
+                    }
+                    H64.diag = 2.0 * H64.diag - 1.0;
+                    HT.diag = (T)H64.diag;
+                    use_pc = false;
+                }
+            }
             double rn2, bb;
             int kr;  // the stored FP32 residual rv holds r 2^kr
             if (have_r0) {
@@ -1557,17 +1605,37 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 kr = kq;
                 have_c = true;
             } else {
-                // right-hand side b = x_{s-1} + dt f; optional initial guess
-                if (a.guess) {
+                // right-hand side b = x_{s-1} + dt f; optional initial guess;
+                // second SDIRK stage: b = (1 - beta) u_n + beta U1 (b holds u_n,
+                // x holds U1, the stage's initial iterate)
+                // (extrapolated steps: u_n saved at stage 0; stage 1 from U1;
+                // stage 2 from u_n, with U2 moved to the saved place)
+                if (stage > 0 && !a.ext) {
+                    for (int j = tid; j < n; j += nt) bvec[j] = SD_ALPHA * bvec[j] + SD_BETA * x[j];
+                } else if (stage == 1) {
+                    for (int j = tid; j < n; j += nt) bvec[j] = x[j];
+                } else if (stage == 2) {
+                    for (int j = tid; j < n; j += nt) {
+                        const double un = cvec[j];
+                        cvec[j] = x[j];
+                        bvec[j] = un;
+                    }
+                } else if (a.guess) {
                     const long long sb0 = (long long)(step - 1);
                     const double *gu = a.guess + (long long)b * a.guess_stride + sb0 * a.guess_step + GI.off;
                     const double *gf = a.g ? a.g + (long long)b * a.g_stride + sb0 * a.g_step + GI.off : nullptr;
                     for (int j = tid; j < n; j += nt) {
-                        bvec[j] = f ? x[j] + dt * f[j] : x[j];
+                        const double bj = f ? x[j] + dt * f[j] : x[j];
+                        bvec[j] = bj;
+                        if (a.ext) cvec[j] = bj;
                         x[j] = gf ? gu[j] - gf[j] : gu[j];
                     }
                 } else {
-                    for (int j = tid; j < n; j += nt) bvec[j] = f ? x[j] + dt * f[j] : x[j];
+                    for (int j = tid; j < n; j += nt) {
+                        const double bj = f ? x[j] + dt * f[j] : x[j];
+                        bvec[j] = bj;
+                        if (a.ext) cvec[j] = bj;
+                    }
                 }
                 double acc[1] = {0.0};
                 for (int j = tid; j < n; j += nt) acc[0] += bvec[j] * bvec[j];
@@ -1668,6 +1736,22 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             // the unchanged initial residual when pass 0 met the tolerance)
             have_r0 = carry_ok && st_step == PIT_OK && step < a.nsteps;
             kr_c = kr;
+          }
+            if constexpr (OP == PIT_OP_HEAT) {
+                if (a.ext) {
+                    // back to the half step; u_{n+1} = 2 U2 - U3 (the last
+                    // reduction ordered every read of the stage's x)
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        H64.off[i] *= 0.5;
+                        HT.off[i] *= (T)0.5;
+                    }
+                    H64.diag = diag64h;
+                    HT.diag = diagTh;
+                    use_pc = use_pc0;
+                    for (int j = tid; j < n; j += nt) x[j] = 2.0 * cvec[j] - x[j];
+                }
+            }
         }
         // forcing of this step and the stored outputs (own nodes only)
         const long long sb = (long long)(step - 1);
