@@ -1209,6 +1209,11 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
 
     int status = PIT_OK, iters = 0, passes = 0;
     const bool carry_ok = (f0 == nullptr) && (a.g == nullptr) && (a.guess == nullptr) && !a.sdirk && !a.ext;
+    // MIXED also carries its residual across an additive forcing g (x_s <- x_s
+    // + g_s after the solve): with b_{s+1} = x_s + g_s and the guess x_s (the
+    // solve's result before g), r0 = b_{s+1} - A x_s = r_s + (x_s + g_s - b_s),
+    // again without a stencil pass (no extrapolation then)
+    const bool carry_g = (f0 == nullptr) && (a.guess == nullptr) && !a.sdirk && !a.ext;
     // Two-stage SDIRK steps (a.sdirk, coarse propagators; dt is the stage
     // step gamma dT, gamma = 1 - 1/sqrt 2): stage 1 solves (I + dt L) U1 = u_n,
     // stage 2 (I + dt L) U2 = (1 - beta) u_n + beta U1 with beta =
@@ -1578,6 +1583,9 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 // against dt lambda |x| for the guess x_s).
                 const int kq = kr_c;
                 const bool pred = a.predict && have_c;
+                // additive forcing of the previous step (x holds x_s + g_s)
+                const double *gp =
+                    a.g ? a.g + (long long)b * a.g_stride + (long long)(step - 2) * a.g_step + GI.off : nullptr;
                 float acc[2] = {0.0f, 0.0f};
 #pragma unroll 4
                 for (int j = tid; j < n; j += nt) {
@@ -1591,8 +1599,9 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                         x[j] = xs + d;
                     } else {
                         r0 = to_f32_rn(cn, kq);
+                        if (gp) x[j] = xs - gp[j];
                     }
-                    cvec[j] = cn;
+                    if (!gp) cvec[j] = cn;
                     bvec[j] = xs;
                     rv[j] = r0;
                     const float xf = to_f32(xs, kq);
@@ -1603,7 +1612,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 rn2 = to_f64(acc[0], -2 * kq);
                 bb = to_f64(acc[1], -2 * kq);
                 kr = kq;
-                have_c = true;
+                have_c = (gp == nullptr);
             } else {
                 // right-hand side b = x_{s-1} + dt f; optional initial guess;
                 // second SDIRK stage: b = (1 - beta) u_n + beta U1 (b holds u_n,
@@ -1734,7 +1743,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             if (st_step > status) status = st_step;
             // rv holds the FP64 residual of the final x (from its check, or
             // the unchanged initial residual when pass 0 met the tolerance)
-            have_r0 = carry_ok && st_step == PIT_OK && step < a.nsteps;
+            have_r0 = carry_g && st_step == PIT_OK && step < a.nsteps;
             kr_c = kr;
           }
             if constexpr (OP == PIT_OP_HEAT) {
