@@ -272,7 +272,11 @@ typedef struct {
                              other forms run as one lane                                    */
     int init;             /* initial guess: 0 = u0 at every time point; 1 = one sweep of the
                              level-1 coarse propagator from u0 over the C-points (the paper
-                             leaves the initial guess open; the fixed point is the same)   */
+                             leaves the initial guess open; the fixed point is the same);
+                             2 = that sweep with the extrapolated backward Euler of
+                             PIT_COARSE_EXTRAP while the cycles keep `coarse` (heat
+                             operator, PIT_PREC_MIXED coarse solves, implicit coarse
+                             propagators; PIT_ERR_UNSUPPORTED otherwise)                    */
     int recomb;           /* recombination steps s of Alg. 3 (Sec. 2.2.1): 0 = none (one MGRIT
                              solve over [t0, t1], combined afterwards by pit_combine); s >= 1:
                              [t0, t1] is split at tau_k = t0 + k (t1 - t0) / s, and before each

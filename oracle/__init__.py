@@ -246,7 +246,8 @@ class Problem:
         """Returns (uT, cycles per grid, residual history G x maxit, status);
         with `grids`, only those grids are computed.  relax: "FCF" (Sec. 4.1)
         or "F" (F-relaxation on the finest level).  init: start from one sweep
-        of the level-1 propagator over the C-points instead of u0 everywhere."""
+        of the level-1 propagator over the C-points instead of u0 everywhere
+        (2: that sweep with the extrapolated backward Euler, coarse kind 4)."""
         if relax not in ("FCF", "F"):
             raise ValueError("relax must be 'FCF' or 'F'")
         u0 = _f64(u0)
@@ -259,7 +260,7 @@ class Problem:
         tm = self._tmul(tmul)
         st = lib().or_mgrit(self._h, _p(u0), dt, nsteps, m, levels, tol, maxit, coarse_kind,
                             _p(th), rtol, krylov_maxit, _p(out), _p(its), _p(hist), _p(gm),
-                            1 if relax == "F" else 0, 1 if init else 0, _p(F), _p(tm))
+                            1 if relax == "F" else 0, int(init), _p(F), _p(tm))
         if check and st != 0:
             raise RuntimeError(f"oracle mgrit: {STATUS.get(st, st)}")
         return out, its, hist, st

@@ -997,7 +997,8 @@ int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev,
              int maxit, int coarse_kind, const double *theta, double rtol, int krylov_maxit,
              double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */,
              int relax_f /* 1: F-relaxation on the finest level instead of FCF */,
-             int init /* 1: initial C-points from one sweep of the level-1 propagator */,
+             int init /* 1: initial C-points from one sweep of the level-1 propagator;
+                         2: that sweep with the extrapolated backward Euler */,
              const double *F /* forcing f_n, n = 1..nsteps, packed like states, or NULL */,
              const int *tmul /* per grid steps per common step (own time partition), or NULL */)
 {
@@ -1022,8 +1023,13 @@ int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev,
         if (init) {
             /* initial guess at the C-points: u_{jm} = Phi_c(u_{(j-1)m}); the
              * F-points follow from the first relaxation */
+            /* init = 2: this sweep with the extrapolated backward Euler
+             * (coarse kind 4); the cycles keep their coarse propagator */
+            const int ck = C.coarse_kind;
+            if (init == 2) C.coarse_kind = 4;
             for (int j = 1; j <= Ng / m0; ++j)
                 mg_step(&C, 1, 0, v + (long long)(j - 1) * m0 * n, NULL, v + (long long)j * m0 * n);
+            C.coarse_kind = ck;
         }
         int it = 0, conv = 0;
         while (it < maxit) {

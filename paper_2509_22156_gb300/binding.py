@@ -201,8 +201,9 @@ def mgrit_opts(t0, t1, nsteps, m, levels=2, tol=1e-8, maxit=64, coarse=PIT_COARS
         t = np.ascontiguousarray(tmul, dtype=np.int32)
         keep.append(t)
         tptr = t.ctypes.data
+    init = int(init)  # False/True or 0, 1, 2 (2: extrapolated initial sweep)
     o = pit_mgrit_opts(t0, t1, nsteps, m, levels, tol, maxit, coarse, 1 if fas else 0, fine, crs, relax, lanes,
-                       1 if init else 0, recomb, fptr, tptr, global_every, 1 if residual else 0)
+                       init, recomb, fptr, tptr, global_every, 1 if residual else 0)
     o._keep = keep
     return o
 

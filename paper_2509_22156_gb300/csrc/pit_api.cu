@@ -1720,7 +1720,11 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     if (o->relax != PIT_RELAX_FCF && o->relax != PIT_RELAX_F)
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
-    if (o->init != 0 && o->init != 1) return fail(PIT_ERR_INVALID_ARG, "init must be 0 or 1");
+    if (o->init < 0 || o->init > 2) return fail(PIT_ERR_INVALID_ARG, "init must be 0, 1 or 2");
+    if (o->init == 2 && (o->crs.prec != PIT_PREC_MIXED || P->desc.op != PIT_OP_HEAT || o->coarse == PIT_COARSE_EXACT ||
+                         o->coarse == PIT_COARSE_LEARNED))
+        return fail(PIT_ERR_UNSUPPORTED, "the extrapolated initial sweep is built for the heat operator with "
+                                         "PIT_PREC_MIXED coarse solves and an implicit coarse propagator");
     if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
     if (o->residual != 0 && o->residual != 1) return fail(PIT_ERR_INVALID_ARG, "residual must be 0 or 1");
     if (o->residual && (o->levels != 2 || o->relax != PIT_RELAX_F || o->fas || o->coarse != PIT_COARSE_IMPLICIT ||
@@ -1817,7 +1821,15 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
             sw.osst = nt;
             sw.out_last = U + (long long)Nc * nt;
             sw.ols = nt;
-            TRY(run_coarse(M, sw, 1));
+            // init 2: this sweep alone with the extrapolated backward Euler
+            // (a closer initial guess; the cycles keep the coarse propagator)
+            pit_mgrit_opts o_init = *o;
+            if (o->init == 2) o_init.coarse = PIT_COARSE_EXTRAP;
+            const pit_mgrit_opts *o_cyc = M.o;
+            M.o = &o_init;
+            const pit_status st_init = run_coarse(M, sw, 1);
+            M.o = o_cyc;
+            TRY(st_init);
         }
     }
     // lanes: the correction form with the implicit coarse step for the whole

@@ -135,3 +135,31 @@ def test_higher_order_coarse_rejects_unsupported_forms():
     opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=1e-8, maxit=10, coarse=B.PIT_COARSE_EXTRAP, crs=so)
     with pytest.raises(B.PitError, match="UNSUPPORTED"):
         P.mgrit_solve(cuda(u0), opts, torch.empty(P.n_total, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("name", ["w2_small", "w2_3lev", "w5_small"])
+def test_extrapolated_initial_sweep_matches_oracle(name):
+    """init = 2: the initial sweep with the extrapolated step, the cycles with
+    the coarse backward Euler; against the oracle's MGRIT with the same start."""
+    wl, P, O, u0, N, m, lev = setup(name)
+    tol = 1e-10 * np.abs(u0).max()
+    so = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-13, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, coarse=B.PIT_COARSE_IMPLICIT, fine=so, crs=so,
+                        relax=B.PIT_RELAX_F, init=2)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    dt = (wl.t1 - wl.t0) / N
+    ref, its, hist, _ = O.mgrit(u0, dt, N, m, lev, tol=tol, maxit=60, coarse_kind=0, rtol=1e-15, relax="F", init=2)
+    assert st.n_converged == P.G
+    assert rel(host(uT), ref) < 1e-9
+    assert abs(st.max_cycles - int(its.max())) <= 1
+    assert st.res_hist[0] < 1.5 * float(np.nanmax(hist[:, 0])) + 1e-300
+
+
+def test_extrapolated_initial_sweep_rejects_unsupported_forms():
+    wl, P, O, u0, N, m, lev = setup("w2_small")
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=50000)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=1e-8, maxit=10, crs=crs, init=2)
+    with pytest.raises(B.PitError, match="UNSUPPORTED"):
+        P.mgrit_solve(cuda(u0), opts, uT)

@@ -141,3 +141,20 @@ def test_mgrit_with_higher_order_coarse_needs_fewer_cycles_on_smooth_heat_data()
                              rtol=1e-12, relax="F", init=True)
         cyc[kind] = int(its.max())
     assert cyc[3] < cyc[0] and cyc[4] < cyc[0], cyc
+
+
+def test_extrapolated_initial_sweep_lowers_every_residual_and_keeps_the_fixed_point():
+    """init = 2: the initial coarse sweep with the extrapolated step, the cycles
+    with the coarse backward Euler: the same fixed point, and on smooth heat
+    data a first residual an order of magnitude below the plain sweep's."""
+    wl = W.workload(2)
+    P = oracle.Problem(wl.d, 6, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = P.initial(wl.ic_kind, wl.ic_params)
+    seq = P.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14)
+    res = {}
+    for init in (1, 2):
+        uT, its, hist, _ = P.mgrit(u0, wl.dt, wl.nsteps, wl.m, 2, tol=1e-12, maxit=40, coarse_kind=0, rtol=1e-14,
+                                   relax="F", init=init)
+        np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-10)
+        res[init] = np.nanmax(hist[:, 0])
+    assert res[2] < 0.2 * res[1], res
