@@ -275,8 +275,9 @@ typedef struct {
                              leaves the initial guess open; the fixed point is the same);
                              2 = that sweep with the extrapolated backward Euler of
                              PIT_COARSE_EXTRAP while the cycles keep `coarse` (heat
-                             operator, PIT_PREC_MIXED coarse solves, implicit coarse
-                             propagators; PIT_ERR_UNSUPPORTED otherwise)                    */
+                             operator, PIT_PREC_MIXED coarse solves, any coarse
+                             propagator but PIT_COARSE_EXACT; PIT_ERR_UNSUPPORTED
+                             otherwise)                                                     */
     int recomb;           /* recombination steps s of Alg. 3 (Sec. 2.2.1): 0 = none (one MGRIT
                              solve over [t0, t1], combined afterwards by pit_combine); s >= 1:
                              [t0, t1] is split at tau_k = t0 + k (t1 - t0) / s, and before each

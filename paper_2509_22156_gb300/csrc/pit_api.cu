@@ -1721,10 +1721,9 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     if (o->init < 0 || o->init > 2) return fail(PIT_ERR_INVALID_ARG, "init must be 0, 1 or 2");
-    if (o->init == 2 && (o->crs.prec != PIT_PREC_MIXED || P->desc.op != PIT_OP_HEAT || o->coarse == PIT_COARSE_EXACT ||
-                         o->coarse == PIT_COARSE_LEARNED))
+    if (o->init == 2 && (o->crs.prec != PIT_PREC_MIXED || P->desc.op != PIT_OP_HEAT || o->coarse == PIT_COARSE_EXACT))
         return fail(PIT_ERR_UNSUPPORTED, "the extrapolated initial sweep is built for the heat operator with "
-                                         "PIT_PREC_MIXED coarse solves and an implicit coarse propagator");
+                                         "PIT_PREC_MIXED coarse solves, without the exact coarse propagator");
     if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
     if (o->residual != 0 && o->residual != 1) return fail(PIT_ERR_INVALID_ARG, "residual must be 0 or 1");
     if (o->residual && (o->levels != 2 || o->relax != PIT_RELAX_F || o->fas || o->coarse != PIT_COARSE_IMPLICIT ||
@@ -1823,12 +1822,18 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
             sw.ols = nt;
             // init 2: this sweep alone with the extrapolated backward Euler
             // (a closer initial guess; the cycles keep the coarse propagator)
+            // (also when the cycles use the learned propagator)
             pit_mgrit_opts o_init = *o;
-            if (o->init == 2) o_init.coarse = PIT_COARSE_EXTRAP;
+            const bool learned_cyc = M.learned;
+            if (o->init == 2) {
+                o_init.coarse = PIT_COARSE_EXTRAP;
+                M.learned = false;
+            }
             const pit_mgrit_opts *o_cyc = M.o;
             M.o = &o_init;
             const pit_status st_init = run_coarse(M, sw, 1);
             M.o = o_cyc;
+            M.learned = learned_cyc;
             TRY(st_init);
         }
     }
