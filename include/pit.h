@@ -121,9 +121,11 @@ typedef enum {
                                 whole decaying spectrum (smooth modes to second order, stiff
                                 ones damped like 1/(lambda dT)), so MGRIT needs fewer
                                 cycles; its fixed point is still the fine solution.  Heat
-                                operator with PIT_PREC_MIXED coarse solves
-                                (PIT_ERR_UNSUPPORTED otherwise); not with the residual mode
-                                or global MGRIT                                           */
+                                operator with PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves
+                                (PIT_ERR_UNSUPPORTED otherwise; the FP32 form keeps u_n and
+                                the second half step's result in a library-owned global
+                                slab of n_batch x n_total floats); not with the residual
+                                mode or global MGRIT                                      */
 } pit_coarse;
 
 /* Problem: d-dimensional box [lo, hi], zero Dirichlet values, combination
@@ -275,9 +277,9 @@ typedef struct {
                              leaves the initial guess open; the fixed point is the same);
                              2 = that sweep with the extrapolated backward Euler of
                              PIT_COARSE_EXTRAP while the cycles keep `coarse` (heat
-                             operator, PIT_PREC_MIXED coarse solves, any coarse
-                             propagator but PIT_COARSE_EXACT; PIT_ERR_UNSUPPORTED
-                             otherwise)                                                     */
+                             operator, PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves,
+                             any coarse propagator but PIT_COARSE_EXACT;
+                             PIT_ERR_UNSUPPORTED otherwise)                                 */
     int recomb;           /* recombination steps s of Alg. 3 (Sec. 2.2.1): 0 = none (one MGRIT
                              solve over [t0, t1], combined afterwards by pit_combine); s >= 1:
                              [t0, t1] is split at tau_k = t0 + k (t1 - t0) / s, and before each

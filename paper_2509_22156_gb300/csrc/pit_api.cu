@@ -151,6 +151,7 @@ struct pit_problem {
     cudaStream_t sides[NPART - 1] = {};  // streams of the launch parts beside the first
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf w_xg;                       // FP64 state of class-1 items
+    DBuf w_scr;                      // FP32 scratch of extrapolated steps in the FP32 form
     std::vector<pit_lane> lanes;     // MGRIT lanes (built on first use)
     std::vector<int> lane_assign;    // grid -> lane when given explicitly; empty: balanced
     // workspaces
@@ -440,6 +441,9 @@ StepArgs make_args(pit_problem *P, const pit_solve_opts &o, const StepCall &c, c
     a.predict = o.guess != PIT_GUESS_PREVIOUS;
     a.sdirk = c.sdirk;
     a.ext = c.ext;
+    // (the FP32 form's extrapolated steps keep u_n and U2 in a global slab per
+    // item; run_steps and lanes_prime size it before any such launch)
+    a.scr = (c.ext && prec_form(o.prec) == SINGLE) ? (float *)P->w_scr.p : nullptr;
     a.stats = P->d_stats;
     return a;
 }
@@ -561,6 +565,9 @@ pit_status run_steps(pit_problem *P, const pit_solve_opts &o, const StepCall &c,
     // (a lane's workspaces and CTA sizes are prepared before its first launch)
     if (v[NBKT].n > 0 && !L)
         CU(P->w_xg.ensure(sizeof(double) * P->ntot * (size_t)c.nb * xg_slabs(prec, P->desc.op, P->desc.d)));
+    if (c.ext && prec == SINGLE && !L) CU(P->w_scr.ensure(sizeof(float) * P->ntot * (size_t)c.nb));
+    if (c.ext && prec == SINGLE && P->w_scr.bytes < sizeof(float) * P->ntot * (size_t)c.nb)
+        return fail(PIT_ERR_INVALID_ARG, "extrapolated FP32 steps without their scratch");
     if (!L)
         for (int q = 0; q < NPART; ++q) TRY(tune(P, prec, wide, q, o, c, active));
     cudaStream_t st[NPART];
@@ -916,7 +923,7 @@ pit_status pit_problem_destroy(pit_problem_t P)
                     &P->m_UT,     &P->m_GC,   &P->m_res, &P->m_UT1,   &P->m_GC1,  &P->m_T0,    &P->m_act,
                     &P->w_tune,   &P->n_master, &P->n_m, &P->n_v,     &P->n_w,    &P->n_rows,  &P->n_loss,
                     &P->n_act,    &P->n_items, &P->n_U,  &P->n_Y,     &P->n_grad, &P->n_tmp,   &P->n_prm,
-                    &P->w_xg,     &P->m_Z,     &P->m_E,   &P->w_part};
+                    &P->w_xg,     &P->m_Z,     &P->m_E,   &P->w_part, &P->w_scr};
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
     delete P;
@@ -1683,6 +1690,8 @@ pit_status lanes_prime(Mg &M, int Nc)
         c.in = P->m_U.d();  // u0 at every C-point
         c.is = nt;
         if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op, P->desc.d)));
+        if (prec == SINGLE && (o->coarse == PIT_COARSE_EXTRAP || o->init == 2))
+            CU(P->w_scr.ensure(sizeof(float) * nt * (size_t)Nc));
         for (int part = 0; part < NPART; ++part) TRY(tune(P, prec, c.nb >= 8, part, *reps[r].so, c, M.active));
     }
     return PIT_OK;
@@ -1703,9 +1712,10 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     if (o->coarse != PIT_COARSE_IMPLICIT && o->coarse != PIT_COARSE_EXACT && o->coarse != PIT_COARSE_LEARNED &&
         o->coarse != PIT_COARSE_SDIRK2 && o->coarse != PIT_COARSE_EXTRAP)
         return fail(PIT_ERR_INVALID_ARG, "unknown coarse propagator %d", o->coarse);
-    if (o->coarse == PIT_COARSE_EXTRAP && (o->crs.prec != PIT_PREC_MIXED || P->desc.op != PIT_OP_HEAT))
+    if (o->coarse == PIT_COARSE_EXTRAP &&
+        ((o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32) || P->desc.op != PIT_OP_HEAT))
         return fail(PIT_ERR_UNSUPPORTED, "the extrapolated coarse propagator is built for the heat operator with "
-                                         "PIT_PREC_MIXED coarse solves");
+                                         "PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves");
     if (o->coarse == PIT_COARSE_SDIRK2 && o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32)
         return fail(PIT_ERR_UNSUPPORTED, "the SDIRK coarse propagator needs PIT_PREC_MIXED or PIT_PREC_FP32 coarse "
                                          "solves");
@@ -1721,9 +1731,11 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     if (o->init < 0 || o->init > 2) return fail(PIT_ERR_INVALID_ARG, "init must be 0, 1 or 2");
-    if (o->init == 2 && (o->crs.prec != PIT_PREC_MIXED || P->desc.op != PIT_OP_HEAT || o->coarse == PIT_COARSE_EXACT))
+    if (o->init == 2 && ((o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32) ||
+                         P->desc.op != PIT_OP_HEAT || o->coarse == PIT_COARSE_EXACT))
         return fail(PIT_ERR_UNSUPPORTED, "the extrapolated initial sweep is built for the heat operator with "
-                                         "PIT_PREC_MIXED coarse solves, without the exact coarse propagator");
+                                         "PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves, without the exact coarse "
+                                         "propagator");
     if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
     if (o->residual != 0 && o->residual != 1) return fail(PIT_ERR_INVALID_ARG, "residual must be 0 or 1");
     if (o->residual && (o->levels != 2 || o->relax != PIT_RELAX_F || o->fas || o->coarse != PIT_COARSE_IMPLICIT ||

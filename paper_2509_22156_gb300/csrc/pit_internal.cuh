@@ -148,7 +148,8 @@ struct StepArgs {
     int precond;             // pit_precond of the Krylov solves
     int predict;             // MIXED without forcing: extrapolated initial guess 2 x_s - x_{s-1}
     int sdirk;               // MIXED or SINGLE: every step is a two-stage SDIRK step, dt its stage step
-    int ext;                 // MIXED heat: every step is an extrapolated backward-Euler step, dt its half step
+    int ext;                 // heat, MIXED or SINGLE: every step is an extrapolated backward-Euler step, dt its half step
+    float *scr;              // SINGLE extrapolated steps: n_batch x n_total FP32 scratch (u_n, then U2)
     DevStats *stats;
 };
 

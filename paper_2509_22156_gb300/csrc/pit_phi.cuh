@@ -1282,9 +1282,44 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             float *xs = f32, *r = f32 + ld, *q1 = f32 + 2 * ld, *q2 = f32 + 3 * ld, *q3 = f32 + 4 * ld,
                   *q4 = f32 + 5 * ld;
             const float dtf = (float)dt;
+            // extrapolated steps: u_n, then U2, wait in the item's global scratch
+            float *scr = a.scr ? a.scr + (long long)b * a.n_total + GI.off : nullptr;
+            const bool use_pc0 = use_pc;
+            const T diagTh = HT.diag;
+#pragma unroll 1
           for (int stage = 0; stage < nstage; ++stage) {
+            if constexpr (OP == PIT_OP_HEAT) {
+                if (a.ext && stage == 2) {
+                    // the full step I + 2 dt L, without the line preconditioner
+#pragma unroll
+                    for (int i = 0; i < D; ++i) HT.off[i] *= (T)2;
+                    HT.diag = (T)(2.0 * H64.diag - 1.0);
+                    use_pc = false;
+                }
+            }
             float bb[1] = {0.0f};
-            if (stage == 1) {
+            if (stage == 1 && a.ext) {
+                // second half step from U1 (in xs): b = U1
+                for (int j = tid; j < n; j += nt) {
+                    float Ax;
+                    if constexpr (OP == PIT_OP_HEAT) Ax = HT(xs, j);
+                    else Ax = T32(xs, j);
+                    const float xj = xs[j];
+                    r[j] = xj - Ax;
+                    bb[0] += xj * xj;
+                }
+            } else if (stage == 2) {
+                // full step from u_n, started from U2, which takes u_n's place
+                for (int j = tid; j < n; j += nt) {
+                    float Ax;
+                    if constexpr (OP == PIT_OP_HEAT) Ax = HT(xs, j);
+                    else Ax = T32(xs, j);
+                    const float un = scr[j];
+                    scr[j] = xs[j];
+                    r[j] = un - Ax;
+                    bb[0] += un * un;
+                }
+            } else if (stage == 1) {
                 // second stage: b = (1 - beta) u_n + beta U1 with u_n = A U1
                 // (the first stage's equation, met to its tolerance), so
                 // b = beta U1 - sqrt 2 A U1 from U1 (in xs) alone, and
@@ -1305,6 +1340,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 for (int j = tid; j < n; j += nt) {
                     const float bj = f ? xs[j] + dtf * to_f32(f[j], ks) : xs[j];
                     r[j] = bj;
+                    if (a.ext) scr[j] = bj;
                     bb[0] += bj * bj;
                     xs[j] = to_f32(gf ? gu[j] - gf[j] : gu[j], ks);
                 }
@@ -1320,6 +1356,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                     if constexpr (OP == PIT_OP_HEAT) Ax = HT(xs, j);
                     else Ax = T32(xs, j);
                     r[j] = bj - Ax;
+                    if (a.ext) scr[j] = bj;
                     bb[0] += bj * bj;
                 }
             }
@@ -1333,6 +1370,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
                 for (int j = tid; j < n; j += nt) {
                     xs[j] *= sc;
                     r[j] *= sc;
+                    if (a.ext) scr[j] *= sc;  // u_n or U2, in the same scale
                 }
                 bb[0] = (bb[0] * sc) * sc;
                 ks += kq;
@@ -1350,6 +1388,16 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             if (st > status) status = st;
             __syncthreads();  // xs complete
           }
+            if constexpr (OP == PIT_OP_HEAT) {
+                if (a.ext) {
+                    // back to the half step; u_{n+1} = 2 U2 - U3
+#pragma unroll
+                    for (int i = 0; i < D; ++i) HT.off[i] *= (T)0.5;
+                    HT.diag = diagTh;
+                    use_pc = use_pc0;
+                    for (int j = tid; j < n; j += nt) xs[j] = 2.0f * scr[j] - xs[j];
+                }
+            }
             // forcing of this step and the stored outputs (FP64, own nodes only)
             const long long sb = (long long)(step - 1);
             if (a.g) {

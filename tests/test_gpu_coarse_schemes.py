@@ -88,14 +88,17 @@ def test_higher_order_coarse_mgrit_matches_oracle(name, coarse, relax):
     assert rel(got, O.sequential(u0, dt, N, rtol=1e-15)) < 1e-7
 
 
-@pytest.mark.parametrize("name", ["w2_small", "w3_small", "w4_small"])
-def test_sdirk_coarse_with_fp32_coarse_solves_reaches_the_sequential_solution(name):
+@pytest.mark.parametrize("name,coarse,init", [("w2_small", B.PIT_COARSE_SDIRK2, 1), ("w3_small", B.PIT_COARSE_SDIRK2, 1),
+                                              ("w4_small", B.PIT_COARSE_SDIRK2, 1), ("w2_small", B.PIT_COARSE_EXTRAP, 1),
+                                              ("w2_small", B.PIT_COARSE_IMPLICIT, 2),
+                                              ("w2_3lev", B.PIT_COARSE_EXTRAP, 2), ("w1", B.PIT_COARSE_EXTRAP, 2)])
+def test_higher_order_coarse_with_fp32_coarse_solves_reaches_the_sequential_solution(name, coarse, init):
     wl, P, O, u0, N, m, lev = setup(name)
     tol = 1e-10 * np.abs(u0).max()
     fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-13, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
     crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-5, maxit=50000)
-    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, coarse=B.PIT_COARSE_SDIRK2, fine=fine, crs=crs,
-                        relax=B.PIT_RELAX_F, init=True)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=60, coarse=coarse, fine=fine, crs=crs,
+                        relax=B.PIT_RELAX_F, init=init)
     uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
     st = P.mgrit_solve(cuda(u0), opts, uT)
     assert st.n_converged == P.G
@@ -123,7 +126,7 @@ def test_higher_order_coarse_rejects_unsupported_forms():
     wl, P, O, u0, N, m, lev = setup("w2_small")
     uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
     bad = [(B.PIT_COARSE_SDIRK2, B.PIT_PREC_FP64), (B.PIT_COARSE_SDIRK2, B.PIT_PREC_MIXED_PAIR),
-           (B.PIT_COARSE_EXTRAP, B.PIT_PREC_FP64), (B.PIT_COARSE_EXTRAP, B.PIT_PREC_FP32)]
+           (B.PIT_COARSE_EXTRAP, B.PIT_PREC_FP64), (B.PIT_COARSE_EXTRAP, B.PIT_PREC_MIXED_PAIR)]
     for coarse, prec in bad:
         so = B.solve_opts(prec, rtol=1e-10, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
         opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=1e-8, maxit=10, coarse=coarse, crs=so)
@@ -159,7 +162,7 @@ def test_extrapolated_initial_sweep_matches_oracle(name):
 def test_extrapolated_initial_sweep_rejects_unsupported_forms():
     wl, P, O, u0, N, m, lev = setup("w2_small")
     uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
-    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-2, maxit=50000)
+    crs = B.solve_opts(B.PIT_PREC_FP64, rtol=1e-2, maxit=50000)
     opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=1e-8, maxit=10, crs=crs, init=2)
     with pytest.raises(B.PitError, match="UNSUPPORTED"):
         P.mgrit_solve(cuda(u0), opts, uT)
