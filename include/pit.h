@@ -171,7 +171,10 @@ typedef struct {
  *                          whose tolerance lies far above FP32 rounding, such
  *                          as the coarse correction solves of MGRIT (rtol of
  *                          1e-5 or looser).  Values below 2^-126 of the largest
- *                          input are flushed to zero.
+ *                          input are flushed to zero.  Grids whose FP32 state
+ *                          does not fit in shared memory are solved in the
+ *                          PIT_PREC_MIXED form with their FP64 state in global
+ *                          memory, to the same rtol on the true residual.
  *   prec = PIT_PREC_MIXED_PAIR: the refinement of PIT_PREC_MIXED with the
  *                          state held as pairs of FP32 numbers (hi + lo, about
  *                          48 significant bits, scaled by a power of two) and

@@ -316,12 +316,13 @@ pit_status plan(pit_problem *P, int prec)
             need[0] = bytes > need[0] ? bytes : need[0];
             continue;
         }
-        const size_t bx = prec != SINGLE ? phi_smem_bytes_xg(prec, P->desc.op, P->desc.d, n) : (size_t)-1;
+        // (class 1 of the FP32 form runs the refinement form's global-state kernel)
+        const size_t bx = phi_smem_bytes_xg(prec, P->desc.op, P->desc.d, n);
         if (bx > P->max_smem)
             return fail(PIT_ERR_UNSUPPORTED,
                         "grid %d (%d nodes) needs %zu bytes of shared memory for the on-chip solve in this precision "
                         "form; the device offers %zu",
-                        g, n, prec != SINGLE ? bx : bytes, P->max_smem);
+                        g, n, bx, P->max_smem);
         cls[1].push_back(g);
         need[1] = bx > need[1] ? bx : need[1];
     }
@@ -1690,8 +1691,10 @@ pit_status lanes_prime(Mg &M, int Nc)
         c.in = P->m_U.d();  // u0 at every C-point
         c.is = nt;
         if (P->n_cls[prec][1] > 0) CU(P->w_xg.ensure(sizeof(double) * nt * (size_t)Nc * xg_slabs(prec, P->desc.op, P->desc.d)));
+        // (lane launches of extrapolated FP32 steps: the sweeps (one state per
+        // grid) and, with three levels, the level-1 relaxations (Nc / m states)
         if (prec == SINGLE && (o->coarse == PIT_COARSE_EXTRAP || o->init == 2))
-            CU(P->w_scr.ensure(sizeof(float) * nt * (size_t)Nc));
+            CU(P->w_scr.ensure(sizeof(float) * nt * (size_t)(o->levels == 3 && Nc / o->m > 1 ? Nc / o->m : 1)));
         for (int part = 0; part < NPART; ++part) TRY(tune(P, prec, c.nb >= 8, part, *reps[r].so, c, M.active));
     }
     return PIT_OK;

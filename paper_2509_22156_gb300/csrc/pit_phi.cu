@@ -14,6 +14,8 @@ size_t phi_smem_bytes(int prec, int op, int d, int n, int na)
 
 size_t phi_smem_bytes_xg(int prec, int op, int d, int n)
 {
+    // (the FP32 form's oversize grids run the refinement form's global-state kernel)
+    if (prec == SINGLE) prec = MIXED;
     // the FP64 form keeps its coefficient table in global memory as well
     const size_t ld = (size_t)((n + 3) & ~3);
     return (size_t)(prec == PLAIN ? 0 : n_tab(op, d)) * ld * 8 + (size_t)n_f32(op, prec, d, true) * ld * 4 + ld * 2 +
@@ -52,6 +54,23 @@ cudaError_t launch_steps(int prec, const StepArgs &a, int threads, size_t smem, 
     if (blocks > 0x7fffffffLL || smem > g_max_smem || threads < 32 || threads > 512 || (threads & 31))
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)blocks), block(threads);
+    if (prec == SINGLE && xg) {
+        // the FP32 form has no global-state variant: grids whose FP32 state does
+        // not fit on chip take the refinement form's global-state kernel (FP64
+        // state in global memory, FP32 Krylov vectors on chip), which meets the
+        // same tolerance on the true residual
+        StepArgs m = a;
+        if (!(m.inner_rtol > 0.0f && m.inner_rtol < 1.0f)) m.inner_rtol = 1e-4f;
+        if (m.ir_maxit < 4) m.ir_maxit = 12;
+        switch (a.op.op) {
+        case PIT_OP_HEAT: return steps_launch_heat_mixed(a.op.d, m, grid, block, smem, s, true);
+        case PIT_OP_VARHEAT: return steps_launch_varheat_mixed(a.op.d, m, grid, block, smem, s, true);
+        case PIT_OP_OU: return steps_launch_ou_mixed(a.op.d, m, grid, block, smem, s, true);
+        case PIT_OP_LSDE: return steps_launch_lsde_mixed(a.op.d, m, grid, block, smem, s, true);
+        case PIT_OP_CME: return steps_launch_cme_mixed(a.op.d, m, grid, block, smem, s, true);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (prec == PAIR) {
         // symmetric operators only (the plan rejects the drift operator)
         if (a.op.op == PIT_OP_HEAT) return steps_launch_heat_pair(a.op.d, a, grid, block, smem, s, xg);

@@ -102,3 +102,32 @@ def test_heat6d_n10_full_size_grid_sample_matches_oracle_sequential():
     grids = sorted(chosen | set(int(g) for g in rest[:64 - len(chosen)]))
     assert len(grids) == 64
     solve_and_check(5, tol=5e-9, rtol=1e-11, grids=grids)
+
+
+def test_heat6d_n10_fp32_coarse_solves_and_extrapolated_sweep_match_oracle_sequential():
+    """The level-1 and level-2 solves in the FP32 form (the 9,261-node grids,
+    whose FP32 state does not fit on chip, in the refinement form's
+    global-state kernel) and the extrapolated initial sweep: the grid sample
+    of the test above stays within the accuracy target."""
+    wl = W.workload(5)
+    lev, _ = oracle.enumerate_grids(wl.d, wl.n, wl.L0)
+    npts = np.prod(2 ** lev.astype(np.int64) - 1, axis=1)
+    big = [int(g) for g in np.flatnonzero(npts == npts.max())]
+    rest = [int(g) for g in np.argsort(W.uniform(12, len(lev)), kind="stable") if g not in big]
+    grids = sorted(big + rest[:12])
+    P = B.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi)
+    O = oracle.Problem(wl.d, wl.n, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = O.initial(wl.ic_kind, wl.ic_params)
+    seq = O.sequential(u0, wl.dt, wl.nsteps, rtol=1e-14, grids=grids)
+    fine = B.solve_opts(B.PIT_PREC_MIXED, rtol=5e-12, maxit=4000, inner_rtol=1e-6, ir_maxit=12)
+    crs = B.solve_opts(B.PIT_PREC_FP32, rtol=1e-5, maxit=4000)
+    o = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=4e-8, maxit=64, fine=fine, crs=crs,
+                     relax=B.PIT_RELAX_F, init=2)
+    u0d = torch.from_numpy(u0).cuda()
+    uT = torch.empty_like(u0d)
+    st = P.mgrit_solve(u0d, o, uT)
+    assert st.n_converged == P.G
+    u = uT.cpu().numpy()
+    errs = [rel(u[O.grid_slice(g)], seq[O.grid_slice(g)]) for g in grids]
+    assert max(errs) < TOL, (max(errs), grids[int(np.argmax(errs))])
+    P.close()
