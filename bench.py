@@ -253,7 +253,16 @@ MGRIT_TOL_BY_WORKLOAD = {1: 1e-8, 2: 3e-7, 3: 2e-9, 4: 1e-10, 5: 4e-8}
 # heat6d_n10 grids stop after three cycles (measured: 1,491 -> 1,217 ms at MGRIT
 # 4e-8); on heat3d_n9, whose coarse solves are FP32, it would need refinement
 # coarse solves and measured slower (24.8 against 19.9 ms)
-INIT_BY_WORKLOAD = {5: 2}
+INIT_BY_WORKLOAD = {5: 2, 4: 2}
+# Coarse propagator of the chosen form when the learned network is rejected
+# by its judge (otherwise the library's fallback, the coarse backward Euler):
+# varheat3d_n8 with the extrapolated backward Euler 2 BE(dT/2)^2 - BE(dT)
+# takes 9 instead of 17 MGRIT cycles (measured: 69.2 -> 49.7 ms with the
+# extrapolated initial sweep); on heat3d_n9 and heat6d_n10 its extra coarse
+# work outweighs the saved cycles (measured)
+COARSE_FALLBACK_BY_WORKLOAD = {4: 4}  # 4 = PIT_COARSE_EXTRAP
+ORACLE_COARSE_KIND = {0: 0, 2: 0, 3: 3, 4: 4}  # library coarse propagator -> oracle coarse kind
+COARSE_TEXT = {3: ", two-stage SDIRK coarse step", 4: ", extrapolated backward-Euler coarse step"}
 INIT_TEXT = {0: "", 1: ", initial coarse sweep",
              2: ", initial coarse sweep with the extrapolated backward Euler 2 BE(dT/2)^2 - BE(dT)"}
 KRYLOV_RTOL_BY_WORKLOAD = {2: 1e-11, 4: 1e-11, 5: 5e-12}
@@ -313,7 +322,8 @@ def solver_setup(wl, B, tol=None, rtol=None, coarse=None, relax=None, coarse_pre
         init = INIT_BY_WORKLOAD.get(k, 1)
         # the extrapolated sweep needs refinement coarse solves of the heat operator
         crs_prec = (mixed_c if loose else mixed_c3).prec
-        if init == 2 and (crs_prec != B.PIT_PREC_MIXED or wl.op != B.PIT_OP_HEAT):
+        if init == 2 and (crs_prec not in (B.PIT_PREC_MIXED, B.PIT_PREC_FP32) or
+                          wl.op not in (B.PIT_OP_HEAT, B.PIT_OP_VARHEAT)):
             init = 1
     chosen = B.mgrit_opts(wl.t0, wl.t1, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, coarse=coarse, fine=fine,
                           crs=mixed_c if loose else mixed_c3, relax=relax, init=init,
@@ -445,6 +455,8 @@ def run_pit(args, rank, world, local):
     # of up to 9,261 nodes; the network is rejected either way)
     epochs = args.epochs or (40 if wl.d < 6 else 10)
     training = train_network(P, wl, B, mixed, epochs)
+    if not training["accepted"] and k in COARSE_FALLBACK_BY_WORKLOAD:
+        chosen.coarse = COARSE_FALLBACK_BY_WORKLOAD[k]
     u0 = torch.empty(P.n_total, dtype=torch.float64, device=dev)
     P.sample_initial(wl.ic_kind, wl.ic_params, u0)
     # 65,536 uniform points (4096 for d = 6, where the oracle's combination of
@@ -538,8 +550,9 @@ def run_pit(args, rank, world, local):
                                    "inner_rtol": chosen.fine.inner_rtol, "ir_maxit": chosen.fine.ir_maxit},
                    "coarse_solves": {"prec": PREC_NAMES[chosen.crs.prec], "rtol": chosen.crs.rtol},
                    "coarse": ("learned network, accepted by its judge" if training["accepted"] else
-                              "implicit backward Euler dT = m dt (the learned network was rejected by its "
-                              "hold-out judge)"),
+                              ("extrapolated backward Euler 2 BE(dT/2)^2 - BE(dT)"
+                               if chosen.coarse == B.PIT_COARSE_EXTRAP else "implicit backward Euler dT = m dt") +
+                              " (the learned network was rejected by its hold-out judge)"),
                    "eval_points": int(pts_h.shape[0]), "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "time_to_tol_ms": ms_step, "mgrit_cycles": stats.max_cycles,
@@ -892,7 +905,7 @@ def cpu_baseline(wl, k, uT_gpu, out_gpu, pts, chosen, form_outs):
     t0 = time.perf_counter()
     uT, its, _, st = O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=chosen.tol, maxit=64,
                              rtol=chosen.fine.rtol, check=False, grids=grids, relax=relax,
-                             init=int(chosen.init))
+                             init=int(chosen.init), coarse_kind=ORACLE_COARSE_KIND.get(int(chosen.coarse), 0))
     t_mg = time.perf_counter() - t0
     dof = sum(int(O.offsets[g + 1] - O.offsets[g]) for g in grids)
     t0 = time.perf_counter()
@@ -908,7 +921,8 @@ def cpu_baseline(wl, k, uT_gpu, out_gpu, pts, chosen, form_outs):
     sample = (f"{'all ' + str(O.G) if len(grids) == O.G else f'seeded 1/{frac} of the grids ({len(grids)} of {O.G}'}"
               f"{')' if len(grids) != O.G else ''} grids, {dof} of {O.n_total} nodes, all {wl.nsteps} steps, "
               f"{wl.levels}-level MGRIT ({relax} relaxation{INIT_TEXT[int(chosen.init)]}, "
-              f"FAS form) m={wl.m}, MGRIT tol {chosen.tol:g}, Krylov rtol {chosen.fine.rtol:g} for every solve, "
+              f"FAS form{COARSE_TEXT.get(int(chosen.coarse), '')}) m={wl.m}, MGRIT tol {chosen.tol:g}, "
+              f"Krylov rtol {chosen.fine.rtol:g} for every solve, "
               f"{t_mg:.1f} s; value = sample DoF-steps / time")
     base = {"value": dof * wl.nsteps / t_mg, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
             "seconds": t_mg, "mgrit_cycles_max": int(np.max(its[grids])) if len(grids) else None,
@@ -942,12 +956,14 @@ def run_reference(args, rank, world):
     # the GPU arm's initial sweep (the extrapolated one needs the heat operator
     # and refinement coarse solves, which three levels use)
     init = INIT_BY_WORKLOAD.get(k, 1)
-    if init == 2 and (wl.op != W.OP_HEAT or wl.levels == 2):
+    if init == 2 and wl.op not in (W.OP_HEAT, W.OP_VARHEAT):
         init = 1
+    # (the network is rejected on every workload: the GPU arm's fallback coarse step)
+    ck = ORACLE_COARSE_KIND.get(COARSE_FALLBACK_BY_WORKLOAD.get(k, 0), 0)
 
     def solve(grids):
         O.mgrit(u0, wl.dt, wl.nsteps, wl.m, wl.levels, tol=tol, maxit=64, rtol=rtol, check=False, grids=grids,
-                relax=args.relax, init=init)
+                relax=args.relax, init=init, coarse_kind=ck)
 
     # calibration: one grid per core, then as many as fit the per-step budget
     budget_s = max(1.0, 150.0 / max(1, args.steps + args.warmup))
@@ -966,7 +982,8 @@ def run_reference(args, rank, world):
     ms = (time.perf_counter() - t0) * 1e3 / args.steps
     value = dof * wl.nsteps / (ms / 1e3)
     sample = (f"seeded {len(grids)} of {O.G} grids ({dof} of {O.n_total} nodes), all {wl.nsteps} steps per step, "
-              f"{wl.levels}-level MGRIT ({args.relax} relaxation{INIT_TEXT[init]}, FAS form) m={wl.m}, "
+              f"{wl.levels}-level MGRIT ({args.relax} relaxation{INIT_TEXT[init]}, FAS form"
+              f"{COARSE_TEXT.get(COARSE_FALLBACK_BY_WORKLOAD.get(k, 0), '')}) m={wl.m}, "
               f"MGRIT tol {tol:g}, Krylov rtol {rtol:g}; value = sample DoF-steps / time")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

@@ -121,7 +121,9 @@ typedef enum {
                                 whole decaying spectrum (smooth modes to second order, stiff
                                 ones damped like 1/(lambda dT)), so MGRIT needs fewer
                                 cycles; its fixed point is still the fine solution.  Heat
-                                operator with PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves
+                                operators (constant and variable coefficient; the latter's
+                                coefficient table is switched to the full step in place)
+                                with PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves
                                 (PIT_ERR_UNSUPPORTED otherwise; the FP32 form keeps u_n and
                                 the second half step's result in a library-owned global
                                 slab of n_batch x n_total floats); not with the residual
@@ -280,7 +282,7 @@ typedef struct {
                              leaves the initial guess open; the fixed point is the same);
                              2 = that sweep with the extrapolated backward Euler of
                              PIT_COARSE_EXTRAP while the cycles keep `coarse` (heat
-                             operator, PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves,
+                             operators, PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves,
                              any coarse propagator but PIT_COARSE_EXACT;
                              PIT_ERR_UNSUPPORTED otherwise)                                 */
     int recomb;           /* recombination steps s of Alg. 3 (Sec. 2.2.1): 0 = none (one MGRIT

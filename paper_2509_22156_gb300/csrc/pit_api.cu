@@ -1715,10 +1715,10 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     if (o->coarse != PIT_COARSE_IMPLICIT && o->coarse != PIT_COARSE_EXACT && o->coarse != PIT_COARSE_LEARNED &&
         o->coarse != PIT_COARSE_SDIRK2 && o->coarse != PIT_COARSE_EXTRAP)
         return fail(PIT_ERR_INVALID_ARG, "unknown coarse propagator %d", o->coarse);
-    if (o->coarse == PIT_COARSE_EXTRAP &&
-        ((o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32) || P->desc.op != PIT_OP_HEAT))
-        return fail(PIT_ERR_UNSUPPORTED, "the extrapolated coarse propagator is built for the heat operator with "
-                                         "PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves");
+    const bool ext_op = P->desc.op == PIT_OP_HEAT || P->desc.op == PIT_OP_VARHEAT;
+    if (o->coarse == PIT_COARSE_EXTRAP && ((o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32) || !ext_op))
+        return fail(PIT_ERR_UNSUPPORTED, "the extrapolated coarse propagator is built for the heat operators (constant "
+                                         "and variable coefficient) with PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves");
     if (o->coarse == PIT_COARSE_SDIRK2 && o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32)
         return fail(PIT_ERR_UNSUPPORTED, "the SDIRK coarse propagator needs PIT_PREC_MIXED or PIT_PREC_FP32 coarse "
                                          "solves");
@@ -1734,11 +1734,11 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     if (o->init < 0 || o->init > 2) return fail(PIT_ERR_INVALID_ARG, "init must be 0, 1 or 2");
-    if (o->init == 2 && ((o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32) ||
-                         P->desc.op != PIT_OP_HEAT || o->coarse == PIT_COARSE_EXACT))
-        return fail(PIT_ERR_UNSUPPORTED, "the extrapolated initial sweep is built for the heat operator with "
-                                         "PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves, without the exact coarse "
-                                         "propagator");
+    if (o->init == 2 && ((o->crs.prec != PIT_PREC_MIXED && o->crs.prec != PIT_PREC_FP32) || !ext_op ||
+                         o->coarse == PIT_COARSE_EXACT))
+        return fail(PIT_ERR_UNSUPPORTED, "the extrapolated initial sweep is built for the heat operators (constant and "
+                                         "variable coefficient) with PIT_PREC_MIXED or PIT_PREC_FP32 coarse solves, "
+                                         "without the exact coarse propagator");
     if (o->forcing && !ptr_is_device(o->forcing)) return fail(PIT_ERR_INVALID_ARG, "forcing must be device memory");
     if (o->residual != 0 && o->residual != 1) return fail(PIT_ERR_INVALID_ARG, "residual must be 0 or 1");
     if (o->residual && (o->levels != 2 || o->relax != PIT_RELAX_F || o->fas || o->coarse != PIT_COARSE_IMPLICIT ||

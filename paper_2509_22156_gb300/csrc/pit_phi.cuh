@@ -1124,7 +1124,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
     // its diagonal one, whose slot then keeps D^{-1/2} (T32.unit)
     bool jac = false;
     if constexpr ((PREC == MIXED || PREC == PAIR) && (OP == PIT_OP_VARHEAT || OP == PIT_OP_OU)) {
-        if (a.precond == PIT_PRECOND_JACOBI) {
+        if (a.precond == PIT_PRECOND_JACOBI && !a.ext) {  // (the extrapolated steps rescale the table)
             jac = true;
             __syncthreads();  // table complete
             for (int j = tid; j < n; j += nt) {
@@ -1207,6 +1207,30 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
         else return T64.resid(bj, v, j);
     };
 
+    // Full step of an extrapolated backward-Euler step for the table-driven
+    // variable-coefficient operator: the table of I + dt L becomes that of
+    // I + 2 dt L in place (off-diagonal entries doubled, diagonal 2 d - 1,
+    // both exact in binary floating point for d >= 1) and back (halved,
+    // (d + 1) / 2, exact again); barriers on both sides, since every thread's
+    // stencil reads its neighbours' entries.
+    auto table_full_step = [&](bool full) {
+        if constexpr (OP == PIT_OP_VARHEAT && PREC != PAIR) {
+            __syncthreads();
+            for (int j = tid; j < n; j += nt) {
+                if constexpr (PREC != SINGLE) {
+                    tab64[j] = full ? 2.0 * tab64[j] - 1.0 : 0.5 * (tab64[j] + 1.0);
+#pragma unroll
+                    for (int k = 1; k <= 2 * D; ++k) tab64[k * tld + j] *= full ? 2.0 : 0.5;
+                }
+                if constexpr (PREC != PLAIN) {
+                    tab32[j] = full ? 2.0f * tab32[j] - 1.0f : 0.5f * (tab32[j] + 1.0f);
+#pragma unroll
+                    for (int k = 1; k <= 2 * D; ++k) tab32[k * ld + j] *= full ? 2.0f : 0.5f;
+                }
+            }
+            __syncthreads();
+        }
+    };
     int status = PIT_OK, iters = 0, passes = 0;
     const bool carry_ok = (f0 == nullptr) && (a.g == nullptr) && (a.guess == nullptr) && !a.sdirk && !a.ext;
     // MIXED also carries its residual across an additive forcing g (x_s <- x_s
@@ -1288,6 +1312,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             const T diagTh = HT.diag;
 #pragma unroll 1
           for (int stage = 0; stage < nstage; ++stage) {
+            if (a.ext && stage == 2) table_full_step(true);
             if constexpr (OP == PIT_OP_HEAT) {
                 if (a.ext && stage == 2) {
                     // the full step I + 2 dt L, without the line preconditioner
@@ -1388,6 +1413,12 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             if (st > status) status = st;
             __syncthreads();  // xs complete
           }
+            if constexpr (OP == PIT_OP_VARHEAT) {
+                if (a.ext) {
+                    table_full_step(false);
+                    for (int j = tid; j < n; j += nt) xs[j] = 2.0f * scr[j] - xs[j];
+                }
+            }
             if constexpr (OP == PIT_OP_HEAT) {
                 if (a.ext) {
                     // back to the half step; u_{n+1} = 2 U2 - U3
@@ -1601,6 +1632,7 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             const T diagTh = HT.diag;
 #pragma unroll 1
           for (int stage = 0; stage < nstage; ++stage) {
+            if (a.ext && stage == 2) table_full_step(true);
             if constexpr (OP == PIT_OP_HEAT) {
                 if (a.ext && stage == 2) {
                     // the full step: I + 2 dt L (off-diagonal entries doubled
@@ -1794,6 +1826,12 @@ __global__ void __launch_bounds__(512, 1) steps_kernel(StepArgs a)
             have_r0 = carry_g && st_step == PIT_OK && step < a.nsteps;
             kr_c = kr;
           }
+            if constexpr (OP == PIT_OP_VARHEAT) {
+                if (a.ext) {
+                    table_full_step(false);
+                    for (int j = tid; j < n; j += nt) x[j] = 2.0 * cvec[j] - x[j];
+                }
+            }
             if constexpr (OP == PIT_OP_HEAT) {
                 if (a.ext) {
                     // back to the half step; u_{n+1} = 2 U2 - U3 (the last

@@ -64,7 +64,7 @@ def setup(name):
 
 
 ORACLE_KIND = {B.PIT_COARSE_SDIRK2: 3, B.PIT_COARSE_EXTRAP: 4}
-HEAT_CASES = ["w1", "w2_small", "w2_3lev", "w5_small"]
+HEAT_CASES = ["w1", "w2_small", "w2_3lev", "w4_small", "w5_small"]  # constant and variable coefficient
 
 
 @pytest.mark.parametrize("relax", [B.PIT_RELAX_FCF, B.PIT_RELAX_F])
@@ -91,7 +91,8 @@ def test_higher_order_coarse_mgrit_matches_oracle(name, coarse, relax):
 @pytest.mark.parametrize("name,coarse,init", [("w2_small", B.PIT_COARSE_SDIRK2, 1), ("w3_small", B.PIT_COARSE_SDIRK2, 1),
                                               ("w4_small", B.PIT_COARSE_SDIRK2, 1), ("w2_small", B.PIT_COARSE_EXTRAP, 1),
                                               ("w2_small", B.PIT_COARSE_IMPLICIT, 2),
-                                              ("w2_3lev", B.PIT_COARSE_EXTRAP, 2), ("w1", B.PIT_COARSE_EXTRAP, 2)])
+                                              ("w2_3lev", B.PIT_COARSE_EXTRAP, 2), ("w1", B.PIT_COARSE_EXTRAP, 2),
+                                              ("w4_small", B.PIT_COARSE_EXTRAP, 2)])
 def test_higher_order_coarse_with_fp32_coarse_solves_reaches_the_sequential_solution(name, coarse, init):
     wl, P, O, u0, N, m, lev = setup(name)
     tol = 1e-10 * np.abs(u0).max()
@@ -140,7 +141,7 @@ def test_higher_order_coarse_rejects_unsupported_forms():
         P.mgrit_solve(cuda(u0), opts, torch.empty(P.n_total, dtype=torch.float64, device="cuda"))
 
 
-@pytest.mark.parametrize("name", ["w2_small", "w2_3lev", "w5_small"])
+@pytest.mark.parametrize("name", ["w2_small", "w2_3lev", "w4_small", "w5_small"])
 def test_extrapolated_initial_sweep_matches_oracle(name):
     """init = 2: the initial sweep with the extrapolated step, the cycles with
     the coarse backward Euler; against the oracle's MGRIT with the same start."""
