@@ -247,11 +247,13 @@ typedef struct {
 
 /* Relaxation of the finest MGRIT level (Sec. 3.3.1 defines F- and C-relaxation;
  * the experiments of Sec. 4.1 use FCF).  Coarser levels of a three-level
- * hierarchy always use FCF. */
+ * hierarchy use FCF, except with PIT_RELAX_F_ALL. */
 typedef enum {
-    PIT_RELAX_FCF = 0, /* F-, C- and F-relaxation before the residual (Sec. 4.1) */
-    PIT_RELAX_F = 1    /* F-relaxation only: half the fine steps per cycle, exactness
-                          advances one coarse interval per cycle instead of two    */
+    PIT_RELAX_FCF = 0,  /* F-, C- and F-relaxation before the residual (Sec. 4.1) */
+    PIT_RELAX_F = 1,    /* F-relaxation only: half the fine steps per cycle, exactness
+                           advances one coarse interval per cycle instead of two    */
+    PIT_RELAX_F_ALL = 2 /* F-relaxation on the finest and on the middle level of a
+                           three-level hierarchy                                      */
 } pit_relax;
 
 /* MGRIT options (Sec. 3.3, Alg. 2; Sec. 4.1 stopping rule: a grid stops when

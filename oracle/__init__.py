@@ -245,11 +245,12 @@ class Problem:
               forcing=None, tmul=None):
         """Returns (uT, cycles per grid, residual history G x maxit, status);
         with `grids`, only those grids are computed.  relax: "FCF" (Sec. 4.1)
-        or "F" (F-relaxation on the finest level).  init: start from one sweep
+        or "F" (F-relaxation on the finest level) or "F_ALL" (F-relaxation on
+        every level).  init: start from one sweep
         of the level-1 propagator over the C-points instead of u0 everywhere
         (2: that sweep with the extrapolated backward Euler, coarse kind 4)."""
-        if relax not in ("FCF", "F"):
-            raise ValueError("relax must be 'FCF' or 'F'")
+        if relax not in ("FCF", "F", "F_ALL"):
+            raise ValueError("relax must be 'FCF', 'F' or 'F_ALL'")
         u0 = _f64(u0)
         out = np.zeros_like(u0)
         gm = self._gmask(grids)
@@ -260,7 +261,7 @@ class Problem:
         tm = self._tmul(tmul)
         st = lib().or_mgrit(self._h, _p(u0), dt, nsteps, m, levels, tol, maxit, coarse_kind,
                             _p(th), rtol, krylov_maxit, _p(out), _p(its), _p(hist), _p(gm),
-                            1 if relax == "F" else 0, int(init), _p(F), _p(tm))
+                            {"FCF": 0, "F": 1, "F_ALL": 2}[relax], int(init), _p(F), _p(tm))
         if check and st != 0:
             raise RuntimeError(f"oracle mgrit: {STATUS.get(st, st)}")
         return out, its, hist, st

@@ -837,7 +837,7 @@ typedef struct {
                            3 two-stage SDIRK, 4 extrapolated BE (3 and 4 on
                            every coarse level) */
     const double *theta;/* net parameters (coarse_kind 2) */
-    int relax_f;        /* 1: F-relaxation on the finest level, 0: FCF */
+    int relax_f;        /* 1: F-relaxation on the finest level, 2: on every level, 0: FCF */
     int status;
     const double *F;    /* forcing of the common steps 1..N (grid's part), stride nt, or NULL */
     long long nt;
@@ -941,7 +941,8 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
      * C-point jm over the F-points jm+1 .. jm+m-1. */
     for (int j = 0; j < Nc; ++j)
         for (int i = 1; i < m; ++i) mg_step(C, level, j * m + i, V(j * m + i - 1), GF(j * m + i), V(j * m + i));
-    if (!(level == 0 && C->relax_f)) {
+    /* relax_f = 1: F-relaxation on the finest level; 2: on every level */
+    if (!((level == 0 || C->relax_f == 2) && C->relax_f)) {
         /* C-relaxation: one step into every C-point. */
         for (int j = 1; j <= Nc; ++j) mg_step(C, level, j * m, V(j * m - 1), GF(j * m), V(j * m));
         /* F-relaxation again (FCF, Sec. 4.1). */
@@ -996,7 +997,7 @@ static double mg_cycle(mg_ctx *C, int level, int N, double *v, const double *g)
 int or_mgrit(void *vp, const double *u0, double dt, int nsteps, int m, int nlev, double tol,
              int maxit, int coarse_kind, const double *theta, double rtol, int krylov_maxit,
              double *uT, int *iters, double *res_hist, const unsigned char *gmask /* G or NULL */,
-             int relax_f /* 1: F-relaxation on the finest level instead of FCF */,
+             int relax_f /* 1: F-relaxation on the finest level instead of FCF, 2: on every level */,
              int init /* 1: initial C-points from one sweep of the level-1 propagator;
                          2: that sweep with the extrapolated backward Euler */,
              const double *F /* forcing f_n, n = 1..nsteps, packed like states, or NULL */,

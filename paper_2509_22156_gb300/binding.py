@@ -31,7 +31,7 @@ PIT_OP_HEAT, PIT_OP_VARHEAT, PIT_OP_OU, PIT_OP_LSDE, PIT_OP_CME = 0, 1, 2, 3, 4
 PIT_DRIFT_UPWIND, PIT_DRIFT_CENTRAL = 0, 1
 PIT_PREC_FP64, PIT_PREC_MIXED, PIT_PREC_FP32, PIT_PREC_MIXED_PAIR = 0, 1, 2, 3
 PIT_COARSE_IMPLICIT, PIT_COARSE_EXACT, PIT_COARSE_LEARNED, PIT_COARSE_SDIRK2, PIT_COARSE_EXTRAP = 0, 1, 2, 3, 4
-PIT_RELAX_FCF, PIT_RELAX_F = 0, 1
+PIT_RELAX_FCF, PIT_RELAX_F, PIT_RELAX_F_ALL = 0, 1, 2
 
 EXPORTED = ["pit_problem_create", "pit_problem_destroy", "pit_problem_info", "pit_sample_initial", "pit_apply",
             "pit_phi_batch", "pit_sequential_solve", "pit_mgrit_solve", "pit_combine", "pit_profile_enable",

@@ -1344,11 +1344,13 @@ pit_status mg_level1_cycle(Mg &M, const double *V, long long vstride, double *W,
     fc.osst = nt;
     fc.out_last = W + sm;
     fc.ols = sm;
-    TRY(run_coarse(M, fc, 1));
+    // (PIT_RELAX_F_ALL: F-relaxation on this level too, from the old C-points)
+    const bool f_only = M.o->relax == PIT_RELAX_F_ALL;
+    if (!f_only) TRY(run_coarse(M, fc, 1));
     // F-relaxation from the new C-points (F-points in place) and utilde
     StepCall fr = fc;
-    fr.in = W;
-    fr.is = sm;
+    fr.in = f_only ? V : W;
+    fr.is = f_only ? vstride * m : sm;
     fr.out_last = UT1;
     fr.ols = nt;
     TRY(run_coarse(M, fr, 1));
@@ -1356,8 +1358,8 @@ pit_status mg_level1_cycle(Mg &M, const double *V, long long vstride, double *W,
     StepCall gc;
     gc.nb = Nc;
     gc.nsteps = 1;
-    gc.in = W;
-    gc.is = sm;
+    gc.in = f_only ? V : W;
+    gc.is = f_only ? vstride * m : sm;
     gc.out_last = GC1;
     gc.ols = nt;
     gc.scale = -1.0;
@@ -1395,7 +1397,7 @@ pit_status mg_cycle(Mg &M, int Nc, bool corr, double *h_res)
     double *U = P->m_U.d(), *R = P->m_R.d(), *UT = P->m_UT.d(), *GC = P->m_GC.d(), *res = P->m_res.d();
     // F-relaxation alone leaves the C-points as they are: the relaxed C-points
     // are U itself, and the correction updates U in place
-    const bool relax_f = o->relax == PIT_RELAX_F;
+    const bool relax_f = o->relax == PIT_RELAX_F || o->relax == PIT_RELAX_F_ALL;
     double *Rx = relax_f ? U : R;
     if (o->residual) {
         // residual mode: the m - 1 F-points of every interval by the fine
@@ -1730,7 +1732,7 @@ pit_status mgrit_run(pit_problem_t P, const double *u0, const pit_mgrit_opts *o,
     if (o->nsteps % div != 0) return fail(PIT_ERR_INVALID_ARG, "nsteps must be a multiple of m^(levels-1)");
     if (o->levels == 3 && o->coarse == PIT_COARSE_EXACT)
         return fail(PIT_ERR_UNSUPPORTED, "the exact coarse propagator is a two-level option");
-    if (o->relax != PIT_RELAX_FCF && o->relax != PIT_RELAX_F)
+    if (o->relax != PIT_RELAX_FCF && o->relax != PIT_RELAX_F && o->relax != PIT_RELAX_F_ALL)
         return fail(PIT_ERR_INVALID_ARG, "unknown relaxation %d", o->relax);
     if (o->lanes < 0) return fail(PIT_ERR_INVALID_ARG, "lanes must be >= 0");
     if (o->init < 0 || o->init > 2) return fail(PIT_ERR_INVALID_ARG, "init must be 0, 1 or 2");

@@ -167,3 +167,24 @@ def test_extrapolated_initial_sweep_rejects_unsupported_forms():
     opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=1e-8, maxit=10, crs=crs, init=2)
     with pytest.raises(B.PitError, match="UNSUPPORTED"):
         P.mgrit_solve(cuda(u0), opts, uT)
+
+
+@pytest.mark.parametrize("name", ["w2_3lev", "w5_small"])
+@pytest.mark.parametrize("init", [1, 2])
+def test_f_relaxation_on_every_level_matches_oracle(name, init):
+    """PIT_RELAX_F_ALL: F-relaxation on the middle level of three levels too,
+    against the oracle's MGRIT with the same relaxation."""
+    wl, P, O, u0, N, m, lev = setup(name)
+    tol = 1e-10 * np.abs(u0).max()
+    so = B.solve_opts(B.PIT_PREC_MIXED, rtol=1e-13, maxit=50000, inner_rtol=1e-4, ir_maxit=40)
+    opts = B.mgrit_opts(wl.t0, wl.t1, N, m, lev, tol=tol, maxit=80, fine=so, crs=so, relax=B.PIT_RELAX_F_ALL,
+                        init=init)
+    uT = torch.empty(P.n_total, dtype=torch.float64, device="cuda")
+    st = P.mgrit_solve(cuda(u0), opts, uT)
+    dt = (wl.t1 - wl.t0) / N
+    ref, its, hist, _ = O.mgrit(u0, dt, N, m, lev, tol=tol, maxit=80, coarse_kind=0, rtol=1e-15, relax="F_ALL",
+                                init=init)
+    assert st.n_converged == P.G
+    assert rel(host(uT), ref) < 1e-9
+    assert abs(st.max_cycles - int(its.max())) <= 1
+    assert rel(host(uT), O.sequential(u0, dt, N, rtol=1e-15)) < 1e-7

@@ -158,3 +158,22 @@ def test_extrapolated_initial_sweep_lowers_every_residual_and_keeps_the_fixed_po
         np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-10)
         res[init] = np.nanmax(hist[:, 0])
     assert res[2] < 0.2 * res[1], res
+
+
+def test_f_relaxation_on_every_level_keeps_the_fixed_point():
+    """relax "F_ALL": F-relaxation also on the middle level of three levels;
+    converged MGRIT is still sequential stepping (also after the extrapolated
+    initial sweep), and the middle level's relaxation does change the iterates
+    (the second cycle's residuals differ from those with FCF there)."""
+    wl = W.workload(2)
+    P = oracle.Problem(wl.d, 4, wl.L0, wl.op, wl.lo, wl.hi)
+    u0 = P.initial(wl.ic_kind, wl.ic_params)
+    N, dt = 64, 0.05 / 64
+    seq = P.sequential(u0, dt, N, rtol=1e-15)
+    for init in (1, 2):
+        uT, its, *_ = P.mgrit(u0, dt, N, 4, 3, tol=1e-13, maxit=80, rtol=1e-15, relax="F_ALL", init=init)
+        np.testing.assert_allclose(uT, seq, rtol=0, atol=1e-11)
+    # the middle level's relaxation changes the iterates, not the two-level exactness
+    _, its_f, hist_f, _ = P.mgrit(u0, dt, N, 4, 3, tol=0.0, maxit=2, rtol=1e-15, relax="F", check=False)
+    _, its_a, hist_a, _ = P.mgrit(u0, dt, N, 4, 3, tol=0.0, maxit=2, rtol=1e-15, relax="F_ALL", check=False)
+    assert np.any(np.abs(hist_f[:, 1] - hist_a[:, 1]) > 0)
